@@ -1,0 +1,214 @@
+/*
+ * rgs.h -- C ABI of the GB300 hierarchical 3D Gaussian splatting library
+ * (RetinaGS, arXiv 2406.11836).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Tensors are caller-owned, contiguous, device memory unless a name ends in _host.
+ *    float = IEEE fp32, int32/int64 as named.  The library never frees caller memory.
+ *  - Splat parameters are structure-of-arrays (Sec. 3.1: centre mu, covariance from scale
+ *    and rotation, opacity, SH colour):  means [N,3], log_scales [N,3], quats [N,4] stored
+ *    (w,x,y,z) and normalised inside, opacity_logits [N], sh [N,(deg+1)^2,3]
+ *    (coefficient-major, RGB innermost).
+ *  - Cameras: world->camera 4x4 view matrix, row-major, OpenCV axes (x right, y down,
+ *    z forward), pinhole intrinsics; pixel (px,py) has its centre at (px+0.5, py+0.5).
+ *  - Images are planar: [3,H,W]; partial maps [K,3,H,W] and [K,H,W] are indexed by the
+ *    KD leaf (subset) id k, not by the view order.
+ *  - Calls taking a `stream` (a cudaStream_t passed as void*) only enqueue work on it and
+ *    return without waiting, except where a call says it synchronises.
+ *  - Every call returns an int status.  Nothing throws across the ABI.  On failure
+ *    rgs_last_error() (thread-local) holds a one-line reason.
+ *
+ * Readings of the paper that this library implements (the oracle in the test suite
+ * implements the same ones):
+ *  - depth order along a ray = camera-space depth z_i of the splat centre, ties by
+ *    ascending splat index;
+ *  - x_i (Sec. 3.2, Eq. 6) = the point of the pixel ray at camera depth z_i;
+ *  - a (pixel, splat) pair contributes iff z_i > near_z, d^2 <= trunc_mult^2 (Mahalanobis
+ *    distance in the projected 2D Gaussian), |x_i - mu_i| <= D_i and
+ *    sigma = min(alpha_max, alpha exp(-d^2/2)) >= alpha_min;
+ *  - D_i = trunc_mult * max_j exp(log_scale_j) (Sec. 3.3, "three times the major axis");
+ *  - leaf boxes are half-open (left child x[a] < s, right child x[a] >= s);
+ *  - the merge order of Eq. 5 is one near-child-first KD traversal per view.
+ */
+#ifndef RGS_H
+#define RGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define RGS_OK 0
+#define RGS_EINVAL (-1)     /* invalid argument (see rgs_last_error) */
+#define RGS_ENOMEM (-2)     /* a library-internal allocation failed */
+#define RGS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define RGS_EOVERFLOW (-4)  /* caller workspace too small; rgs_last_required_workspace() */
+#define RGS_ETIMEOUT (-5)   /* a bounded wait gave up (serving) */
+#define RGS_EAGAIN (-6)     /* not ready yet / no room right now (serving) */
+
+/* ------------------------------------------------------------------ types */
+typedef struct {
+    const float* means;           /* [N,3] */
+    const float* log_scales;      /* [N,3] */
+    const float* quats;           /* [N,4] (w,x,y,z) */
+    const float* opacity_logits;  /* [N]   */
+    const float* sh;              /* [N,(sh_degree+1)^2,3] */
+    int64_t n;                    /* N >= 1 */
+    int sh_degree;                /* 0..3 */
+} rgs_gaussians;
+
+typedef struct {                  /* gradients, same shapes as rgs_gaussians; accumulated (+=) */
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logits;
+    float* sh;
+} rgs_gaussian_grads;
+
+typedef struct {
+    float viewmat[16];            /* world->camera, row-major, OpenCV axes */
+    float fx, fy, cx, cy;         /* pixels */
+    int width, height;            /* 1..16384 */
+    float near_z;                 /* splats with camera depth <= near_z are culled */
+} rgs_camera;
+
+typedef struct {
+    int tile;                     /* tile edge in pixels; must be 16 */
+    float trunc_mult;             /* 3: d^2 <= trunc_mult^2 and D_i = trunc_mult * max scale */
+    float eps_T;                  /* 1e-6: a subset stops once its transmittance drops below */
+    float alpha_min;              /* 1/255: smaller sigma does not contribute */
+    float alpha_max;              /* 0.99: sigma clamp */
+    float dilation;               /* 0.3: added to the diagonal of the 2D covariance */
+    float bg[3];                  /* background colour behind every ray (merge only) */
+} rgs_render_opts;
+
+typedef struct rgs_kd rgs_kd;          /* KD partition: splits, leaf boxes, subset lists */
+typedef struct rgs_server rgs_server;  /* render server with a device-resident scene */
+
+/* ------------------------------------------------------------------ misc */
+const char* rgs_last_error(void);           /* thread-local, never NULL */
+size_t rgs_last_required_workspace(void);   /* thread-local; set when a call returns RGS_EOVERFLOW */
+int rgs_version(void);                      /* major*10000 + minor*100 + patch */
+void rgs_default_opts(rgs_render_opts* opts);
+
+/* ------------------------------------------------------------------ KD partition (Sec. 3.3)
+ * rgs_kd_partition: builds a KD tree of depth L (K = 2^L leaves) on the splat centres:
+ * level d splits along axis d mod 3 at the median (for an even count the fp32 midpoint
+ * of the two middle coordinates, raised to the upper one if it rounds onto the lower;
+ * for an odd count the median coordinate itself), so every node's two children differ in
+ * size by at most one when coordinates are distinct.  Then forms the overlapping subsets
+ * N_k = {i : n.mu_i + d <= D_i for every plane of S_k} (Sec. 3.3) as CSR lists, leaf-major,
+ * ascending splat index.  Only means and log_scales are read.  L in [0,8].
+ * Synchronises with `stream` before returning (the handle holds host copies of the
+ * splits).  Allocates its own device memory; *out is owned by the caller and released
+ * with rgs_kd_destroy.  Errors: EINVAL (NULL pointers, N < 1, L out of range,
+ * trunc_mult <= 0), ENOMEM, ECUDA. */
+int rgs_kd_partition(const rgs_gaussians* g, int depth_L, float trunc_mult, rgs_kd** out, void* stream);
+
+/* Depth L, leaf count K and total subset-list length M of a partition. */
+int rgs_kd_info(const rgs_kd* kd, int* depth_L, int* K, int64_t* total_members);
+
+/* Splits in heap order (node j has children 2j+1 left, 2j+2 right; leaf k is node K-1+k):
+ * axis_host [K-1] int32 in {0,1,2}, split_host [K-1] float.  Either may be NULL. */
+int rgs_kd_splits(const rgs_kd* kd, int32_t* axis_host, float* split_host);
+
+/* CSR subset lists: offsets_host [K+1] int64 (host), idx_dev [M] int32 (device, may be
+ * NULL to query offsets only).  Synchronous copy. */
+int rgs_kd_subsets(const rgs_kd* kd, int64_t* offsets_host, int32_t* idx_dev);
+
+int rgs_kd_destroy(rgs_kd* kd);
+
+/* Merge order o_l of Eq. 5 for every ray of a view: the KD leaves in a near-child-first
+ * traversal, where at each node the child containing the camera centre o goes first (o on
+ * the plane: the left child).  A ray from o crosses each plane at most once, from o's
+ * side, so this order lists the leaves every ray crosses in the order it crosses them.
+ * order_host [K] int32 (host).  Pure host computation. */
+int rgs_view_order(const rgs_kd* kd, const rgs_camera* cam, int32_t* order_host);
+
+/* ------------------------------------------------------------------ render
+ * Workspace bytes for a render of this scene/view whose tile-instance count is at most
+ * `instance_capacity` ((subset, tile, splat) triples; unknown until the splats are
+ * projected, so rgs_render_fwd/bwd report the exact need via RGS_EOVERFLOW and
+ * rgs_last_required_workspace()).  Pure host arithmetic. */
+int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                              const rgs_render_opts* opts, int64_t instance_capacity, size_t* bytes);
+
+/* Forward render, Sec. 3.2: projects every splat (EWA, SH colour), bins it into the
+ * 16x16 tiles it can touch once per subset N_k that contains it, sorts the instances by
+ * (tile, subset position in the view order, depth), and alpha-blends each subset front
+ * to back into its partial colour C_k (Eq. 3) and partial transmittance T_k (Eq. 4), with
+ * the indicator of Eq. 6 deciding per pixel which subset a straddling splat belongs to.
+ * Writes partial_C [K,3,H,W] and partial_T [K,H,W] (a subset a ray never meets gets
+ * C = 0, T = 1).  If `image` [3,H,W] is non-NULL the partials are also merged in view
+ * order (Eq. 5) with the background behind, and T_final [H,W] (nullable) receives the
+ * product of all T_k.  Synchronises once with `stream` to size the instance buffers.
+ * Errors: EINVAL (shapes, sh_degree, tile != 16, L > 6 for rendering, non-finite camera,
+ * misaligned pointers), EOVERFLOW (workspace too small; required size via
+ * rgs_last_required_workspace()), ECUDA. */
+int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                   float* partial_C, float* partial_T, float* image, float* T_final, void* workspace,
+                   size_t ws_bytes, void* stream);
+
+/* Eq. 5 over caller-owned partial maps: image = sum_r C_{o_r} prod_{m<r} T_{o_m} +
+ * bg * prod_m T_m.  order_dev [K] int32 (device) lists the subsets front to back.
+ * partial_C [K,3,H,W], partial_T [K,H,W], image [3,H,W], T_out [H,W] (nullable). */
+int rgs_merge_partials(const float* partial_C, const float* partial_T, const int32_t* order_dev, int K, int H,
+                       int W, const float bg[3], float* image, float* T_out, void* stream);
+
+/* Adjoint of rgs_merge_partials: with P_r = prod_{m<r} T_{o_m} and S_r the colour seen
+ * behind subset o_r, dL/dC_{o_r} = g P_r and dL/dT_{o_r} = P_r <g, S_r> (+ gT prod_{m!=r}
+ * T_{o_m} when dL_dT_out is non-NULL).  Outputs [K,3,H,W] and [K,H,W] are overwritten. */
+int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const int32_t* order_dev, int K, int H,
+                           int W, const float bg[3], const float* dL_dimage, const float* dL_dT_out,
+                           float* dL_dpartial_C, float* dL_dpartial_T, void* stream);
+
+/* Backward of rgs_render_fwd with the merge (the "backward process" of Sec. 3.4): routes
+ * dL/dimage [3,H,W] through Eq. 5 to each subset's (C_k, T_k), replays each subset's blend
+ * from the stored partials (re-deriving the per-tile lists rather than storing them),
+ * and pulls the per-splat 2D gradients back through the projection.  Gradients are
+ * accumulated into `grads` (same shapes as the parameters; the caller zeroes them).  A
+ * splat shared by several subsets accumulates into its single parameter slot.
+ * partial_C/partial_T must be the ones rgs_render_fwd wrote for the same inputs.
+ * Synchronises once with `stream`.  Errors as rgs_render_fwd. */
+int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                   const float* partial_C, const float* partial_T, const float* dL_dimage,
+                   const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ Adam (Sec. 4 details)
+ * One Adam step over a flat parameter buffer split into `nseg` contiguous segments, each
+ * with its own learning rate: seg_offsets_host [nseg+1] (elements), seg_lr_host [nseg].
+ * param/grad/m/v [n] float (device, 16-byte aligned).  `step` is 1-based.  If zero_grad
+ * is non-zero the gradient is cleared after it is read.  nseg in [1,16]. */
+int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,
+                  const float* seg_lr_host, int nseg, float beta1, float beta2, float eps, int step, int zero_grad,
+                  void* stream);
+
+/* Exponential decay of the position learning rate, 1.6e-4 -> 1.6e-6 in the paper
+ * (log-linear between lr_init at step 0 and lr_final at max_steps, then constant). */
+float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_final);
+
+/* ------------------------------------------------------------------ tracing
+ * Per-pass timing.  While enabled, every pass of the library (projection, compaction,
+ * depth sort, offsets, emission, instance sort, ranges, blend forward, blend backward,
+ * projection backward, Adam, merge, merge backward, KD build) records a pair of CUDA
+ * events on the stream it is launched on, and the blend kernels count the (pixel, splat)
+ * pairs they evaluate and the ones that contribute.  Timing adds two event records per
+ * pass; counting adds one atomic per warp per blend kernel.  Process-wide.
+ * rgs_profile_read synchronises with the recorded events and writes, per stage index
+ * 0..rgs_profile_num_stages()-1, the accumulated milliseconds (ms_host) and pass counts
+ * (launches_host), and counters_host[6] = {fwd pairs evaluated, fwd pairs contributing,
+ * bwd pairs evaluated, bwd pairs contributing, tile instances, visible splats}, summed
+ * since the last reset.  Any output pointer may be NULL.  reset != 0 clears the sums. */
+int rgs_profile_enable(int on);
+int rgs_profile_num_stages(void);
+const char* rgs_profile_stage_name(int stage);
+int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_host, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RGS_H */

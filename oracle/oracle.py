@@ -73,13 +73,14 @@ class Opts:
     alpha_max: float = 0.99
     dilation: float = 0.3
     bg: tuple = (0.0, 0.0, 0.0)
-    flag_rel: float = 1e-5      # relative rounding margin of the ambiguity flags
+    flag_rel: float = 1e-5      # relative rounding margin of the truncation/plane ambiguity flags
+    flag_depth_rel: float = 1e-6  # relative margin for two contributors at (nearly) equal depth
 
     def vec(self) -> np.ndarray:
         f = lambda v: float(np.float32(v))
         return np.array([f(self.trunc_mult), f(self.eps_T), f(self.alpha_min), f(self.alpha_max),
-                         f(self.dilation), f(self.bg[0]), f(self.bg[1]), f(self.bg[2]), self.flag_rel],
-                        np.float64)
+                         f(self.dilation), f(self.bg[0]), f(self.bg[1]), f(self.bg[2]), self.flag_rel,
+                         self.flag_depth_rel], np.float64)
 
 
 def cam_vec(cam) -> np.ndarray:

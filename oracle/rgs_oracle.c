@@ -44,9 +44,10 @@
  * Ambiguity flags.  A float32 implementation of the same definition may take a different
  * discrete decision when a decision quantity lies within rounding error of its threshold.
  * For each pixel the oracle reports which of those cases occur, with a relative margin
- * `flag_rel`: bit 1 truncation decision, bit 2 two contributors at (nearly) equal depth,
- * bit 4 x_i (nearly) on a split plane (affects the partial maps only), bit 8 a kink of a
- * clamp (sigma at alpha_max or a colour channel at 0; affects gradients only).
+ * `flag_rel` (`flag_depth_rel` for depths): bit 1 truncation decision, bit 2 two
+ * contributors at (nearly) equal depth, bit 4 x_i (nearly) on a split plane (affects the
+ * partial maps only), bit 8 a kink of a clamp (sigma at alpha_max or a colour channel at
+ * 0; affects gradients only).
  */
 #include <math.h>
 #include <stdint.h>
@@ -68,7 +69,7 @@ typedef struct {
 } cam_t;
 
 typedef struct {
-    double trunc_mult, eps_T, alpha_min, alpha_max, dilation, bg[3], flag_rel;
+    double trunc_mult, eps_T, alpha_min, alpha_max, dilation, bg[3], flag_rel, flag_depth_rel;
 } opt_t;
 
 typedef struct {
@@ -92,6 +93,7 @@ static void read_opt(const double* o, opt_t* opt) {
     opt->trunc_mult = o[0]; opt->eps_T = o[1]; opt->alpha_min = o[2]; opt->alpha_max = o[3];
     opt->dilation = o[4]; opt->bg[0] = o[5]; opt->bg[1] = o[6]; opt->bg[2] = o[7];
     opt->flag_rel = o[8];
+    opt->flag_depth_rel = o[9];
 }
 
 /* ------------------------------------------------------------------ real SH, degree <= 3
@@ -559,7 +561,7 @@ static int gather_pixel(const proj_t* P, int64_t n, const cam_t* cam, const opt_
     }
     qsort(out->v, (size_t)out->n, sizeof(pair_t), cmp_pair);
     for (int64_t j = 1; j < out->n; ++j)
-        if (out->v[j].z - out->v[j - 1].z <= opt->flag_rel * out->v[j].z) flags |= OR_FLAG_DEPTH;
+        if (out->v[j].z - out->v[j - 1].z <= opt->flag_depth_rel * out->v[j].z) flags |= OR_FLAG_DEPTH;
     return flags;
 }
 

@@ -1,0 +1,604 @@
+// C ABI of the library (include/rgs.h): argument checks, workspace layout and the order
+// of the passes of a render.  All arithmetic of the method runs in the kernels of
+// project.cu, raster.cu, sort.cu, kd.cu and adam.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "rgs_internal.cuh"
+
+// ------------------------------------------------------------------ opaque handles
+struct rgs_kd {
+    rgs::KdBuild b;
+    int device;
+    float trunc_mult;
+};
+
+namespace rgs {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local char g_err[512] = "";
+thread_local size_t g_required = 0;
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+void set_required_workspace(size_t bytes) { g_required = bytes; }
+
+// ------------------------------------------------------------------ profiler
+namespace {
+const char* kStageNames[ST_COUNT] = {"project", "compact", "depth_sort", "offsets", "emit", "instance_sort", "ranges",
+                                     "blend_fwd", "blend_bwd", "project_bwd", "adam", "merge", "merge_bwd", "kd"};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> open;      // started, not yet ended (indexed by token)
+    std::vector<Rec> done;
+    double ms[ST_COUNT] = {};
+    int64_t launches[ST_COUNT] = {};
+    int64_t host_counts[2] = {};
+    unsigned long long* dev_pairs = nullptr;
+    cudaEvent_t take() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+};
+Profiler g_prof;
+}  // namespace
+
+ProfScope::ProfScope(int stage, cudaStream_t st) : token(-1), s(st) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on) return;
+    Profiler::Rec r{stage, g_prof.take(), g_prof.take()};
+    cudaEventRecord(r.a, s);
+    g_prof.open.push_back(r);
+    token = (int)g_prof.open.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (token < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (token >= (int)g_prof.open.size()) return;
+    Profiler::Rec r = g_prof.open[token];
+    cudaEventRecord(r.b, s);
+    g_prof.done.push_back(r);
+    if (token == (int)g_prof.open.size() - 1) g_prof.open.pop_back();
+    else g_prof.open[token].stage = -1;
+    while (!g_prof.open.empty() && g_prof.open.back().stage < 0) g_prof.open.pop_back();
+}
+
+unsigned long long* prof_pair_counters() { return g_prof.on ? g_prof.dev_pairs : nullptr; }
+
+void prof_add_host_counts(int64_t instances, int64_t visible) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on) return;
+    g_prof.host_counts[0] += instances;
+    g_prof.host_counts[1] += visible;
+}
+
+namespace {
+
+__global__ void compact_kernel(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ pos,
+                               const uint32_t* __restrict__ dkey, int64_t n, uint32_t* __restrict__ skey,
+                               uint32_t* __restrict__ sid) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || cnt[i] == 0) return;
+    uint32_t p = pos[i];
+    skey[p] = dkey[i];
+    sid[p] = (uint32_t)i;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_gaussians(const rgs_gaussians* g) {
+    if (!g) { set_error("gaussians: NULL"); return RGS_EINVAL; }
+    if (g->n < 1 || g->n > 0x7fffffffll) { set_error("gaussians: n = %lld out of range [1, 2^31)", (long long)g->n); return RGS_EINVAL; }
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh) {
+        set_error("gaussians: NULL parameter pointer");
+        return RGS_EINVAL;
+    }
+    if (g->sh_degree < 0 || g->sh_degree > 3) { set_error("gaussians: sh_degree %d not in 0..3", g->sh_degree); return RGS_EINVAL; }
+    if (!aligned(g->quats, 16) || !aligned(g->means, 4) || !aligned(g->log_scales, 4) || !aligned(g->sh, 4) ||
+        !aligned(g->opacity_logits, 4)) {
+        set_error("gaussians: misaligned pointer (quats must be 16-byte aligned)");
+        return RGS_EINVAL;
+    }
+    return RGS_OK;
+}
+
+int check_camera(const rgs_camera* c) {
+    if (!c) { set_error("camera: NULL"); return RGS_EINVAL; }
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(c->viewmat[i])) { set_error("camera: non-finite view matrix"); return RGS_EINVAL; }
+    if (!(std::isfinite(c->fx) && std::isfinite(c->fy) && std::isfinite(c->cx) && std::isfinite(c->cy) && c->fx > 0 &&
+          c->fy > 0)) {
+        set_error("camera: invalid intrinsics");
+        return RGS_EINVAL;
+    }
+    if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) {
+        set_error("camera: image size %dx%d out of range [1, 16384]", c->width, c->height);
+        return RGS_EINVAL;
+    }
+    if (!(c->near_z > 0) || !std::isfinite(c->near_z)) { set_error("camera: near_z must be > 0"); return RGS_EINVAL; }
+    return RGS_OK;
+}
+
+int check_opts(const rgs_render_opts* o) {
+    if (!o) { set_error("opts: NULL"); return RGS_EINVAL; }
+    if (o->tile != kTile) { set_error("opts: tile must be %d", kTile); return RGS_EINVAL; }
+    if (!(o->trunc_mult > 0) || !(o->alpha_min > 0) || !(o->alpha_max > o->alpha_min) || !(o->alpha_max < 1) ||
+        !(o->eps_T >= 0) || !(o->dilation >= 0) || !std::isfinite(o->trunc_mult)) {
+        set_error("opts: need trunc_mult > 0, 0 < alpha_min < alpha_max < 1, eps_T >= 0, dilation >= 0");
+        return RGS_EINVAL;
+    }
+    return RGS_OK;
+}
+
+void view_order_host(const rgs_kd* kd, const rgs_camera* cam, int32_t* order) {
+    const int L = kd->b.L;
+    double R[9], t[3], o[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = cam->viewmat[4 * r + c];
+        t[r] = cam->viewmat[4 * r + 3];
+    }
+    for (int c = 0; c < 3; ++c) o[c] = -(R[c] * t[0] + R[3 + c] * t[1] + R[6 + c] * t[2]);
+    // near-child-first traversal; the child holding o (o on the plane: left) goes first
+    int n = 0;
+    int stack[2 * kMaxKdDepth + 4];
+    int sp = 0;
+    stack[sp++] = 0;
+    const int first_leaf = (1 << L) - 1;
+    while (sp > 0) {
+        int j = stack[--sp];
+        if (j >= first_leaf) {
+            order[n++] = j - first_leaf;
+            continue;
+        }
+        double s = kd->b.split[j];
+        bool left_first = o[kd->b.axis[j]] <= s;
+        int nearc = left_first ? 2 * j + 1 : 2 * j + 2, farc = left_first ? 2 * j + 2 : 2 * j + 1;
+        stack[sp++] = farc;
+        stack[sp++] = nearc;
+    }
+}
+
+void fill_view(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+               ViewParams* vp, TreeParams* tp) {
+    memset(vp, 0, sizeof *vp);
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) vp->R[3 * r + c] = cam->viewmat[4 * r + c];
+        vp->t[r] = cam->viewmat[4 * r + 3];
+    }
+    for (int c = 0; c < 3; ++c) {
+        double oc = -((double)vp->R[c] * vp->t[0] + (double)vp->R[3 + c] * vp->t[1] + (double)vp->R[6 + c] * vp->t[2]);
+        vp->o[c] = (float)oc;
+    }
+    vp->fx = cam->fx; vp->fy = cam->fy; vp->cx = cam->cx; vp->cy = cam->cy;
+    vp->ifx = 1.f / cam->fx; vp->ify = 1.f / cam->fy;
+    vp->near_z = cam->near_z;
+    vp->W = cam->width; vp->H = cam->height;
+    vp->tiles_x = (cam->width + kTile - 1) / kTile;
+    vp->tiles_y = (cam->height + kTile - 1) / kTile;
+    vp->trunc_mult = opts->trunc_mult; vp->eps_T = opts->eps_T;
+    vp->alpha_min = opts->alpha_min; vp->alpha_max = opts->alpha_max; vp->dilation = opts->dilation;
+    for (int c = 0; c < 3; ++c) vp->bg[c] = opts->bg[c];
+    vp->L = kd->b.L;
+    vp->K = 1 << kd->b.L;
+    vp->sh_degree = g ? g->sh_degree : 0;
+    int ntiles = vp->tiles_x * vp->tiles_y;
+    int bits = 0;
+    while ((1 << bits) < ntiles) ++bits;
+    vp->tile_bits = bits;
+    int32_t order[64];
+    view_order_host(kd, cam, order);
+    for (int r = 0; r < vp->K; ++r) {
+        vp->order[r] = (int8_t)order[r];
+        vp->rank_of[order[r]] = (int8_t)r;
+    }
+    memset(tp, 0, sizeof *tp);
+    tp->L = kd->b.L;
+    for (int j = 0; j < (1 << kd->b.L) - 1; ++j) {
+        tp->axis[j] = kd->b.axis[j];
+        tp->split[j] = kd->b.split[j];
+    }
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves the workspace; returns the bytes needed (b may be NULL to only measure).
+size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, RasterBuffers* b) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += a256(bytes);
+        return p;
+    };
+    RasterBuffers t;
+    memset(&t, 0, sizeof t);
+    t.rec = (float4*)take(sizeof(float4) * 3 * N);
+    t.g2d = (float4*)take(sizeof(float4) * 3 * N);
+    t.cnt = (uint32_t*)take(4 * N);
+    t.rect = (ushort4*)take(8 * N);
+    t.mask = (unsigned long long*)take(8 * N);
+    t.dkey = (uint32_t*)take(4 * N);
+    t.vis_pos = (uint32_t*)take(4 * N);
+    t.skey = (uint32_t*)take(4 * N);
+    t.sid = (uint32_t*)take(4 * N);
+    t.skey_alt = (uint32_t*)take(4 * N);
+    t.sid_alt = (uint32_t*)take(4 * N);
+    t.ioff = (uint32_t*)take(4 * N);
+    t.counters = (unsigned long long*)take(64);
+    t.ranges = (uint2*)take(sizeof(uint2) * tiles * K);
+    t.ikey = (uint32_t*)take(4 * inst_cap);
+    t.ival = (uint32_t*)take(4 * inst_cap);
+    t.ikey_alt = (uint32_t*)take(4 * inst_cap);
+    t.ival_alt = (uint32_t*)take(4 * inst_cap);
+    t.inst_cap = inst_cap;
+    size_t tb = radix_temp_bytes(N > inst_cap ? N : inst_cap);
+    size_t sb = scan_temp_bytes(N);
+    t.temp_bytes = tb > sb ? tb : sb;
+    t.temp = take(t.temp_bytes);
+    if (b) *b = t;
+    return off;
+}
+
+struct PinnedCounters {
+    unsigned long long* h = nullptr;
+    ~PinnedCounters() {
+        if (h) cudaFreeHost(h);
+    }
+};
+thread_local PinnedCounters g_pinned;
+
+// Projection, binning and sorting shared by the forward and the backward: on success
+// `b` holds the records and the (tile, subset) ranges, and *sorted_ival the instance
+// payloads in blend order.
+int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
+                const uint32_t** sorted_ival) {
+    int rc;
+    if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
+    if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
+    if (kd->b.L > kMaxRenderDepth) {
+        set_error("render: KD depth %d > %d (at most 64 subsets per render)", kd->b.L, kMaxRenderDepth);
+        return RGS_EINVAL;
+    }
+    fill_view(kd, g, cam, opts, vp, tp);
+    const int64_t N = g->n;
+    const int64_t tiles = (int64_t)vp->tiles_x * vp->tiles_y;
+    if (vp->tile_bits + vp->L > 32) { set_error("render: tile index and subset rank exceed 32 key bits"); return RGS_EINVAL; }
+    size_t fixed = layout(nullptr, N, tiles, vp->K, 0, nullptr);
+    if (!workspace || ws_bytes < fixed) {
+        set_required_workspace(layout(nullptr, N, tiles, vp->K, 1 << 20, nullptr));
+        set_error("render: workspace of %zu bytes is smaller than the %zu needed before binning", ws_bytes, fixed);
+        return RGS_EOVERFLOW;
+    }
+    if (!aligned(workspace, 256)) { set_error("render: workspace must be 256-byte aligned"); return RGS_EINVAL; }
+    // the instance capacity that fits the workspace
+    int64_t lo = 0, hi = (int64_t)(ws_bytes / 16) + 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (layout(nullptr, N, tiles, vp->K, mid, nullptr) <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    layout((char*)workspace, N, tiles, vp->K, lo, b);
+
+    RGS_CUDA_TRY(cudaMemsetAsync(b->counters, 0, 64, s));
+    {
+        ProfScope ps(ST_PROJECT, s);
+        rc = launch_project_fwd(*g, *vp, *tp, *b, s);
+    }
+    if (rc) return rc;
+    if (!g_pinned.h) RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
+    RGS_CUDA_TRY(cudaMemcpyAsync(g_pinned.h, b->counters, 16, cudaMemcpyDeviceToHost, s));
+    RGS_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t I = (int64_t)g_pinned.h[0];
+    const int64_t n_vis = (int64_t)g_pinned.h[1];
+    if (I > 0xFFFFFFFFll - 1) {
+        set_error("render: %lld tile instances exceed the 32-bit instance index", (long long)I);
+        return RGS_EOVERFLOW;
+    }
+    if (I > b->inst_cap) {
+        set_required_workspace(layout(nullptr, N, tiles, vp->K, I, nullptr));
+        set_error("render: %lld tile instances need a larger workspace", (long long)I);
+        return RGS_EOVERFLOW;
+    }
+    prof_add_host_counts(I, n_vis);
+    // compact the visible splats in index order, sort them by depth
+    {
+        ProfScope ps(ST_COMPACT, s);
+        rc = exclusive_scan_u32(b->cnt, b->vis_pos, N, 1, nullptr, b->temp, b->temp_bytes, s);
+        if (rc) return rc;
+        compact_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(b->cnt, b->vis_pos, b->dkey, N, b->skey, b->sid);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
+    bool alt = false;
+    {
+        ProfScope ps(ST_DEPTH_SORT, s);
+        rc = radix_sort_pairs(b->skey, b->sid, b->skey_alt, b->sid_alt, n_vis, 32, b->temp, b->temp_bytes, s, &alt);
+        if (rc) return rc;
+    }
+    const uint32_t* sorted_ids = alt ? b->sid_alt : b->sid;
+    // instance offsets in depth order, emission, (tile, rank) sort, ranges
+    {
+        ProfScope ps(ST_OFFSETS, s);
+        rc = exclusive_scan_u32(b->cnt, b->ioff, n_vis, 2, sorted_ids, b->temp, b->temp_bytes, s);
+        if (rc) return rc;
+    }
+    {
+        ProfScope ps(ST_EMIT, s);
+        rc = launch_emit(*vp, *b, sorted_ids, n_vis, s);
+        if (rc) return rc;
+    }
+    {
+        ProfScope ps(ST_INST_SORT, s);
+        rc = radix_sort_pairs(b->ikey, b->ival, b->ikey_alt, b->ival_alt, I, vp->tile_bits + vp->L, b->temp,
+                              b->temp_bytes, s, &alt);
+        if (rc) return rc;
+    }
+    const uint32_t* keys = alt ? b->ikey_alt : b->ikey;
+    *sorted_ival = alt ? b->ival_alt : b->ival;
+    ProfScope ps(ST_RANGES, s);
+    rc = launch_ranges(keys, I, b->ranges, tiles * vp->K, s);
+    return rc;
+}
+
+}  // namespace
+}  // namespace rgs
+
+using namespace rgs;
+
+extern "C" {
+
+const char* rgs_last_error(void) { return g_err; }
+size_t rgs_last_required_workspace(void) { return g_required; }
+int rgs_version(void) { return 100; }
+
+void rgs_default_opts(rgs_render_opts* o) {
+    if (!o) return;
+    o->tile = kTile;
+    o->trunc_mult = 3.f;
+    o->eps_T = 1e-6f;
+    o->alpha_min = 1.f / 255.f;
+    o->alpha_max = 0.99f;
+    o->dilation = 0.3f;
+    o->bg[0] = o->bg[1] = o->bg[2] = 0.f;
+}
+
+int rgs_kd_partition(const rgs_gaussians* g, int depth_L, float trunc_mult, rgs_kd** out, void* stream) {
+    if (!out) { set_error("kd_partition: out is NULL"); return RGS_EINVAL; }
+    *out = nullptr;
+    if (!g || !g->means || !g->log_scales || g->n < 1 || g->n > 0x7fffffffll) {
+        set_error("kd_partition: need means, log_scales and 1 <= n < 2^31");
+        return RGS_EINVAL;
+    }
+    if (depth_L < 0 || depth_L > kMaxKdDepth) { set_error("kd_partition: depth %d not in [0, %d]", depth_L, kMaxKdDepth); return RGS_EINVAL; }
+    if (!(trunc_mult > 0) || !std::isfinite(trunc_mult)) { set_error("kd_partition: trunc_mult must be > 0"); return RGS_EINVAL; }
+    rgs_kd* kd = new (std::nothrow) rgs_kd;
+    if (!kd) { set_error("kd_partition: out of host memory"); return RGS_ENOMEM; }
+    cudaGetDevice(&kd->device);
+    kd->trunc_mult = trunc_mult;
+    int rc;
+    {
+        ProfScope ps(ST_KD, (cudaStream_t)stream);
+        rc = kd_build(*g, depth_L, trunc_mult, &kd->b, (cudaStream_t)stream);
+    }
+    if (rc != RGS_OK) {
+        if (kd->b.idx_dev) cudaFree(kd->b.idx_dev);
+        delete kd;
+        return rc;
+    }
+    *out = kd;
+    return RGS_OK;
+}
+
+int rgs_kd_info(const rgs_kd* kd, int* depth_L, int* K, int64_t* total) {
+    if (!kd) { set_error("kd_info: NULL"); return RGS_EINVAL; }
+    if (depth_L) *depth_L = kd->b.L;
+    if (K) *K = 1 << kd->b.L;
+    if (total) *total = kd->b.M;
+    return RGS_OK;
+}
+
+int rgs_kd_splits(const rgs_kd* kd, int32_t* axis_host, float* split_host) {
+    if (!kd) { set_error("kd_splits: NULL"); return RGS_EINVAL; }
+    int nn = (1 << kd->b.L) - 1;
+    for (int j = 0; j < nn; ++j) {
+        if (axis_host) axis_host[j] = kd->b.axis[j];
+        if (split_host) split_host[j] = kd->b.split[j];
+    }
+    return RGS_OK;
+}
+
+int rgs_kd_subsets(const rgs_kd* kd, int64_t* offsets_host, int32_t* idx_dev) {
+    if (!kd || !offsets_host) { set_error("kd_subsets: NULL argument"); return RGS_EINVAL; }
+    int K = 1 << kd->b.L;
+    for (int k = 0; k <= K; ++k) offsets_host[k] = kd->b.offsets[k];
+    if (idx_dev) RGS_CUDA_TRY(cudaMemcpy(idx_dev, kd->b.idx_dev, sizeof(int32_t) * kd->b.M, cudaMemcpyDeviceToDevice));
+    return RGS_OK;
+}
+
+int rgs_kd_destroy(rgs_kd* kd) {
+    if (!kd) return RGS_OK;
+    if (kd->b.idx_dev) cudaFree(kd->b.idx_dev);
+    delete kd;
+    return RGS_OK;
+}
+
+int rgs_view_order(const rgs_kd* kd, const rgs_camera* cam, int32_t* order_host) {
+    if (!kd || !order_host) { set_error("view_order: NULL argument"); return RGS_EINVAL; }
+    int rc = check_camera(cam);
+    if (rc) return rc;
+    view_order_host(kd, cam, order_host);
+    return RGS_OK;
+}
+
+int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                              const rgs_render_opts* opts, int64_t instance_capacity, size_t* bytes) {
+    int rc;
+    if (!kd || !bytes) { set_error("workspace_size: NULL argument"); return RGS_EINVAL; }
+    if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
+    if (instance_capacity < 0) { set_error("workspace_size: negative capacity"); return RGS_EINVAL; }
+    int64_t tiles = (int64_t)((cam->width + kTile - 1) / kTile) * ((cam->height + kTile - 1) / kTile);
+    *bytes = layout(nullptr, g->n, tiles, 1 << kd->b.L, instance_capacity, nullptr);
+    return RGS_OK;
+}
+
+int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                   float* partial_C, float* partial_T, float* image, float* T_final, void* workspace, size_t ws_bytes,
+                   void* stream) {
+    if (!partial_C || !partial_T) { set_error("render_fwd: partial maps are required"); return RGS_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival);
+    if (rc) return rc;
+    ProfScope ps(ST_BLEND_FWD, s);
+    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, s);
+}
+
+int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                   const float* partial_C, const float* partial_T, const float* dL_dimage,
+                   const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream) {
+    if (!partial_C || !partial_T || !dL_dimage || !grads || !grads->means || !grads->log_scales || !grads->quats ||
+        !grads->opacity_logits || !grads->sh) {
+        set_error("render_bwd: NULL argument");
+        return RGS_EINVAL;
+    }
+    if (!aligned(grads->quats, 16)) { set_error("render_bwd: grads->quats must be 16-byte aligned"); return RGS_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival);
+    if (rc) return rc;
+    {
+        ProfScope ps(ST_BLEND_BWD, s);
+        RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
+        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, s);
+        if (rc) return rc;
+    }
+    ProfScope ps(ST_PROJECT_BWD, s);
+    return launch_project_bwd(*g, *grads, vp, b, s);
+}
+
+int rgs_merge_partials(const float* partial_C, const float* partial_T, const int32_t* order_dev, int K, int H, int W,
+                       const float bg[3], float* image, float* T_out, void* stream) {
+    if (!partial_C || !partial_T || !order_dev || !image || !bg || K < 1 || H < 1 || W < 1) {
+        set_error("merge_partials: invalid argument");
+        return RGS_EINVAL;
+    }
+    ProfScope ps(ST_MERGE, (cudaStream_t)stream);
+    return launch_merge(partial_C, partial_T, order_dev, K, H, W, bg, image, T_out, (cudaStream_t)stream);
+}
+
+int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const int32_t* order_dev, int K, int H,
+                           int W, const float bg[3], const float* dL_dimage, const float* dL_dT_out,
+                           float* dL_dpartial_C, float* dL_dpartial_T, void* stream) {
+    if (!partial_C || !partial_T || !order_dev || !bg || !dL_dimage || !dL_dpartial_C || !dL_dpartial_T || K < 1 ||
+        H < 1 || W < 1) {
+        set_error("merge_partials_bwd: invalid argument");
+        return RGS_EINVAL;
+    }
+    ProfScope ps(ST_MERGE_BWD, (cudaStream_t)stream);
+    return launch_merge_bwd(partial_C, partial_T, order_dev, K, H, W, bg, dL_dimage, dL_dT_out, dL_dpartial_C,
+                            dL_dpartial_T, (cudaStream_t)stream);
+}
+
+int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,
+                  const float* seg_lr_host, int nseg, float beta1, float beta2, float eps, int step, int zero_grad,
+                  void* stream) {
+    if (!param || !grad || !m || !v || n < 1 || !seg_offsets_host || !seg_lr_host || nseg < 1 || nseg > 16 || step < 1) {
+        set_error("adam_step: invalid argument");
+        return RGS_EINVAL;
+    }
+    if (!aligned(param, 16) || !aligned(grad, 16) || !aligned(m, 16) || !aligned(v, 16)) {
+        set_error("adam_step: buffers must be 16-byte aligned");
+        return RGS_EINVAL;
+    }
+    if (seg_offsets_host[0] != 0 || seg_offsets_host[nseg] != n) {
+        set_error("adam_step: segments must cover [0, n)");
+        return RGS_EINVAL;
+    }
+    float bc1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
+    float bc2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
+    ProfScope ps(ST_ADAM, (cudaStream_t)stream);
+    return launch_adam(param, grad, m, v, n, seg_offsets_host, seg_lr_host, nseg, beta1, beta2, eps, bc1, bc2,
+                       zero_grad, (cudaStream_t)stream);
+}
+
+int rgs_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (on && !g_prof.dev_pairs) {
+        RGS_CUDA_TRY(cudaMalloc(&g_prof.dev_pairs, 8 * sizeof(unsigned long long)));
+        RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
+    }
+    g_prof.on = on != 0;
+    return RGS_OK;
+}
+
+int rgs_profile_num_stages(void) { return ST_COUNT; }
+
+const char* rgs_profile_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : ""; }
+
+int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_host, int reset) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto& r : g_prof.done) {
+        RGS_CUDA_TRY(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        RGS_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+        g_prof.ms[r.stage] += ms;
+        g_prof.launches[r.stage] += 1;
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.done.clear();
+    for (int i = 0; i < ST_COUNT; ++i) {
+        if (ms_host) ms_host[i] = g_prof.ms[i];
+        if (launches_host) launches_host[i] = g_prof.launches[i];
+    }
+    unsigned long long pairs[4] = {0, 0, 0, 0};
+    if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemcpy(pairs, g_prof.dev_pairs, sizeof pairs, cudaMemcpyDeviceToHost));
+    if (counters_host) {
+        for (int i = 0; i < 4; ++i) counters_host[i] = (int64_t)pairs[i];
+        counters_host[4] = g_prof.host_counts[0];
+        counters_host[5] = g_prof.host_counts[1];
+    }
+    if (reset) {
+        for (int i = 0; i < ST_COUNT; ++i) {
+            g_prof.ms[i] = 0;
+            g_prof.launches[i] = 0;
+        }
+        g_prof.host_counts[0] = g_prof.host_counts[1] = 0;
+        if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
+    }
+    return RGS_OK;
+}
+
+float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_final) {
+    double t = max_steps > 0 ? (double)step / (double)max_steps : 1.0;
+    if (t < 0) t = 0;
+    if (t > 1) t = 1;
+    return (float)std::exp(std::log((double)lr_init) * (1.0 - t) + std::log((double)lr_final) * t);
+}
+
+}  // extern "C"

@@ -1,0 +1,500 @@
+// Per-splat projection of Sec. 3.1 and its adjoint.
+//
+// Forward, one thread per splat: camera transform, near cull, EWA 2D covariance
+// Sigma' = J W Sigma W^T J^T + dilation I (Jacobian linearisation of the pinhole model),
+// conic and its Cholesky factor, SH colour at the viewing direction, sigmoid opacity,
+// D_i = trunc_mult * max scale (Sec. 3.3), the conservative tile rectangle, the set of KD
+// subsets N_k holding the splat (the D_i rule of Sec. 3.3) and the instance count.
+//
+// Precision.  A 4K frame puts projected centres at pixel coordinates up to ~4000, where
+// one fp32 ulp is 2.4e-4 px, and the world->camera transform of a splat 30 units from
+// the origin loses another ~1e-6 units; either alone moves a sub-pixel splat by more than
+// the 1e-4 pixel tolerance allows.  The centre is therefore carried as an unevaluated
+// sum hi + lo of two floats: the camera transform is a compensated dot product
+// (error-free products and sums), and the perspective division and the intrinsics are
+// done with error-free transformations too.  The blend kernels shift it to tile-relative
+// coordinates once per instance.  The 2D covariance is formed as A A^T with A = J W R S,
+// and its determinant by the Lagrange identity |A0|^2 |A1|^2 - (A0.A1)^2 = |A0 x A1|^2,
+// so no cancellation occurs for elongated splats.  Everything else is plain fp32.
+#include <cuda_fp16.h>
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+namespace {
+
+// ------------------------------------------------------------------ error-free transformations
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// a0*b0 + a1*b1 + a2*b2 + c as hi + lo (Ogita-Rump-Oishi Dot2 style)
+__device__ __forceinline__ void dot3_plus(float a0, float b0, float a1, float b1, float a2, float b2, float c,
+                                          float& hi, float& lo) {
+    float s, e, p, q, t;
+    two_prod(a0, b0, s, e);
+    two_prod(a1, b1, p, q);
+    two_sum(s, p, s, t);
+    e = __fadd_rn(e, __fadd_rn(q, t));
+    two_prod(a2, b2, p, q);
+    two_sum(s, p, s, t);
+    e = __fadd_rn(e, __fadd_rn(q, t));
+    two_sum(s, c, s, t);
+    e = __fadd_rn(e, t);
+    fast_two_sum(s, e, hi, lo);
+}
+
+// ------------------------------------------------------------------ real SH basis, degree <= 3
+// Real spherical harmonics with the Condon-Shortley phase: for m != 0,
+// Y_lm = sqrt(2) K_l|m| P_l^|m|(cos theta) {cos, sin}(|m| phi), K_lm^2 = (2l+1)/(4 pi) (l-m)!/(l+m)!,
+// and r^l P_l^m(cos theta) e^{i m phi} written as polynomials of the unit direction.
+constexpr double cx_sqrt(double x) {
+    double r = x > 1 ? x : 1.0;
+    for (int i = 0; i < 64; ++i) r = 0.5 * (r + x / r);
+    return r;
+}
+constexpr double kPi = 3.14159265358979323846;
+constexpr double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
+constexpr double Klm(int l, int m) { return cx_sqrt((2 * l + 1) / (4 * kPi) * fact(l - m) / fact(l + m)); }
+constexpr double S2 = 1.41421356237309504880;
+// coefficient = normalisation times the leading integer of the Legendre polynomial
+constexpr float c00 = (float)Klm(0, 0);
+constexpr float c10 = (float)Klm(1, 0);             // z
+constexpr float c11 = (float)(-S2 * Klm(1, 1));     // P_1^1 = -sin: -x, -y
+constexpr float c20 = (float)(0.5 * Klm(2, 0));     // (3z^2 - 1)/2
+constexpr float c21 = (float)(-3.0 * S2 * Klm(2, 1));  // P_2^1 = -3 sin cos: -3 xz, -3 yz
+constexpr float c22 = (float)(3.0 * S2 * Klm(2, 2));   // P_2^2 = 3 sin^2: 3(x^2-y^2), 3*2xy
+constexpr float c30 = (float)(0.5 * Klm(3, 0));        // (5z^3 - 3z)/2
+constexpr float c31 = (float)(-1.5 * S2 * Klm(3, 1));  // P_3^1 = -3/2 (5z^2-1) sin
+constexpr float c32 = (float)(15.0 * S2 * Klm(3, 2));  // P_3^2 = 15 sin^2 cos
+constexpr float c33 = (float)(-15.0 * S2 * Klm(3, 3)); // P_3^3 = -15 sin^3
+
+// Basis values Y[k] (k = l*l + m + l) and, when dY != nullptr, their gradients as
+// polynomials of (x, y, z).
+template <int DEG>
+__device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y, float3* dY) {
+    Y[0] = c00;
+    if (dY) dY[0] = make_float3(0.f, 0.f, 0.f);
+    if (DEG >= 1) {
+        Y[1] = c11 * y;  // m = -1
+        Y[2] = c10 * z;  // m = 0
+        Y[3] = c11 * x;  // m = 1
+        if (dY) {
+            dY[1] = make_float3(0.f, c11, 0.f);
+            dY[2] = make_float3(0.f, 0.f, c10);
+            dY[3] = make_float3(c11, 0.f, 0.f);
+        }
+    }
+    if (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = c22 * 2.f * x * y;                     // m = -2
+        Y[5] = c21 * y * z;                           // m = -1
+        Y[6] = c20 * (3.f * zz - (xx + yy + zz));     // m = 0: 3z^2 - r^2
+        Y[7] = c21 * x * z;                           // m = 1
+        Y[8] = c22 * (xx - yy);                       // m = 2
+        if (dY) {
+            dY[4] = make_float3(c22 * 2.f * y, c22 * 2.f * x, 0.f);
+            dY[5] = make_float3(0.f, c21 * z, c21 * y);
+            dY[6] = make_float3(-2.f * c20 * x, -2.f * c20 * y, 4.f * c20 * z);
+            dY[7] = make_float3(c21 * z, 0.f, c21 * x);
+            dY[8] = make_float3(2.f * c22 * x, -2.f * c22 * y, 0.f);
+        }
+    }
+    if (DEG >= 3) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        float q = 5.f * zz - (xx + yy + zz);          // 5 z^2 - r^2
+        Y[9] = c33 * (3.f * xx * y - yy * y);         // m = -3: Im (x+iy)^3
+        Y[10] = c32 * 2.f * x * y * z;                // m = -2
+        Y[11] = c31 * y * q;                          // m = -1
+        Y[12] = c30 * z * (5.f * zz - 3.f * (xx + yy + zz));  // m = 0
+        Y[13] = c31 * x * q;                          // m = 1
+        Y[14] = c32 * z * (xx - yy);                  // m = 2
+        Y[15] = c33 * (xx * x - 3.f * x * yy);        // m = 3: Re (x+iy)^3
+        if (dY) {
+            dY[9] = make_float3(c33 * 6.f * x * y, c33 * (3.f * xx - 3.f * yy), 0.f);
+            dY[10] = make_float3(c32 * 2.f * y * z, c32 * 2.f * x * z, c32 * 2.f * x * y);
+            dY[11] = make_float3(c31 * y * (-2.f * x), c31 * (q - 2.f * yy), c31 * y * 8.f * z);
+            dY[12] = make_float3(c30 * z * (-6.f * x), c30 * z * (-6.f * y), c30 * (15.f * zz - 3.f * (xx + yy + zz) - 6.f * zz));
+            dY[13] = make_float3(c31 * (q - 2.f * xx), c31 * x * (-2.f * y), c31 * x * 8.f * z);
+            dY[14] = make_float3(c32 * 2.f * x * z, -c32 * 2.f * y * z, c32 * (xx - yy));
+            dY[15] = make_float3(c33 * (3.f * xx - 3.f * yy), c33 * (-6.f * x * y), 0.f);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ rotation from a quaternion
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Subsets holding a splat: leaves of the KD tree whose box, dilated by D in every axis,
+// contains mu (left branch: mu[a] - D < s, right branch: mu[a] + D >= s).  Iterative DFS.
+__device__ __forceinline__ unsigned long long subset_mask(const TreeParams& tp, float mx, float my, float mz, float D) {
+    if (tp.L == 0) return 1ull;
+    unsigned long long mask = 0;
+    int stack[kMaxRenderDepth + 2];
+    int sp = 0;
+    stack[sp++] = 0;
+    const int first_leaf = (1 << tp.L) - 1;
+    while (sp > 0) {
+        int j = stack[--sp];
+        if (j >= first_leaf) {
+            mask |= 1ull << (j - first_leaf);
+            continue;
+        }
+        int a = tp.axis[j];
+        float s = tp.split[j];
+        float c = a == 0 ? mx : (a == 1 ? my : mz);
+        if (c + D >= s) stack[sp++] = 2 * j + 2;
+        if (c - D < s) stack[sp++] = 2 * j + 1;
+    }
+    return mask;
+}
+
+struct SplatIn {
+    float mu[3], ls[3], q[4], logit;
+};
+
+__device__ __forceinline__ void load_splat(const rgs_gaussians& g, int64_t i, SplatIn& s) {
+    s.mu[0] = g.means[3 * i]; s.mu[1] = g.means[3 * i + 1]; s.mu[2] = g.means[3 * i + 2];
+    s.ls[0] = g.log_scales[3 * i]; s.ls[1] = g.log_scales[3 * i + 1]; s.ls[2] = g.log_scales[3 * i + 2];
+    float4 q = reinterpret_cast<const float4*>(g.quats)[i];
+    s.q[0] = q.x; s.q[1] = q.y; s.q[2] = q.z; s.q[3] = q.w;
+    s.logit = g.opacity_logits[i];
+}
+
+// Camera-space centre with the compensated transform; returns z (hi) and the projected
+// centre as hi + lo pairs.
+__device__ __forceinline__ void project_centre(const ViewParams& vp, const float mu[3], float p[3], float& mxh,
+                                               float& mxl, float& myh, float& myl) {
+    float xh, xl, yh, yl, zh, zl;
+    dot3_plus(vp.R[0], mu[0], vp.R[1], mu[1], vp.R[2], mu[2], vp.t[0], xh, xl);
+    dot3_plus(vp.R[3], mu[0], vp.R[4], mu[1], vp.R[5], mu[2], vp.t[1], yh, yl);
+    dot3_plus(vp.R[6], mu[0], vp.R[7], mu[1], vp.R[8], mu[2], vp.t[2], zh, zl);
+    p[0] = xh; p[1] = yh; p[2] = zh;
+    // u = x/z to about two floats: q + (x - q z)/z
+    float qx = __fdiv_rn(xh, zh);
+    float rx = __fmaf_rn(-qx, zh, xh);
+    rx = __fadd_rn(rx, __fsub_rn(xl, __fmul_rn(qx, zl)));
+    float qxl = __fdiv_rn(rx, zh);
+    float qy = __fdiv_rn(yh, zh);
+    float ry = __fmaf_rn(-qy, zh, yh);
+    ry = __fadd_rn(ry, __fsub_rn(yl, __fmul_rn(qy, zl)));
+    float qyl = __fdiv_rn(ry, zh);
+    // mean = f * u + c
+    float m, e, s, t;
+    two_prod(vp.fx, qx, m, e);
+    e = __fmaf_rn(vp.fx, qxl, e);
+    two_sum(m, vp.cx, s, t);
+    fast_two_sum(s, __fadd_rn(e, t), mxh, mxl);
+    two_prod(vp.fy, qy, m, e);
+    e = __fmaf_rn(vp.fy, qyl, e);
+    two_sum(m, vp.cy, s, t);
+    fast_two_sum(s, __fadd_rn(e, t), myh, myl);
+}
+
+// Shared forward intermediates (recomputed by the backward).
+struct Proj {
+    float p[3], z, u, v;       // camera-space centre, u = x/z, v = y/z
+    float s[3], Rq[9], qn[4], qnorm;
+    float T0[3], T1[3];        // T = J W
+    float A0[3], A1[3];        // A = T R_q S
+    float sxx, sxy, syy, det;  // Sigma' and its determinant
+    float ca, cb, cc;          // conic
+    float alpha;
+};
+
+__device__ __forceinline__ void ewa(const ViewParams& vp, const SplatIn& si, const float p[3], Proj& P) {
+    P.p[0] = p[0]; P.p[1] = p[1]; P.p[2] = p[2];
+    P.z = p[2];
+    float iz = 1.f / P.z;
+    P.u = p[0] * iz;
+    P.v = p[1] * iz;
+    float qn2 = si.q[0] * si.q[0] + si.q[1] * si.q[1] + si.q[2] * si.q[2] + si.q[3] * si.q[3];
+    P.qnorm = sqrtf(qn2);
+    float iq = 1.f / P.qnorm;
+    for (int j = 0; j < 4; ++j) P.qn[j] = si.q[j] * iq;
+    quat_rot(P.qn[0], P.qn[1], P.qn[2], P.qn[3], P.Rq);
+    for (int j = 0; j < 3; ++j) P.s[j] = __expf(si.ls[j]);
+    // T = J W: rows (fx/z)(W0 - u W2), (fy/z)(W1 - v W2)
+    float ax = vp.fx * iz, ay = vp.fy * iz;
+    for (int c = 0; c < 3; ++c) {
+        P.T0[c] = ax * (vp.R[c] - P.u * vp.R[6 + c]);
+        P.T1[c] = ay * (vp.R[3 + c] - P.v * vp.R[6 + c]);
+    }
+    // A = T Rq diag(s)
+    for (int c = 0; c < 3; ++c) {
+        float r0 = P.T0[0] * P.Rq[c] + P.T0[1] * P.Rq[3 + c] + P.T0[2] * P.Rq[6 + c];
+        float r1 = P.T1[0] * P.Rq[c] + P.T1[1] * P.Rq[3 + c] + P.T1[2] * P.Rq[6 + c];
+        P.A0[c] = r0 * P.s[c];
+        P.A1[c] = r1 * P.s[c];
+    }
+    float n0 = P.A0[0] * P.A0[0] + P.A0[1] * P.A0[1] + P.A0[2] * P.A0[2];
+    float n1 = P.A1[0] * P.A1[0] + P.A1[1] * P.A1[1] + P.A1[2] * P.A1[2];
+    float d01 = P.A0[0] * P.A1[0] + P.A0[1] * P.A1[1] + P.A0[2] * P.A1[2];
+    float cx = P.A0[1] * P.A1[2] - P.A0[2] * P.A1[1];
+    float cy = P.A0[2] * P.A1[0] - P.A0[0] * P.A1[2];
+    float cz = P.A0[0] * P.A1[1] - P.A0[1] * P.A1[0];
+    float dl = vp.dilation;
+    P.sxx = n0 + dl;
+    P.syy = n1 + dl;
+    P.sxy = d01;
+    P.det = (cx * cx + cy * cy + cz * cz) + dl * (n0 + n1) + dl * dl;
+    float idet = 1.f / P.det;
+    P.ca = P.syy * idet;
+    P.cb = -P.sxy * idet;
+    P.cc = P.sxx * idet;
+    P.alpha = 1.f / (1.f + __expf(-si.logit));
+}
+
+// ------------------------------------------------------------------ forward kernel
+template <int DEG>
+__global__ void __launch_bounds__(256)
+project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
+    constexpr int NSH = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t count = 0;
+    if (i < g.n) {
+        SplatIn si;
+        load_splat(g, i, si);
+        float p[3], mxh, mxl, myh, myl;
+        project_centre(vp, si.mu, p, mxh, mxl, myh, myl);
+        float z = p[2];
+        float smax = fmaxf(si.ls[0], fmaxf(si.ls[1], si.ls[2]));
+        float D = vp.trunc_mult * __expf(smax);
+        float alpha = 1.f / (1.f + __expf(-si.logit));
+        // A splat contributes nowhere unless z > near and alpha >= alpha_min.
+        bool vis = z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh);
+        if (vis) {
+            Proj P;
+            ewa(vp, si, p, P);
+            // Mahalanobis bound: d^2 <= trunc^2 and alpha exp(-d^2/2) >= alpha_min
+            float d2max = fminf(vp.trunc_mult * vp.trunc_mult, 2.f * __logf(alpha / vp.alpha_min));
+            d2max = fmaxf(d2max, 0.f) * 1.001f + 1e-3f;
+            float rb = D / z;                      // ball radius in normalised image units
+            float hx = fminf(sqrtf(d2max * P.sxx), vp.fx * rb) * 1.001f + 1e-3f;
+            float hy = fminf(sqrtf(d2max * P.syy), vp.fy * rb) * 1.001f + 1e-3f;
+            float fx0 = floorf((mxh - hx - 0.5f) * (1.f / kTile));
+            float fx1 = floorf((mxh + hx - 0.5f) * (1.f / kTile));
+            float fy0 = floorf((myh - hy - 0.5f) * (1.f / kTile));
+            float fy1 = floorf((myh + hy - 0.5f) * (1.f / kTile));
+            int tx0 = (int)fmaxf(fx0, 0.f), ty0 = (int)fmaxf(fy0, 0.f);
+            int tx1 = (int)fminf(fx1, (float)(vp.tiles_x - 1)), ty1 = (int)fminf(fy1, (float)(vp.tiles_y - 1));
+            if (tx0 <= tx1 && ty0 <= ty1 && isfinite(P.det) && P.det > 0.f) {
+                unsigned long long mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
+                int nsub = __popcll(mask);
+                count = (uint32_t)nsub * (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                // colour at dir = normalise(mu - o)
+                float dx = si.mu[0] - vp.o[0], dy = si.mu[1] - vp.o[1], dz = si.mu[2] - vp.o[2];
+                float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+                float Y[16];
+                sh_eval<DEG>(dx * inv, dy * inv, dz * inv, Y, nullptr);
+                const float* sh = g.sh + i * NSH * 3;
+                float rgb[3];
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.5f;
+#pragma unroll
+                    for (int k = 0; k < NSH; ++k) acc = fmaf(sh[3 * k + c], Y[k], acc);
+                    rgb[c] = fmaxf(acc, 0.f);
+                }
+                float l11 = sqrtf(P.ca);
+                float l12 = P.cb / l11;
+                float l22 = rsqrtf(P.det * P.ca);
+                __half2 lo = __floats2half2_rn(mxl, myl);
+                float lo_bits = __uint_as_float(*reinterpret_cast<uint32_t*>(&lo));
+                float rho2 = rb * rb;
+                b.rec[3 * i] = make_float4(mxh, myh, lo_bits, alpha);
+                b.rec[3 * i + 1] = make_float4(l11, l12, l22, nsub > 1 ? -rho2 : rho2);
+                b.rec[3 * i + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
+                b.rect[i] = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1,
+                                         (unsigned short)ty1);
+                b.mask[i] = mask;
+                b.dkey[i] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
+            }
+        }
+        b.cnt[i] = count;
+    }
+    // totals: instances and visible splats
+    unsigned long long c64 = count;
+    unsigned vis_n = count > 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+        vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (c64 | vis_n)) {
+        atomicAdd(&b.counters[0], c64);
+        atomicAdd(&b.counters[1], (unsigned long long)vis_n);
+    }
+}
+
+// ------------------------------------------------------------------ backward kernel
+// Pulls the per-splat 2D gradients (mean, conic, alpha, colour) back to the parameters:
+// colour -> SH coefficients and viewing direction; conic -> Sigma' -> A = J W Rq S ->
+// (J, Rq, S); J and the mean -> camera-space centre -> world centre; Rq -> normalised
+// quaternion -> quaternion; S -> log-scales; alpha -> logit.  Gradients are added to the
+// caller's buffers; one thread owns one splat, so no atomics are needed.
+template <int DEG>
+__global__ void __launch_bounds__(128)
+project_bwd_kernel(rgs_gaussians g, rgs_gaussian_grads gr, ViewParams vp, const float4* __restrict__ g2d) {
+    constexpr int NSH = (DEG + 1) * (DEG + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    float4 ga = g2d[3 * i], gb = g2d[3 * i + 1], gc = g2d[3 * i + 2];
+    if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f && gb.z == 0.f &&
+        gb.w == 0.f && gc.x == 0.f)
+        return;
+    const float g_mx = ga.x, g_my = ga.y, g_ca = ga.z, g_cb = ga.w, g_cc = gb.x, g_alpha = gb.y;
+    const float g_rgb[3] = {gb.z, gb.w, gc.x};
+
+    SplatIn si;
+    load_splat(g, i, si);
+    float p[3], mxh, mxl, myh, myl;
+    project_centre(vp, si.mu, p, mxh, mxl, myh, myl);
+    Proj P;
+    ewa(vp, si, p, P);
+    float gmu[3] = {0.f, 0.f, 0.f};
+
+    // opacity
+    gr.opacity_logits[i] += g_alpha * P.alpha * (1.f - P.alpha);
+
+    // colour -> SH coefficients and direction
+    {
+        float dx = si.mu[0] - vp.o[0], dy = si.mu[1] - vp.o[1], dz = si.mu[2] - vp.o[2];
+        float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float d[3] = {dx * inv, dy * inv, dz * inv};
+        float Y[16];
+        float3 dY[16];
+        sh_eval<DEG>(d[0], d[1], d[2], Y, dY);
+        const float* sh = g.sh + i * NSH * 3;
+        float* gsh = gr.sh + i * NSH * 3;
+        float gd[3] = {0.f, 0.f, 0.f};
+        for (int c = 0; c < 3; ++c) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < NSH; ++k) raw = fmaf(sh[3 * k + c], Y[k], raw);
+            if (!(raw > 0.f)) continue;
+            float gcol = g_rgb[c];
+#pragma unroll
+            for (int k = 0; k < NSH; ++k) {
+                gsh[3 * k + c] += gcol * Y[k];
+                float w = gcol * sh[3 * k + c];
+                gd[0] = fmaf(w, dY[k].x, gd[0]);
+                gd[1] = fmaf(w, dY[k].y, gd[1]);
+                gd[2] = fmaf(w, dY[k].z, gd[2]);
+            }
+        }
+        float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+        for (int j = 0; j < 3; ++j) gmu[j] += (gd[j] - d[j] * dd) * inv;
+    }
+
+    // conic (a, b, c) = inverse(Sigma'): dL/dSigma' = -Q G Q, G = [[ga, gb/2], [gb/2, gc]]
+    float Q00 = P.ca, Q01 = P.cb, Q11 = P.cc;
+    float G00 = g_ca, G01 = 0.5f * g_cb, G11 = g_cc;
+    float t00 = Q00 * G00 + Q01 * G01, t01 = Q00 * G01 + Q01 * G11;
+    float t10 = Q01 * G00 + Q11 * G01, t11 = Q01 * G01 + Q11 * G11;
+    float S00 = -(t00 * Q00 + t01 * Q01);
+    float S01 = -(t00 * Q01 + t01 * Q11);
+    float S11 = -(t10 * Q01 + t11 * Q11);
+    // Sigma' = A A^T + dl I:  dL/dA = 2 S A   (S symmetric)
+    float GA0[3], GA1[3];
+    for (int c = 0; c < 3; ++c) {
+        GA0[c] = 2.f * (S00 * P.A0[c] + S01 * P.A1[c]);
+        GA1[c] = 2.f * (S01 * P.A0[c] + S11 * P.A1[c]);
+    }
+    // A[r][c] = s_c (T_r . Rq[:,c]):  dL/ds_c, dL/dRq, dL/dT
+    float GT0[3] = {0.f, 0.f, 0.f}, GT1[3] = {0.f, 0.f, 0.f};
+    float GRq[9];
+    for (int c = 0; c < 3; ++c) {
+        float r0 = P.T0[0] * P.Rq[c] + P.T0[1] * P.Rq[3 + c] + P.T0[2] * P.Rq[6 + c];
+        float r1 = P.T1[0] * P.Rq[c] + P.T1[1] * P.Rq[3 + c] + P.T1[2] * P.Rq[6 + c];
+        float gs = GA0[c] * r0 + GA1[c] * r1;
+        gr.log_scales[3 * i + c] += gs * P.s[c];
+        float h0 = GA0[c] * P.s[c], h1 = GA1[c] * P.s[c];
+        for (int j = 0; j < 3; ++j) {
+            GRq[3 * j + c] = h0 * P.T0[j] + h1 * P.T1[j];
+            GT0[j] += h0 * P.Rq[3 * j + c];
+            GT1[j] += h1 * P.Rq[3 * j + c];
+        }
+    }
+    // T0 = (fx/z)(W0 - u W2), T1 = (fy/z)(W1 - v W2), u = x/z, v = y/z
+    float iz = 1.f / P.z;
+    float gax = 0.f, gay = 0.f, gu = 0.f, gv = 0.f;
+    for (int c = 0; c < 3; ++c) {
+        gax += GT0[c] * (vp.R[c] - P.u * vp.R[6 + c]);
+        gay += GT1[c] * (vp.R[3 + c] - P.v * vp.R[6 + c]);
+        gu -= GT0[c] * vp.fx * iz * vp.R[6 + c];
+        gv -= GT1[c] * vp.fy * iz * vp.R[6 + c];
+    }
+    // mean = (fx u + cx, fy v + cy)
+    gu += g_mx * vp.fx;
+    gv += g_my * vp.fy;
+    // ax = fx/z, ay = fy/z, u = x/z, v = y/z  ->  camera-space centre
+    float gp0 = gu * iz;
+    float gp1 = gv * iz;
+    float gp2 = -(gax * vp.fx + gay * vp.fy) * iz * iz - (gu * P.u + gv * P.v) * iz;
+    // p = W mu + t
+    for (int j = 0; j < 3; ++j) gmu[j] += vp.R[j] * gp0 + vp.R[3 + j] * gp1 + vp.R[6 + j] * gp2;
+    gr.means[3 * i] += gmu[0];
+    gr.means[3 * i + 1] += gmu[1];
+    gr.means[3 * i + 2] += gmu[2];
+
+    // Rq(w,x,y,z) -> normalised quaternion -> quaternion
+    float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+    float gw = 2.f * (-z * GRq[1] + y * GRq[2] + z * GRq[3] - x * GRq[5] - y * GRq[6] + x * GRq[7]);
+    float gx = 2.f * (y * GRq[1] + z * GRq[2] + y * GRq[3] - 2.f * x * GRq[4] - w * GRq[5] + z * GRq[6] + w * GRq[7] -
+                      2.f * x * GRq[8]);
+    float gy = 2.f * (-2.f * y * GRq[0] + x * GRq[1] + w * GRq[2] + x * GRq[3] + z * GRq[5] - w * GRq[6] + z * GRq[7] -
+                      2.f * y * GRq[8]);
+    float gz = 2.f * (-2.f * z * GRq[0] - w * GRq[1] + x * GRq[2] + w * GRq[3] - 2.f * z * GRq[4] + y * GRq[5] +
+                      x * GRq[6] + y * GRq[7]);
+    float dot = gw * w + gx * x + gy * y + gz * z;
+    float iq = 1.f / P.qnorm;
+    float4* gq = reinterpret_cast<float4*>(gr.quats) + i;
+    float4 cur = *gq;
+    cur.x += (gw - w * dot) * iq;
+    cur.y += (gx - x * dot) * iq;
+    cur.z += (gy - y * dot) * iq;
+    cur.w += (gz - z * dot) * iq;
+    *gq = cur;
+}
+
+}  // namespace
+
+int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
+                       cudaStream_t s) {
+    unsigned grid = (unsigned)((g.n + 255) / 256);
+    switch (g.sh_degree) {
+        case 0: project_fwd_kernel<0><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
+        case 1: project_fwd_kernel<1><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
+        case 2: project_fwd_kernel<2><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
+        default: project_fwd_kernel<3><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
+    }
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
+                       const RasterBuffers& b, cudaStream_t s) {
+    unsigned grid = (unsigned)((g.n + 127) / 128);
+    switch (g.sh_degree) {
+        case 0: project_bwd_kernel<0><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
+        case 1: project_bwd_kernel<1><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
+        case 2: project_bwd_kernel<2><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
+        default: project_bwd_kernel<3><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
+    }
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+}  // namespace rgs

@@ -1,0 +1,544 @@
+// Tile binning, partial-map blending (Eq. 3-4 with the indicator of Eq. 6), the ordered
+// merge (Eq. 5) and their adjoints.
+//
+// Instances.  After the visible splats are sorted by depth, each splat emits one
+// instance per (subset N_k holding it, 16x16 tile its footprint may touch), keyed by
+// (tile, view rank of k).  A stable radix sort on that key leaves every (tile, subset)
+// run in depth order, which is the order of Eq. 3.  A warp emits the instances of 32
+// consecutive splats cooperatively so that giant splats do not serialise one thread and
+// the writes are contiguous.
+//
+// Blend.  One CTA per tile, one thread per pixel.  For each subset in view order the CTA
+// walks the run in batches of 256 records staged in shared memory, every pixel applies
+// the truncation tests and Eq. 6 (only for splats held by several subsets), and stops
+// the subset once its transmittance drops below eps_T (block vote, and a warp vote to
+// skip work).  The partial (C_k, T_k) is stored; the merge of Eq. 5 is accumulated on
+// the fly, so the image costs no extra pass.
+//
+// Backward.  The adjoint of Eq. 5 gives dL/dC_k = g P_k and dL/dT_k = P_k <g, S_k> per
+// pixel (P_k: transmittance in front of subset k, S_k: colour behind it).  Each subset
+// is then replayed front to back from its stored partials: recomputing sigma and T
+// exactly as the forward did, with A_i the colour accumulated up to and including pair i,
+//   dC_k/dsigma_i = T_i c_i - (C_k - A_i)/(1 - sigma_i),   dT_k/dsigma_i = -T_k/(1 - sigma_i).
+// Per-splat 2D gradients are reduced across the warp with shuffles, across the CTA in
+// shared memory, and added to global memory with one vector reduction per float4.
+#include <cuda_fp16.h>
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+namespace {
+
+constexpr int kBlendThreads = kTilePixels;  // 256
+constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -0.5 * log2(e)
+
+// exp(-d2/2) as 2^(d2 * -0.5 log2 e) on the SFU (ex2.approx, ~2 ulp); the forward and
+// the backward call the same function, so the backward sees the forward's sigma exactly.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ emission
+__global__ void __launch_bounds__(256)
+emit_kernel(ViewParams vp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis, const uint32_t* __restrict__ ioff,
+            const uint32_t* __restrict__ cnt, const ushort4* __restrict__ rect,
+            const unsigned long long* __restrict__ mask, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t warp_first = p - lane;
+    if (warp_first >= n_vis) return;
+    uint32_t id = 0, off = 0, c = 0;
+    ushort4 r = make_ushort4(0, 0, 0, 0);
+    unsigned long long m = 0;
+    if (p < n_vis) {
+        id = sorted_ids[p];
+        off = ioff[p];
+        c = cnt[id];
+        r = rect[id];
+        m = mask[id];
+    }
+    // warp range of output positions
+    int last = (int)min((int64_t)31, n_vis - 1 - warp_first);
+    uint32_t wbeg = __shfl_sync(0xffffffffu, off, 0);
+    uint32_t lend = off + c;
+    uint32_t wend = __shfl_sync(0xffffffffu, lend, last);
+    if (lane > last) off = 0xffffffffu;    // never owns a position
+    for (uint32_t j0 = wbeg; j0 < wend; j0 += 32) {
+        uint32_t j = j0 + lane;
+        // owner = last lane whose offset <= j (offsets are non-decreasing over lanes)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            uint32_t o = __shfl_sync(0xffffffffu, off, lo + step);
+            if (lo + step <= last && o <= j) lo += step;
+        }
+        uint32_t o_id = __shfl_sync(0xffffffffu, id, lo);
+        uint32_t o_off = __shfl_sync(0xffffffffu, off, lo);
+        unsigned rx = __shfl_sync(0xffffffffu, (unsigned)r.x | ((unsigned)r.y << 16), lo);
+        unsigned rz = __shfl_sync(0xffffffffu, (unsigned)r.z | ((unsigned)r.w << 16), lo);
+        unsigned long long o_m = __shfl_sync(0xffffffffu, m, lo);
+        if (j < wend) {
+            int x0 = rx & 0xffff, y0 = rx >> 16, x1 = rz & 0xffff, y1 = rz >> 16;
+            int w = x1 - x0 + 1;
+            int nt = w * (y1 - y0 + 1);
+            int e = (int)(j - o_off);
+            int si = e / nt;
+            int t = e - si * nt;
+            int ty = y0 + t / w;
+            int tx = x0 + (t - (ty - y0) * w);
+            // si-th subset of the mask
+            unsigned long long mm = o_m;
+            for (int q = 0; q < si; ++q) mm &= mm - 1;
+            int k = __ffsll((long long)mm) - 1;
+            uint32_t tile = (uint32_t)(ty * vp.tiles_x + tx);
+            ikey[j] = (tile << vp.L) | (uint32_t)vp.rank_of[k];
+            ival[j] = o_id;
+        }
+    }
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t k = keys[j];
+    if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
+    if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+}
+
+// ------------------------------------------------------------------ shared pieces of the blend
+// The L plane constraints of the current subset's leaf (Eq. 6), kept in shared memory:
+// they are uniform across the CTA and only read for splats held by several subsets.
+struct LeafPath {
+    float split[kMaxRenderDepth];
+    int axis_right[kMaxRenderDepth];   // axis | (right << 2)
+};
+
+__device__ __forceinline__ void leaf_path(const TreeParams& tp, int k, LeafPath& lp) {
+    int node = 0;
+    for (int d = 0; d < tp.L; ++d) {
+        int right = (k >> (tp.L - 1 - d)) & 1;
+        lp.split[d] = tp.split[node];
+        lp.axis_right[d] = tp.axis[node] | (right << 2);
+        node = 2 * node + 1 + right;
+    }
+}
+
+// x_i = o + z d_p lies in S_k (half-open boxes: left x[a] < s, right x[a] >= s)
+__device__ __forceinline__ bool in_leaf(const LeafPath& lp, int L, const float o[3], const float dray[3], float z) {
+    bool ok = true;
+    for (int d = 0; d < L; ++d) {
+        const int ar = lp.axis_right[d];
+        const int a = ar & 3;
+        const float oa = a == 0 ? o[0] : (a == 1 ? o[1] : o[2]);
+        const float da = a == 0 ? dray[0] : (a == 1 ? dray[1] : dray[2]);
+        const float x = fmaf(z, da, oa);
+        ok = ok && ((x >= lp.split[d]) == (bool)(ar >> 2));
+    }
+    return ok;
+}
+
+struct StagedRec {   // tile-relative record in shared memory (3 x float4)
+    float4 a;        // mx, my, alpha, rho2 (sign: straddles several subsets)
+    float4 b;        // l11, l12, l22, z
+    float4 c;        // r, g, b, (splat id as bits)
+};
+
+__device__ __forceinline__ StagedRec stage_record(const float4* __restrict__ rec, uint32_t id, float x0, float y0) {
+    float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+    uint32_t lo_bits = __float_as_uint(r0.z);
+    __half2 lo = *reinterpret_cast<__half2*>(&lo_bits);
+    float2 lof = __half22float2(lo);
+    StagedRec s;
+    s.a = make_float4(__fadd_rn(__fsub_rn(r0.x, x0), lof.x), __fadd_rn(__fsub_rn(r0.y, y0), lof.y), r0.w, r1.w);
+    s.b = make_float4(r1.x, r1.y, r1.z, r2.w);
+    s.c = make_float4(r2.x, r2.y, r2.z, __uint_as_float(id));
+    return s;
+}
+
+// warp-aggregated pair counters (tracing only)
+__device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t n_eval, uint32_t n_contrib) {
+    unsigned long long e = n_eval, c = n_contrib;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(pairs, e);
+        atomicAdd(pairs + 1, c);
+    }
+}
+
+// ------------------------------------------------------------------ blend forward
+__global__ void __launch_bounds__(kBlendThreads)
+blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                 const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
+                 float* __restrict__ image, float* __restrict__ Tfin, unsigned long long* __restrict__ pairs) {
+    __shared__ StagedRec srec[kBlendThreads];
+    uint32_t n_eval = 0, n_contrib = 0;
+    __shared__ LeafPath lp;
+    const int tile = blockIdx.x;
+    const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int px = txi * kTile + lx, py = tyi * kTile + ly;
+    const bool inside = px < vp.W && py < vp.H;
+    const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
+    const float pcx = lx + 0.5f, pcy = ly + 0.5f;
+    const float o[3] = {vp.o[0], vp.o[1], vp.o[2]};
+    // world direction of this pixel's ray with unit camera-z component (Eq. 6 test)
+    float dray[3];
+    {
+        float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
+        for (int a = 0; a < 3; ++a) dray[a] = fmaf(vp.R[a], u, fmaf(vp.R[3 + a], v, vp.R[6 + a]));
+    }
+    const float tm2 = vp.trunc_mult * vp.trunc_mult;
+    const size_t HW = (size_t)vp.W * vp.H;
+    const size_t pix = (size_t)py * vp.W + px;
+    float img0 = 0.f, img1 = 0.f, img2 = 0.f, Pm = 1.f;
+
+    for (int r = 0; r < vp.K; ++r) {
+        const int k = vp.order[r];
+        if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
+        const uint2 rg = ranges[(size_t)tile * vp.K + r];
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        bool done = !inside;
+        for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
+            const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
+            __syncthreads();
+            if ((int)threadIdx.x < nb) srec[threadIdx.x] = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+            __syncthreads();
+            if (!__all_sync(0xffffffffu, done)) {
+                for (int j = 0; j < nb && !done; ++j) {
+                    ++n_eval;
+                    const float4 A = srec[j].a;
+                    const float4 B = srec[j].b;
+                    const float dx = pcx - A.x, dy = pcy - A.y;
+                    const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
+                    const float d2 = fmaf(u1, u1, u2 * u2);
+                    if (d2 > tm2) continue;
+                    const float bx = dx * vp.ifx, by = dy * vp.ify;
+                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) continue;
+                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) continue;
+                    const float sig = fminf(A.z * ex2_approx(d2 * kNegHalfLog2e), vp.alpha_max);
+                    if (sig < vp.alpha_min) continue;
+                    ++n_contrib;
+                    const float4 Cc = srec[j].c;
+                    const float w = sig * T;
+                    C0 = fmaf(Cc.x, w, C0);
+                    C1 = fmaf(Cc.y, w, C1);
+                    C2 = fmaf(Cc.z, w, C2);
+                    T = fmaf(-sig, T, T);
+                    if (T < vp.eps_T) done = true;
+                }
+            }
+            if (__syncthreads_count(done) == kBlendThreads) break;
+        }
+        if (inside) {
+            pC[((size_t)k * 3 + 0) * HW + pix] = C0;
+            pC[((size_t)k * 3 + 1) * HW + pix] = C1;
+            pC[((size_t)k * 3 + 2) * HW + pix] = C2;
+            pT[(size_t)k * HW + pix] = T;
+            img0 = fmaf(C0, Pm, img0);
+            img1 = fmaf(C1, Pm, img1);
+            img2 = fmaf(C2, Pm, img2);
+            Pm *= T;
+        }
+    }
+    if (inside && image) {
+        image[0 * HW + pix] = fmaf(vp.bg[0], Pm, img0);
+        image[1 * HW + pix] = fmaf(vp.bg[1], Pm, img1);
+        image[2 * HW + pix] = fmaf(vp.bg[2], Pm, img2);
+        if (Tfin) Tfin[pix] = Pm;
+    }
+    if (pairs) count_pairs(pairs, n_eval, n_contrib);
+}
+
+// ------------------------------------------------------------------ blend backward
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+// dynamic shared memory: s_behind [K][256] floats
+__global__ void __launch_bounds__(kBlendThreads)
+blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                 const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
+                 const float* __restrict__ gI, float4* __restrict__ g2d, unsigned long long* __restrict__ pairs) {
+    extern __shared__ float s_behind[];
+    uint32_t n_eval = 0, n_contrib = 0;
+    __shared__ StagedRec srec[kBlendThreads];
+    __shared__ float sacc[kBlendThreads][9];
+    __shared__ LeafPath lp;
+    const float o[3] = {vp.o[0], vp.o[1], vp.o[2]};
+    const int tile = blockIdx.x;
+    const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int px = txi * kTile + lx, py = tyi * kTile + ly;
+    const bool inside = px < vp.W && py < vp.H;
+    const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
+    const float pcx = lx + 0.5f, pcy = ly + 0.5f;
+    const int lane = threadIdx.x & 31;
+    float dray[3];
+    {
+        float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
+        for (int a = 0; a < 3; ++a) dray[a] = fmaf(vp.R[a], u, fmaf(vp.R[3 + a], v, vp.R[6 + a]));
+    }
+    const float tm2 = vp.trunc_mult * vp.trunc_mult;
+    const size_t HW = (size_t)vp.W * vp.H;
+    const size_t pix = inside ? (size_t)py * vp.W + px : 0;
+
+    for (int i = threadIdx.x; i < kBlendThreads * 9; i += kBlendThreads) (&sacc[0][0])[i] = 0.f;
+
+    // adjoint of Eq. 5: <g, S_r> for every rank, back to front
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) {
+        g0 = gI[0 * HW + pix];
+        g1 = gI[1 * HW + pix];
+        g2 = gI[2 * HW + pix];
+    }
+    {
+        float behind = g0 * vp.bg[0] + g1 * vp.bg[1] + g2 * vp.bg[2];
+        for (int r = vp.K - 1; r >= 0; --r) {
+            s_behind[r * kBlendThreads + threadIdx.x] = behind;
+            if (inside) {
+                const int k = vp.order[r];
+                float c0 = pC[((size_t)k * 3 + 0) * HW + pix], c1 = pC[((size_t)k * 3 + 1) * HW + pix],
+                      c2 = pC[((size_t)k * 3 + 2) * HW + pix], t = pT[(size_t)k * HW + pix];
+                behind = fmaf(t, behind, g0 * c0 + g1 * c1 + g2 * c2);
+            }
+        }
+    }
+    float Pm = 1.f;
+    for (int r = 0; r < vp.K; ++r) {
+        const int k = vp.order[r];
+        float Ck0 = 0.f, Ck1 = 0.f, Ck2 = 0.f, Tk = 1.f;
+        if (inside) {
+            Ck0 = pC[((size_t)k * 3 + 0) * HW + pix];
+            Ck1 = pC[((size_t)k * 3 + 1) * HW + pix];
+            Ck2 = pC[((size_t)k * 3 + 2) * HW + pix];
+            Tk = pT[(size_t)k * HW + pix];
+        }
+        const float gC0 = g0 * Pm, gC1 = g1 * Pm, gC2 = g2 * Pm;
+        const float gT = Pm * s_behind[r * kBlendThreads + threadIdx.x];
+        const float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
+        Pm *= Tk;
+        if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
+        const uint2 rg = ranges[(size_t)tile * vp.K + r];
+        bool active = inside && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
+        if (__syncthreads_count(active) == 0) continue;
+        bool done = !active;
+        float T = 1.f, acc = 0.f;   // acc = <gC, A_i>
+        for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
+            const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
+            __syncthreads();
+            if ((int)threadIdx.x < nb) srec[threadIdx.x] = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+            __syncthreads();
+            if (!__all_sync(0xffffffffu, done)) {
+                for (int j = 0; j < nb; ++j) {
+                    float gmx = 0.f, gmy = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gal = 0.f, gr0 = 0.f, gr1 = 0.f,
+                          gr2 = 0.f;
+                    bool contrib = false;
+                    if (!done) {
+                        ++n_eval;
+                        const float4 A = srec[j].a;
+                        const float4 B = srec[j].b;
+                        const float dx = pcx - A.x, dy = pcy - A.y;
+                        const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
+                        const float d2 = fmaf(u1, u1, u2 * u2);
+                        const float bx = dx * vp.ifx, by = dy * vp.ify;
+                        bool pass = d2 <= tm2 && fmaf(bx, bx, by * by) <= fabsf(A.w);
+                        if (pass && A.w < 0.f) pass = in_leaf(lp, vp.L, o, dray, B.w);
+                        if (pass) {
+                            const float G = ex2_approx(d2 * kNegHalfLog2e);
+                            const float raw = A.z * G;
+                            const float sig = fminf(raw, vp.alpha_max);
+                            if (sig >= vp.alpha_min) {
+                                contrib = true;
+                                ++n_contrib;
+                                const float4 Cc = srec[j].c;
+                                const float w = sig * T;
+                                const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
+                                acc = fmaf(w, grgb, acc);
+                                const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
+                                gr0 = gC0 * w;
+                                gr1 = gC1 * w;
+                                gr2 = gC2 * w;
+                                if (raw < vp.alpha_max) {
+                                    gal = dsig * G;
+                                    const float gd2 = -0.5f * sig * dsig;
+                                    ga = gd2 * dx * dx;
+                                    gb = gd2 * 2.f * dx * dy;
+                                    gc = gd2 * dy * dy;
+                                    // d(d2)/d(mean) = -2 Q delta, Q delta = L^T (u1, u2)
+                                    gmx = -2.f * gd2 * (B.x * u1);
+                                    gmy = -2.f * gd2 * fmaf(B.y, u1, B.z * u2);
+                                }
+                                T = fmaf(-sig, T, T);
+                                if (T < vp.eps_T) done = true;
+                            }
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, contrib)) {
+                        gmx = warp_sum(gmx);
+                        gmy = warp_sum(gmy);
+                        ga = warp_sum(ga);
+                        gb = warp_sum(gb);
+                        gc = warp_sum(gc);
+                        gal = warp_sum(gal);
+                        gr0 = warp_sum(gr0);
+                        gr1 = warp_sum(gr1);
+                        gr2 = warp_sum(gr2);
+                        if (lane == 0) {
+                            atomicAdd(&sacc[j][0], gmx);
+                            atomicAdd(&sacc[j][1], gmy);
+                            atomicAdd(&sacc[j][2], ga);
+                            atomicAdd(&sacc[j][3], gb);
+                            atomicAdd(&sacc[j][4], gc);
+                            atomicAdd(&sacc[j][5], gal);
+                            atomicAdd(&sacc[j][6], gr0);
+                            atomicAdd(&sacc[j][7], gr1);
+                            atomicAdd(&sacc[j][8], gr2);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < nb) {
+                float* a = sacc[threadIdx.x];
+                bool nz = false;
+                for (int t = 0; t < 9; ++t) nz |= a[t] != 0.f;
+                if (nz) {
+                    const uint32_t id = __float_as_uint(srec[threadIdx.x].c.w);
+                    float4* dst = g2d + 3 * (size_t)id;
+                    red_add_v4(dst, make_float4(a[0], a[1], a[2], a[3]));
+                    red_add_v4(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
+                    red_add_v4(dst + 2, make_float4(a[8], 0.f, 0.f, 0.f));
+                    for (int t = 0; t < 9; ++t) a[t] = 0.f;
+                }
+            }
+            if (__syncthreads_count(done) == kBlendThreads) break;
+        }
+    }
+    if (pairs) count_pairs(pairs + 2, n_eval, n_contrib);
+}
+
+// ------------------------------------------------------------------ standalone merge (Eq. 5)
+__global__ void merge_kernel(const float* __restrict__ pC, const float* __restrict__ pT,
+                             const int32_t* __restrict__ order, int K, int64_t HW, float bg0, float bg1, float bg2,
+                             float* __restrict__ image, float* __restrict__ Tout) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= HW) return;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, P = 1.f;
+    for (int r = 0; r < K; ++r) {
+        const int64_t k = order[r];
+        c0 = fmaf(pC[(k * 3 + 0) * HW + i], P, c0);
+        c1 = fmaf(pC[(k * 3 + 1) * HW + i], P, c1);
+        c2 = fmaf(pC[(k * 3 + 2) * HW + i], P, c2);
+        P *= pT[k * HW + i];
+    }
+    image[0 * HW + i] = fmaf(bg0, P, c0);
+    image[1 * HW + i] = fmaf(bg1, P, c1);
+    image[2 * HW + i] = fmaf(bg2, P, c2);
+    if (Tout) Tout[i] = P;
+}
+
+// Adjoint of Eq. 5 per pixel: a back-to-front pass gives <g, S_r> and the suffix products,
+// a front-to-back pass the prefix products.
+__global__ void merge_bwd_kernel(const float* __restrict__ pC, const float* __restrict__ pT,
+                                 const int32_t* __restrict__ order, int K, int64_t HW, float bg0, float bg1,
+                                 float bg2, const float* __restrict__ gI, const float* __restrict__ gTo,
+                                 float* __restrict__ dC, float* __restrict__ dT) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= HW) return;
+    const float g0 = gI[i], g1 = gI[HW + i], g2 = gI[2 * HW + i];
+    const float gt = gTo ? gTo[i] : 0.f;
+    // back to front: dT_k <- <g, S_r> and the suffix product behind r (stored temporarily)
+    float behind = g0 * bg0 + g1 * bg1 + g2 * bg2, suffix = 1.f;
+    for (int r = K - 1; r >= 0; --r) {
+        const int64_t k = order[r];
+        dT[k * HW + i] = behind;
+        dC[(k * 3) * HW + i] = suffix;
+        const float t = pT[k * HW + i];
+        behind = fmaf(t, behind, g0 * pC[(k * 3) * HW + i] + g1 * pC[(k * 3 + 1) * HW + i] + g2 * pC[(k * 3 + 2) * HW + i]);
+        suffix *= t;
+    }
+    float P = 1.f;
+    for (int r = 0; r < K; ++r) {
+        const int64_t k = order[r];
+        const float suf = dC[(k * 3) * HW + i];
+        dT[k * HW + i] = P * dT[k * HW + i] + gt * P * suf;
+        dC[(k * 3 + 0) * HW + i] = g0 * P;
+        dC[(k * 3 + 1) * HW + i] = g1 * P;
+        dC[(k * 3 + 2) * HW + i] = g2 * P;
+        P *= pT[k * HW + i];
+    }
+}
+
+}  // namespace
+
+int launch_emit(const ViewParams& vp, const RasterBuffers& b, const uint32_t* sorted_ids, int64_t n_vis,
+                cudaStream_t s) {
+    if (n_vis <= 0) return RGS_OK;
+    unsigned grid = (unsigned)((n_vis + 255) / 256);
+    emit_kernel<<<grid, 256, 0, s>>>(vp, sorted_ids, n_vis, b.ioff, b.cnt, b.rect, b.mask, b.ikey, b.ival);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s) {
+    RGS_CUDA_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s));
+    if (n <= 0) return RGS_OK;
+    ranges_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, ranges);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                     float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s) {
+    unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
+    blend_fwd_kernel<<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
+                                                    T_final, prof_pair_counters());
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                     const float* partial_C, const float* partial_T, const float* dL_dimage, cudaStream_t s) {
+    unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
+    size_t smem = sizeof(float) * (size_t)vp.K * kBlendThreads;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr_set = true;
+    }
+    blend_bwd_kernel<<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
+                                                       dL_dimage, b.g2d, prof_pair_counters());
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
+                 float* image, float* T_out, cudaStream_t s) {
+    int64_t HW = (int64_t)H * W;
+    merge_kernel<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(pC, pT, order, K, HW, bg[0], bg[1], bg[2], image, T_out);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
+                     const float* gI, const float* gT, float* dC, float* dT, cudaStream_t s) {
+    int64_t HW = (int64_t)H * W;
+    merge_bwd_kernel<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(pC, pT, order, K, HW, bg[0], bg[1], bg[2], gI, gT, dC,
+                                                                  dT);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+}  // namespace rgs

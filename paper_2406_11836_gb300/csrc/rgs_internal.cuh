@@ -1,0 +1,170 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/rgs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rgs.h"
+
+namespace rgs {
+
+// ------------------------------------------------------------------ limits and layout
+constexpr int kTile = 16;                 // tile edge (pixels)
+constexpr int kTilePixels = kTile * kTile;
+constexpr int kMaxRenderDepth = 6;        // K <= 64 subsets in a render (64-bit masks)
+constexpr int kMaxKdDepth = 8;            // K <= 256 leaves in a partition
+constexpr int kMaxNodes = (1 << kMaxKdDepth) - 1;
+
+// Projected splat record: three float4 per splat (48 bytes), written by the projection
+// and gathered by the blend kernels once per (tile, subset) instance.
+//   r0 = (mean_x hi, mean_y hi, half2(mean_x lo, mean_y lo) bits, alpha)
+//   r1 = (l11, l12, l22, rho2)   conic = L^T L with L = [[l11, l12], [0, l22]];
+//                                rho2 = (D/z)^2, stored negated when the splat lies in
+//                                more than one subset (the per-pixel Eq. 6 test is needed)
+//   r2 = (r, g, b, z)
+constexpr int kRecFloat4 = 3;
+
+// Per-splat gradient record of the blend backward: 12 floats (three float4 so that
+// accumulation can use vector reductions):
+//   (mean_x, mean_y, conic_a, conic_b, conic_c, alpha, r, g, b, 0, 0, 0)
+constexpr int kG2dFloats = 12;
+
+// ------------------------------------------------------------------ kernel parameters
+struct TreeParams {            // KD splits in heap order
+    int L;
+    int8_t axis[kMaxNodes];
+    float split[kMaxNodes];
+};
+
+struct ViewParams {
+    float R[9];                // world->camera rotation (row-major)
+    float t[3];
+    float o[3];                // camera centre (fp32 rounding of -R^T t)
+    float fx, fy, cx, cy, ifx, ify, near_z;
+    int W, H, tiles_x, tiles_y;
+    float trunc_mult, eps_T, alpha_min, alpha_max, dilation;
+    float bg[3];
+    int K, L, sh_degree;
+    int tile_bits;             // bits of the tile index in an instance key
+    int8_t order[64];          // order[r]  = subset at view rank r
+    int8_t rank_of[64];        // rank_of[k] = view rank of subset k
+};
+
+// ------------------------------------------------------------------ tracing
+// Passes timed by the profiler (rgs_profile_*): a pair of CUDA events is recorded on the
+// launching stream around each pass while profiling is on.
+enum Stage {
+    ST_PROJECT = 0, ST_COMPACT, ST_DEPTH_SORT, ST_OFFSETS, ST_EMIT, ST_INST_SORT, ST_RANGES, ST_BLEND_FWD,
+    ST_BLEND_BWD, ST_PROJECT_BWD, ST_ADAM, ST_MERGE, ST_MERGE_BWD, ST_KD, ST_COUNT
+};
+struct ProfScope {
+    int token;
+    cudaStream_t s;
+    ProfScope(int stage, cudaStream_t st);
+    ~ProfScope();
+};
+// Device counters of evaluated / contributing (pixel, splat) pairs, or nullptr when
+// profiling is off: [0] fwd evaluated, [1] fwd contributing, [2] bwd evaluated, [3] bwd
+// contributing.
+unsigned long long* prof_pair_counters();
+void prof_add_host_counts(int64_t instances, int64_t visible);
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+void set_required_workspace(size_t bytes);
+
+#define RGS_CUDA_TRY(expr)                                                                 \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            ::rgs::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e)); \
+            return RGS_ECUDA;                                                              \
+        }                                                                                  \
+    } while (0)
+
+#define RGS_CUDA_LAUNCH_CHECK()                                                            \
+    do {                                                                                   \
+        cudaError_t _e = cudaGetLastError();                                               \
+        if (_e != cudaSuccess) {                                                           \
+            ::rgs::set_error("%s:%d: kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \
+            return RGS_ECUDA;                                                              \
+        }                                                                                  \
+    } while (0)
+
+// ------------------------------------------------------------------ scan / sort (sort.cu)
+// Exclusive prefix sum of n uint32 values; `in` may equal `out`.  `load` selects what
+// is summed: 0 = the value, 1 = (value != 0), 2 = in[gather[i]].
+size_t scan_temp_bytes(int64_t n);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int load, const uint32_t* gather, void* temp,
+                       size_t temp_bytes, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit), 8-bit digits.
+// The sorted pairs end in (keys, vals) or (keys_alt, vals_alt): *in_alt tells which.
+size_t radix_temp_bytes(int64_t n);
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int end_bit,
+                     void* temp, size_t temp_bytes, cudaStream_t s, bool* in_alt);
+
+// ------------------------------------------------------------------ raster (raster.cu)
+struct RasterBuffers {
+    // per splat
+    float4* rec;          // [N * 3]
+    uint32_t* cnt;        // [N] instances of the splat (0: culled)
+    ushort4* rect;        // [N] tile rectangle (x0, y0, x1, y1), inclusive
+    unsigned long long* mask;  // [N] subsets containing the splat
+    uint32_t* dkey;       // [N] depth key (float bits of z)
+    uint32_t* vis_pos;    // [N] compaction positions
+    uint32_t* skey;       // [N] compacted depth keys   (sort buffer a)
+    uint32_t* sid;        // [N] compacted splat ids     (sort buffer a)
+    uint32_t* skey_alt;   // [N]                         (sort buffer b)
+    uint32_t* sid_alt;    // [N]
+    uint32_t* ioff;       // [N] instance offsets in depth order
+    unsigned long long* counters;  // [4]: total instances, visible splats
+    float4* g2d;          // [N * 3] (backward only)
+    // per (tile, subset)
+    uint2* ranges;        // [tiles * K]
+    // per instance
+    uint32_t* ikey;
+    uint32_t* ival;
+    uint32_t* ikey_alt;
+    uint32_t* ival_alt;
+    int64_t inst_cap;
+    // scratch for scans and sorts
+    void* temp;
+    size_t temp_bytes;
+};
+
+int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
+                       cudaStream_t s);
+int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
+                       const RasterBuffers& b, cudaStream_t s);
+int launch_emit(const ViewParams& vp, const RasterBuffers& b, const uint32_t* sorted_ids, int64_t n_vis,
+                cudaStream_t s);
+int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
+int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                     float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s);
+int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                     const float* partial_C, const float* partial_T, const float* dL_dimage, cudaStream_t s);
+int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
+                 float* image, float* T_out, cudaStream_t s);
+int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
+                     const float* gI, const float* gT, float* dC, float* dT, cudaStream_t s);
+
+// ------------------------------------------------------------------ KD (kd.cu)
+struct KdBuild {
+    int L;
+    int8_t axis[kMaxNodes];
+    float split[kMaxNodes];
+    int64_t offsets[(1 << kMaxKdDepth) + 1];
+    int32_t* idx_dev;   // cudaMalloc'd, M entries
+    int64_t M;
+};
+int kd_build(const rgs_gaussians& g, int L, float trunc_mult, KdBuild* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ Adam (adam.cu)
+int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t* seg_off, const float* seg_lr,
+                int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s);
+
+}  // namespace rgs

@@ -1,0 +1,287 @@
+// Device-wide exclusive scan and stable LSD radix sort of (uint32 key, uint32 value)
+// pairs.  They carry the tile binning ("tile-binned") and the per-subset depth order
+// ("depth-sorted", Sec. 3.1-3.2) of the render, and the median splits of the KD tree.
+//
+// Scan: reduce-then-scan over 4096-element tiles, recursive on the tile sums.
+// Radix sort: per 8-bit digit an upsweep (per-tile digit histogram), a scan of the
+// digit-major histogram, and a downsweep that ranks keys stably inside the tile with
+// warp-level match/popc, stages the tile in shared memory in digit order and writes runs
+// of equal digits to their global positions.
+#include <cstdio>
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 4096
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096
+
+__device__ __forceinline__ uint32_t load_item(const uint32_t* in, const uint32_t* gather, int64_t i, int mode) {
+    uint32_t v = mode == 2 ? in[gather[i]] : in[i];
+    return mode == 1 ? (v != 0u) : v;
+}
+
+// Sum of one tile (block) of the input.
+__global__ void __launch_bounds__(kScanThreads)
+scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, int mode, const uint32_t* __restrict__ gather,
+                   uint32_t* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        int64_t i = base + (int64_t)j * kScanThreads + threadIdx.x;
+        if (i < n) acc += load_item(in, gather, i, mode);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ uint32_t ws[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of one tile plus the tile's offset.  Items are loaded coalesced into
+// shared memory (padded against bank conflicts), each thread scans 16 consecutive items,
+// and the thread totals are scanned across the block.
+__global__ void __launch_bounds__(kScanThreads)
+scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const uint32_t* __restrict__ gather,
+                 const uint32_t* __restrict__ tile_offsets) {
+    __shared__ uint32_t sm[kScanTile + kScanTile / 32];
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    auto pad = [](int i) { return i + (i >> 5); };
+    for (int j = 0; j < kScanItems; ++j) {
+        int li = j * kScanThreads + threadIdx.x;
+        int64_t i = base + li;
+        sm[pad(li)] = i < n ? load_item(in, gather, i, mode) : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = sm[pad(threadIdx.x * kScanItems + j)];
+        tsum += v[j];
+    }
+    // inclusive warp scan of the thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = tile_offsets ? tile_offsets[blockIdx.x] : 0u;
+    for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+    uint32_t run = wbase + incl - tsum;
+    for (int j = 0; j < kScanItems; ++j) {
+        uint32_t x = v[j];
+        sm[pad(threadIdx.x * kScanItems + j)] = run;
+        run += x;
+    }
+    __syncthreads();
+    for (int j = 0; j < kScanItems; ++j) {
+        int li = j * kScanThreads + threadIdx.x;
+        int64_t i = base + li;
+        if (i < n) out[i] = sm[pad(li)];
+    }
+}
+
+// Per-tile histogram of one 8-bit digit, written digit-major: counts[d * nblocks + b].
+__global__ void __launch_bounds__(kSortThreads)
+radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
+                     uint32_t nblocks) {
+    __shared__ uint32_t hist[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < kSortItems; ++j) {
+        int64_t i = base + (int64_t)j * kSortThreads + threadIdx.x;
+        int d = i < n ? (int)((keys[i] >> shift) & (kRadix - 1)) : kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < kRadix && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
+}
+
+// Stable scatter of one tile by one digit.  Warp w owns tile items [w*512, (w+1)*512) and
+// walks them in 16 rounds of 32 lanes, so (round, lane) order is the input order; a
+// per-warp digit counter plus the rank among equal digits of the round gives each key's
+// rank within its warp, the per-digit scan over warps gives its rank within the tile.
+__global__ void __launch_bounds__(kSortThreads)
+radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                       uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
+                       uint32_t nblocks) {
+    __shared__ uint32_t whist[kSortWarps][kRadix];
+    __shared__ uint32_t dstart[kRadix];
+    __shared__ uint32_t dtot[kRadix];
+    __shared__ uint32_t goff[kRadix];
+    __shared__ uint32_t skeys[kSortTile];
+    __shared__ uint32_t svals[kSortTile];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
+    __syncthreads();
+
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    int dig[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = base + warp * (kSortItems * 32) + r * 32 + lane;
+        bool ok = i < n;
+        key[r] = ok ? kin[i] : 0u;
+        val[r] = ok ? vin[i] : 0u;
+        dig[r] = ok ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+        unsigned lower = peers & ((1u << lane) - 1u);
+        uint32_t prior = dig[r] < kRadix ? whist[warp][dig[r]] : 0u;
+        rank[r] = prior + (uint32_t)__popc(lower);
+        __syncwarp();
+        if (dig[r] < kRadix && lower == 0u) whist[warp][dig[r]] = prior + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t c = whist[w][d];
+            whist[w][d] = run;
+            run += c;
+        }
+        dtot[d] = run;
+        goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    // exclusive scan of the digit totals (kRadix == kSortThreads: one per thread)
+    {
+        uint32_t x = dtot[threadIdx.x];
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __shared__ uint32_t wsum[kSortWarps];
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t b = 0;
+        for (int w = 0; w < warp; ++w) b += wsum[w];
+        dstart[threadIdx.x] = b + incl - x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (dig[r] < kRadix) {
+            uint32_t pos = dstart[dig[r]] + whist[warp][dig[r]] + rank[r];
+            skeys[pos] = key[r];
+            svals[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    int64_t rem = n - base;
+    int count = rem < kSortTile ? (int)rem : kSortTile;
+    for (int i = threadIdx.x; i < count; i += kSortThreads) {
+        uint32_t k = skeys[i];
+        int d = (int)((k >> shift) & (kRadix - 1));
+        uint32_t o = goff[d] + (uint32_t)i - dstart[d];
+        kout[o] = k;
+        vout[o] = svals[i];
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+size_t scan_temp_bytes(int64_t n) {
+    size_t total = 0;
+    int64_t m = cdiv(n, kScanTile);
+    while (m > 1) {
+        total += align256((size_t)m * 4);
+        m = cdiv(m, kScanTile);
+    }
+    return total + 256;
+}
+
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int load, const uint32_t* gather, void* temp,
+                       size_t temp_bytes, cudaStream_t s) {
+    if (n <= 0) return RGS_OK;
+    int64_t nb = cdiv(n, kScanTile);
+    if (nb == 1) {
+        scan_tile_kernel<<<1, kScanThreads, 0, s>>>(in, out, n, load, gather, nullptr);
+        RGS_CUDA_LAUNCH_CHECK();
+        return RGS_OK;
+    }
+    size_t need = align256((size_t)nb * 4);
+    if (need > temp_bytes) {
+        set_error("scan: temporary buffer too small (%zu < %zu)", temp_bytes, need);
+        return RGS_EOVERFLOW;
+    }
+    uint32_t* sums = (uint32_t*)temp;
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, load, gather, sums);
+    RGS_CUDA_LAUNCH_CHECK();
+    int rc = exclusive_scan_u32(sums, sums, nb, 0, nullptr, (char*)temp + need, temp_bytes - need, s);
+    if (rc != RGS_OK) return rc;
+    scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, load, gather, sums);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+size_t radix_temp_bytes(int64_t n) {
+    int64_t nb = cdiv(n > 0 ? n : 1, kSortTile);
+    int64_t nc = nb * kRadix;
+    return align256((size_t)nc * 4) + scan_temp_bytes(nc);
+}
+
+int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int end_bit,
+                     void* temp, size_t temp_bytes, cudaStream_t s, bool* in_alt) {
+    *in_alt = false;
+    if (n <= 1 || end_bit <= 0) return RGS_OK;
+    if (n > 0xFFFFFFFFll) {
+        set_error("radix sort: %lld elements exceed the 32-bit index range", (long long)n);
+        return RGS_EOVERFLOW;
+    }
+    int64_t nb = cdiv(n, kSortTile);
+    int64_t nc = nb * kRadix;
+    size_t cbytes = align256((size_t)nc * 4);
+    if (temp_bytes < cbytes + scan_temp_bytes(nc)) {
+        set_error("radix sort: temporary buffer too small");
+        return RGS_EOVERFLOW;
+    }
+    uint32_t* counts = (uint32_t*)temp;
+    void* stemp = (char*)temp + cbytes;
+    size_t sbytes = temp_bytes - cbytes;
+    uint32_t *ka = keys, *va = vals, *kb = keys_alt, *vb = vals_alt;
+    for (int shift = 0; shift < end_bit; shift += kRadixBits) {
+        radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb);
+        RGS_CUDA_LAUNCH_CHECK();
+        int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
+        if (rc != RGS_OK) return rc;
+        radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, counts, (uint32_t)nb);
+        RGS_CUDA_LAUNCH_CHECK();
+        uint32_t* t;
+        t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+        *in_alt = !*in_alt;
+    }
+    return RGS_OK;
+}
+
+}  // namespace rgs

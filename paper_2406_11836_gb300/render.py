@@ -1,0 +1,138 @@
+"""Differentiable hierarchical render (autograd) and a training step (Sec. 3.4 pipeline).
+
+``RetinaGSRender`` wraps the C ABI: its forward renders every subset's partial colour and
+transmittance and merges them (Eq. 3-5); its backward routes dL/dimage through the merge
+to each subset, replays each subset's blend from the stored partials with the per-tile
+lists re-derived, and pulls the 2D gradients back to means, scales, rotations, opacity and
+SH.  ``Trainer`` runs the full step (render, L1 loss, backward, Adam with the position
+learning-rate decay of Sec. 4) on flat parameter buffers without extra copies.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import rgs
+
+
+class RenderContext:
+    """Non-tensor state of a render: KD partition, camera, options and workspace."""
+
+    def __init__(self, kd: rgs.KD, cam, opts: rgs.RenderOpts | None = None, ws: rgs.Workspace | None = None,
+                 sh_degree: int = 0):
+        self.kd = kd
+        self.cam = cam
+        self.opts = opts if opts is not None else rgs.default_opts()
+        self.ws = ws if ws is not None else rgs.Workspace()
+        self.sh_degree = sh_degree
+        self.last = None
+
+
+class RetinaGSRender(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, rc: RenderContext):
+        g = rgs.gaussians_c(means, log_scales, quats, opacity_logits, sh, rc.sh_degree)
+        out = rgs.render_fwd(rc.kd, g, rc.cam, rc.opts, rc.ws, image=True)
+        ctx.rc = rc
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, out["partial_C"], out["partial_T"])
+        rc.last = out
+        ctx.mark_non_differentiable(out["partial_C"], out["partial_T"], out["T_final"])
+        return out["image"], out["partial_C"], out["partial_T"], out["T_final"]
+
+    @staticmethod
+    def backward(ctx, g_image, g_pc, g_pt, g_tf):
+        means, log_scales, quats, opacity_logits, sh, pc, pt = ctx.saved_tensors
+        rc = ctx.rc
+        grads = tuple(torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh))
+        if g_image is None:
+            return (*grads, None)
+        g = rgs.gaussians_c(means, log_scales, quats, opacity_logits, sh, rc.sh_degree)
+        rgs.render_bwd(rc.kd, g, rc.cam, rc.opts, pc, pt, g_image.contiguous(), grads, rc.ws)
+        return (*grads, None)
+
+
+def render(means, log_scales, quats, opacity_logits, sh, rc: RenderContext):
+    """Differentiable render: returns (image [3,H,W], partial_C, partial_T, T_final)."""
+    return RetinaGSRender.apply(means, log_scales, quats, opacity_logits, sh, rc)
+
+
+# --------------------------------------------------------------------------- training step
+class Trainer:
+    """Parameters, gradients and Adam moments in flat float32 buffers (one Adam launch per
+    step).  Groups, in buffer order: quats, means, log_scales, opacity_logits, sh."""
+
+    # learning rates of the non-position groups: the paper gives only the position schedule
+    # (1.6e-4 -> 1.6e-6); the others are the usual 3DGS values
+    LR = {"quats": 1e-3, "log_scales": 5e-3, "opacity_logits": 5e-2, "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20}
+
+    def __init__(self, scene, depth_L: int, opts: rgs.RenderOpts | None = None, max_steps: int = 60000,
+                 device="cuda"):
+        n = scene.n
+        self.n = n
+        self.sh_degree = scene.sh_degree
+        self.nsh = (scene.sh_degree + 1) ** 2
+        sizes = [("quats", 4 * n), ("means", 3 * n), ("log_scales", 3 * n), ("opacity_logits", n),
+                 ("sh", 3 * self.nsh * n)]
+        offs = np.cumsum([0] + [s for _, s in sizes])
+        total = int(offs[-1])
+        self.flat = torch.empty(total, dtype=torch.float32, device=device)
+        self.grad = torch.zeros(total, dtype=torch.float32, device=device)
+        self.m = torch.zeros(total, dtype=torch.float32, device=device)
+        self.v = torch.zeros(total, dtype=torch.float32, device=device)
+        src = {"quats": scene.quats, "means": scene.means, "log_scales": scene.log_scales,
+               "opacity_logits": scene.opacity_logits, "sh": scene.sh}
+        shapes = {"quats": (n, 4), "means": (n, 3), "log_scales": (n, 3), "opacity_logits": (n,),
+                  "sh": (n, self.nsh, 3)}
+        self.p, self.g = {}, {}
+        for (name, _), a, b in zip(sizes, offs[:-1], offs[1:]):
+            self.p[name] = self.flat[a:b].view(shapes[name])
+            self.g[name] = self.grad[a:b].view(shapes[name])
+            self.p[name].copy_(src[name].reshape(shapes[name]).to(device))
+        # Adam segments: quats, means, log_scales, opacity, sh dc, sh rest
+        sh0 = int(offs[4])
+        self.seg = [0, int(offs[1]), int(offs[2]), int(offs[3]), int(offs[4])]
+        if self.nsh > 1:
+            self.seg += [sh0 + 3 * n, total]
+        else:
+            self.seg += [total]
+        self.max_steps = max_steps
+        self.step_count = 0
+        self.opts = opts if opts is not None else rgs.default_opts()
+        self.ws = rgs.Workspace(device)
+        self.kd = rgs.kd_partition(self.gaussians(), depth_L, float(self.opts.trunc_mult))
+
+    def gaussians(self):
+        p = self.p
+        return rgs.gaussians_c(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], self.sh_degree)
+
+    def grads(self):
+        g = self.g
+        return (g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"])
+
+    def lrs(self, step):
+        lrs = [self.LR["quats"], rgs.position_lr(step, self.max_steps), self.LR["log_scales"],
+               self.LR["opacity_logits"], self.LR["sh_dc"]]
+        if self.nsh > 1:
+            lrs.append(self.LR["sh_rest"])
+        return lrs
+
+    def repartition(self, depth_L: int | None = None):
+        """Re-run the KD partition on the current centres (Sec. 3.4: repeated after a set
+        number of epochs)."""
+        self.kd = rgs.kd_partition(self.gaussians(), depth_L if depth_L is not None else self.kd.L,
+                                   float(self.opts.trunc_mult))
+
+    def step(self, cam, target: torch.Tensor, return_loss: bool = True):
+        """One training step: forward, L1 loss against `target` [3,H,W], backward, Adam.
+        Returns the loss as a 0-d tensor (left on the device)."""
+        g = self.gaussians()
+        out = rgs.render_fwd(self.kd, g, cam, self.opts, self.ws, image=True)
+        img = out["image"]
+        diff = img - target
+        loss = diff.abs().mean() if return_loss else None
+        dL = torch.sign(diff).div_(float(diff.numel()))
+        rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws)
+        self.step_count += 1
+        rgs.adam_step(self.flat, self.grad, self.m, self.v, self.seg, self.lrs(self.step_count), self.step_count,
+                      zero_grad=True)
+        return loss

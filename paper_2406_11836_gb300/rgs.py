@@ -1,0 +1,317 @@
+"""Thin Python binding of the C ABI in ``include/rgs.h`` (ctypes; argument marshalling only).
+
+Every step of the render runs in the CUDA library ``_build/librgs.so``; PyTorch only
+provides device memory and streams.  There is no CPU fallback: if the library is not
+built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_float, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librgs.so")
+
+RGS_OK, RGS_EINVAL, RGS_ENOMEM, RGS_ECUDA, RGS_EOVERFLOW, RGS_ETIMEOUT, RGS_EAGAIN = 0, -1, -2, -3, -4, -5, -6
+
+
+class RGSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rgs error {code}: {msg}")
+        self.code = code
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
+                ("sh", c_void_p), ("n", c_int64), ("sh_degree", c_int)]
+
+
+class GaussianGrads(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("opacity_logits", c_void_p),
+                ("sh", c_void_p)]
+
+
+class CameraC(ctypes.Structure):
+    _fields_ = [("viewmat", c_float * 16), ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float),
+                ("width", c_int), ("height", c_int), ("near_z", c_float)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("tile", c_int), ("trunc_mult", c_float), ("eps_T", c_float), ("alpha_min", c_float),
+                ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_2406_11836_gb300.build.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    L.rgs_last_error.restype = ctypes.c_char_p
+    L.rgs_last_required_workspace.restype = c_size_t
+    L.rgs_position_lr.restype = c_float
+    L.rgs_position_lr.argtypes = [c_int64, c_int64, c_float, c_float]
+    L.rgs_kd_partition.argtypes = [POINTER(Gaussians), c_int, c_float, POINTER(c_void_p), c_void_p]
+    L.rgs_kd_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int64)]
+    L.rgs_kd_splits.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.rgs_kd_subsets.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.rgs_kd_destroy.argtypes = [c_void_p]
+    L.rgs_view_order.argtypes = [c_void_p, POINTER(CameraC), c_void_p]
+    L.rgs_render_workspace_size.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts),
+                                            c_int64, POINTER(c_size_t)]
+    L.rgs_render_fwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.rgs_render_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
+                                 c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
+    L.rgs_merge_partials.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]
+    L.rgs_merge_partials_bwd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p]
+    L.rgs_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int, c_float,
+                                c_float, c_float, c_int, c_int, c_void_p]
+    L.rgs_default_opts.argtypes = [POINTER(RenderOpts)]
+    L.rgs_profile_enable.argtypes = [c_int]
+    L.rgs_profile_stage_name.restype = ctypes.c_char_p
+    L.rgs_profile_stage_name.argtypes = [c_int]
+    L.rgs_profile_read.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != RGS_OK:
+        raise RGSError(rc, lib().rgs_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t is not None else c_void_p(0)
+
+
+# --------------------------------------------------------------------------- conversions
+def default_opts(**kw) -> RenderOpts:
+    o = RenderOpts()
+    lib().rgs_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            for i in range(3):
+                o.bg[i] = float(v[i])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def camera_c(cam) -> CameraC:
+    c = CameraC()
+    vm = np.asarray(cam.viewmat, np.float32).reshape(16)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(cam.near_z)
+    return c
+
+
+def gaussians_c(means, log_scales, quats, opacity_logits, sh, sh_degree) -> Gaussians:
+    for t in (means, log_scales, quats, opacity_logits, sh):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("splat parameters must be contiguous float32 CUDA tensors")
+    return Gaussians(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
+                     int(means.shape[0]), int(sh_degree))
+
+
+def scene_c(scene) -> Gaussians:
+    return gaussians_c(scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh, scene.sh_degree)
+
+
+# --------------------------------------------------------------------------- KD partition
+class KD:
+    """Owner of an ``rgs_kd`` handle (KD tree, leaf boxes and CSR subset lists)."""
+
+    def __init__(self, handle: c_void_p):
+        self.handle = handle
+        L, K, M = c_int(), c_int(), c_int64()
+        _check(lib().rgs_kd_info(handle, ctypes.byref(L), ctypes.byref(K), ctypes.byref(M)))
+        self.L, self.K, self.M = L.value, K.value, M.value
+
+    def splits(self):
+        n = max(self.K - 1, 1)
+        axis = np.zeros(n, np.int32)
+        split = np.zeros(n, np.float32)
+        _check(lib().rgs_kd_splits(self.handle, c_void_p(axis.ctypes.data), c_void_p(split.ctypes.data)))
+        return axis[:self.K - 1], split[:self.K - 1]
+
+    def subsets(self, device="cuda"):
+        offsets = np.zeros(self.K + 1, np.int64)
+        idx = torch.empty(max(self.M, 1), dtype=torch.int32, device=device)
+        torch.cuda.synchronize()
+        _check(lib().rgs_kd_subsets(self.handle, c_void_p(offsets.ctypes.data), _ptr(idx)))
+        return offsets, idx[:self.M]
+
+    def view_order(self, cam) -> np.ndarray:
+        order = np.zeros(self.K, np.int32)
+        c = camera_c(cam)
+        _check(lib().rgs_view_order(self.handle, ctypes.byref(c), c_void_p(order.ctypes.data)))
+        return order
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().rgs_kd_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def kd_partition(scene, depth_L: int, trunc_mult: float = 3.0, stream=None) -> KD:
+    g = scene if isinstance(scene, Gaussians) else scene_c(scene)
+    h = c_void_p()
+    _check(lib().rgs_kd_partition(ctypes.byref(g), int(depth_L), float(trunc_mult), ctypes.byref(h), _stream(stream)))
+    return KD(h)
+
+
+# --------------------------------------------------------------------------- render
+class Workspace:
+    """Caller-owned render workspace (a CUDA byte tensor) that grows on demand."""
+
+    def __init__(self, device="cuda", nbytes: int = 0):
+        self.device = device
+        self.buf = None
+        if nbytes:
+            self.ensure(nbytes)
+
+    def ensure(self, nbytes: int):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = None
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    @property
+    def nbytes(self):
+        return 0 if self.buf is None else self.buf.numel()
+
+    def ptr(self):
+        return c_void_p(0) if self.buf is None else c_void_p(self.buf.data_ptr())
+
+
+def _retry(call, ws: Workspace):
+    for _ in range(4):
+        rc = call()
+        if rc == RGS_EOVERFLOW:
+            need = lib().rgs_last_required_workspace()
+            if need and need > ws.nbytes:
+                ws.ensure(int(need * 1.15) + (1 << 20))
+                continue
+        _check(rc)
+        return
+    _check(rc)
+
+
+def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image=True, stream=None, out=None):
+    """Partial maps [K,3,H,W] / [K,H,W] and, if image, the merged image [3,H,W] and T_final."""
+    H, W = int(cam.height), int(cam.width)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = {"partial_C": torch.empty(kd.K, 3, H, W, device=dev), "partial_T": torch.empty(kd.K, H, W, device=dev)}
+        if image:
+            out["image"] = torch.empty(3, H, W, device=dev)
+            out["T_final"] = torch.empty(H, W, device=dev)
+    c = camera_c(cam)
+    s = _stream(stream)
+    _retry(lambda: lib().rgs_render_fwd(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
+                                        _ptr(out["partial_C"]), _ptr(out["partial_T"]), _ptr(out.get("image")),
+                                        _ptr(out.get("T_final")), ws.ptr(), ws.nbytes, s), ws)
+    return out
+
+
+def render_bwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, partial_C, partial_T, dL_dimage, grads, ws: Workspace,
+               stream=None):
+    """Accumulate dL/d(params) into grads = (means, log_scales, quats, opacity_logits, sh) tensors."""
+    gg = GaussianGrads(*(_ptr(t) for t in grads))
+    c = camera_c(cam)
+    s = _stream(stream)
+    dL = dL_dimage.contiguous()
+    _retry(lambda: lib().rgs_render_bwd(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
+                                        _ptr(partial_C), _ptr(partial_T), _ptr(dL), ctypes.byref(gg), ws.ptr(),
+                                        ws.nbytes, s), ws)
+
+
+def merge_partials(partial_C, partial_T, order, bg=(0.0, 0.0, 0.0), stream=None):
+    K, _, H, W = partial_C.shape
+    order_d = torch.as_tensor(np.asarray(order, np.int32), device=partial_C.device)
+    image = torch.empty(3, H, W, device=partial_C.device)
+    T = torch.empty(H, W, device=partial_C.device)
+    bgv = (c_float * 3)(*bg)
+    _check(lib().rgs_merge_partials(_ptr(partial_C), _ptr(partial_T), _ptr(order_d), K, H, W, ctypes.cast(bgv, c_void_p),
+                                    _ptr(image), _ptr(T), _stream(stream)))
+    torch.cuda.current_stream().synchronize()
+    return image, T
+
+
+def merge_partials_bwd(partial_C, partial_T, order, dL_dimage, dL_dT=None, bg=(0.0, 0.0, 0.0), stream=None):
+    K, _, H, W = partial_C.shape
+    order_d = torch.as_tensor(np.asarray(order, np.int32), device=partial_C.device)
+    dC = torch.empty_like(partial_C)
+    dT = torch.empty_like(partial_T)
+    bgv = (c_float * 3)(*bg)
+    _check(lib().rgs_merge_partials_bwd(_ptr(partial_C), _ptr(partial_T), _ptr(order_d), K, H, W,
+                                        ctypes.cast(bgv, c_void_p), _ptr(dL_dimage.contiguous()),
+                                        _ptr(dL_dT.contiguous() if dL_dT is not None else None), _ptr(dC), _ptr(dT),
+                                        _stream(stream)))
+    torch.cuda.current_stream().synchronize()
+    return dC, dT
+
+
+def adam_step(param, grad, m, v, seg_offsets, seg_lr, step, beta1=0.9, beta2=0.999, eps=1e-15, zero_grad=True,
+              stream=None):
+    offs = np.asarray(seg_offsets, np.int64)
+    lrs = np.asarray(seg_lr, np.float32)
+    _check(lib().rgs_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()),
+                               c_void_p(offs.ctypes.data), c_void_p(lrs.ctypes.data), len(lrs), float(beta1),
+                               float(beta2), float(eps), int(step), 1 if zero_grad else 0, _stream(stream)))
+
+
+def position_lr(step, max_steps, lr_init=1.6e-4, lr_final=1.6e-6) -> float:
+    return float(lib().rgs_position_lr(int(step), int(max_steps), float(lr_init), float(lr_final)))
+
+
+# --------------------------------------------------------------------------- tracing
+def profile_enable(on: bool = True):
+    _check(lib().rgs_profile_enable(1 if on else 0))
+
+
+PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible")
+
+
+def profile_read(reset: bool = True) -> dict:
+    """Per-stage milliseconds and pass counts since the last reset, plus the pair/instance
+    counters: {"stages": {name: (ms, launches)}, "counters": {...}}."""
+    L = lib()
+    n = L.rgs_profile_num_stages()
+    ms = np.zeros(n, np.float64)
+    launches = np.zeros(n, np.int64)
+    counters = np.zeros(6, np.int64)
+    _check(L.rgs_profile_read(c_void_p(ms.ctypes.data), c_void_p(launches.ctypes.data),
+                              c_void_p(counters.ctypes.data), 1 if reset else 0))
+    stages = {L.rgs_profile_stage_name(i).decode(): (float(ms[i]), int(launches[i])) for i in range(n)}
+    return {"stages": stages, "counters": dict(zip(PAIR_COUNTERS, (int(c) for c in counters)))}
+
+
+ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
+               "rgs_kd_info", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
+               "rgs_render_workspace_size", "rgs_render_fwd", "rgs_merge_partials", "rgs_merge_partials_bwd",
+               "rgs_render_bwd", "rgs_adam_step", "rgs_position_lr", "rgs_profile_enable",
+               "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read")

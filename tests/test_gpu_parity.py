@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Forward images and partial maps are compared element by element (max abs error 1e-4
+over pixels the oracle does not flag as ambiguous); gradients per parameter tensor by
+relative L2 error (1e-3).  KD splits and subset lists are index work and must match
+exactly (subset memberships within rounding of a plane are allowed either way).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from _helpers import (FWD_FLAGS, GRAD_FLAGS, GRAD_RTOL, MAX_FLAGGED, PART_FLAGS, PIXEL_TOL, image_at, oracle_opts,
+                      partials_at, rel_l2)
+from oracle import oracle as O
+from paper_2406_11836_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_11836_gb300 import build as B
+    B.build()
+    from paper_2406_11836_gb300 import rgs
+    return rgs
+
+
+def _dev_scene(scene):
+    return scene.to("cuda")
+
+
+# --------------------------------------------------------------------------- KD partition
+@pytest.mark.parametrize("n,L", [(4096, 1), (10_000, 3), (10_000, 4), (50_000, 6), (777, 8)])
+def test_kd_partition_matches_oracle(R, n, L):
+    scene = W.uniform_cube_scene(n, seed=n + L, log_scale_mean=-3.0) if n != 4096 else W.tiny().scene
+    kd = R.kd_partition(_dev_scene(scene), L)
+    axis, split = kd.splits()
+    o_axis, o_split = O.kd_partition(scene.means, L)
+    np.testing.assert_array_equal(axis, o_axis)
+    np.testing.assert_array_equal(split.view(np.uint32), o_split.view(np.uint32))
+    offs, idx = kd.subsets()
+    idx = idx.cpu().numpy()
+    o_offs, o_idx, amb = O.subsets(scene.means, scene.log_scales, L, o_axis, o_split)
+    for k in range(1 << L):
+        a = set(idx[offs[k]:offs[k + 1]].tolist())
+        b = set(o_idx[o_offs[k]:o_offs[k + 1]].tolist())
+        diff = a ^ b
+        assert all(amb[i] for i in diff), (k, sorted(diff)[:10])
+        got = idx[offs[k]:offs[k + 1]]
+        assert np.all(np.diff(got) > 0)          # ascending splat index within a subset
+
+
+def test_view_order_lists_crossed_leaves_in_ray_order(R):
+    wl = W.tiny()
+    scene = _dev_scene(wl.scene)
+    kd = R.kd_partition(scene, 4)
+    axis, split = kd.splits()
+    r = np.random.default_rng(0)
+    for _ in range(8):
+        eye = r.uniform(-1.5, 1.5, 3) if r.random() < 0.5 else r.normal(size=3) * 4
+        cam = W.look_at(eye, r.uniform(-0.5, 0.5, 3), 64, 48)
+        order = kd.view_order(cam).tolist()
+        assert sorted(order) == list(range(16))
+        o = O.camera_center(cam)
+        for px, py in r.integers(0, 48, (20, 2)):
+            d = O.pixel_ray(cam, px, py)
+            oo, nc = O.ray_order(4, axis, split, o, d)
+            pos = [order.index(k) for k in oo[:nc]]
+            assert pos == sorted(pos)
+
+
+# --------------------------------------------------------------------------- forward
+def _render(R, scene, cam, L, opts=None, kd=None):
+    dev = _dev_scene(scene)
+    kd = kd if kd is not None else R.kd_partition(dev, L)
+    opts = opts if opts is not None else R.default_opts()
+    ws = R.Workspace()
+    out = R.render_fwd(kd, R.scene_c(dev), cam, opts, ws)
+    torch.cuda.synchronize()
+    return kd, out
+
+
+def _check_forward(R, scene, cam, L, pix=None, opts=None):
+    kd, out = _render(R, scene, cam, L, opts)
+    oo = oracle_opts(opts)
+    pix = np.arange(cam.width * cam.height) if pix is None else pix
+    flat = O.render(scene, cam, oo, pix=pix)
+    ok = (flat["flags"] & FWD_FLAGS) == 0
+    assert ok.mean() >= 1 - MAX_FLAGGED, ok.mean()
+    got = image_at(out["image"], pix)
+    err = np.abs(got - flat["C"])[ok].max()
+    assert err <= PIXEL_TOL, err
+    terr = np.abs(out["T_final"].reshape(-1).double().cpu().numpy()[pix] - flat["T"])[ok].max()
+    assert terr <= PIXEL_TOL, terr
+    # partial maps against the literal Eq. 3-4 of the oracle with the same termination
+    axis, split = kd.splits()
+    hier = O.render(scene, cam, oracle_opts(opts, eps_T=float(np.float32(1e-6))), pix=pix, hier=True, L=L, axis=axis,
+                    split=split)
+    okp = (hier["flags"] & PART_FLAGS) == 0
+    pc, pt = partials_at(out["partial_C"], out["partial_T"], pix)
+    perr = max(np.abs(pc - hier["partC"])[okp].max(), np.abs(pt - hier["partT"])[okp].max())
+    assert perr <= PIXEL_TOL, perr
+    return kd, out, flat
+
+
+def test_forward_tiny_full_image(R):
+    """4,096 splats, 128x128, K = 2: every pixel, image and partial maps."""
+    wl = W.tiny()
+    _, out, flat = _check_forward(R, wl.scene, wl.cameras[0], wl.depth_L)
+    assert (flat["ncontrib"] > 0).mean() > 0.3
+
+
+@pytest.mark.parametrize("L", [0, 2, 3, 6])
+def test_forward_partition_depths_and_ragged_image(R, L):
+    """Several tiles with a ragged edge (100x70), partitions from 1 to 64 subsets, SH degree 3,
+    a camera inside the scene so that rays cross many subspaces."""
+    scene = W.uniform_cube_scene(3000, seed=7 + L, log_scale_mean=-3.2, sh_degree=3)
+    cam = W.look_at((0.15, -0.2, 0.1), (0.3, 1.0, -0.2), 100, 70)
+    _check_forward(R, scene, cam, L)
+
+
+def test_forward_straddling_splats_and_validity_plane(R):
+    """Optical axis on the first split plane (Sec. 4 validity test): every pixel's far-side
+    partial is exactly (0, 1)."""
+    scene = W.uniform_cube_scene(2000, seed=3, log_scale_mean=-2.6)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 1)
+    axis, split = kd.splits()
+    assert axis[0] == 0
+    cam = W.axis_camera((float(split[0]), 0.05, -3.0), 64, 48)
+    opts = R.default_opts()
+    out = R.render_fwd(kd, R.scene_c(dev), cam, opts, R.Workspace())
+    torch.cuda.synchronize()
+    pc = out["partial_C"].cpu().numpy()
+    pt = out["partial_T"].cpu().numpy()
+    assert np.all(pc[1, :, :, :32] == 0) and np.all(pt[1, :, :32] == 1)
+    assert np.all(pc[0, :, :, 32:] == 0) and np.all(pt[0, :, 32:] == 1)
+    assert (pt[0, :, :32] < 1).sum() > 50 and (pt[1, :, 32:] < 1).sum() > 50
+    _check_forward(R, scene, cam, 1)
+
+
+def test_forward_edge_cases(R):
+    opts = R.default_opts(bg=(0.25, 0.5, 0.75))
+    # every splat behind the camera: background only, partials (0, 1)
+    scene = W.uniform_cube_scene(100, seed=1)
+    cam = W.axis_camera((0.0, 0.0, 5.0), 33, 17)
+    kd, out = _render(R, scene, cam, 2, opts)
+    img = out["image"].cpu().numpy()
+    for c, v in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(img[c] == np.float32(v))
+    assert np.all(out["partial_C"].cpu().numpy() == 0) and np.all(out["partial_T"].cpu().numpy() == 1)
+    # a single splat, 1x1 image
+    one = W.uniform_cube_scene(1, seed=2, log_scale_mean=-1.0)
+    cam1 = W.axis_camera((0.0, 0.0, -3.0), 1, 1)
+    _check_forward(R, one, cam1, 0, opts=opts)
+    # image smaller than one tile with the splats straddling every subset
+    _check_forward(R, W.uniform_cube_scene(500, seed=5, log_scale_mean=-2.0), W.axis_camera((0.1, 0.0, -2.5), 7, 5), 3)
+
+
+def test_forward_deterministic(R):
+    wl = W.tiny()
+    _, a = _render(R, wl.scene, wl.cameras[0], 2)
+    _, b = _render(R, wl.scene, wl.cameras[0], 2)
+    assert torch.equal(a["image"], b["image"]) and torch.equal(a["partial_T"], b["partial_T"])
+
+
+# --------------------------------------------------------------------------- merge (Eq. 5)
+def test_merge_partials_and_adjoint(R):
+    r = np.random.default_rng(0)
+    K, H, W_ = 6, 19, 23
+    T = r.uniform(0.05, 1.0, (K, H, W_)).astype(np.float32)
+    C = (r.uniform(0, 1, (K, 3, H, W_)) * (1 - T)[:, None]).astype(np.float32)
+    order = np.array([3, 1, 5, 0, 2, 4], np.int32)
+    bg = (0.1, 0.2, 0.3)
+    img, Tf = R.merge_partials(torch.tensor(C, device="cuda"), torch.tensor(T, device="cuda"), order, bg)
+    oC, oT = O.merge(C.reshape(K, 3, -1), T.reshape(K, -1), order, bg)
+    np.testing.assert_allclose(img.cpu().numpy().reshape(3, -1), oC, atol=1e-6)
+    np.testing.assert_allclose(Tf.cpu().numpy().reshape(-1), oT, atol=1e-6)
+    g = r.uniform(-1, 1, (3, H, W_)).astype(np.float32)
+    gT = r.uniform(-1, 1, (H, W_)).astype(np.float32)
+    dC, dT = R.merge_partials_bwd(torch.tensor(C, device="cuda"), torch.tensor(T, device="cuda"), order,
+                                  torch.tensor(g, device="cuda"), torch.tensor(gT, device="cuda"), bg)
+    odC, odT = O.merge_backward(C.reshape(K, 3, -1), T.reshape(K, -1), order, g.reshape(3, -1), gT.reshape(-1), bg)
+    np.testing.assert_allclose(dC.cpu().numpy().reshape(K, 3, -1), odC, atol=1e-5)
+    np.testing.assert_allclose(dT.cpu().numpy().reshape(K, -1), odT, atol=1e-5)
+
+
+# --------------------------------------------------------------------------- backward
+def _grad_parity(R, scene, cam, L, pix_loss=None, seed=1, use_autograd=True, rtol=GRAD_RTOL):
+    """L1 loss against a random target; dL/dC is formed from the GPU image and zeroed on
+    pixels the oracle flags, and both sides get the same dL/dC."""
+    from paper_2406_11836_gb300.render import RenderContext, render
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, L)
+    H, Wd = cam.height, cam.width
+    params = [t.clone().requires_grad_(True) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh)]
+    rc = RenderContext(kd, cam, sh_degree=scene.sh_degree)
+    img = render(*params, rc)[0]
+    pix = np.arange(H * Wd) if pix_loss is None else np.asarray(pix_loss)
+    flat = O.render(scene, cam, oracle_opts(), pix=pix)
+    ok = (flat["flags"] & GRAD_FLAGS) == 0
+    target = W.target_image(Wd, H, seed=seed, device="cuda")
+    mask = torch.zeros(H * Wd, device="cuda")
+    mask[torch.as_tensor(pix[ok], device="cuda")] = 1.0
+    mask = mask.view(1, H, Wd)
+    loss = ((img - target).abs() * mask).sum() / float(len(pix))
+    loss.backward()
+    g_img = (torch.sign(img.detach() - target) * mask / float(len(pix))).reshape(3, -1)
+    dLdC = g_img[:, torch.as_tensor(pix, device="cuda")].T.double().cpu().numpy()
+    adj = O.adjoint(scene, cam, dLdC, oracle_opts(), pix=pix)
+    names = ["means", "log_scales", "quats", "opacity_logits", "sh"]
+    errs = {n: rel_l2(p.grad.double().cpu().numpy(), adj[n]) for n, p in zip(names, params)}
+    for n in names:
+        assert np.abs(adj[n]).max() > 0, n
+        assert errs[n] <= rtol, errs
+    return errs
+
+
+def test_backward_tiny_matches_oracle_adjoint(R):
+    wl = W.tiny()
+    _grad_parity(R, wl.scene, wl.cameras[0], wl.depth_L)
+
+
+@pytest.mark.parametrize("L", [0, 3])
+def test_backward_sh3_inside_camera(R, L):
+    scene = W.uniform_cube_scene(1500, seed=11 + L, log_scale_mean=-3.0, sh_degree=3)
+    cam = W.look_at((0.1, -0.15, 0.05), (0.2, 1.0, 0.1), 64, 40)
+    _grad_parity(R, scene, cam, L)
+
+
+def test_backward_directional_fd_of_definition(R):
+    """<grad_gpu, v> against a central difference of the FP64 forward along a random
+    direction v of all parameters (smooth loss <w, C>).  Directions whose +-h step changes
+    the set of contributing (pixel, splat) pairs (a jump, not a derivative) are skipped."""
+    scene = W.uniform_cube_scene(120, seed=21, log_scale_mean=-2.4, sh_degree=2)
+    cam = W.look_at((0.3, -2.8, 0.5), (0, 0, 0), 40, 32)
+    from paper_2406_11836_gb300.render import RenderContext, render
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 2)
+    params = [t.clone().requires_grad_(True) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh)]
+    img = render(*params, RenderContext(kd, cam, sh_degree=2))[0]
+    w = np.random.default_rng(3).uniform(-1, 1, (3, cam.height, cam.width))
+    (img * torch.tensor(w, device="cuda", dtype=torch.float32)).sum().backward()
+    grads = [p.grad.double().cpu().numpy() for p in params]
+    base = [t.detach().double().cpu().numpy() for t in params]
+
+    class S:
+        pass
+
+    def scene_at(eps, vs):
+        s = S()
+        s.means, s.log_scales, s.quats, s.opacity_logits, s.sh = (b + eps * v for b, v in zip(base, vs))
+        s.sh_degree = 2
+        return s
+
+    sig0 = O.pair_signature(scene_at(0.0, [np.zeros_like(b) for b in base]), cam)
+    h = 1e-7
+    checked = 0
+    for seed in range(12):
+        r = np.random.default_rng(100 + seed)
+        vs = [r.normal(size=b.shape) for b in base]
+        if O.pair_signature(scene_at(h, vs), cam) != sig0 or O.pair_signature(scene_at(-h, vs), cam) != sig0:
+            continue
+        loss = [float((O.render(scene_at(e, vs), cam)["C"].T.reshape(3, cam.height, cam.width) * w).sum())
+                for e in (h, -h)]
+        fd = (loss[0] - loss[1]) / (2 * h)
+        dot = sum(float((g * v).sum()) for g, v in zip(grads, vs))
+        assert abs(fd - dot) <= 2e-3 * abs(fd) + 1e-4, (seed, fd, dot)
+        checked += 1
+    assert checked >= 3
+
+
+# --------------------------------------------------------------------------- adam
+def test_adam_step_matches_oracle(R):
+    r = np.random.default_rng(0)
+    n = 1003
+    p = r.normal(size=n).astype(np.float32)
+    segs = [0, 100, 555, n]
+    lrs = [1e-3, 1.6e-4, 5e-2]
+    pd = torch.tensor(p, device="cuda")
+    md = torch.zeros(n, device="cuda")
+    vd = torch.zeros(n, device="cuda")
+    po, mo, vo = p.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in (1, 2, 3):
+        g = r.normal(size=n).astype(np.float32)
+        gd = torch.tensor(g, device="cuda")
+        R.adam_step(pd, gd, md, vd, segs, lrs, step, eps=1e-15, zero_grad=True)
+        lr_el = np.concatenate([np.full(b - a, l) for a, b, l in zip(segs[:-1], segs[1:], lrs)])
+        po, mo, vo = O.adam_step(po, g, mo, vo, step, lr=lr_el)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(gd) == 0
+        np.testing.assert_allclose(pd.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+    assert abs(R.position_lr(30000, 60000) - 1.6e-5) < 1e-10
