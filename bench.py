@@ -1,0 +1,374 @@
+"""Benchmark: one training step of hierarchical 3D Gaussian splatting on the 10M-splat
+city workload at 3840x2160 with 16 KD subsets (forward, L1 loss, backward, Adam).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload city|object|tiny]
+
+Prints one JSON line.  `value` is Mpix/s over all ranks (pixels rendered and
+back-propagated per second of device time, inputs resident in HBM); `e2e` is the same
+metric through the public training-step API with each step's target image copied from
+pinned host memory and the loss read back.  `--impl reference` times the FP64 CPU
+oracle on this host's cores on a bounded pixel sample of the same workload and
+extrapolates to the full frame.  With N > 1 (torchrun) every rank trains its own replica
+on its own cameras (the path does not shard on one GPU: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+Adam Mpix/s, 10M Gaussians, 3840x2160, 16 KD subsets"
+UNIT = "Mpix/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workloads
+def make_workload(name, device):
+    from paper_2406_11836_gb300 import workloads as W
+    if name == "city":
+        return W.city_10m(device=device)
+    if name == "object":
+        return W.object_1m(device=device)
+    return W.tiny(device=device)
+
+
+# --------------------------------------------------------------------------- CPU oracle timing
+def oracle_step_estimate(wl, budget_s=20.0, cam_index=0, threads=None):
+    """Time the FP64 oracle on a bounded sample of one training step and extrapolate to
+    the full frame: forward (Eq. 2) and adjoint over S sampled pixels with every splat
+    projected, at two sample sizes to separate the per-pixel cost from the fixed cost;
+    Adam (numpy float64) on 1% of the parameters, scaled."""
+    from oracle import oracle as O
+    from paper_2406_11836_gb300 import workloads as W
+    cam = wl.cameras[cam_index]
+    HW = cam.width * cam.height
+    host = wl.scene.to("cpu")
+
+    def run(S):
+        pix = W.sample_pixels(cam.width, cam.height, S, seed=123)
+        t0 = time.perf_counter()
+        out = O.render(host, cam, pix=pix)
+        g = np.sign(out["C"] - 0.5) / (3.0 * HW)
+        O.adjoint(host, cam, g, pix=pix)
+        return time.perf_counter() - t0
+
+    S1 = 64
+    t_start = time.perf_counter()
+    t1 = run(S1)
+    # grow the second sample until its extra pixels cost at least half the fixed part
+    # (so the per-pixel slope is measured, not noise), within the time budget
+    S2, t2 = min(8 * S1, HW), None
+    while True:
+        t2 = run(S2)
+        spent = time.perf_counter() - t_start
+        if t2 - t1 >= 0.5 * t1 or S2 >= min(16384, HW) or spent + 2.2 * t2 > budget_s:
+            break
+        S2 = min(4 * S2, HW)
+    c = max((t2 - t1) / (S2 - S1), 1e-9)
+    fixed = max(t1 - c * S1, 0.0)
+    n_par = sum(int(t.numel()) for t in host.tensors())
+    m = max(n_par // 100, 1)
+    r = np.random.default_rng(0)
+    p, gr = r.normal(size=m), r.normal(size=m)
+    t0 = time.perf_counter()
+    O.adam_step(p, gr, np.zeros(m), np.zeros(m), 1, 1e-3)
+    t_adam = (time.perf_counter() - t0) * (n_par / m)
+    step_s = fixed + c * HW + t_adam
+    cores = threads or int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{host.n} splats projected twice (forward, adjoint); blend+adjoint on {S1} and {S2} sampled "
+              f"pixels, per-pixel cost extrapolated linearly to {cam.width}x{cam.height}; Adam on {m} of {n_par} "
+              f"parameters, scaled; {t1 + t2:.1f} s of CPU work")
+    return {"value": HW / step_s / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "step_s_extrapolated": step_s}
+
+
+# --------------------------------------------------------------------------- roofline of the dominant kernel
+# Algorithmic FP32 operations per (pixel, splat) pair of the blend kernels (an FMA counts 2):
+#   every evaluated pair: offset (2), Cholesky-factored Mahalanobis distance (7), ball test (5)      = 14
+#   forward, contributing pair: exponent scale, alpha*G, weight, colour FMAs (6), transmittance FMA (2) = 11
+#   backward, contributing pair: the forward's 11 plus the adjoint (colour dot 5, prefix 2, dsigma 5,
+#   colour grads 3, alpha 1, d2 grad 2, conic grads 7, mean grads 7) minus the colour FMAs     = ~40
+FLOPS_EVAL = 14
+FLOPS_FWD_CONTRIB = 11
+FLOPS_BWD_CONTRIB = 40
+
+
+def roofline(prof, peaks, peak_src, source, traffic_table):
+    stages = prof["stages"]
+    cnt = prof["counters"]
+    cand = {k: v for k, v in stages.items() if v[1] > 0}
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, launches = cand[dom]
+    avg_s = ms / 1e3 / launches
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12     # TFLOP/s
+    if dom in ("blend_fwd", "blend_bwd"):
+        if dom == "blend_fwd":
+            flops = FLOPS_EVAL * cnt["fwd_pairs"] + FLOPS_FWD_CONTRIB * cnt["fwd_contrib"]
+        else:
+            flops = FLOPS_EVAL * cnt["bwd_pairs"] + FLOPS_BWD_CONTRIB * cnt["bwd_contrib"]
+        achieved = flops / launches / avg_s / 1e12
+        out = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+               "frac": achieved / fp32_peak,
+               "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz (derived)"}
+    else:
+        # bandwidth-bound passes: algorithmic bytes per launch
+        I = cnt["instances"] / max(launches, 1)
+        Nv = cnt["visible"] / max(launches, 1)
+        per = {"instance_sort": 60 * I, "depth_sort": 80 * Nv, "emit": 8 * I, "ranges": 4 * I}
+        byts = per.get(dom, 0.0)
+        achieved = byts / avg_s / 1e9
+        out = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": achieved / peaks["hbm_gbs"]}
+    t = traffic_table.get(dom)
+    out["traffic"] = t["dram_bytes_per_launch"] if t and t.get("source_sha") == source.get(t.get("source")) else None
+    out["avg_launch_ms"] = avg_s * 1e3
+    out["launches"] = launches
+    out["peak_kind"] = "of " + peak_src
+    return out
+
+
+def _source_hashes():
+    out = {}
+    for f in ("raster.cu", "sort.cu", "project.cu"):
+        p = os.path.join(ROOT, "paper_2406_11836_gb300", "csrc", f)
+        out[f] = hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    return out
+
+
+def _traffic_table():
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------- arms
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2406_11836_gb300 import build as B
+    B.build()
+    from paper_2406_11836_gb300 import rgs
+    from paper_2406_11836_gb300 import workloads as W
+    from paper_2406_11836_gb300.render import Trainer
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = make_workload(args.workload, dev)
+    cams = wl.cameras[rank::world] or wl.cameras
+    H, Wd = cams[0].height, cams[0].width
+    trainer = Trainer(wl.scene, wl.depth_L, device=dev)
+    del wl.scene
+    targets = [W.target_image(c.width, c.height, seed=1000 + i, device=dev) for i, c in enumerate(cams)]
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        return trainer.step(cams[i % len(cams)], targets[i % len(cams)], return_loss=False)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    peaks, peak_src = _peaks()
+
+    # ---- device-timed region (inputs resident in HBM)
+    rgs.profile_enable(True)
+    rgs.profile_read(reset=True)
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = rgs.profile_read(reset=True)
+    rgs.profile_enable(False)
+    launches_timed = prof["counters"]["kernel_launches"]
+
+    # ---- end to end through the public step API with host inputs
+    pinned = [t.cpu().pin_memory() for t in targets]
+    dev_target = torch.empty_like(targets[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = (args.warmup + i) % len(cams)
+        dev_target.copy_(pinned[j], non_blocking=True)
+        loss = trainer.step(cams[j], dev_target, return_loss=True)
+        float(loss.item())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    t = torch.tensor([ms, e2e_s * 1e3], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    pix_per_step = H * Wd
+    value = world * args.steps * pix_per_step / (ms_max / 1e3) / 1e6
+    e2e = world * args.steps * pix_per_step / (e2e_ms_max / 1e3) / 1e6
+    rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table())
+    line = {
+        "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded city-like scene and cameras)",
+        "config": {"workload": {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8",
+                                "tiny": "tiny-4k-128px-K2"}[args.workload],
+                   "splats": trainer.n, "width": Wd, "height": H, "subsets": trainer.kd.K, "sh_degree": trainer.sh_degree,
+                   "step": "render fwd + L1 loss + render bwd + Adam", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (parameters and Adam state 9.4 GB, instance buffers several GB)"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(targets[0].numel() * 4),
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches_timed),
+        "roofline": rl,
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof["stages"].items() if v[1] > 0},
+        "counters_per_step": {k: v / args.steps for k, v in prof["counters"].items()},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        wl_host = make_workload(args.workload, "cpu")
+        line["cpu_baseline"] = oracle_step_estimate(wl_host, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (only for the generators)
+    from paper_2406_11836_gb300 import workloads as W  # noqa: F401
+    wl = make_workload(args.workload, "cpu")
+    cam = wl.cameras[0]
+    HW = cam.width * cam.height
+    budget = max(5.0, 150.0 / max(args.steps + args.warmup, 1))
+    vals = []
+    est = None
+    for i in range(args.warmup + args.steps):
+        est = oracle_step_estimate(wl, budget_s=budget, cam_index=i % len(wl.cameras))
+        if i >= args.warmup:
+            vals.append(est["step_s_extrapolated"])
+    step_s = float(np.mean(vals))
+    value = HW / step_s / 1e6
+    line = {"impl": "reference", "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded city-like scene and cameras)",
+            "config": {"workload": {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8",
+                                    "tiny": "tiny-4k-128px-K2"}[args.workload], "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": est["cores"], "kind": "oracle",
+                             "sample": est["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("city", "object", "tiny"), default="city")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -537,17 +537,34 @@ static void plist_push(plist_t* l, const pair_t* p) {
     l->v[l->n++] = *p;
 }
 
+/* Compact copy of the conservative pixel bounds (x0, x1, y0, y1) of every splat, empty for
+ * splats behind the near plane; it only decides which splats get the exact tests. */
+static double* bbox_array(const proj_t* P, int64_t n) {
+    double* bb = (double*)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        if (P[i].visible) {
+            for (int j = 0; j < 4; ++j) bb[4 * i + j] = P[i].bbox[j];
+        } else {
+            bb[4 * i] = 1.0; bb[4 * i + 1] = -1.0; bb[4 * i + 2] = 1.0; bb[4 * i + 3] = -1.0;
+        }
+    }
+    return bb;
+}
+
 /* Gather the sorted contributors of pixel (px,py) and the pixel's ambiguity flags. */
-static int gather_pixel(const proj_t* P, int64_t n, const cam_t* cam, const opt_t* opt, int px, int py, int brute,
-                        plist_t* out) {
+static int gather_pixel(const proj_t* P, const double* bb, int64_t n, const cam_t* cam, const opt_t* opt, int px,
+                        int py, int brute, plist_t* out) {
     int flags = 0;
     double dray[3];
     pixel_ray(cam, px, py, dray);
     out->n = 0;
     for (int64_t i = 0; i < n; ++i) {
+        if (!brute) {
+            const double* b = bb + 4 * i;
+            if (px < b[0] || px > b[1] || py < b[2] || py > b[3]) continue;
+        }
         const proj_t* s = &P[i];
         if (!s->visible) continue;
-        if (!brute && (px < s->bbox[0] || px > s->bbox[1] || py < s->bbox[2] || py > s->bbox[3])) continue;
         pair_t pr;
         int c = eval_pair(s, i, cam, opt, px, py, dray, &pr);
         if (pr.amb > -1.0 && pr.amb < 1.0) flags |= OR_FLAG_TRUNC;
@@ -579,6 +596,7 @@ int or_render(int hier, int64_t n, const double* means, const double* log_scales
     scene_t sc = make_scene(n, means, log_scales, quats, logits, sh, deg);
     proj_t* P = project_all(&sc, &cam, &opt);
     if (!P) return -2;
+    double* bb = bbox_array(P, n);
     int K = 1 << (hier ? L : 0);
     int err = 0;
 #pragma omp parallel
@@ -588,7 +606,7 @@ int or_render(int hier, int64_t n, const double* means, const double* log_scales
 #pragma omp for schedule(dynamic, 16)
         for (int64_t q = 0; q < npix; ++q) {
             int px = (int)(pix[q] % cam.W), py = (int)(pix[q] / cam.W);
-            int fl = gather_pixel(P, n, &cam, &opt, px, py, brute, &lst);
+            int fl = gather_pixel(P, bb, n, &cam, &opt, px, py, brute, &lst);
             if (!hier) {
                 /* Eq. 2: C = sum_i c_i sigma_i prod_{j<i} (1 - sigma_j), then the background. */
                 double acc[3] = {0, 0, 0}, Tr = 1.0;
@@ -638,6 +656,7 @@ int or_render(int hier, int64_t n, const double* means, const double* log_scales
         free(lst.v);
         free(ord);
     }
+    free(bb);
     free(P);
     return err;
 }
@@ -773,14 +792,16 @@ int or_adjoint(int64_t n, const double* means, const double* log_scales, const d
     scene_t sc = make_scene(n, means, log_scales, quats, logits, sh, deg);
     proj_t* P = project_all(&sc, &cam, &opt);
     if (!P) return -2;
+    double* bb = bbox_array(P, n);
     g2d_t* G = (g2d_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(g2d_t));
     plist_t* lists = (plist_t*)calloc((size_t)(npix > 0 ? npix : 1), sizeof(plist_t));
     /* gather contributors in parallel, accumulate serially (deterministic sums) */
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t q = 0; q < npix; ++q) {
         int px = (int)(pix[q] % cam.W), py = (int)(pix[q] / cam.W);
-        gather_pixel(P, n, &cam, &opt, px, py, 0, &lists[q]);
+        gather_pixel(P, bb, n, &cam, &opt, px, py, 0, &lists[q]);
     }
+    free(bb);
     for (int64_t q = 0; q < npix; ++q) {
         const double* g = dLdC + 3 * q;
         plist_t* l = &lists[q];
@@ -848,13 +869,15 @@ int or_pair_signature(int64_t n, const double* means, const double* log_scales, 
     int64_t cnt = 0;
     double cs = 0;
     plist_t lst = {0, 0, 0};
+    double* bb = bbox_array(P, n);
     for (int64_t q = 0; q < npix; ++q) {
         int px = (int)(pix[q] % cam.W), py = (int)(pix[q] / cam.W);
-        gather_pixel(P, n, &cam, &opt, px, py, 0, &lst);
+        gather_pixel(P, bb, n, &cam, &opt, px, py, 0, &lst);
         cnt += lst.n;
         for (int64_t j = 0; j < lst.n; ++j) cs += (double)(q + 1) * 1e-3 * (double)(lst.v[j].id + 1) * (double)(j + 1);
     }
     free(lst.v);
+    free(bb);
     free(P);
     *count = cnt;
     *checksum = cs;

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -85,6 +86,11 @@ ProfScope::~ProfScope() {
 }
 
 unsigned long long* prof_pair_counters() { return g_prof.on ? g_prof.dev_pairs : nullptr; }
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void prof_add_host_counts(int64_t instances, int64_t visible) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -582,6 +588,7 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
         for (int i = 0; i < 4; ++i) counters_host[i] = (int64_t)pairs[i];
         counters_host[4] = g_prof.host_counts[0];
         counters_host[5] = g_prof.host_counts[1];
+        counters_host[6] = g_launches.load();
     }
     if (reset) {
         for (int i = 0; i < ST_COUNT; ++i) {
@@ -589,6 +596,7 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
             g_prof.launches[i] = 0;
         }
         g_prof.host_counts[0] = g_prof.host_counts[1] = 0;
+        g_launches.store(0);
         if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
     }
     return RGS_OK;

@@ -71,6 +71,7 @@ struct ProfScope {
 // contributing.
 unsigned long long* prof_pair_counters();
 void prof_add_host_counts(int64_t instances, int64_t visible);
+void count_launch();   // every kernel launch of the library (reported with the tracing counters)
 
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
@@ -87,6 +88,7 @@ void set_required_workspace(size_t bytes);
 
 #define RGS_CUDA_LAUNCH_CHECK()                                                            \
     do {                                                                                   \
+        ::rgs::count_launch();                                                             \
         cudaError_t _e = cudaGetLastError();                                               \
         if (_e != cudaSuccess) {                                                           \
             ::rgs::set_error("%s:%d: kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \

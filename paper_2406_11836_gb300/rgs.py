@@ -293,7 +293,7 @@ def profile_enable(on: bool = True):
     _check(lib().rgs_profile_enable(1 if on else 0))
 
 
-PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible")
+PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible", "kernel_launches")
 
 
 def profile_read(reset: bool = True) -> dict:
@@ -303,7 +303,7 @@ def profile_read(reset: bool = True) -> dict:
     n = L.rgs_profile_num_stages()
     ms = np.zeros(n, np.float64)
     launches = np.zeros(n, np.int64)
-    counters = np.zeros(6, np.int64)
+    counters = np.zeros(len(PAIR_COUNTERS), np.int64)
     _check(L.rgs_profile_read(c_void_p(ms.ctypes.data), c_void_p(launches.ctypes.data),
                               c_void_p(counters.ctypes.data), 1 if reset else 0))
     stages = {L.rgs_profile_stage_name(i).decode(): (float(ms[i]), int(launches[i])) for i in range(n)}
