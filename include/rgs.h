@@ -200,10 +200,12 @@ float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_f
  * pass; counting adds one atomic per warp per blend kernel.  Process-wide.
  * rgs_profile_read synchronises with the recorded events and writes, per stage index
  * 0..rgs_profile_num_stages()-1, the accumulated milliseconds (ms_host) and pass counts
- * (launches_host), and counters_host[7] = {fwd pairs evaluated, fwd pairs contributing,
+ * (launches_host), and counters_host[11] = {fwd pairs evaluated, fwd pairs contributing,
  * bwd pairs evaluated, bwd pairs contributing, tile instances, visible splats, kernel
- * launches of the library (counted whether or not profiling is on)}, summed since the
- * last reset.  Any output pointer may be NULL.  reset != 0 clears the sums. */
+ * launches of the library (counted whether or not profiling is on), fwd pairs failing the
+ * Mahalanobis test, failing the ball test, failing the Eq. 6 subset test, fwd pairs
+ * evaluated for splats held by several subsets}, summed since the last reset.  Any
+ * output pointer may be NULL.  reset != 0 clears the sums. */
 int rgs_profile_enable(int on);
 int rgs_profile_num_stages(void);
 const char* rgs_profile_stage_name(int stage);

@@ -349,7 +349,7 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
     }
     {
         ProfScope ps(ST_EMIT, s);
-        rc = launch_emit(*vp, *b, sorted_ids, n_vis, s);
+        rc = launch_emit(*vp, *tp, *b, sorted_ids, n_vis, s);
         if (rc) return rc;
     }
     {
@@ -582,13 +582,14 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
         if (ms_host) ms_host[i] = g_prof.ms[i];
         if (launches_host) launches_host[i] = g_prof.launches[i];
     }
-    unsigned long long pairs[4] = {0, 0, 0, 0};
+    unsigned long long pairs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemcpy(pairs, g_prof.dev_pairs, sizeof pairs, cudaMemcpyDeviceToHost));
     if (counters_host) {
         for (int i = 0; i < 4; ++i) counters_host[i] = (int64_t)pairs[i];
         counters_host[4] = g_prof.host_counts[0];
         counters_host[5] = g_prof.host_counts[1];
         counters_host[6] = g_launches.load();
+        for (int i = 0; i < 4; ++i) counters_host[7 + i] = (int64_t)pairs[4 + i];
     }
     if (reset) {
         for (int i = 0; i < ST_COUNT; ++i) {

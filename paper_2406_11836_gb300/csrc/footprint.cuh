@@ -1,0 +1,172 @@
+// Screen-space footprint of a projected splat: the pixels whose centre can pass the
+// truncation tests of a (pixel, splat) pair, i.e. the ellipse d^2 <= d2max of the 2D
+// Gaussian (d2max = min(trunc^2, 2 ln(alpha / alpha_min)): beyond it sigma < alpha_min)
+// intersected with the ball test (dx/fx)^2 + (dy/fy)^2 <= (D/z)^2.  Used, with identical
+// arithmetic on identical inputs, to count a splat's tile instances, to emit them, and to
+// mark which warp blocks of a tile a staged record can touch; the margins make it a
+// superset of what the fp32 per-pair tests accept.
+#pragma once
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+
+struct Footprint {
+    float cx, cy;            // centre (pixels; hi part of the projected centre)
+    float qa, qb, qc, det;   // conic Q = [[qa, qb], [qb, qc]] = L^T L, det = det(Q)
+    float r2;                // d2max with margin
+    float ex, ey;            // ellipse half-extents
+    float bx, by;            // ball half-extents (pixels)
+    float rho2;              // (D/z)^2 with margin
+    float ystar;             // y offset of the ellipse's rightmost point
+    bool empty;
+};
+
+__device__ __forceinline__ Footprint make_footprint(float mxh, float myh, float l11, float l12, float l22, float alpha,
+                                                    float rho2_signed, const ViewParams& vp) {
+    Footprint f;
+    f.cx = mxh;
+    f.cy = myh;
+    f.qa = l11 * l11;
+    f.qb = l11 * l12;
+    f.qc = fmaf(l12, l12, l22 * l22);
+    const float sd = l11 * l22;
+    f.det = sd * sd;
+    float d2max = fminf(vp.trunc_mult * vp.trunc_mult, 2.f * __logf(alpha / vp.alpha_min));
+    f.empty = !(d2max >= 0.f);
+    f.r2 = fmaxf(d2max, 0.f) * 1.002f + 2e-3f;
+    // covariance = Q^{-1}: xx = qc/det, yy = qa/det, xy = -qb/det
+    const float idet = 1.f / f.det;
+    const float sxx = f.qc * idet, syy = f.qa * idet, sxy = -f.qb * idet;
+    f.ex = sqrtf(f.r2 * sxx);
+    f.ey = sqrtf(f.r2 * syy);
+    f.ystar = sqrtf(f.r2) * sxy * rsqrtf(sxx);
+    f.rho2 = fabsf(rho2_signed) * 1.002f;
+    const float rb = sqrtf(f.rho2);
+    f.bx = vp.fx * rb;
+    f.by = vp.fy * rb;
+    return f;
+}
+
+// Horizontal extent [x0, x1] (offsets from the centre) of the footprint over the band of
+// pixel-centre offsets y in [ylo, yhi].  Returns false if the band misses it.
+__device__ __forceinline__ bool footprint_span(const Footprint& f, const ViewParams& vp, float ylo, float yhi,
+                                               float& x0, float& x1) {
+    const float yl = fmaxf(ylo, fmaxf(-f.ey, -f.by)), yh = fminf(yhi, fminf(f.ey, f.by));
+    if (!(yl <= yh)) return false;
+    // ellipse: x(y) = (-qb y +- sqrt(qa r2 - det y^2)) / qa; the right branch is concave and
+    // peaks at ystar, the left branch is convex with its minimum at -ystar
+    const float yr = fminf(fmaxf(f.ystar, yl), yh);
+    const float yq = fminf(fmaxf(-f.ystar, yl), yh);
+    const float iqa = 1.f / f.qa;
+    const float xr = fmaf(-f.qb, yr, sqrtf(fmaxf(fmaf(-f.det, yr * yr, f.qa * f.r2), 0.f))) * iqa;
+    const float xl = fmaf(-f.qb, yq, -sqrtf(fmaxf(fmaf(-f.det, yq * yq, f.qa * f.r2), 0.f))) * iqa;
+    // ball: widest where |y| is smallest
+    const float y0 = fminf(fmaxf(0.f, yl), yh) * vp.ify;
+    const float xb = vp.fx * sqrtf(fmaxf(f.rho2 - y0 * y0, 0.f));
+    x0 = fmaxf(xl, -xb) - 0.02f;
+    x1 = fminf(xr, xb) + 0.02f;
+    return x0 <= x1;
+}
+
+// Rows of tiles the footprint can touch.
+__device__ __forceinline__ void footprint_tile_rows(const Footprint& f, const ViewParams& vp, int& ty0, int& ty1) {
+    const float h = fminf(f.ey, f.by) + 0.02f;
+    ty0 = (int)fmaxf(floorf((f.cy - h - 0.5f) * (1.f / kTile)), 0.f);
+    ty1 = (int)fminf(floorf((f.cy + h - 0.5f) * (1.f / kTile)), (float)(vp.tiles_y - 1));
+}
+
+// Tile columns [c0, c1] the footprint touches in tile row ty (c0 > c1: none).
+__device__ __forceinline__ void footprint_row_tiles(const Footprint& f, const ViewParams& vp, int ty, int& c0, int& c1) {
+    const float ylo = (float)(ty * kTile) + 0.5f - f.cy, yhi = (float)(ty * kTile) + (kTile - 0.5f) - f.cy;
+    float x0, x1;
+    if (!footprint_span(f, vp, ylo, yhi, x0, x1)) {
+        c0 = 1;
+        c1 = 0;
+        return;
+    }
+    // pixel columns px with centre px + 0.5 in [cx + x0, cx + x1]
+    c0 = (int)fmaxf(floorf(ceilf(f.cx + x0 - 0.5f) * (1.f / kTile)), 0.f);
+    c1 = (int)fminf(floorf(floorf(f.cx + x1 - 0.5f) * (1.f / kTile)), (float)(vp.tiles_x - 1));
+}
+
+// ------------------------------------------------------------------ subset clipping (Eq. 6)
+// The L plane constraints of one KD leaf.
+struct LeafPath {
+    float split[kMaxRenderDepth];
+    int axis_right[kMaxRenderDepth];   // axis | (right << 2)
+};
+
+__device__ __forceinline__ void leaf_path(const TreeParams& tp, int k, LeafPath& lp) {
+    int node = 0;
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= tp.L) break;
+        const int right = (k >> (tp.L - 1 - d)) & 1;
+        lp.split[d] = tp.split[node];
+        lp.axis_right[d] = tp.axis[node] | (right << 2);
+        node = 2 * node + 1 + right;
+    }
+}
+
+// For a splat at camera depth z, the point x_i = o + z d_p of pixel-centre (X, Y) has
+// coordinate x_i[a] = A X + B Y + C + s along the split's axis (d_p is affine in X, Y), so
+// each plane of the leaf is a half-plane of the image: sign * (A X + B Y + C) >= 0 with
+// sign +1 on the right branch and -1 on the left.  `m` is a margin in world units, far
+// above the fp32 error of the per-pixel test, so clipping never drops a pixel the test
+// would accept.
+struct SubsetClip {
+    int n;
+    float A[kMaxRenderDepth], B[kMaxRenderDepth], C[kMaxRenderDepth], m[kMaxRenderDepth];
+};
+
+__device__ __forceinline__ void make_clip(const ViewParams& vp, const LeafPath& lp, int L, float z, SubsetClip& c) {
+    c.n = L;
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= L) break;
+        const int ar = lp.axis_right[d];
+        const int a = ar & 3;
+        const float sg = (ar >> 2) ? 1.f : -1.f;
+        const float Ra = vp.R[a], Rb = vp.R[3 + a], Rc = vp.R[6 + a];
+        const float oa = a == 0 ? vp.o[0] : (a == 1 ? vp.o[1] : vp.o[2]);
+        const float s = lp.split[d];
+        const float gam = Rc - Ra * vp.cx * vp.ifx - Rb * vp.cy * vp.ify;
+        c.A[d] = sg * z * Ra * vp.ifx;
+        c.B[d] = sg * z * Rb * vp.ify;
+        c.C[d] = sg * (fmaf(z, gam, oa) - s);
+        c.m[d] = 1e-5f * (fabsf(oa) + fabsf(s) + 4.f * z) + 1e-6f;
+    }
+}
+
+// Narrow [xlo, xhi] (absolute pixel-centre X) to the X where, for some Y in [ylo, yhi],
+// every half-plane holds within its margin.  Returns false if nothing is left.
+__device__ __forceinline__ bool clip_span(const SubsetClip& c, float ylo, float yhi, float& xlo, float& xhi) {
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= c.n) break;
+        const float by = fmaxf(c.B[d] * ylo, c.B[d] * yhi);
+        const float rhs = -c.m[d] - c.C[d] - by;       // need A X >= rhs
+        if (c.A[d] > 0.f) xlo = fmaxf(xlo, rhs / c.A[d]);
+        else if (c.A[d] < 0.f) xhi = fminf(xhi, rhs / c.A[d]);
+        else if (rhs > 0.f) return false;
+    }
+    return xlo <= xhi;
+}
+
+// Tile columns [c0, c1] of tile row ty touched by the footprint restricted to subset clip
+// `c` (c == nullptr: no restriction).
+__device__ __forceinline__ void footprint_row_tiles_clipped(const Footprint& f, const ViewParams& vp, int ty,
+                                                            const SubsetClip* c, int& c0, int& c1) {
+    const float Ylo = (float)(ty * kTile) + 0.5f, Yhi = (float)(ty * kTile) + (kTile - 0.5f);
+    float x0, x1;
+    c0 = 1;
+    c1 = 0;
+    if (!footprint_span(f, vp, Ylo - f.cy, Yhi - f.cy, x0, x1)) return;
+    float X0 = f.cx + x0, X1 = f.cx + x1;
+    if (c && !clip_span(*c, Ylo, Yhi, X0, X1)) return;
+    c0 = (int)fmaxf(floorf(ceilf(X0 - 0.5f) * (1.f / kTile)), 0.f);
+    c1 = (int)fminf(floorf(floorf(X1 - 0.5f) * (1.f / kTile)), (float)(vp.tiles_x - 1));
+}
+
+}  // namespace rgs

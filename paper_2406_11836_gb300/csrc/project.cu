@@ -18,6 +18,7 @@
 // so no cancellation occurs for elongated splats.  Everything else is plain fp32.
 #include <cuda_fp16.h>
 
+#include "footprint.cuh"
 #include "rgs_internal.cuh"
 
 namespace rgs {
@@ -279,22 +280,44 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         if (vis) {
             Proj P;
             ewa(vp, si, p, P);
-            // Mahalanobis bound: d^2 <= trunc^2 and alpha exp(-d^2/2) >= alpha_min
-            float d2max = fminf(vp.trunc_mult * vp.trunc_mult, 2.f * __logf(alpha / vp.alpha_min));
-            d2max = fmaxf(d2max, 0.f) * 1.001f + 1e-3f;
-            float rb = D / z;                      // ball radius in normalised image units
-            float hx = fminf(sqrtf(d2max * P.sxx), vp.fx * rb) * 1.001f + 1e-3f;
-            float hy = fminf(sqrtf(d2max * P.syy), vp.fy * rb) * 1.001f + 1e-3f;
-            float fx0 = floorf((mxh - hx - 0.5f) * (1.f / kTile));
-            float fx1 = floorf((mxh + hx - 0.5f) * (1.f / kTile));
-            float fy0 = floorf((myh - hy - 0.5f) * (1.f / kTile));
-            float fy1 = floorf((myh + hy - 0.5f) * (1.f / kTile));
-            int tx0 = (int)fmaxf(fx0, 0.f), ty0 = (int)fmaxf(fy0, 0.f);
-            int tx1 = (int)fminf(fx1, (float)(vp.tiles_x - 1)), ty1 = (int)fminf(fy1, (float)(vp.tiles_y - 1));
-            if (tx0 <= tx1 && ty0 <= ty1 && isfinite(P.det) && P.det > 0.f) {
-                unsigned long long mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
-                int nsub = __popcll(mask);
-                count = (uint32_t)nsub * (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+            const float l11 = sqrtf(P.ca);
+            const float l12 = P.cb / l11;
+            const float l22 = rsqrtf(P.det * P.ca);
+            const float rb = D / z;                 // ball radius in normalised image units
+            const unsigned long long mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
+            const int nsub = __popcll(mask);
+            const float rho2 = nsub > 1 ? -(rb * rb) : rb * rb;
+            // tiles touched by the footprint, row by row (the emission repeats this exactly)
+            uint32_t ntiles = 0;
+            int cmin = vp.tiles_x, cmax = -1, ty0 = 0, ty1 = -1;
+            if (isfinite(P.det) && P.det > 0.f && isfinite(l11) && isfinite(l22)) {
+                const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
+                footprint_tile_rows(f, vp, ty0, ty1);
+                // A splat held by several subsets is clipped, per subset, to the part of
+                // the image where its ray points can lie in that subspace (Eq. 6).
+                unsigned long long mm = nsub > 1 ? mask : 1ull;
+                while (mm) {
+                    const int k = __ffsll((long long)mm) - 1;
+                    mm &= mm - 1;
+                    SubsetClip clip;
+                    if (nsub > 1) {
+                        LeafPath lpk;
+                        leaf_path(tp, k, lpk);
+                        make_clip(vp, lpk, tp.L, z, clip);
+                    }
+                    for (int ty = ty0; ty <= ty1; ++ty) {
+                        int c0, c1;
+                        footprint_row_tiles_clipped(f, vp, ty, nsub > 1 ? &clip : nullptr, c0, c1);
+                        if (c0 <= c1) {
+                            ntiles += (uint32_t)(c1 - c0 + 1);
+                            cmin = min(cmin, c0);
+                            cmax = max(cmax, c1);
+                        }
+                    }
+                }
+            }
+            if (ntiles > 0) {
+                count = ntiles;
                 // colour at dir = normalise(mu - o)
                 float dx = si.mu[0] - vp.o[0], dy = si.mu[1] - vp.o[1], dz = si.mu[2] - vp.o[2];
                 float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -308,16 +331,12 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
                     for (int k = 0; k < NSH; ++k) acc = fmaf(sh[3 * k + c], Y[k], acc);
                     rgb[c] = fmaxf(acc, 0.f);
                 }
-                float l11 = sqrtf(P.ca);
-                float l12 = P.cb / l11;
-                float l22 = rsqrtf(P.det * P.ca);
                 __half2 lo = __floats2half2_rn(mxl, myl);
                 float lo_bits = __uint_as_float(*reinterpret_cast<uint32_t*>(&lo));
-                float rho2 = rb * rb;
                 b.rec[3 * i] = make_float4(mxh, myh, lo_bits, alpha);
-                b.rec[3 * i + 1] = make_float4(l11, l12, l22, nsub > 1 ? -rho2 : rho2);
+                b.rec[3 * i + 1] = make_float4(l11, l12, l22, rho2);
                 b.rec[3 * i + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
-                b.rect[i] = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1,
+                b.rect[i] = make_ushort4((unsigned short)cmin, (unsigned short)ty0, (unsigned short)cmax,
                                          (unsigned short)ty1);
                 b.mask[i] = mask;
                 b.dkey[i] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value

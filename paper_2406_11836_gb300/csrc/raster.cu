@@ -24,6 +24,7 @@
 // shared memory, and added to global memory with one vector reduction per float4.
 #include <cuda_fp16.h>
 
+#include "footprint.cuh"
 #include "rgs_internal.cuh"
 
 namespace rgs {
@@ -41,60 +42,61 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // ------------------------------------------------------------------ emission
+// One warp per depth-sorted splat; lanes take the splat's (subset, tile row) items, find
+// the row's tile columns from the footprint (the same arithmetic as the count), and
+// write the row's instances at the positions a warp prefix sum gives them.
 __global__ void __launch_bounds__(256)
-emit_kernel(ViewParams vp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis, const uint32_t* __restrict__ ioff,
-            const uint32_t* __restrict__ cnt, const ushort4* __restrict__ rect,
-            const unsigned long long* __restrict__ mask, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
+            const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
+            const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, uint32_t* __restrict__ ikey,
+            uint32_t* __restrict__ ival) {
     const int lane = threadIdx.x & 31;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t warp_first = p - lane;
-    if (warp_first >= n_vis) return;
-    uint32_t id = 0, off = 0, c = 0;
-    ushort4 r = make_ushort4(0, 0, 0, 0);
-    unsigned long long m = 0;
-    if (p < n_vis) {
-        id = sorted_ids[p];
-        off = ioff[p];
-        c = cnt[id];
-        r = rect[id];
-        m = mask[id];
-    }
-    // warp range of output positions
-    int last = (int)min((int64_t)31, n_vis - 1 - warp_first);
-    uint32_t wbeg = __shfl_sync(0xffffffffu, off, 0);
-    uint32_t lend = off + c;
-    uint32_t wend = __shfl_sync(0xffffffffu, lend, last);
-    if (lane > last) off = 0xffffffffu;    // never owns a position
-    for (uint32_t j0 = wbeg; j0 < wend; j0 += 32) {
-        uint32_t j = j0 + lane;
-        // owner = last lane whose offset <= j (offsets are non-decreasing over lanes)
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            uint32_t o = __shfl_sync(0xffffffffu, off, lo + step);
-            if (lo + step <= last && o <= j) lo += step;
-        }
-        uint32_t o_id = __shfl_sync(0xffffffffu, id, lo);
-        uint32_t o_off = __shfl_sync(0xffffffffu, off, lo);
-        unsigned rx = __shfl_sync(0xffffffffu, (unsigned)r.x | ((unsigned)r.y << 16), lo);
-        unsigned rz = __shfl_sync(0xffffffffu, (unsigned)r.z | ((unsigned)r.w << 16), lo);
-        unsigned long long o_m = __shfl_sync(0xffffffffu, m, lo);
-        if (j < wend) {
-            int x0 = rx & 0xffff, y0 = rx >> 16, x1 = rz & 0xffff, y1 = rz >> 16;
-            int w = x1 - x0 + 1;
-            int nt = w * (y1 - y0 + 1);
-            int e = (int)(j - o_off);
-            int si = e / nt;
-            int t = e - si * nt;
-            int ty = y0 + t / w;
-            int tx = x0 + (t - (ty - y0) * w);
-            // si-th subset of the mask
-            unsigned long long mm = o_m;
-            for (int q = 0; q < si; ++q) mm &= mm - 1;
-            int k = __ffsll((long long)mm) - 1;
-            uint32_t tile = (uint32_t)(ty * vp.tiles_x + tx);
-            ikey[j] = (tile << vp.L) | (uint32_t)vp.rank_of[k];
-            ival[j] = o_id;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < n_vis; p += nwarps) {
+        const uint32_t id = sorted_ids[p];
+        uint32_t base = ioff[p];
+        const ushort4 r = rect[id];
+        const unsigned long long m = mask[id];
+        const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+        const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+        const int ty0 = r.y, rows = (int)r.w - (int)r.y + 1;
+        const int nsub = __popcll(m);
+        const int items = nsub * rows;
+        for (int it0 = 0; it0 < items; it0 += 32) {
+            const int it = it0 + lane;
+            int c0 = 1, c1 = 0, ty = 0;
+            uint32_t rank = 0;
+            if (it < items) {
+                const int si = it / rows;
+                ty = ty0 + (it - si * rows);
+                unsigned long long mm = m;
+                for (int q = 0; q < si; ++q) mm &= mm - 1;
+                const int k = __ffsll((long long)mm) - 1;
+                rank = (uint32_t)vp.rank_of[k];
+                if (nsub > 1) {
+                    LeafPath lpk;
+                    leaf_path(tp, k, lpk);
+                    SubsetClip clip;
+                    make_clip(vp, lpk, tp.L, r2.w, clip);
+                    footprint_row_tiles_clipped(f, vp, ty, &clip, c0, c1);
+                } else {
+                    footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);
+                }
+            }
+            const uint32_t w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+            uint32_t incl = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t pos = base + incl - w;
+            const uint32_t first = (uint32_t)(ty * vp.tiles_x + c0);
+            for (uint32_t t = 0; t < w; ++t) {
+                ikey[pos + t] = ((first + t) << vp.L) | rank;
+                ival[pos + t] = id;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
 }
@@ -108,35 +110,36 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint
 }
 
 // ------------------------------------------------------------------ shared pieces of the blend
-// The L plane constraints of the current subset's leaf (Eq. 6), kept in shared memory:
-// they are uniform across the CTA and only read for splats held by several subsets.
-struct LeafPath {
-    float split[kMaxRenderDepth];
-    int axis_right[kMaxRenderDepth];   // axis | (right << 2)
-};
-
-__device__ __forceinline__ void leaf_path(const TreeParams& tp, int k, LeafPath& lp) {
-    int node = 0;
-    for (int d = 0; d < tp.L; ++d) {
-        int right = (k >> (tp.L - 1 - d)) & 1;
-        lp.split[d] = tp.split[node];
-        lp.axis_right[d] = tp.axis[node] | (right << 2);
-        node = 2 * node + 1 + right;
-    }
-}
+// The current subset's leaf constraints (Eq. 6) live in shared memory (LeafPath): they
+// are uniform across the CTA and only read for splats held by several subsets.
 
 // x_i = o + z d_p lies in S_k (half-open boxes: left x[a] < s, right x[a] >= s)
-__device__ __forceinline__ bool in_leaf(const LeafPath& lp, int L, const float o[3], const float dray[3], float z) {
+__device__ __forceinline__ bool in_leaf(const LeafPath& lp, int L, float3 o, float3 dray, float z) {
     bool ok = true;
     for (int d = 0; d < L; ++d) {
         const int ar = lp.axis_right[d];
         const int a = ar & 3;
-        const float oa = a == 0 ? o[0] : (a == 1 ? o[1] : o[2]);
-        const float da = a == 0 ? dray[0] : (a == 1 ? dray[1] : dray[2]);
+        const float oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
+        const float da = a == 0 ? dray.x : (a == 1 ? dray.y : dray.z);
         const float x = fmaf(z, da, oa);
         ok = ok && ((x >= lp.split[d]) == (bool)(ar >> 2));
     }
     return ok;
+}
+
+// Each warp owns an 8x4 block of the 16x16 tile: warp w covers columns 8 (w & 1) .. +7
+// and rows 4 (w >> 1) .. +3, so a splat that misses a block costs that warp nothing.
+__device__ __forceinline__ void thread_pixel(int tid, int& lx, int& ly) {
+    const int w = tid >> 5, l = tid & 31;
+    lx = ((w & 1) << 3) | (l & 7);
+    ly = ((w >> 1) << 2) | (l >> 3);
+}
+
+// World direction of the ray through pixel (px, py), scaled to unit camera-space z.
+__device__ __forceinline__ float3 pixel_ray(const ViewParams& vp, int px, int py) {
+    const float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
+    return make_float3(fmaf(vp.R[0], u, fmaf(vp.R[3], v, vp.R[6])), fmaf(vp.R[1], u, fmaf(vp.R[4], v, vp.R[7])),
+                       fmaf(vp.R[2], u, fmaf(vp.R[5], v, vp.R[8])));
 }
 
 struct StagedRec {   // tile-relative record in shared memory (3 x float4)
@@ -144,6 +147,29 @@ struct StagedRec {   // tile-relative record in shared memory (3 x float4)
     float4 b;        // l11, l12, l22, z
     float4 c;        // r, g, b, (splat id as bits)
 };
+
+// Bit w set: the footprint can touch warp w's 8x4 block (one span per 4-row band); for a
+// splat held by several subsets the span is also clipped to the current subset (Eq. 6).
+__device__ __forceinline__ uint32_t block_mask(const StagedRec& r, const ViewParams& vp, const LeafPath& lp, float x0t,
+                                               float y0t) {
+    const Footprint f = make_footprint(r.a.x, r.a.y, r.b.x, r.b.y, r.b.z, r.a.z, r.a.w, vp);
+    const bool straddles = r.a.w < 0.f;
+    SubsetClip clip;
+    if (straddles) make_clip(vp, lp, vp.L, r.b.w, clip);
+    uint32_t m = 0;
+#pragma unroll
+    for (int band = 0; band < 4; ++band) {
+        float x0, x1;
+        const float ylo = (float)(4 * band) + 0.5f - f.cy, yhi = (float)(4 * band) + 3.5f - f.cy;
+        if (!footprint_span(f, vp, ylo, yhi, x0, x1)) continue;
+        float X0 = f.cx + x0 + x0t, X1 = f.cx + x1 + x0t;          // absolute pixel-centre X
+        if (straddles && !clip_span(clip, ylo + f.cy + y0t, yhi + f.cy + y0t, X0, X1)) continue;
+        const float pl = ceilf(X0 - x0t - 0.5f), ph = floorf(X1 - x0t - 0.5f);   // tile pixel columns
+        if (pl <= 7.f && ph >= 0.f) m |= 1u << (2 * band);
+        if (pl <= 15.f && ph >= 8.f) m |= 1u << (2 * band + 1);
+    }
+    return m;
+}
 
 __device__ __forceinline__ StagedRec stage_record(const float4* __restrict__ rec, uint32_t id, float x0, float y0) {
     float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
@@ -158,6 +184,12 @@ __device__ __forceinline__ StagedRec stage_record(const float4* __restrict__ rec
 }
 
 // warp-aggregated pair counters (tracing only)
+__device__ __forceinline__ void count_add(unsigned long long* dst, uint32_t v) {
+    unsigned long long e = v;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0 && e) atomicAdd(dst, e);
+}
+
 __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t n_eval, uint32_t n_contrib) {
     unsigned long long e = n_eval, c = n_contrib;
     for (int o = 16; o > 0; o >>= 1) {
@@ -171,27 +203,26 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 }
 
 // ------------------------------------------------------------------ blend forward
-__global__ void __launch_bounds__(kBlendThreads)
+__global__ void __launch_bounds__(kBlendThreads, 4)
 blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
                  float* __restrict__ image, float* __restrict__ Tfin, unsigned long long* __restrict__ pairs) {
     __shared__ StagedRec srec[kBlendThreads];
-    uint32_t n_eval = 0, n_contrib = 0;
+    __shared__ uint32_t smask[kBlendThreads];
     __shared__ LeafPath lp;
+    uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0;
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    int lx, ly;
+    thread_pixel(threadIdx.x, lx, ly);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = txi * kTile + lx, py = tyi * kTile + ly;
     const bool inside = px < vp.W && py < vp.H;
     const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
-    const float o[3] = {vp.o[0], vp.o[1], vp.o[2]};
+    const float3 o = make_float3(vp.o[0], vp.o[1], vp.o[2]);
     // world direction of this pixel's ray with unit camera-z component (Eq. 6 test)
-    float dray[3];
-    {
-        float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
-        for (int a = 0; a < 3; ++a) dray[a] = fmaf(vp.R[a], u, fmaf(vp.R[3 + a], v, vp.R[6 + a]));
-    }
+    const float3 dray = pixel_ray(vp, px, py);
     const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = (size_t)py * vp.W + px;
@@ -206,20 +237,29 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
-            if ((int)threadIdx.x < nb) srec[threadIdx.x] = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+            if ((int)threadIdx.x < nb) {
+                const StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                srec[threadIdx.x] = sr;
+                smask[threadIdx.x] = block_mask(sr, vp, lp, x0, y0);
+            }
             __syncthreads();
-            if (!__all_sync(0xffffffffu, done)) {
-                for (int j = 0; j < nb && !done; ++j) {
+            for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
+                unsigned bits = __ballot_sync(0xffffffffu, c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u));
+                while (bits) {
+                    const int j = c0 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (done) continue;
                     ++n_eval;
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
+                    n_strad += A.w < 0.f;
                     const float dx = pcx - A.x, dy = pcy - A.y;
                     const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    if (d2 > tm2) continue;
+                    if (d2 > tm2) { ++n_d2; continue; }
                     const float bx = dx * vp.ifx, by = dy * vp.ify;
-                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) continue;
-                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) continue;
+                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) { ++n_ball; continue; }
+                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) { ++n_leaf; continue; }
                     const float sig = fminf(A.z * ex2_approx(d2 * kNegHalfLog2e), vp.alpha_max);
                     if (sig < vp.alpha_min) continue;
                     ++n_contrib;
@@ -251,13 +291,37 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         image[2 * HW + pix] = fmaf(vp.bg[2], Pm, img2);
         if (Tfin) Tfin[pix] = Pm;
     }
-    if (pairs) count_pairs(pairs, n_eval, n_contrib);
+    if (pairs) {
+        count_pairs(pairs, n_eval, n_contrib);
+        count_add(pairs + 4, n_d2);
+        count_add(pairs + 5, n_ball);
+        count_add(pairs + 6, n_leaf);
+        count_add(pairs + 7, n_strad);
+    }
 }
 
 // ------------------------------------------------------------------ blend backward
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sums v[0..15] over the 32 lanes of a warp with 16 shuffles (reduce-scatter by halving):
+// at each step a lane keeps one half of its values, sends the other half to its partner
+// and adds what it receives.  Returns the total of value index (lane >> 1) & 15; both
+// lanes of each pair hold it.
+__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = upper ? v[k] : v[k + h];
+            const float keep = upper ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
@@ -267,29 +331,28 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
 }
 
 // dynamic shared memory: s_behind [K][256] floats
-__global__ void __launch_bounds__(kBlendThreads)
+__global__ void __launch_bounds__(kBlendThreads, 4)
 blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
                  const float* __restrict__ gI, float4* __restrict__ g2d, unsigned long long* __restrict__ pairs) {
     extern __shared__ float s_behind[];
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ StagedRec srec[kBlendThreads];
+    __shared__ uint32_t smask[kBlendThreads];
     __shared__ float sacc[kBlendThreads][9];
     __shared__ LeafPath lp;
-    const float o[3] = {vp.o[0], vp.o[1], vp.o[2]};
+    const float3 o = make_float3(vp.o[0], vp.o[1], vp.o[2]);
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    int lx, ly;
+    thread_pixel(threadIdx.x, lx, ly);
+    const int warp = threadIdx.x >> 5;
     const int px = txi * kTile + lx, py = tyi * kTile + ly;
     const bool inside = px < vp.W && py < vp.H;
     const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
     const int lane = threadIdx.x & 31;
-    float dray[3];
-    {
-        float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
-        for (int a = 0; a < 3; ++a) dray[a] = fmaf(vp.R[a], u, fmaf(vp.R[3 + a], v, vp.R[6 + a]));
-    }
+    const float3 dray = pixel_ray(vp, px, py);
     const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = inside ? (size_t)py * vp.W + px : 0;
@@ -338,10 +401,17 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
-            if ((int)threadIdx.x < nb) srec[threadIdx.x] = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+            if ((int)threadIdx.x < nb) {
+                const StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                srec[threadIdx.x] = sr;
+                smask[threadIdx.x] = block_mask(sr, vp, lp, x0, y0);
+            }
             __syncthreads();
-            if (!__all_sync(0xffffffffu, done)) {
-                for (int j = 0; j < nb; ++j) {
+            for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
+                unsigned bits = __ballot_sync(0xffffffffu, c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u));
+                while (bits) {
+                    const int j = c0 + __ffs(bits) - 1;
+                    bits &= bits - 1;
                     float gmx = 0.f, gmy = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gal = 0.f, gr0 = 0.f, gr1 = 0.f,
                           gr2 = 0.f;
                     bool contrib = false;
@@ -386,26 +456,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                         }
                     }
                     if (__any_sync(0xffffffffu, contrib)) {
-                        gmx = warp_sum(gmx);
-                        gmy = warp_sum(gmy);
-                        ga = warp_sum(ga);
-                        gb = warp_sum(gb);
-                        gc = warp_sum(gc);
-                        gal = warp_sum(gal);
-                        gr0 = warp_sum(gr0);
-                        gr1 = warp_sum(gr1);
-                        gr2 = warp_sum(gr2);
-                        if (lane == 0) {
-                            atomicAdd(&sacc[j][0], gmx);
-                            atomicAdd(&sacc[j][1], gmy);
-                            atomicAdd(&sacc[j][2], ga);
-                            atomicAdd(&sacc[j][3], gb);
-                            atomicAdd(&sacc[j][4], gc);
-                            atomicAdd(&sacc[j][5], gal);
-                            atomicAdd(&sacc[j][6], gr0);
-                            atomicAdd(&sacc[j][7], gr1);
-                            atomicAdd(&sacc[j][8], gr2);
-                        }
+                        float v[16] = {gmx, gmy, ga, gb, gc, gal, gr0, gr1, gr2, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        const float tot = warp_reduce16(v, lane);
+                        const int vi = (lane >> 1) & 15;
+                        if ((lane & 1) == 0 && vi < 9) atomicAdd(&sacc[j][vi], tot);
                     }
                 }
             }
@@ -483,11 +537,12 @@ __global__ void merge_bwd_kernel(const float* __restrict__ pC, const float* __re
 
 }  // namespace
 
-int launch_emit(const ViewParams& vp, const RasterBuffers& b, const uint32_t* sorted_ids, int64_t n_vis,
-                cudaStream_t s) {
+int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
+                int64_t n_vis, cudaStream_t s) {
     if (n_vis <= 0) return RGS_OK;
-    unsigned grid = (unsigned)((n_vis + 255) / 256);
-    emit_kernel<<<grid, 256, 0, s>>>(vp, sorted_ids, n_vis, b.ioff, b.cnt, b.rect, b.mask, b.ikey, b.ival);
+    const int64_t want = (n_vis + 7) / 8;          // one warp per splat
+    unsigned grid = (unsigned)(want < (1 << 20) ? want : (1 << 20));
+    emit_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.ikey, b.ival);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

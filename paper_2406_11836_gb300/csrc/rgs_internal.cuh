@@ -142,8 +142,8 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
                        cudaStream_t s);
 int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
                        const RasterBuffers& b, cudaStream_t s);
-int launch_emit(const ViewParams& vp, const RasterBuffers& b, const uint32_t* sorted_ids, int64_t n_vis,
-                cudaStream_t s);
+int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
+                int64_t n_vis, cudaStream_t s);
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s);

@@ -293,7 +293,8 @@ def profile_enable(on: bool = True):
     _check(lib().rgs_profile_enable(1 if on else 0))
 
 
-PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible", "kernel_launches")
+PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible", "kernel_launches",
+                 "fwd_fail_d2", "fwd_fail_ball", "fwd_fail_subset", "fwd_pairs_straddling")
 
 
 def profile_read(reset: bool = True) -> dict:
