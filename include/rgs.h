@@ -109,6 +109,15 @@ void rgs_default_opts(rgs_render_opts* opts);
  * trunc_mult <= 0), ENOMEM, ECUDA. */
 int rgs_kd_partition(const rgs_gaussians* g, int depth_L, float trunc_mult, rgs_kd** out, void* stream);
 
+/* A partition with caller-given planes: axis_host [K-1] in {0,1,2} and split_host [K-1]
+ * (heap order, as rgs_kd_splits returns them), with the overlapping subsets N_k formed by
+ * the same D_i rule as rgs_kd_partition.  Any axis-aligned convex partition of this form
+ * is valid for the method (Sec. 3.2 only needs convex subspaces); it restores a saved
+ * partition exactly and serves comparison partitions (e.g. a fixed grid).  Errors:
+ * EINVAL (axis out of range, non-finite split, L out of [0,8]), ENOMEM, ECUDA. */
+int rgs_kd_from_splits(const rgs_gaussians* g, int depth_L, const int32_t* axis_host, const float* split_host,
+                       float trunc_mult, rgs_kd** out, void* stream);
+
 /* Depth L, leaf count K and total subset-list length M of a partition. */
 int rgs_kd_info(const rgs_kd* kd, int* depth_L, int* K, int64_t* total_members);
 
@@ -192,12 +201,13 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
 float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_final);
 
 /* ------------------------------------------------------------------ tracing
- * Per-pass timing.  While enabled, every pass of the library (projection, compaction,
- * depth sort, offsets, emission, instance sort, ranges, blend forward, blend backward,
- * projection backward, Adam, merge, merge backward, KD build) records a pair of CUDA
- * events on the stream it is launched on, and the blend kernels count the (pixel, splat)
- * pairs they evaluate and the ones that contribute.  Timing adds two event records per
- * pass; counting adds one atomic per warp per blend kernel.  Process-wide.
+ * rgs_profile_enable(flags): bit 0 turns on per-pass timing: every pass of the library
+ * (projection, compaction, depth sort, offsets, emission, instance sort, ranges, blend
+ * forward, blend backward, projection backward, Adam, merge, merge backward, KD build)
+ * records a pair of CUDA events on the stream it is launched on (two event records per
+ * pass).  Bit 1 turns on pair counting: the blend kernels run in a counting variant that
+ * tallies the (pixel, splat) pairs they evaluate, the ones that contribute and why the
+ * others fail (slower; keep it off where time is measured).  Process-wide.
  * rgs_profile_read synchronises with the recorded events and writes, per stage index
  * 0..rgs_profile_num_stages()-1, the accumulated milliseconds (ms_host) and pass counts
  * (launches_host), and counters_host[11] = {fwd pairs evaluated, fwd pairs contributing,
@@ -206,7 +216,7 @@ float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_f
  * Mahalanobis test, failing the ball test, failing the Eq. 6 subset test, fwd pairs
  * evaluated for splats held by several subsets}, summed since the last reset.  Any
  * output pointer may be NULL.  reset != 0 clears the sums. */
-int rgs_profile_enable(int on);
+int rgs_profile_enable(int flags);
 int rgs_profile_num_stages(void);
 const char* rgs_profile_stage_name(int stage);
 int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_host, int reset);

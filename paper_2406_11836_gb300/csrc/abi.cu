@@ -41,7 +41,8 @@ const char* kStageNames[ST_COUNT] = {"project", "compact", "depth_sort", "offset
                                      "blend_fwd", "blend_bwd", "project_bwd", "adam", "merge", "merge_bwd", "kd"};
 struct Profiler {
     std::mutex mu;
-    bool on = false;
+    bool on = false;      // stage timing
+    bool count = false;   // pair counters (counting kernel variants)
     std::vector<cudaEvent_t> pool;
     struct Rec { int stage; cudaEvent_t a, b; };
     std::vector<Rec> open;      // started, not yet ended (indexed by token)
@@ -85,7 +86,7 @@ ProfScope::~ProfScope() {
     while (!g_prof.open.empty() && g_prof.open.back().stage < 0) g_prof.open.pop_back();
 }
 
-unsigned long long* prof_pair_counters() { return g_prof.on ? g_prof.dev_pairs : nullptr; }
+unsigned long long* prof_pair_counters() { return g_prof.count ? g_prof.dev_pairs : nullptr; }
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -94,7 +95,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void prof_add_host_counts(int64_t instances, int64_t visible) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    if (!g_prof.on) return;
+    if (!g_prof.on && !g_prof.count) return;
     g_prof.host_counts[0] += instances;
     g_prof.host_counts[1] += visible;
 }
@@ -414,6 +415,48 @@ int rgs_kd_partition(const rgs_gaussians* g, int depth_L, float trunc_mult, rgs_
     return RGS_OK;
 }
 
+int rgs_kd_from_splits(const rgs_gaussians* g, int depth_L, const int32_t* axis_host, const float* split_host,
+                       float trunc_mult, rgs_kd** out, void* stream) {
+    if (!out) { set_error("kd_from_splits: out is NULL"); return RGS_EINVAL; }
+    *out = nullptr;
+    if (!g || !g->means || !g->log_scales || g->n < 1 || g->n > 0x7fffffffll) {
+        set_error("kd_from_splits: need means, log_scales and 1 <= n < 2^31");
+        return RGS_EINVAL;
+    }
+    if (depth_L < 0 || depth_L > kMaxKdDepth) { set_error("kd_from_splits: depth %d not in [0, %d]", depth_L, kMaxKdDepth); return RGS_EINVAL; }
+    if (!(trunc_mult > 0) || !std::isfinite(trunc_mult)) { set_error("kd_from_splits: trunc_mult must be > 0"); return RGS_EINVAL; }
+    const int nn = (1 << depth_L) - 1;
+    if (nn > 0 && (!axis_host || !split_host)) { set_error("kd_from_splits: NULL splits"); return RGS_EINVAL; }
+    for (int j = 0; j < nn; ++j) {
+        if (axis_host[j] < 0 || axis_host[j] > 2 || !std::isfinite(split_host[j])) {
+            set_error("kd_from_splits: node %d has axis %d / split %g", j, axis_host[j], (double)split_host[j]);
+            return RGS_EINVAL;
+        }
+    }
+    rgs_kd* kd = new (std::nothrow) rgs_kd;
+    if (!kd) { set_error("kd_from_splits: out of host memory"); return RGS_ENOMEM; }
+    cudaGetDevice(&kd->device);
+    kd->trunc_mult = trunc_mult;
+    memset(&kd->b, 0, sizeof kd->b);
+    kd->b.L = depth_L;
+    for (int j = 0; j < nn; ++j) {
+        kd->b.axis[j] = (int8_t)axis_host[j];
+        kd->b.split[j] = split_host[j];
+    }
+    int rc;
+    {
+        ProfScope ps(ST_KD, (cudaStream_t)stream);
+        rc = kd_subsets(*g, trunc_mult, &kd->b, (cudaStream_t)stream);
+    }
+    if (rc != RGS_OK) {
+        if (kd->b.idx_dev) cudaFree(kd->b.idx_dev);
+        delete kd;
+        return rc;
+    }
+    *out = kd;
+    return RGS_OK;
+}
+
 int rgs_kd_info(const rgs_kd* kd, int* depth_L, int* K, int64_t* total) {
     if (!kd) { set_error("kd_info: NULL"); return RGS_EINVAL; }
     if (depth_L) *depth_L = kd->b.L;
@@ -552,13 +595,14 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
                        zero_grad, (cudaStream_t)stream);
 }
 
-int rgs_profile_enable(int on) {
+int rgs_profile_enable(int flags) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    if (on && !g_prof.dev_pairs) {
+    if ((flags & 2) && !g_prof.dev_pairs) {
         RGS_CUDA_TRY(cudaMalloc(&g_prof.dev_pairs, 8 * sizeof(unsigned long long)));
         RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
     }
-    g_prof.on = on != 0;
+    g_prof.on = (flags & 1) != 0;
+    g_prof.count = (flags & 2) != 0;
     return RGS_OK;
 }
 

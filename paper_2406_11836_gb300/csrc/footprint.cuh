@@ -169,4 +169,34 @@ __device__ __forceinline__ void footprint_row_tiles_clipped(const Footprint& f, 
     c1 = (int)fminf(floorf(floorf(X1 - 0.5f) * (1.f / kTile)), (float)(vp.tiles_x - 1));
 }
 
+// Item `it` of a splat (subset index it / rows, tile row ty0 + it % rows): its tile row,
+// its subset k and the tile columns [c0, c1] the footprint touches there, clipped to the
+// subset when the splat is held by several (Eq. 6).  The count in the projection and the
+// emission call this same function on the same record values, so they always agree.
+__device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
+                                          unsigned long long mask, int nsub, float z, int ty0, int rows, int it,
+                                          int& ty, int& k, int& c0, int& c1) {
+    const int si = it / rows;
+    ty = ty0 + (it - si * rows);
+    unsigned long long mm = mask;
+    for (int q = 0; q < si; ++q) mm &= mm - 1;
+    k = __ffsll((long long)mm) - 1;
+    if (nsub > 1) {
+        LeafPath lpk;
+        leaf_path(tp, k, lpk);
+        SubsetClip clip;
+        make_clip(vp, lpk, tp.L, z, clip);
+        footprint_row_tiles_clipped(f, vp, ty, &clip, c0, c1);
+    } else {
+        footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);
+    }
+}
+
+__device__ __forceinline__ uint32_t item_tiles(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
+                                               unsigned long long mask, int nsub, float z, int ty0, int rows, int it) {
+    int ty, k, c0, c1;
+    item_span(f, vp, tp, mask, nsub, z, ty0, rows, it, ty, k, c0, c1);
+    return c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+}
+
 }  // namespace rgs

@@ -205,7 +205,23 @@ int kd_build(const rgs_gaussians& g, int L, float trunc_mult, KdBuild* out, cuda
     }
     if (K > 1) RGS_CUDA_TRY(cudaMemcpyAsync(out->split, split_dev, sizeof(float) * (K - 1), cudaMemcpyDeviceToHost, s));
     RGS_CUDA_TRY(cudaStreamSynchronize(s));
+    return kd_subsets(g, trunc_mult, out, s);
+}
 
+int kd_subsets(const rgs_gaussians& g, float trunc_mult, KdBuild* out, cudaStream_t s) {
+    const int64_t N = g.n;
+    const int L = out->L;
+    const int K = 1 << L;
+    DevBuf buf(s);
+    uint32_t* cnt = buf.get<uint32_t>(N);
+    uint32_t* off = buf.get<uint32_t>(N);
+    uint32_t* node_counts = buf.get<uint32_t>(K + 1);
+    size_t tbytes = scan_temp_bytes(N);
+    void* temp = buf.get<char>(tbytes);
+    if (!cnt || !off || !node_counts || !temp) {
+        set_error("kd_partition: device allocation failed");
+        return RGS_ENOMEM;
+    }
     // subsets N_k
     TreeParams tp;
     tp.L = L;

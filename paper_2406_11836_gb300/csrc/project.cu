@@ -260,64 +260,45 @@ __device__ __forceinline__ void ewa(const ViewParams& vp, const SplatIn& si, con
 }
 
 // ------------------------------------------------------------------ forward kernel
+constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are counted by the whole warp
+
 template <int DEG>
 __global__ void __launch_bounds__(256)
 project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
     constexpr int NSH = (DEG + 1) * (DEG + 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t count = 0;
+    const int lane = threadIdx.x & 31;
+    // candidate state handed to the counting phase
+    bool cand = false;
+    float mxh = 0.f, myh = 0.f, l11 = 0.f, l12 = 0.f, l22 = 0.f, alpha = 0.f, rho2 = 0.f, z = 0.f;
+    unsigned long long mask = 0;
+    int ty0 = 0, ty1 = -1, nsub = 0;
     if (i < g.n) {
         SplatIn si;
         load_splat(g, i, si);
-        float p[3], mxh, mxl, myh, myl;
+        float p[3], mxl, myl;
         project_centre(vp, si.mu, p, mxh, mxl, myh, myl);
-        float z = p[2];
-        float smax = fmaxf(si.ls[0], fmaxf(si.ls[1], si.ls[2]));
-        float D = vp.trunc_mult * __expf(smax);
-        float alpha = 1.f / (1.f + __expf(-si.logit));
+        z = p[2];
+        const float smax = fmaxf(si.ls[0], fmaxf(si.ls[1], si.ls[2]));
+        const float D = vp.trunc_mult * __expf(smax);
+        alpha = 1.f / (1.f + __expf(-si.logit));
         // A splat contributes nowhere unless z > near and alpha >= alpha_min.
-        bool vis = z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh);
-        if (vis) {
+        if (z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh)) {
             Proj P;
             ewa(vp, si, p, P);
-            const float l11 = sqrtf(P.ca);
-            const float l12 = P.cb / l11;
-            const float l22 = rsqrtf(P.det * P.ca);
-            const float rb = D / z;                 // ball radius in normalised image units
-            const unsigned long long mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
-            const int nsub = __popcll(mask);
-            const float rho2 = nsub > 1 ? -(rb * rb) : rb * rb;
-            // tiles touched by the footprint, row by row (the emission repeats this exactly)
-            uint32_t ntiles = 0;
-            int cmin = vp.tiles_x, cmax = -1, ty0 = 0, ty1 = -1;
+            l11 = sqrtf(P.ca);
+            l12 = P.cb / l11;
+            l22 = rsqrtf(P.det * P.ca);
+            const float rb = D / z;                   // ball radius in normalised image units
+            mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
+            nsub = __popcll(mask);
+            rho2 = nsub > 1 ? -(rb * rb) : rb * rb;
             if (isfinite(P.det) && P.det > 0.f && isfinite(l11) && isfinite(l22)) {
                 const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
                 footprint_tile_rows(f, vp, ty0, ty1);
-                // A splat held by several subsets is clipped, per subset, to the part of
-                // the image where its ray points can lie in that subspace (Eq. 6).
-                unsigned long long mm = nsub > 1 ? mask : 1ull;
-                while (mm) {
-                    const int k = __ffsll((long long)mm) - 1;
-                    mm &= mm - 1;
-                    SubsetClip clip;
-                    if (nsub > 1) {
-                        LeafPath lpk;
-                        leaf_path(tp, k, lpk);
-                        make_clip(vp, lpk, tp.L, z, clip);
-                    }
-                    for (int ty = ty0; ty <= ty1; ++ty) {
-                        int c0, c1;
-                        footprint_row_tiles_clipped(f, vp, ty, nsub > 1 ? &clip : nullptr, c0, c1);
-                        if (c0 <= c1) {
-                            ntiles += (uint32_t)(c1 - c0 + 1);
-                            cmin = min(cmin, c0);
-                            cmax = max(cmax, c1);
-                        }
-                    }
-                }
+                cand = ty0 <= ty1;
             }
-            if (ntiles > 0) {
-                count = ntiles;
+            if (cand) {
                 // colour at dir = normalise(mu - o)
                 float dx = si.mu[0] - vp.o[0], dy = si.mu[1] - vp.o[1], dz = si.mu[2] - vp.o[2];
                 float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
@@ -336,14 +317,39 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
                 b.rec[3 * i] = make_float4(mxh, myh, lo_bits, alpha);
                 b.rec[3 * i + 1] = make_float4(l11, l12, l22, rho2);
                 b.rec[3 * i + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
-                b.rect[i] = make_ushort4((unsigned short)cmin, (unsigned short)ty0, (unsigned short)cmax,
-                                         (unsigned short)ty1);
+                b.rect[i] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
                 b.mask[i] = mask;
                 b.dkey[i] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
             }
         }
-        b.cnt[i] = count;
     }
+    // ---- count the tile instances: small splats per thread, large ones per warp
+    const int rows = ty1 - ty0 + 1;
+    const int items = cand ? nsub * rows : 0;
+    uint32_t count = 0;
+    if (cand && items <= kWarpCountItems) {
+        const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
+        for (int it = 0; it < items; ++it) count += item_tiles(f, vp, tp, mask, nsub, z, ty0, rows, it);
+    }
+    unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const float fx_ = __shfl_sync(0xffffffffu, mxh, src), fy_ = __shfl_sync(0xffffffffu, myh, src);
+        const float a_ = __shfl_sync(0xffffffffu, l11, src), b_ = __shfl_sync(0xffffffffu, l12, src);
+        const float c_ = __shfl_sync(0xffffffffu, l22, src), al_ = __shfl_sync(0xffffffffu, alpha, src);
+        const float r_ = __shfl_sync(0xffffffffu, rho2, src), z_ = __shfl_sync(0xffffffffu, z, src);
+        const unsigned long long m_ = __shfl_sync(0xffffffffu, mask, src);
+        const int t0_ = __shfl_sync(0xffffffffu, ty0, src), rows_ = __shfl_sync(0xffffffffu, rows, src);
+        const int items_ = __shfl_sync(0xffffffffu, items, src);
+        const Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
+        const int ns = __popcll(m_);
+        uint32_t acc = 0;
+        for (int it = lane; it < items_; it += 32) acc += item_tiles(f, vp, tp, m_, ns, z_, t0_, rows_, it);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == src) count = acc;
+    }
+    if (i < g.n) b.cnt[i] = count;
     // totals: instances and visible splats
     unsigned long long c64 = count;
     unsigned vis_n = count > 0;
@@ -351,7 +357,7 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         c64 += __shfl_xor_sync(0xffffffffu, c64, o);
         vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
     }
-    if ((threadIdx.x & 31) == 0 && (c64 | vis_n)) {
+    if (lane == 0 && (c64 | vis_n)) {
         atomicAdd(&b.counters[0], c64);
         atomicAdd(&b.counters[1], (unsigned long long)vis_n);
     }

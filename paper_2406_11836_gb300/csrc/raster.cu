@@ -31,6 +31,10 @@ namespace rgs {
 namespace {
 
 constexpr int kBlendThreads = kTilePixels;  // 256
+// Resident CTAs per SM the blend kernels are compiled for (register budget 65536 / (256 x this)).
+#ifndef RGS_BLEND_MIN_BLOCKS
+#define RGS_BLEND_MIN_BLOCKS 3
+#endif
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -0.5 * log2(e)
 
 // exp(-d2/2) as 2^(d2 * -0.5 log2 e) on the SFU (ex2.approx, ~2 ulp); the forward and
@@ -68,21 +72,9 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             int c0 = 1, c1 = 0, ty = 0;
             uint32_t rank = 0;
             if (it < items) {
-                const int si = it / rows;
-                ty = ty0 + (it - si * rows);
-                unsigned long long mm = m;
-                for (int q = 0; q < si; ++q) mm &= mm - 1;
-                const int k = __ffsll((long long)mm) - 1;
+                int k;
+                item_span(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
                 rank = (uint32_t)vp.rank_of[k];
-                if (nsub > 1) {
-                    LeafPath lpk;
-                    leaf_path(tp, k, lpk);
-                    SubsetClip clip;
-                    make_clip(vp, lpk, tp.L, r2.w, clip);
-                    footprint_row_tiles_clipped(f, vp, ty, &clip, c0, c1);
-                } else {
-                    footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);
-                }
             }
             const uint32_t w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
             uint32_t incl = w;
@@ -203,7 +195,8 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 }
 
 // ------------------------------------------------------------------ blend forward
-__global__ void __launch_bounds__(kBlendThreads, 4)
+template <bool kCount>
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
                  float* __restrict__ image, float* __restrict__ Tfin, unsigned long long* __restrict__ pairs) {
@@ -249,20 +242,31 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                     const int j = c0 + __ffs(bits) - 1;
                     bits &= bits - 1;
                     if (done) continue;
-                    ++n_eval;
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
-                    n_strad += A.w < 0.f;
+                    if (kCount) {
+                        ++n_eval;
+                        n_strad += A.w < 0.f;
+                    }
                     const float dx = pcx - A.x, dy = pcy - A.y;
                     const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    if (d2 > tm2) { ++n_d2; continue; }
+                    if (d2 > tm2) {
+                        if (kCount) ++n_d2;
+                        continue;
+                    }
                     const float bx = dx * vp.ifx, by = dy * vp.ify;
-                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) { ++n_ball; continue; }
-                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) { ++n_leaf; continue; }
+                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) {
+                        if (kCount) ++n_ball;
+                        continue;
+                    }
+                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) {
+                        if (kCount) ++n_leaf;
+                        continue;
+                    }
                     const float sig = fminf(A.z * ex2_approx(d2 * kNegHalfLog2e), vp.alpha_max);
                     if (sig < vp.alpha_min) continue;
-                    ++n_contrib;
+                    if (kCount) ++n_contrib;
                     const float4 Cc = srec[j].c;
                     const float w = sig * T;
                     C0 = fmaf(Cc.x, w, C0);
@@ -291,7 +295,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         image[2 * HW + pix] = fmaf(vp.bg[2], Pm, img2);
         if (Tfin) Tfin[pix] = Pm;
     }
-    if (pairs) {
+    if (kCount) {
         count_pairs(pairs, n_eval, n_contrib);
         count_add(pairs + 4, n_d2);
         count_add(pairs + 5, n_ball);
@@ -331,7 +335,8 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
 }
 
 // dynamic shared memory: s_behind [K][256] floats
-__global__ void __launch_bounds__(kBlendThreads, 4)
+template <bool kCount>
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
                  const float* __restrict__ gI, float4* __restrict__ g2d, unsigned long long* __restrict__ pairs) {
@@ -416,7 +421,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                           gr2 = 0.f;
                     bool contrib = false;
                     if (!done) {
-                        ++n_eval;
+                        if (kCount) ++n_eval;
                         const float4 A = srec[j].a;
                         const float4 B = srec[j].b;
                         const float dx = pcx - A.x, dy = pcy - A.y;
@@ -431,7 +436,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                             const float sig = fminf(raw, vp.alpha_max);
                             if (sig >= vp.alpha_min) {
                                 contrib = true;
-                                ++n_contrib;
+                                if (kCount) ++n_contrib;
                                 const float4 Cc = srec[j].c;
                                 const float w = sig * T;
                                 const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
@@ -480,7 +485,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             if (__syncthreads_count(done) == kBlendThreads) break;
         }
     }
-    if (pairs) count_pairs(pairs + 2, n_eval, n_contrib);
+    if (kCount) count_pairs(pairs + 2, n_eval, n_contrib);
 }
 
 // ------------------------------------------------------------------ standalone merge (Eq. 5)
@@ -558,8 +563,13 @@ int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_rang
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
-    blend_fwd_kernel<<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
-                                                    T_final, prof_pair_counters());
+    unsigned long long* pairs = prof_pair_counters();
+    if (pairs)
+        blend_fwd_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
+                                                              T_final, pairs);
+    else
+        blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
+                                                               image, T_final, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -570,11 +580,17 @@ int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
     size_t smem = sizeof(float) * (size_t)vp.K * kBlendThreads;
     static bool attr_set = false;
     if (!attr_set) {
-        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         attr_set = true;
     }
-    blend_bwd_kernel<<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                       dL_dimage, b.g2d, prof_pair_counters());
+    unsigned long long* pairs = prof_pair_counters();
+    if (pairs)
+        blend_bwd_kernel<true><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
+                                                                 dL_dimage, b.g2d, pairs);
+    else
+        blend_bwd_kernel<false><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
+                                                                  dL_dimage, b.g2d, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -164,6 +164,8 @@ struct KdBuild {
     int64_t M;
 };
 int kd_build(const rgs_gaussians& g, int L, float trunc_mult, KdBuild* out, cudaStream_t s);
+// Subset lists N_k for the splits already in `out` (out->L, axis, split).
+int kd_subsets(const rgs_gaussians& g, float trunc_mult, KdBuild* out, cudaStream_t s);
 
 // ------------------------------------------------------------------ Adam (adam.cu)
 int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t* seg_off, const float* seg_lr,

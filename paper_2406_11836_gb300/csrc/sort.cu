@@ -22,8 +22,8 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 4096
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 2048
 
 __device__ __forceinline__ uint32_t load_item(const uint32_t* in, const uint32_t* gather, int64_t i, int mode) {
     uint32_t v = mode == 2 ? in[gather[i]] : in[i];
@@ -99,7 +99,7 @@ scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const u
 }
 
 // Per-tile histogram of one 8-bit digit, written digit-major: counts[d * nblocks + b].
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
                      uint32_t nblocks) {
     __shared__ uint32_t hist[kRadix];
@@ -117,11 +117,11 @@ radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, ui
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
 }
 
-// Stable scatter of one tile by one digit.  Warp w owns tile items [w*512, (w+1)*512) and
-// walks them in 16 rounds of 32 lanes, so (round, lane) order is the input order; a
+// Stable scatter of one tile by one digit.  Warp w owns tile items [w*256, (w+1)*256) and
+// walks them in 8 rounds of 32 lanes, so (round, lane) order is the input order; a
 // per-warp digit counter plus the rank among equal digits of the round gives each key's
 // rank within its warp, the per-digit scan over warps gives its rank within the tile.
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                        uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
                        uint32_t nblocks) {

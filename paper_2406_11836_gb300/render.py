@@ -122,6 +122,34 @@ class Trainer:
         self.kd = rgs.kd_partition(self.gaussians(), depth_L if depth_L is not None else self.kd.L,
                                    float(self.opts.trunc_mult))
 
+    # ---------------------------------------------------------------- checkpoint / resume
+    def checkpoint(self, device=None) -> dict:
+        """Parameters, Adam moments, step count and KD splits (device copies by default)."""
+        dev = device if device is not None else self.flat.device
+        axis, split = self.kd.splits()
+        return {"flat": self.flat.detach().to(dev, copy=True), "m": self.m.to(dev, copy=True),
+                "v": self.v.to(dev, copy=True), "step": self.step_count, "seg": list(self.seg),
+                "n": self.n, "sh_degree": self.sh_degree, "kd_L": self.kd.L,
+                "kd_axis": torch.as_tensor(axis), "kd_split": torch.as_tensor(split)}
+
+    def restore(self, ck: dict):
+        """Resume from `checkpoint()`: parameters, moments, step and the KD partition (its
+        planes, with the subsets re-formed on the restored parameters) come back exactly."""
+        assert ck["n"] == self.n and ck["sh_degree"] == self.sh_degree
+        self.flat.copy_(ck["flat"])
+        self.m.copy_(ck["m"])
+        self.v.copy_(ck["v"])
+        self.grad.zero_()
+        self.step_count = int(ck["step"])
+        self.kd = rgs.kd_from_splits(self.gaussians(), int(ck["kd_L"]), np.asarray(ck["kd_axis"]),
+                                     np.asarray(ck["kd_split"]), float(self.opts.trunc_mult))
+
+    def save(self, path: str):
+        torch.save(self.checkpoint(device="cpu"), path)
+
+    def load(self, path: str):
+        self.restore(torch.load(path, map_location="cpu"))
+
     def step(self, cam, target: torch.Tensor, return_loss: bool = True):
         """One training step: forward, L1 loss against `target` [3,H,W], backward, Adam.
         Returns the loss as a 0-d tensor (left on the device)."""

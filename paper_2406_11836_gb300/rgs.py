@@ -62,6 +62,8 @@ def lib():
     L.rgs_position_lr.argtypes = [c_int64, c_int64, c_float, c_float]
     L.rgs_kd_partition.argtypes = [POINTER(Gaussians), c_int, c_float, POINTER(c_void_p), c_void_p]
     L.rgs_kd_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int64)]
+    L.rgs_kd_from_splits.argtypes = [POINTER(Gaussians), c_int, c_void_p, c_void_p, c_float, POINTER(c_void_p),
+                                     c_void_p]
     L.rgs_kd_splits.argtypes = [c_void_p, c_void_p, c_void_p]
     L.rgs_kd_subsets.argtypes = [c_void_p, c_void_p, c_void_p]
     L.rgs_kd_destroy.argtypes = [c_void_p]
@@ -183,6 +185,19 @@ def kd_partition(scene, depth_L: int, trunc_mult: float = 3.0, stream=None) -> K
     return KD(h)
 
 
+def kd_from_splits(scene, depth_L: int, axis, split, trunc_mult: float = 3.0, stream=None) -> KD:
+    """Partition with the given planes (heap order), subsets by the D_i rule."""
+    g = scene if isinstance(scene, Gaussians) else scene_c(scene)
+    ax = np.ascontiguousarray(np.asarray(axis, np.int32).reshape(-1))
+    sp = np.ascontiguousarray(np.asarray(split, np.float32).reshape(-1))
+    if ax.size == 0:
+        ax, sp = np.zeros(1, np.int32), np.zeros(1, np.float32)
+    h = c_void_p()
+    _check(lib().rgs_kd_from_splits(ctypes.byref(g), int(depth_L), c_void_p(ax.ctypes.data), c_void_p(sp.ctypes.data),
+                                    float(trunc_mult), ctypes.byref(h), _stream(stream)))
+    return KD(h)
+
+
 # --------------------------------------------------------------------------- render
 class Workspace:
     """Caller-owned render workspace (a CUDA byte tensor) that grows on demand."""
@@ -289,8 +304,9 @@ def position_lr(step, max_steps, lr_init=1.6e-4, lr_final=1.6e-6) -> float:
 
 
 # --------------------------------------------------------------------------- tracing
-def profile_enable(on: bool = True):
-    _check(lib().rgs_profile_enable(1 if on else 0))
+def profile_enable(timing: bool = True, counters: bool = False):
+    """Per-pass CUDA-event timing (cheap) and/or pair counters (counting kernel variants)."""
+    _check(lib().rgs_profile_enable((1 if timing else 0) | (2 if counters else 0)))
 
 
 PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible", "kernel_launches",
@@ -312,7 +328,7 @@ def profile_read(reset: bool = True) -> dict:
 
 
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
-               "rgs_kd_info", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
+               "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_merge_partials", "rgs_merge_partials_bwd",
                "rgs_render_bwd", "rgs_adam_step", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read")

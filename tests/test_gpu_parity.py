@@ -295,3 +295,56 @@ def test_adam_step_matches_oracle(R):
         assert torch.count_nonzero(gd) == 0
         np.testing.assert_allclose(pd.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
     assert abs(R.position_lr(30000, 60000) - 1.6e-5) < 1e-10
+
+
+# --------------------------------------------------------------------------- partitions from given planes
+def test_kd_from_splits_matches_partition_and_random_trees_render_flat(R):
+    scene = W.uniform_cube_scene(4000, seed=31, log_scale_mean=-3.0, sh_degree=1)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 3)
+    axis, split = kd.splits()
+    kd2 = R.kd_from_splits(dev, 3, axis, split)
+    o1, i1 = kd.subsets()
+    o2, i2 = kd2.subsets()
+    np.testing.assert_array_equal(o1, o2)
+    assert torch.equal(i1, i2)
+    # any axis-aligned convex partition gives the flat result (Sec. 3.2, appendix proof)
+    r = np.random.default_rng(5)
+    ax = r.integers(0, 3, 7).astype(np.int32)
+    sp = r.uniform(-0.5, 0.5, 7).astype(np.float32)
+    kd3 = R.kd_from_splits(dev, 3, ax, sp)
+    cam = W.look_at((0.1, -0.2, 0.05), (0.2, 1.0, -0.1), 80, 56)
+    out = R.render_fwd(kd3, R.scene_c(dev), cam, R.default_opts(), R.Workspace())
+    torch.cuda.synchronize()
+    flat = O.render(scene, cam, oracle_opts())
+    ok = (flat["flags"] & FWD_FLAGS) == 0
+    assert ok.mean() >= 1 - MAX_FLAGGED
+    err = np.abs(image_at(out["image"], np.arange(80 * 56)) - flat["C"])[ok].max()
+    assert err <= PIXEL_TOL, err
+    with pytest.raises(R.RGSError):
+        R.kd_from_splits(dev, 2, np.array([0, 3, 1], np.int32), np.zeros(3, np.float32))
+
+
+def test_checkpoint_resume_reproduces_next_step(R, tmp_path):
+    from paper_2406_11836_gb300.render import Trainer
+    scene = W.uniform_cube_scene(3000, seed=41, log_scale_mean=-3.0, sh_degree=2)
+    cam = W.look_at((0.3, -2.5, 0.4), (0, 0, 0), 96, 64)
+    target = W.target_image(96, 64, seed=2, device="cuda")
+    a = Trainer(scene, 2)
+    for _ in range(3):
+        a.step(cam, target)
+    path = str(tmp_path / "ck.pt")
+    a.save(path)
+    a.step(cam, target)
+    b = Trainer(scene, 2)
+    b.load(path)
+    assert b.step_count == 3
+    ax_a, sp_a = a.kd.splits()
+    ax_b, sp_b = b.kd.splits()
+    np.testing.assert_array_equal(sp_a, sp_b)
+    b.step(cam, target)
+    torch.cuda.synchronize()
+    # the forward is deterministic; gradients are summed with atomics, so the order of
+    # additions (and the last bits of the update) may differ
+    diff = (a.flat - b.flat).abs().max().item()
+    assert diff <= 1e-5, diff
