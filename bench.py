@@ -29,6 +29,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd+Adam Mpix/s, 10M Gaussians, 3840x2160, 16 KD subsets"
+WORKLOAD_NAMES = {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8", "tiny": "tiny-4k-128px-K2",
+                  "city-small": "city-1M-1920x1080-K16"}
 UNIT = "Mpix/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -102,6 +104,8 @@ def make_workload(name, device):
         return W.city_10m(device=device)
     if name == "object":
         return W.object_1m(device=device)
+    if name == "city-small":
+        return W.city_10m(device=device, n=1_000_000, width=1920, height=1080, n_views=4)
     return W.tiny(device=device)
 
 
@@ -313,8 +317,7 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded city-like scene and cameras)",
-        "config": {"workload": {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8",
-                                "tiny": "tiny-4k-128px-K2"}[args.workload],
+        "config": {"workload": WORKLOAD_NAMES[args.workload],
                    "splats": trainer.n, "width": Wd, "height": H, "subsets": trainer.kd.K, "sh_degree": trainer.sh_degree,
                    "step": "render fwd + L1 loss + render bwd + Adam", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (parameters and Adam state 9.4 GB, instance buffers several GB)"},
@@ -354,8 +357,7 @@ def run_reference(args, rank, world):
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic (seeded city-like scene and cameras)",
-            "config": {"workload": {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8",
-                                    "tiny": "tiny-4k-128px-K2"}[args.workload], "parallelism": "host cores"},
+            "config": {"workload": WORKLOAD_NAMES[args.workload], "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": est["cores"], "kind": "oracle",
                              "sample": est["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -368,7 +370,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("city", "object", "tiny"), default="city")
+    ap.add_argument("--workload", choices=("city", "object", "tiny", "city-small"), default="city")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -90,6 +90,19 @@ __device__ __forceinline__ void footprint_row_tiles(const Footprint& f, const Vi
     c1 = (int)fminf(floorf(floorf(f.cx + x1 - 0.5f) * (1.f / kTile)), (float)(vp.tiles_x - 1));
 }
 
+// ------------------------------------------------------------------ plane test (Eq. 6)
+// For a splat at camera depth z, the ray point x_i = o + z d_p of the pixel with centre
+// (X, Y) has x_i[a] - s = A X + B Y + C along a node's axis.  The blend decides "x_i on
+// the right of the node" as A X + B Y + C >= 0 with these coefficients, computed by this one
+// function for every leaf that tests the node, so the leaves' decisions are complementary
+// and every (pixel, splat) pair lands in exactly one subset.
+__device__ __forceinline__ float4 plane_coeffs(const ViewParams& vp, int a, float s, float z) {
+    const float Ra = vp.R[a], Rb = vp.R[3 + a], Rc = vp.R[6 + a];
+    const float oa = a == 0 ? vp.o[0] : (a == 1 ? vp.o[1] : vp.o[2]);
+    const float gam = Rc - Ra * vp.cx * vp.ifx - Rb * vp.cy * vp.ify;
+    return make_float4(z * Ra * vp.ifx, z * Rb * vp.ify, fmaf(z, gam, oa - s), 0.f);
+}
+
 // ------------------------------------------------------------------ subset clipping (Eq. 6)
 // The L plane constraints of one KD leaf.
 struct LeafPath {

@@ -105,16 +105,55 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint
 // The current subset's leaf constraints (Eq. 6) live in shared memory (LeafPath): they
 // are uniform across the CTA and only read for splats held by several subsets.
 
-// x_i = o + z d_p lies in S_k (half-open boxes: left x[a] < s, right x[a] >= s)
-__device__ __forceinline__ bool in_leaf(const LeafPath& lp, int L, float3 o, float3 dray, float z) {
-    bool ok = true;
-    for (int d = 0; d < L; ++d) {
+// The leaf's planes that cut a tile for one staged splat, as affine tests of the pixel
+// centre: float4(A, B, C, side) with side +1 (need A X + B Y + C >= 0) or -1 (need < 0).
+constexpr int kMaxCutPlanes = 3;
+constexpr uint32_t kPlanesAll = 7;   // more cut planes than stored: test every plane per pair
+
+// Classifies the leaf's planes for a splat at depth z over the tile's pixel centres
+// [X0, X0+15] x [Y0, Y0+15]: a plane every centre passes (with a margin far above fp32
+// rounding) is dropped, one every centre fails culls the record (-1), the others are
+// stored.  Returns the number stored, or kPlanesAll.
+__device__ __forceinline__ int classify_planes(const ViewParams& vp, const LeafPath& lp, float z, float X0, float Y0,
+                                               float4* out) {
+    int n = 0;
+    for (int d = 0; d < vp.L; ++d) {
         const int ar = lp.axis_right[d];
         const int a = ar & 3;
-        const float oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
-        const float da = a == 0 ? dray.x : (a == 1 ? dray.y : dray.z);
-        const float x = fmaf(z, da, oa);
-        ok = ok && ((x >= lp.split[d]) == (bool)(ar >> 2));
+        const bool right = (ar >> 2) != 0;
+        const float4 P = plane_coeffs(vp, a, lp.split[d], z);
+        const float ax0 = P.x * X0, ax1 = P.x * (X0 + 15.f), by0 = P.y * Y0, by1 = P.y * (Y0 + 15.f);
+        const float vmin = P.z + fminf(ax0, ax1) + fminf(by0, by1);
+        const float vmax = P.z + fmaxf(ax0, ax1) + fmaxf(by0, by1);
+        const float oa = a == 0 ? vp.o[0] : (a == 1 ? vp.o[1] : vp.o[2]);
+        const float m = 1e-5f * (fabsf(oa) + fabsf(lp.split[d]) + 4.f * z) + 1e-6f;
+        const bool pass_all = right ? vmin >= m : vmax <= -m;
+        const bool fail_all = right ? vmax <= -m : vmin >= m;
+        if (fail_all) return -1;
+        if (pass_all) continue;
+        if (n < kMaxCutPlanes) out[n] = make_float4(P.x, P.y, P.z, right ? 1.f : -1.f);
+        ++n;
+    }
+    return n <= kMaxCutPlanes ? n : (int)kPlanesAll;
+}
+
+// Eq. 6 for one pixel: the stored cut planes, or (rarely) every plane of the leaf.
+__device__ __forceinline__ bool in_subset(const float4* planes, int n, const ViewParams& vp, const LeafPath& lp,
+                                          float z, float X, float Y) {
+    bool ok = true;
+    if (n != (int)kPlanesAll) {
+        for (int c = 0; c < n; ++c) {
+            const float4 P = planes[c];
+            const float v = fmaf(P.x, X, fmaf(P.y, Y, P.z));
+            ok = ok && (P.w > 0.f ? v >= 0.f : v < 0.f);
+        }
+    } else {
+        for (int d = 0; d < vp.L; ++d) {
+            const int ar = lp.axis_right[d];
+            const float4 P = plane_coeffs(vp, ar & 3, lp.split[d], z);
+            const float v = fmaf(P.x, X, fmaf(P.y, Y, P.z));
+            ok = ok && ((ar >> 2) ? v >= 0.f : v < 0.f);
+        }
     }
     return ok;
 }
@@ -125,13 +164,6 @@ __device__ __forceinline__ void thread_pixel(int tid, int& lx, int& ly) {
     const int w = tid >> 5, l = tid & 31;
     lx = ((w & 1) << 3) | (l & 7);
     ly = ((w >> 1) << 2) | (l >> 3);
-}
-
-// World direction of the ray through pixel (px, py), scaled to unit camera-space z.
-__device__ __forceinline__ float3 pixel_ray(const ViewParams& vp, int px, int py) {
-    const float u = ((float)px + 0.5f - vp.cx) * vp.ifx, v = ((float)py + 0.5f - vp.cy) * vp.ify;
-    return make_float3(fmaf(vp.R[0], u, fmaf(vp.R[3], v, vp.R[6])), fmaf(vp.R[1], u, fmaf(vp.R[4], v, vp.R[7])),
-                       fmaf(vp.R[2], u, fmaf(vp.R[5], v, vp.R[8])));
 }
 
 struct StagedRec {   // tile-relative record in shared memory (3 x float4)
@@ -202,6 +234,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                  float* __restrict__ image, float* __restrict__ Tfin, unsigned long long* __restrict__ pairs) {
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
+    __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ LeafPath lp;
     uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0;
     const int tile = blockIdx.x;
@@ -213,9 +246,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     const bool inside = px < vp.W && py < vp.H;
     const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
-    const float3 o = make_float3(vp.o[0], vp.o[1], vp.o[2]);
-    // world direction of this pixel's ray with unit camera-z component (Eq. 6 test)
-    const float3 dray = pixel_ray(vp, px, py);
+    const float Xc = (float)px + 0.5f, Yc = (float)py + 0.5f;   // absolute pixel centre (Eq. 6 tests)
     const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = (size_t)py * vp.W + px;
@@ -231,9 +262,16 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
             if ((int)threadIdx.x < nb) {
-                const StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                uint32_t msk = block_mask(sr, vp, lp, x0, y0);
+                if (sr.a.w < 0.f && msk) {
+                    const int nc = classify_planes(vp, lp, sr.b.w, x0 + 0.5f, y0 + 0.5f, splane[threadIdx.x]);
+                    if (nc < 0) msk = 0;                        // no pixel of the tile is in this subset
+                    else if (nc == 0) sr.a.w = -sr.a.w;         // every pixel is: no per-pixel test
+                    else msk |= (uint32_t)nc << 8;
+                }
                 srec[threadIdx.x] = sr;
-                smask[threadIdx.x] = block_mask(sr, vp, lp, x0, y0);
+                smask[threadIdx.x] = msk;
             }
             __syncthreads();
             for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
@@ -260,7 +298,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                         if (kCount) ++n_ball;
                         continue;
                     }
-                    if (A.w < 0.f && !in_leaf(lp, vp.L, o, dray, B.w)) {
+                    if (A.w < 0.f && !in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc)) {
                         if (kCount) ++n_leaf;
                         continue;
                     }
@@ -344,9 +382,9 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
+    __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ float sacc[kBlendThreads][9];
     __shared__ LeafPath lp;
-    const float3 o = make_float3(vp.o[0], vp.o[1], vp.o[2]);
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
@@ -357,7 +395,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
     const int lane = threadIdx.x & 31;
-    const float3 dray = pixel_ray(vp, px, py);
+    const float Xc = (float)px + 0.5f, Yc = (float)py + 0.5f;   // absolute pixel centre (Eq. 6 tests)
     const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = inside ? (size_t)py * vp.W + px : 0;
@@ -407,9 +445,16 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
             if ((int)threadIdx.x < nb) {
-                const StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
+                uint32_t msk = block_mask(sr, vp, lp, x0, y0);
+                if (sr.a.w < 0.f && msk) {
+                    const int nc = classify_planes(vp, lp, sr.b.w, x0 + 0.5f, y0 + 0.5f, splane[threadIdx.x]);
+                    if (nc < 0) msk = 0;                        // no pixel of the tile is in this subset
+                    else if (nc == 0) sr.a.w = -sr.a.w;         // every pixel is: no per-pixel test
+                    else msk |= (uint32_t)nc << 8;
+                }
                 srec[threadIdx.x] = sr;
-                smask[threadIdx.x] = block_mask(sr, vp, lp, x0, y0);
+                smask[threadIdx.x] = msk;
             }
             __syncthreads();
             for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
@@ -429,7 +474,8 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                         const float d2 = fmaf(u1, u1, u2 * u2);
                         const float bx = dx * vp.ifx, by = dy * vp.ify;
                         bool pass = d2 <= tm2 && fmaf(bx, bx, by * by) <= fabsf(A.w);
-                        if (pass && A.w < 0.f) pass = in_leaf(lp, vp.L, o, dray, B.w);
+                        if (pass && A.w < 0.f)
+                            pass = in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
                         if (pass) {
                             const float G = ex2_approx(d2 * kNegHalfLog2e);
                             const float raw = A.z * G;
