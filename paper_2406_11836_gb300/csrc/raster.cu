@@ -279,39 +279,41 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 while (bits) {
                     const int j = c0 + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    if (done) continue;
+                    // Branch-free body: a pair that fails a test (or a pixel already done)
+                    // gets sigma = 0, which leaves C and T unchanged.  The backward repeats
+                    // this arithmetic exactly.
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
-                    if (kCount) {
-                        ++n_eval;
-                        n_strad += A.w < 0.f;
-                    }
                     const float dx = pcx - A.x, dy = pcy - A.y;
                     const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    if (d2 > tm2) {
-                        if (kCount) ++n_d2;
-                        continue;
-                    }
                     const float bx = dx * vp.ifx, by = dy * vp.ify;
-                    if (fmaf(bx, bx, by * by) > fabsf(A.w)) {
-                        if (kCount) ++n_ball;
-                        continue;
+                    const bool in_ell = d2 <= tm2, in_ball = fmaf(bx, bx, by * by) <= fabsf(A.w);
+                    bool ok = !done && in_ell && in_ball;
+                    bool in_sub = true;
+                    if (A.w < 0.f) {   // uniform across the warp: one record
+                        in_sub = in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
+                        ok = ok && in_sub;
                     }
-                    if (A.w < 0.f && !in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc)) {
-                        if (kCount) ++n_leaf;
-                        continue;
+                    const float G = ex2_approx(d2 * kNegHalfLog2e);
+                    float sig = fminf(A.z * G, vp.alpha_max);
+                    ok = ok && sig >= vp.alpha_min;
+                    if (kCount && !done) {
+                        ++n_eval;
+                        n_strad += A.w < 0.f;
+                        n_d2 += !in_ell;
+                        n_ball += in_ell && !in_ball;
+                        n_leaf += in_ell && in_ball && !in_sub;
+                        n_contrib += ok;
                     }
-                    const float sig = fminf(A.z * ex2_approx(d2 * kNegHalfLog2e), vp.alpha_max);
-                    if (sig < vp.alpha_min) continue;
-                    if (kCount) ++n_contrib;
+                    sig = ok ? sig : 0.f;
                     const float4 Cc = srec[j].c;
                     const float w = sig * T;
                     C0 = fmaf(Cc.x, w, C0);
                     C1 = fmaf(Cc.y, w, C1);
                     C2 = fmaf(Cc.z, w, C2);
                     T = fmaf(-sig, T, T);
-                    if (T < vp.eps_T) done = true;
+                    done = done || T < vp.eps_T;
                 }
             }
             if (__syncthreads_count(done) == kBlendThreads) break;
@@ -462,50 +464,42 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 while (bits) {
                     const int j = c0 + __ffs(bits) - 1;
                     bits &= bits - 1;
-                    float gmx = 0.f, gmy = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gal = 0.f, gr0 = 0.f, gr1 = 0.f,
-                          gr2 = 0.f;
-                    bool contrib = false;
-                    if (!done) {
-                        if (kCount) ++n_eval;
-                        const float4 A = srec[j].a;
-                        const float4 B = srec[j].b;
-                        const float dx = pcx - A.x, dy = pcy - A.y;
-                        const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
-                        const float d2 = fmaf(u1, u1, u2 * u2);
-                        const float bx = dx * vp.ifx, by = dy * vp.ify;
-                        bool pass = d2 <= tm2 && fmaf(bx, bx, by * by) <= fabsf(A.w);
-                        if (pass && A.w < 0.f)
-                            pass = in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
-                        if (pass) {
-                            const float G = ex2_approx(d2 * kNegHalfLog2e);
-                            const float raw = A.z * G;
-                            const float sig = fminf(raw, vp.alpha_max);
-                            if (sig >= vp.alpha_min) {
-                                contrib = true;
-                                if (kCount) ++n_contrib;
-                                const float4 Cc = srec[j].c;
-                                const float w = sig * T;
-                                const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
-                                acc = fmaf(w, grgb, acc);
-                                const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
-                                gr0 = gC0 * w;
-                                gr1 = gC1 * w;
-                                gr2 = gC2 * w;
-                                if (raw < vp.alpha_max) {
-                                    gal = dsig * G;
-                                    const float gd2 = -0.5f * sig * dsig;
-                                    ga = gd2 * dx * dx;
-                                    gb = gd2 * 2.f * dx * dy;
-                                    gc = gd2 * dy * dy;
-                                    // d(d2)/d(mean) = -2 Q delta, Q delta = L^T (u1, u2)
-                                    gmx = -2.f * gd2 * (B.x * u1);
-                                    gmy = -2.f * gd2 * fmaf(B.y, u1, B.z * u2);
-                                }
-                                T = fmaf(-sig, T, T);
-                                if (T < vp.eps_T) done = true;
-                            }
-                        }
+                    // the forward's arithmetic, then the adjoint of the pair with the same
+                    // predicate (a pair that fails gets sigma = 0 and zero gradients)
+                    const float4 A = srec[j].a;
+                    const float4 B = srec[j].b;
+                    const float dx = pcx - A.x, dy = pcy - A.y;
+                    const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
+                    const float d2 = fmaf(u1, u1, u2 * u2);
+                    const float bx = dx * vp.ifx, by = dy * vp.ify;
+                    bool ok = !done && d2 <= tm2 && fmaf(bx, bx, by * by) <= fabsf(A.w);
+                    if (A.w < 0.f)   // uniform across the warp: one record
+                        ok = ok && in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
+                    const float G = ex2_approx(d2 * kNegHalfLog2e);
+                    const float raw = A.z * G;
+                    float sig = fminf(raw, vp.alpha_max);
+                    ok = ok && sig >= vp.alpha_min;
+                    if (kCount && !done) {
+                        ++n_eval;
+                        n_contrib += ok;
                     }
+                    sig = ok ? sig : 0.f;
+                    const float4 Cc = srec[j].c;
+                    const float w = sig * T;
+                    const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
+                    acc = fmaf(w, grgb, acc);
+                    const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
+                    const float gr0 = gC0 * w, gr1 = gC1 * w, gr2 = gC2 * w;
+                    const float ds = (ok && raw < vp.alpha_max) ? dsig : 0.f;
+                    const float gal = ds * G;
+                    const float gd2 = -0.5f * sig * ds;
+                    const float ga = gd2 * dx * dx, gb = gd2 * 2.f * dx * dy, gc = gd2 * dy * dy;
+                    // d(d2)/d(mean) = -2 Q delta, Q delta = L^T (u1, u2)
+                    const float gmx = -2.f * gd2 * (B.x * u1);
+                    const float gmy = -2.f * gd2 * fmaf(B.y, u1, B.z * u2);
+                    T = fmaf(-sig, T, T);
+                    done = done || T < vp.eps_T;
+                    const bool contrib = ok;
                     if (__any_sync(0xffffffffu, contrib)) {
                         float v[16] = {gmx, gmy, ga, gb, gc, gal, gr0, gr1, gr2, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         const float tot = warp_reduce16(v, lane);
