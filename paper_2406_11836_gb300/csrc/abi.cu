@@ -598,8 +598,8 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
 int rgs_profile_enable(int flags) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if ((flags & 2) && !g_prof.dev_pairs) {
-        RGS_CUDA_TRY(cudaMalloc(&g_prof.dev_pairs, 8 * sizeof(unsigned long long)));
-        RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
+        RGS_CUDA_TRY(cudaMalloc(&g_prof.dev_pairs, 16 * sizeof(unsigned long long)));
+        RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 16 * sizeof(unsigned long long)));
     }
     g_prof.on = (flags & 1) != 0;
     g_prof.count = (flags & 2) != 0;
@@ -626,14 +626,14 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
         if (ms_host) ms_host[i] = g_prof.ms[i];
         if (launches_host) launches_host[i] = g_prof.launches[i];
     }
-    unsigned long long pairs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long pairs[16] = {};
     if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemcpy(pairs, g_prof.dev_pairs, sizeof pairs, cudaMemcpyDeviceToHost));
     if (counters_host) {
         for (int i = 0; i < 4; ++i) counters_host[i] = (int64_t)pairs[i];
         counters_host[4] = g_prof.host_counts[0];
         counters_host[5] = g_prof.host_counts[1];
         counters_host[6] = g_launches.load();
-        for (int i = 0; i < 4; ++i) counters_host[7 + i] = (int64_t)pairs[4 + i];
+        for (int i = 0; i < 6; ++i) counters_host[7 + i] = (int64_t)pairs[4 + i];
     }
     if (reset) {
         for (int i = 0; i < ST_COUNT; ++i) {
@@ -642,7 +642,7 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
         }
         g_prof.host_counts[0] = g_prof.host_counts[1] = 0;
         g_launches.store(0);
-        if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 8 * sizeof(unsigned long long)));
+        if (g_prof.dev_pairs) RGS_CUDA_TRY(cudaMemset(g_prof.dev_pairs, 0, 16 * sizeof(unsigned long long)));
     }
     return RGS_OK;
 }

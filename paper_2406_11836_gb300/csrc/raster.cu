@@ -236,7 +236,8 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ LeafPath lp;
-    uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0;
+    __shared__ uint32_t sused[kBlendThreads];
+    uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0, n_staged = 0, n_used = 0;
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
@@ -272,6 +273,10 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 }
                 srec[threadIdx.x] = sr;
                 smask[threadIdx.x] = msk;
+                if (kCount) {
+                    sused[threadIdx.x] = 0;
+                    ++n_staged;
+                }
             }
             __syncthreads();
             for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
@@ -305,6 +310,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                         n_ball += in_ell && !in_ball;
                         n_leaf += in_ell && in_ball && !in_sub;
                         n_contrib += ok;
+                        if (ok) sused[j] = 1;
                     }
                     sig = ok ? sig : 0.f;
                     const float4 Cc = srec[j].c;
@@ -315,6 +321,10 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                     T = fmaf(-sig, T, T);
                     done = done || T < vp.eps_T;
                 }
+            }
+            if (kCount) {
+                __syncthreads();
+                if ((int)threadIdx.x < nb) n_used += sused[threadIdx.x];
             }
             if (__syncthreads_count(done) == kBlendThreads) break;
         }
@@ -341,6 +351,8 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         count_add(pairs + 5, n_ball);
         count_add(pairs + 6, n_leaf);
         count_add(pairs + 7, n_strad);
+        count_add(pairs + 8, n_staged);
+        count_add(pairs + 9, n_used);
     }
 }
 
