@@ -154,13 +154,17 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
  * Writes partial_C [K,3,H,W] and partial_T [K,H,W] (a subset a ray never meets gets
  * C = 0, T = 1).  If `image` [3,H,W] is non-NULL the partials are also merged in view
  * order (Eq. 5) with the background behind, and T_final [H,W] (nullable) receives the
- * product of all T_k.  Synchronises once with `stream` to size the instance buffers.
+ * product of all T_k.  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
+ * by tile then by the subset's position in rgs_view_order, receives per (tile, subset) the
+ * camera depth of the last splat blended before every pixel of the tile had dropped below
+ * eps_T in that subset (+inf if that did not happen); rgs_render_bwd uses it to skip
+ * splats that cannot matter.  Synchronises once with `stream` to size the instance buffers.
  * Errors: EINVAL (shapes, sh_degree, tile != 16, L > 6 for rendering, non-finite camera,
  * misaligned pointers), EOVERFLOW (workspace too small; required size via
  * rgs_last_required_workspace()), ECUDA. */
 int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                   float* partial_C, float* partial_T, float* image, float* T_final, void* workspace,
-                   size_t ws_bytes, void* stream);
+                   float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                   void* workspace, size_t ws_bytes, void* stream);
 
 /* Eq. 5 over caller-owned partial maps: image = sum_r C_{o_r} prod_{m<r} T_{o_m} +
  * bg * prod_m T_m.  order_dev [K] int32 (device) lists the subsets front to back.
@@ -181,10 +185,12 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
  * and pulls the per-splat 2D gradients back through the projection.  Gradients are
  * accumulated into `grads` (same shapes as the parameters; the caller zeroes them).  A
  * splat shared by several subsets accumulates into its single parameter slot.
- * partial_C/partial_T must be the ones rgs_render_fwd wrote for the same inputs.
+ * partial_C/partial_T (and tile_depth when non-NULL) must be the ones rgs_render_fwd wrote
+ * for the same inputs; with tile_depth the re-derived lists omit the splats lying behind
+ * a (tile, subset) the forward had already saturated, which changes no result.
  * Synchronises once with `stream`.  Errors as rgs_render_fwd. */
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                   const float* partial_C, const float* partial_T, const float* dL_dimage,
+                   const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
                    const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ Adam (Sec. 4 details)

@@ -253,6 +253,7 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.ioff = (uint32_t*)take(4 * N);
     t.counters = (unsigned long long*)take(64);
     t.ranges = (uint2*)take(sizeof(uint2) * tiles * K);
+    t.cull_chunk = (float2*)take(sizeof(float2) * (size_t)tiles * K / 16 + sizeof(float2) * 2048 * K);
     t.ikey = (uint32_t*)take(4 * inst_cap);
     t.ival = (uint32_t*)take(4 * inst_cap);
     t.ikey_alt = (uint32_t*)take(4 * inst_cap);
@@ -279,7 +280,7 @@ thread_local PinnedCounters g_pinned;
 // payloads in blend order.
 int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                 void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
-                const uint32_t** sorted_ival) {
+                const uint32_t** sorted_ival, const float* cull) {
     int rc;
     if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
     if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
@@ -305,6 +306,11 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         if (layout(nullptr, N, tiles, vp->K, mid, nullptr) <= ws_bytes) lo = mid; else hi = mid - 1;
     }
     layout((char*)workspace, N, tiles, vp->K, lo, b);
+    b->cull = cull;
+    if (cull) {
+        rc = launch_cull_chunks(*vp, cull, b->cull_chunk, s);
+        if (rc) return rc;
+    }
 
     RGS_CUDA_TRY(cudaMemsetAsync(b->counters, 0, 64, s));
     {
@@ -510,22 +516,22 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
 }
 
 int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                   float* partial_C, float* partial_T, float* image, float* T_final, void* workspace, size_t ws_bytes,
-                   void* stream) {
+                   float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                   void* workspace, size_t ws_bytes, void* stream) {
     if (!partial_C || !partial_T) { set_error("render_fwd: partial maps are required"); return RGS_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     ViewParams vp;
     TreeParams tp;
     RasterBuffers b;
     const uint32_t* ival = nullptr;
-    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival);
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr);
     if (rc) return rc;
     ProfScope ps(ST_BLEND_FWD, s);
-    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, s);
+    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s);
 }
 
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                   const float* partial_C, const float* partial_T, const float* dL_dimage,
+                   const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
                    const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream) {
     if (!partial_C || !partial_T || !dL_dimage || !grads || !grads->means || !grads->log_scales || !grads->quats ||
         !grads->opacity_logits || !grads->sh) {
@@ -538,7 +544,7 @@ int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* c
     TreeParams tp;
     RasterBuffers b;
     const uint32_t* ival = nullptr;
-    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival);
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, tile_depth);
     if (rc) return rc;
     {
         ProfScope ps(ST_BLEND_BWD, s);

@@ -205,11 +205,47 @@ __device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& 
     }
 }
 
+// Depth culling of the backward's instances: `cull` ([tiles, K] by view rank, nullptr:
+// keep all) holds, per (tile, subset), the depth of the last splat the forward staged
+// before every pixel of the tile was done in that subset (+inf if that never happened).
+// A deeper instance cannot change any pixel, in the forward or in its replay.  `chunk`
+// holds the (min, max) of `cull` over runs of kCullChunk tiles of a row, so most of a
+// long span is kept or dropped without reading every tile.
+constexpr int kCullChunk = 16;
+
+__device__ __forceinline__ bool keep_tile(const float* __restrict__ cull, const ViewParams& vp, int ty, int c, int rank,
+                                          float z) {
+    return !cull || z <= cull[((size_t)ty * vp.tiles_x + c) * vp.K + rank];
+}
+
+__device__ __forceinline__ int cull_nchunk(const ViewParams& vp) { return (vp.tiles_x + kCullChunk - 1) / kCullChunk; }
+
+// Number of tiles of [c0, c1] in row ty kept for a splat at depth z in subset `rank`.
+__device__ __forceinline__ uint32_t kept_tiles(const float* __restrict__ cull, const float2* __restrict__ chunk,
+                                               const ViewParams& vp, int ty, int c0, int c1, int rank, float z) {
+    if (c0 > c1) return 0u;
+    if (!cull) return (uint32_t)(c1 - c0 + 1);
+    const int nch = cull_nchunk(vp);
+    uint32_t n = 0;
+    for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+        const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+        const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
+        if (z > mm.y) continue;
+        if (z <= mm.x) {
+            n += (uint32_t)(hi - lo + 1);
+            continue;
+        }
+        for (int c = lo; c <= hi; ++c) n += keep_tile(cull, vp, ty, c, rank, z);
+    }
+    return n;
+}
+
 __device__ __forceinline__ uint32_t item_tiles(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
-                                               unsigned long long mask, int nsub, float z, int ty0, int rows, int it) {
+                                               unsigned long long mask, int nsub, float z, int ty0, int rows, int it,
+                                               const float* __restrict__ cull, const float2* __restrict__ chunk) {
     int ty, k, c0, c1;
     item_span(f, vp, tp, mask, nsub, z, ty0, rows, it, ty, k, c0, c1);
-    return c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+    return kept_tiles(cull, chunk, vp, ty, c0, c1, vp.rank_of[k], z);
 }
 
 }  // namespace rgs

@@ -329,7 +329,7 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
     uint32_t count = 0;
     if (cand && items <= kWarpCountItems) {
         const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
-        for (int it = 0; it < items; ++it) count += item_tiles(f, vp, tp, mask, nsub, z, ty0, rows, it);
+        for (int it = 0; it < items; ++it) count += item_tiles(f, vp, tp, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
     }
     unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
     while (big) {
@@ -345,7 +345,7 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         const Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
         const int ns = __popcll(m_);
         uint32_t acc = 0;
-        for (int it = lane; it < items_; it += 32) acc += item_tiles(f, vp, tp, m_, ns, z_, t0_, rows_, it);
+        for (int it = lane; it < items_; it += 32) acc += item_tiles(f, vp, tp, m_, ns, z_, t0_, rows_, it, b.cull, b.cull_chunk);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == src) count = acc;
     }

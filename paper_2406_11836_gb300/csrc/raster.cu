@@ -52,8 +52,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 __global__ void __launch_bounds__(256)
 emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
-            const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, uint32_t* __restrict__ ikey,
-            uint32_t* __restrict__ ival) {
+            const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
+            const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -76,21 +76,55 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
                 item_span(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
                 rank = (uint32_t)vp.rank_of[k];
             }
-            const uint32_t w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+            const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, r2.w);
             uint32_t incl = w;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            const uint32_t pos = base + incl - w;
-            const uint32_t first = (uint32_t)(ty * vp.tiles_x + c0);
-            for (uint32_t t = 0; t < w; ++t) {
-                ikey[pos + t] = ((first + t) << vp.L) | rank;
-                ival[pos + t] = id;
+            uint32_t pos = base + incl - w;
+            const uint32_t first = (uint32_t)(ty * vp.tiles_x);
+            if (w && !cull) {
+                for (int c = c0; c <= c1; ++c, ++pos) {
+                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                    ival[pos] = id;
+                }
+            } else if (w) {
+                const int nch = cull_nchunk(vp);
+                for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+                    const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+                    const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
+                    if (r2.w > mm.y) continue;
+                    const bool all = r2.w <= mm.x;
+                    for (int c = lo; c <= hi; ++c) {
+                        if (!all && !keep_tile(cull, vp, ty, c, (int)rank, r2.w)) continue;
+                        ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                        ival[pos] = id;
+                        ++pos;
+                    }
+                }
             }
             base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
+}
+
+// (min, max) of the forward depth table over each run of kCullChunk tiles of a row.
+__global__ void cull_chunk_kernel(ViewParams vp, const float* __restrict__ cull, float2* __restrict__ chunk) {
+    const int nch = cull_nchunk(vp);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)vp.tiles_y * nch * vp.K;
+    if (i >= total) return;
+    const int rank = (int)(i % vp.K);
+    const int ch = (int)((i / vp.K) % nch);
+    const int ty = (int)(i / ((int64_t)vp.K * nch));
+    float lo = __int_as_float(0x7f800000), hi = -lo;
+    for (int c = ch * kCullChunk; c < min(vp.tiles_x, (ch + 1) * kCullChunk); ++c) {
+        const float d = cull[((size_t)ty * vp.tiles_x + c) * vp.K + rank];
+        lo = fminf(lo, d);
+        hi = fmaxf(hi, d);
+    }
+    chunk[i] = make_float2(lo, hi);
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
@@ -231,7 +265,8 @@ template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
-                 float* __restrict__ image, float* __restrict__ Tfin, unsigned long long* __restrict__ pairs) {
+                 float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth,
+                 unsigned long long* __restrict__ pairs) {
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -259,6 +294,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         const uint2 rg = ranges[(size_t)tile * vp.K + r];
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
         bool done = !inside;
+        float zsat = __int_as_float(0x7f800000);   // +inf: the subset never saturated the tile
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
@@ -326,8 +362,12 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 __syncthreads();
                 if ((int)threadIdx.x < nb) n_used += sused[threadIdx.x];
             }
-            if (__syncthreads_count(done) == kBlendThreads) break;
+            if (__syncthreads_count(done) == kBlendThreads) {
+                zsat = srec[nb - 1].b.w;   // depth of the last instance staged
+                break;
+            }
         }
+        if (tile_depth && threadIdx.x == 0) tile_depth[(size_t)tile * vp.K + r] = zsat;
         if (inside) {
             pC[((size_t)k * 3 + 0) * HW + pix] = C0;
             pC[((size_t)k * 3 + 1) * HW + pix] = C1;
@@ -599,7 +639,14 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     if (n_vis <= 0) return RGS_OK;
     const int64_t want = (n_vis + 7) / 8;          // one warp per splat
     unsigned grid = (unsigned)(want < (1 << 20) ? want : (1 << 20));
-    emit_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.ikey, b.ival);
+    emit_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s) {
+    const int64_t total = (int64_t)vp.tiles_y * ((vp.tiles_x + kCullChunk - 1) / kCullChunk) * vp.K;
+    cull_chunk_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(vp, cull, chunk);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -613,15 +660,16 @@ int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_rang
 }
 
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s) {
+                     float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                     cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
     unsigned long long* pairs = prof_pair_counters();
     if (pairs)
         blend_fwd_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
-                                                              T_final, pairs);
+                                                              T_final, tile_depth, pairs);
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                               image, T_final, nullptr);
+                                                               image, T_final, tile_depth, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

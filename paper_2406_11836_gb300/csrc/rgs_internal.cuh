@@ -127,6 +127,8 @@ struct RasterBuffers {
     float4* g2d;          // [N * 3] (backward only)
     // per (tile, subset)
     uint2* ranges;        // [tiles * K]
+    const float* cull;    // [tiles * K] forward depth table (backward only; nullptr: no culling)
+    float2* cull_chunk;   // [tiles_y * ceil(tiles_x / 16) * K] (min, max) of `cull` over 16-tile chunks
     // per instance
     uint32_t* ikey;
     uint32_t* ival;
@@ -145,8 +147,10 @@ int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, con
 int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
                 int64_t n_vis, cudaStream_t s);
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
+int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s);
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     float* partial_C, float* partial_T, float* image, float* T_final, cudaStream_t s);
+                     float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                     cudaStream_t s);
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      const float* partial_C, const float* partial_T, const float* dL_dimage, cudaStream_t s);
 int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],

@@ -34,20 +34,21 @@ class RetinaGSRender(torch.autograd.Function):
         g = rgs.gaussians_c(means, log_scales, quats, opacity_logits, sh, rc.sh_degree)
         out = rgs.render_fwd(rc.kd, g, rc.cam, rc.opts, rc.ws, image=True)
         ctx.rc = rc
-        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, out["partial_C"], out["partial_T"])
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh, out["partial_C"], out["partial_T"],
+                              out["tile_depth"])
         rc.last = out
         ctx.mark_non_differentiable(out["partial_C"], out["partial_T"], out["T_final"])
         return out["image"], out["partial_C"], out["partial_T"], out["T_final"]
 
     @staticmethod
     def backward(ctx, g_image, g_pc, g_pt, g_tf):
-        means, log_scales, quats, opacity_logits, sh, pc, pt = ctx.saved_tensors
+        means, log_scales, quats, opacity_logits, sh, pc, pt, td = ctx.saved_tensors
         rc = ctx.rc
         grads = tuple(torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh))
         if g_image is None:
             return (*grads, None)
         g = rgs.gaussians_c(means, log_scales, quats, opacity_logits, sh, rc.sh_degree)
-        rgs.render_bwd(rc.kd, g, rc.cam, rc.opts, pc, pt, g_image.contiguous(), grads, rc.ws)
+        rgs.render_bwd(rc.kd, g, rc.cam, rc.opts, pc, pt, g_image.contiguous(), grads, rc.ws, tile_depth=td)
         return (*grads, None)
 
 
@@ -159,7 +160,8 @@ class Trainer:
         diff = img - target
         loss = diff.abs().mean() if return_loss else None
         dL = torch.sign(diff).div_(float(diff.numel()))
-        rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws)
+        rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws,
+                       tile_depth=out["tile_depth"])
         self.step_count += 1
         rgs.adam_step(self.flat, self.grad, self.m, self.v, self.seg, self.lrs(self.step_count), self.step_count,
                       zero_grad=True)

@@ -71,9 +71,9 @@ def lib():
     L.rgs_render_workspace_size.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts),
                                             c_int64, POINTER(c_size_t)]
     L.rgs_render_fwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
-                                 c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
     L.rgs_render_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
-                                 c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
+                                 c_void_p, c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_merge_partials.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_void_p]
     L.rgs_merge_partials_bwd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -240,7 +240,9 @@ def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image
     H, W = int(cam.height), int(cam.width)
     dev = torch.device("cuda", torch.cuda.current_device())
     if out is None:
-        out = {"partial_C": torch.empty(kd.K, 3, H, W, device=dev), "partial_T": torch.empty(kd.K, H, W, device=dev)}
+        tiles = ((H + 15) // 16) * ((W + 15) // 16)
+        out = {"partial_C": torch.empty(kd.K, 3, H, W, device=dev), "partial_T": torch.empty(kd.K, H, W, device=dev),
+               "tile_depth": torch.empty(tiles, kd.K, device=dev)}
         if image:
             out["image"] = torch.empty(3, H, W, device=dev)
             out["T_final"] = torch.empty(H, W, device=dev)
@@ -248,20 +250,22 @@ def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image
     s = _stream(stream)
     _retry(lambda: lib().rgs_render_fwd(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
                                         _ptr(out["partial_C"]), _ptr(out["partial_T"]), _ptr(out.get("image")),
-                                        _ptr(out.get("T_final")), ws.ptr(), ws.nbytes, s), ws)
+                                        _ptr(out.get("T_final")), _ptr(out.get("tile_depth")), ws.ptr(), ws.nbytes,
+                                        s), ws)
     return out
 
 
 def render_bwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, partial_C, partial_T, dL_dimage, grads, ws: Workspace,
-               stream=None):
-    """Accumulate dL/d(params) into grads = (means, log_scales, quats, opacity_logits, sh) tensors."""
+               stream=None, tile_depth=None):
+    """Accumulate dL/d(params) into grads = (means, log_scales, quats, opacity_logits, sh) tensors.
+    `tile_depth` is the forward's per-(tile, subset) saturation depth (optional)."""
     gg = GaussianGrads(*(_ptr(t) for t in grads))
     c = camera_c(cam)
     s = _stream(stream)
     dL = dL_dimage.contiguous()
     _retry(lambda: lib().rgs_render_bwd(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
-                                        _ptr(partial_C), _ptr(partial_T), _ptr(dL), ctypes.byref(gg), ws.ptr(),
-                                        ws.nbytes, s), ws)
+                                        _ptr(partial_C), _ptr(partial_T), _ptr(dL), _ptr(tile_depth), ctypes.byref(gg),
+                                        ws.ptr(), ws.nbytes, s), ws)
 
 
 def merge_partials(partial_C, partial_T, order, bg=(0.0, 0.0, 0.0), stream=None):

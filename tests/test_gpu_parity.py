@@ -348,3 +348,37 @@ def test_checkpoint_resume_reproduces_next_step(R, tmp_path):
     # additions (and the last bits of the update) may differ
     diff = (a.flat - b.flat).abs().max().item()
     assert diff <= 1e-5, diff
+
+
+def test_backward_depth_culling_changes_nothing(R):
+    """The forward's per-(tile, subset) saturation depths let the backward drop splats
+    behind saturated tiles: same gradients (up to the order of atomic additions), fewer
+    instances."""
+    scene = W.uniform_cube_scene(30_000, seed=51, log_scale_mean=-2.6, sh_degree=1)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 2)
+    cam = W.look_at((0.2, -2.6, 0.3), (0, 0, 0), 160, 112)
+    opts = R.default_opts()
+    ws = R.Workspace()
+    g = R.scene_c(dev)
+    out = R.render_fwd(kd, g, cam, opts, ws)
+    td = out["tile_depth"]
+    assert torch.isfinite(td).sum() > 0          # some (tile, subset) saturated
+    dL = torch.randn(3, 112, 160, device="cuda") * 1e-3
+
+    def grads(tile_depth):
+        gr = tuple(torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh))
+        R.profile_enable(timing=False, counters=True)
+        R.profile_read(reset=True)
+        R.render_bwd(kd, g, cam, opts, out["partial_C"], out["partial_T"], dL, gr, ws, tile_depth=tile_depth)
+        torch.cuda.synchronize()
+        c = R.profile_read(reset=True)["counters"]
+        R.profile_enable(False, False)
+        return gr, c["instances"], c["bwd_contrib"]
+
+    full, n_full, c_full = grads(None)
+    cut, n_cut, c_cut = grads(td)
+    assert n_cut < 0.8 * n_full, (n_cut, n_full)
+    assert c_cut == c_full
+    for a, b in zip(cut, full):
+        assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) <= 1e-5
