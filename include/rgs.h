@@ -166,6 +166,20 @@ int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* c
                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
                    void* workspace, size_t ws_bytes, void* stream);
 
+/* rgs_render_fwd for callers that cannot allocate device memory (the paper has no
+ * counterpart: this is a deployment variant).  Same arguments and results as
+ * rgs_render_fwd minus the workspace, which comes from a fixed 64 MiB device array
+ * inside the library; nothing is allocated.
+ * The first call on a device looks the array up (make it before any stream capture);
+ * every GPU that loads the library holds the array until exit.  All calls share it:
+ * calls that overlap on the GPU race and must be serialised by the caller.  A render
+ * whose workspace exceeds the array returns RGS_EOVERFLOW with the needed size in
+ * rgs_last_error() (roughly 150 bytes per splat plus 16 per tile instance).  Tracing
+ * records no events for this call. */
+int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                           const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
+                           float* T_final, float* tile_depth, void* stream);
+
 /* Eq. 5 over caller-owned partial maps: image = sum_r C_{o_r} prod_{m<r} T_{o_m} +
  * bg * prod_m T_m.  order_dev [K] int32 (device) lists the subsets front to back.
  * partial_C [K,3,H,W], partial_T [K,H,W], image [3,H,W], T_out [H,W] (nullable). */

@@ -65,7 +65,13 @@ struct Profiler {
 Profiler g_prof;
 }  // namespace
 
+namespace {
+thread_local bool g_prof_suppress = false;   // set only while a render must not create events
+}
+void prof_suppress(bool on) { g_prof_suppress = on; }
+
 ProfScope::ProfScope(int stage, cudaStream_t st) : token(-1), s(st) {
+    if (g_prof_suppress) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on) return;
     Profiler::Rec r{stage, g_prof.take(), g_prof.take()};
@@ -280,7 +286,7 @@ thread_local PinnedCounters g_pinned;
 // payloads in blend order.
 int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                 void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
-                const uint32_t** sorted_ival, const float* cull) {
+                const uint32_t** sorted_ival, const float* cull, unsigned long long* host_counters = nullptr) {
     int rc;
     if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
     if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
@@ -318,11 +324,15 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         rc = launch_project_fwd(*g, *vp, *tp, *b, s);
     }
     if (rc) return rc;
-    if (!g_pinned.h) RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
-    RGS_CUDA_TRY(cudaMemcpyAsync(g_pinned.h, b->counters, 16, cudaMemcpyDeviceToHost, s));
+    unsigned long long* hc = host_counters;
+    if (!hc) {
+        if (!g_pinned.h) RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
+        hc = g_pinned.h;
+    }
+    RGS_CUDA_TRY(cudaMemcpyAsync(hc, b->counters, 16, cudaMemcpyDeviceToHost, s));
     RGS_CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t I = (int64_t)g_pinned.h[0];
-    const int64_t n_vis = (int64_t)g_pinned.h[1];
+    const int64_t I = (int64_t)hc[0];
+    const int64_t n_vis = (int64_t)hc[1];
     if (I > 0xFFFFFFFFll - 1) {
         set_error("render: %lld tile instances exceed the 32-bit instance index", (long long)I);
         return RGS_EOVERFLOW;
@@ -373,6 +383,21 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
 }
 
 }  // namespace
+
+int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters) {
+    if (!partial_C || !partial_T) { set_error("render_fwd: partial maps are required"); return RGS_EINVAL; }
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, host_counters);
+    if (rc) return rc;
+    ProfScope ps(ST_BLEND_FWD, s);
+    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s);
+}
+
 }  // namespace rgs
 
 using namespace rgs;
@@ -518,16 +543,8 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
 int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
                    void* workspace, size_t ws_bytes, void* stream) {
-    if (!partial_C || !partial_T) { set_error("render_fwd: partial maps are required"); return RGS_EINVAL; }
-    cudaStream_t s = (cudaStream_t)stream;
-    ViewParams vp;
-    TreeParams tp;
-    RasterBuffers b;
-    const uint32_t* ival = nullptr;
-    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr);
-    if (rc) return rc;
-    ProfScope ps(ST_BLEND_FWD, s);
-    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s);
+    return render_fwd_into(kd, g, cam, opts, partial_C, partial_T, image, T_final, tile_depth, workspace, ws_bytes,
+                           (cudaStream_t)stream, nullptr);
 }
 
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,

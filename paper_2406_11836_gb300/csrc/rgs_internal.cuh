@@ -72,6 +72,7 @@ struct ProfScope {
 unsigned long long* prof_pair_counters();
 void prof_add_host_counts(int64_t instances, int64_t visible);
 void count_launch();   // every kernel launch of the library (reported with the tracing counters)
+void prof_suppress(bool on);   // this thread's passes record no events while on
 
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
@@ -157,6 +158,12 @@ int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, 
                  float* image, float* T_out, cudaStream_t s);
 int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
                      const float* gI, const float* gT, float* dC, float* dT, cudaStream_t s);
+
+// Forward render into a caller-given workspace.  host_counters (2 x uint64, nullable)
+// receives the instance and visible-splat counts; NULL uses a pinned buffer of the library.
+int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters);
 
 // ------------------------------------------------------------------ KD (kd.cu)
 struct KdBuild {
