@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rgs_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "librgs_oracle.so")
 
-FLAG_TRUNC, FLAG_DEPTH, FLAG_SPLIT, FLAG_KINK = 1, 2, 4, 8
+FLAG_TRUNC, FLAG_DEPTH, FLAG_SPLIT, FLAG_KINK, FLAG_DEPTH_PART, FLAG_TRUNC_PART = 1, 2, 4, 8, 16, 32
 
 
 def build(force: bool = False) -> str:
@@ -73,8 +73,8 @@ class Opts:
     alpha_max: float = 0.99
     dilation: float = 0.3
     bg: tuple = (0.0, 0.0, 0.0)
-    flag_rel: float = 1e-5      # relative rounding margin of the truncation/plane ambiguity flags
-    flag_depth_rel: float = 1e-6  # relative margin for two contributors at (nearly) equal depth
+    flag_rel: float = 3e-6      # relative rounding margin of the truncation/plane ambiguity flags (~50 fp32 ulp)
+    flag_depth_rel: float = 1e-11  # relative margin for two contributors at (nearly) equal depth
 
     def vec(self) -> np.ndarray:
         f = lambda v: float(np.float32(v))

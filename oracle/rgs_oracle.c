@@ -44,10 +44,12 @@
  * Ambiguity flags.  A float32 implementation of the same definition may take a different
  * discrete decision when a decision quantity lies within rounding error of its threshold.
  * For each pixel the oracle reports which of those cases occur, with a relative margin
- * `flag_rel` (`flag_depth_rel` for depths): bit 1 truncation decision, bit 2 two
+ * `flag_rel` (`flag_depth_rel` for depths): bit 1 a truncation decision, bit 2 two
  * contributors at (nearly) equal depth, bit 4 x_i (nearly) on a split plane (affects the
  * partial maps only), bit 8 a kink of a clamp (sigma at alpha_max or a colour channel at
- * 0; affects gradients only).
+ * 0; affects gradients only).  Bits 1, 2 and 8 are set only where the decision can move
+ * the pixel (or its derivative) by more than 1e-5; bits 32 and 16 are bits 1 and 2 for
+ * the partial maps, which start every subset at T = 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,7 +60,10 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-enum { OR_FLAG_TRUNC = 1, OR_FLAG_DEPTH = 2, OR_FLAG_SPLIT = 4, OR_FLAG_KINK = 8 };
+enum {
+    OR_FLAG_TRUNC = 1, OR_FLAG_DEPTH = 2, OR_FLAG_SPLIT = 4, OR_FLAG_KINK = 8, OR_FLAG_DEPTH_PART = 16,
+    OR_FLAG_TRUNC_PART = 32
+};
 
 /* ------------------------------------------------------------------ inputs */
 typedef struct {
@@ -153,6 +158,7 @@ typedef struct {
     double qn[4], qnorm, s[3], Rq[3][3], Sigc[3][3], J[2][3];
     double bbox[4];               /* x0, x1, y0, y1 pixel-index bounds that can pass */
     double cond;                  /* eigenvalue ratio of Sigma' (>= 1) */
+    double zscale;                /* |R_z0 mu_0| + |R_z1 mu_1| + |R_z2 mu_2| + |t_z|: size of the terms of z */
 } proj_t;
 
 static void quat_to_rot(const double q[4], double R[3][3]) {
@@ -168,6 +174,8 @@ static void project_one(const scene_t* sc, int64_t i, const cam_t* cam, const op
     for (int r = 0; r < 3; ++r)
         P->p[r] = cam->R[r][0] * mu[0] + cam->R[r][1] * mu[1] + cam->R[r][2] * mu[2] + cam->t[r];
     double z = P->p[2];
+    P->zscale = fabs(cam->t[2]);
+    for (int j = 0; j < 3; ++j) P->zscale += fabs(cam->R[2][j] * mu[j]);
     /* D_i: three times the largest semi-axis (Sec. 3.3). */
     double smax = 0;
     for (int j = 0; j < 3; ++j) {
@@ -268,6 +276,7 @@ typedef struct {
     double z, sigma, G, d2, dx, dy, x[3];   /* x = x_i, the ray point at depth z_i */
     int clamped;                             /* alpha*G >= alpha_max */
     double amb;                              /* max_t q_t / margin_t of the decision */
+    int mark;                                /* 1: truncation ambiguous, 2: at a clamp's kink */
 } pair_t;
 
 /* Pixel ray direction in world coordinates with unit camera-z component:
@@ -551,13 +560,49 @@ static double* bbox_array(const proj_t* P, int64_t n) {
     return bb;
 }
 
-/* Gather the sorted contributors of pixel (px,py) and the pixel's ambiguity flags. */
+/* Eq. 2 applied to the sorted contributors v[m..n) and the background: the colour seen
+ * through everything in front of v[m]. */
+static void blend_behind(const proj_t* P, const pair_t* v, int64_t n, int64_t m, const opt_t* opt, double B[3]) {
+    double Tr = 1.0;
+    for (int ch = 0; ch < 3; ++ch) B[ch] = 0.0;
+    for (int64_t j = m; j < n; ++j) {
+        for (int ch = 0; ch < 3; ++ch) B[ch] += P[v[j].id].rgb[ch] * v[j].sigma * Tr;
+        Tr *= 1.0 - v[j].sigma;
+    }
+    for (int ch = 0; ch < 3; ++ch) B[ch] += Tr * opt->bg[ch];
+}
+
+/* Largest channel of T sigma (c - B): the change of the pixel when a splat of colour c
+ * and opacity sigma, with transmittance T in front and B behind it, is added or removed. */
+static double presence_effect(const double c[3], double T, double sigma, const double B[3]) {
+    double m = 0;
+    for (int ch = 0; ch < 3; ++ch) {
+        double d = fabs(c[ch] - B[ch]);
+        if (d > m) m = d;
+    }
+    return T * sigma * m;
+}
+
+/* Gather the sorted contributors of pixel (px,py) and the pixel's ambiguity flags.
+ *
+ * A decision that rounding can flip matters only as far as it can move the pixel.  Adding
+ * or removing splat j changes the colour by T_j sigma_j (c_j - B_j), with T_j the
+ * transmittance in front of it and B_j the blend behind it; swapping adjacent contributors
+ * j, j+1 changes it by T_j sigma_j sigma_{j+1} (c_j - c_{j+1}); a clamp's kink changes
+ * the pixel's derivative by T_j sigma_j at most.  Image and gradient flags are set only
+ * where such a change can exceed OR_FLAG_EFFECT; the *_PART bits are set without that
+ * test (truncation) or with T_j taken as 1 (depth), since each partial map (Eq. 3-4)
+ * starts its own subset at T = 1. */
+#define OR_FLAG_EFFECT 1e-5
+#define OR_MAX_EXCLUDED_AMB 64
 static int gather_pixel(const proj_t* P, const double* bb, int64_t n, const cam_t* cam, const opt_t* opt, int px,
                         int py, int brute, plist_t* out) {
     int flags = 0;
     double dray[3];
     pixel_ray(cam, px, py, dray);
     out->n = 0;
+    pair_t excl[OR_MAX_EXCLUDED_AMB];           /* ambiguous pairs that were left out */
+    int nexcl = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (!brute) {
             const double* b = bb + 4 * i;
@@ -567,18 +612,58 @@ static int gather_pixel(const proj_t* P, const double* bb, int64_t n, const cam_
         if (!s->visible) continue;
         pair_t pr;
         int c = eval_pair(s, i, cam, opt, px, py, dray, &pr);
-        if (pr.amb > -1.0 && pr.amb < 1.0) flags |= OR_FLAG_TRUNC;
+        pr.mark = 0;
+        if (pr.amb > -1.0 && pr.amb < 1.0) {
+            flags |= OR_FLAG_TRUNC_PART;
+            pr.mark |= 1;
+            if (!c) {
+                if (nexcl < OR_MAX_EXCLUDED_AMB) excl[nexcl++] = pr;   /* with the sigma it would have */
+                else flags |= OR_FLAG_TRUNC;
+            }
+        }
         if (c) {
-            plist_push(out, &pr);
             double a = opt->alpha_max, raw = s->alpha * pr.G;
-            if (fabs(raw - a) <= opt->flag_rel * a) flags |= OR_FLAG_KINK;
+            if (fabs(raw - a) <= opt->flag_rel * a) pr.mark |= 2;
             for (int ch = 0; ch < 3; ++ch)
-                if (fabs(s->rgb_raw[ch]) <= opt->flag_rel) flags |= OR_FLAG_KINK;
+                if (fabs(s->rgb_raw[ch]) <= opt->flag_rel) pr.mark |= 2;
+            plist_push(out, &pr);
         }
     }
     qsort(out->v, (size_t)out->n, sizeof(pair_t), cmp_pair);
-    for (int64_t j = 1; j < out->n; ++j)
-        if (out->v[j].z - out->v[j - 1].z <= opt->flag_depth_rel * out->v[j].z) flags |= OR_FLAG_DEPTH;
+    double Tr = 1.0, B[3];
+    for (int64_t j = 0; j < out->n; ++j) {
+        const pair_t* a = &out->v[j];
+        if (a->mark & 1) {
+            blend_behind(P, out->v, out->n, j + 1, opt, B);
+            if (presence_effect(P[a->id].rgb, Tr, a->sigma, B) > OR_FLAG_EFFECT) flags |= OR_FLAG_TRUNC;
+        }
+        if ((a->mark & 2) && Tr * a->sigma > OR_FLAG_EFFECT) flags |= OR_FLAG_KINK;
+        if (j + 1 < out->n) {
+            const pair_t* b = &out->v[j + 1];
+            /* margin relative to z and to the size of the terms that sum to z */
+            double zs = b->z > P[a->id].zscale ? b->z : P[a->id].zscale;
+            if (P[b->id].zscale > zs) zs = P[b->id].zscale;
+            if (b->z - a->z <= opt->flag_depth_rel * zs) {
+                double dc = 0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    double d = fabs(P[a->id].rgb[ch] - P[b->id].rgb[ch]);
+                    if (d > dc) dc = d;
+                }
+                double swap = a->sigma * b->sigma * dc;
+                if (Tr * swap > OR_FLAG_EFFECT) flags |= OR_FLAG_DEPTH;
+                if (swap > OR_FLAG_EFFECT) flags |= OR_FLAG_DEPTH_PART;
+            }
+        }
+        Tr *= 1.0 - a->sigma;
+    }
+    for (int e = 0; e < nexcl; ++e) {
+        /* transmittance in front of the left-out pair and the blend behind it (Eq. 2 order) */
+        double Te = 1.0;
+        int64_t m = 0;
+        while (m < out->n && cmp_pair(&out->v[m], &excl[e]) < 0) Te *= 1.0 - out->v[m++].sigma;
+        blend_behind(P, out->v, out->n, m, opt, B);
+        if (presence_effect(P[excl[e].id].rgb, Te, excl[e].sigma, B) > OR_FLAG_EFFECT) flags |= OR_FLAG_TRUNC;
+    }
     return flags;
 }
 

@@ -109,13 +109,20 @@ void prof_add_host_counts(int64_t instances, int64_t visible) {
 namespace {
 
 __global__ void compact_kernel(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ pos,
-                               const uint32_t* __restrict__ dkey, int64_t n, uint32_t* __restrict__ skey,
+                               const uint32_t* __restrict__ dkey_lo, int64_t n, uint32_t* __restrict__ skey,
                                uint32_t* __restrict__ sid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || cnt[i] == 0) return;
     uint32_t p = pos[i];
-    skey[p] = dkey[i];
+    skey[p] = dkey_lo[i];
     sid[p] = (uint32_t)i;
+}
+
+// key[j] = dkey[id[j]]: the float bits of z in the order of the first (low-bits) pass.
+__global__ void gather_key_kernel(const uint32_t* __restrict__ dkey, const uint32_t* __restrict__ id, int64_t n,
+                                  uint32_t* __restrict__ key) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) key[j] = dkey[id[j]];
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
@@ -251,6 +258,7 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.rect = (ushort4*)take(8 * N);
     t.mask = (unsigned long long*)take(8 * N);
     t.dkey = (uint32_t*)take(4 * N);
+    t.dkey_lo = (uint32_t*)take(4 * N);
     t.vis_pos = (uint32_t*)take(4 * N);
     t.skey = (uint32_t*)take(4 * N);
     t.sid = (uint32_t*)take(4 * N);
@@ -348,16 +356,31 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         ProfScope ps(ST_COMPACT, s);
         rc = exclusive_scan_u32(b->cnt, b->vis_pos, N, 1, nullptr, b->temp, b->temp_bytes, s);
         if (rc) return rc;
-        compact_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(b->cnt, b->vis_pos, b->dkey, N, b->skey, b->sid);
+        compact_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(b->cnt, b->vis_pos, b->dkey_lo, N, b->skey,
+                                                                   b->sid);
         RGS_CUDA_LAUNCH_CHECK();
     }
+    // depth order as an LSD sort on (float bits of z, 16 bits below them): the low
+    // digits first, then stably the float bits (sign bit 0: 31 bits)
     bool alt = false;
+    const uint32_t* sorted_ids = nullptr;
     {
         ProfScope ps(ST_DEPTH_SORT, s);
-        rc = radix_sort_pairs(b->skey, b->sid, b->skey_alt, b->sid_alt, n_vis, 32, b->temp, b->temp_bytes, s, &alt);
+        rc = radix_sort_pairs(b->skey, b->sid, b->skey_alt, b->sid_alt, n_vis, 16, b->temp, b->temp_bytes, s, &alt);
         if (rc) return rc;
+        uint32_t* k1 = alt ? b->skey_alt : b->skey;
+        uint32_t* v1 = alt ? b->sid_alt : b->sid;
+        uint32_t* k2 = alt ? b->skey : b->skey_alt;
+        uint32_t* v2 = alt ? b->sid : b->sid_alt;
+        if (n_vis > 0) {
+            gather_key_kernel<<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(b->dkey, v1, n_vis, k1);
+            RGS_CUDA_LAUNCH_CHECK();
+        }
+        bool alt2 = false;
+        rc = radix_sort_pairs(k1, v1, k2, v2, n_vis, 31, b->temp, b->temp_bytes, s, &alt2);
+        if (rc) return rc;
+        sorted_ids = alt2 ? v2 : v1;
     }
-    const uint32_t* sorted_ids = alt ? b->sid_alt : b->sid;
     // instance offsets in depth order, emission, (tile, rank) sort, ranges
     {
         ProfScope ps(ST_OFFSETS, s);

@@ -178,12 +178,13 @@ __device__ __forceinline__ void load_splat(const rgs_gaussians& g, int64_t i, Sp
 // Camera-space centre with the compensated transform; returns z (hi) and the projected
 // centre as hi + lo pairs.
 __device__ __forceinline__ void project_centre(const ViewParams& vp, const float mu[3], float p[3], float& mxh,
-                                               float& mxl, float& myh, float& myl) {
+                                               float& mxl, float& myh, float& myl, float* z_lo = nullptr) {
     float xh, xl, yh, yl, zh, zl;
     dot3_plus(vp.R[0], mu[0], vp.R[1], mu[1], vp.R[2], mu[2], vp.t[0], xh, xl);
     dot3_plus(vp.R[3], mu[0], vp.R[4], mu[1], vp.R[5], mu[2], vp.t[1], yh, yl);
     dot3_plus(vp.R[6], mu[0], vp.R[7], mu[1], vp.R[8], mu[2], vp.t[2], zh, zl);
     p[0] = xh; p[1] = yh; p[2] = zh;
+    if (z_lo) *z_lo = zl;
     // u = x/z to about two floats: q + (x - q z)/z
     float qx = __fdiv_rn(xh, zh);
     float rx = __fmaf_rn(-qx, zh, xh);
@@ -259,6 +260,18 @@ __device__ __forceinline__ void ewa(const ViewParams& vp, const SplatIn& si, con
     P.alpha = 1.f / (1.f + __expf(-si.logit));
 }
 
+// Depth below the resolution of the float z = zh + zl (|zl| <= ulp(zh)/2): zl in units of
+// ulp(zh)/2^16, offset to [0, 2^16).  Sorting by this and then stably by the bits of zh
+// orders splats by z to about 2^-39 relative, so that splats whose depths round to the
+// same float still blend in the order of their exact depths.
+__device__ __forceinline__ uint32_t depth_fraction(float zh, float zl) {
+    const uint32_t e = (__float_as_uint(zh) >> 23) & 0xffu;
+    if (e < 24u) return 32768u;                                     // zh below 2^-103: no fraction
+    const float inv_ulp = __uint_as_float((277u - e) << 23);        // 2^(150 - e) = 1 / ulp(zh)
+    const int q = __float2int_rn(zl * inv_ulp * 65536.f) + 32768;  // exact power-of-two scalings
+    return (uint32_t)min(max(q, 0), 65535);
+}
+
 // ------------------------------------------------------------------ forward kernel
 constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are counted by the whole warp
 
@@ -276,8 +289,8 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
     if (i < g.n) {
         SplatIn si;
         load_splat(g, i, si);
-        float p[3], mxl, myl;
-        project_centre(vp, si.mu, p, mxh, mxl, myh, myl);
+        float p[3], mxl, myl, zl;
+        project_centre(vp, si.mu, p, mxh, mxl, myh, myl, &zl);
         z = p[2];
         const float smax = fmaxf(si.ls[0], fmaxf(si.ls[1], si.ls[2]));
         const float D = vp.trunc_mult * __expf(smax);
@@ -320,6 +333,7 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
                 b.rect[i] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
                 b.mask[i] = mask;
                 b.dkey[i] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
+                b.dkey_lo[i] = depth_fraction(z, zl);
             }
         }
     }

@@ -118,6 +118,7 @@ struct RasterBuffers {
     ushort4* rect;        // [N] tile rectangle (x0, y0, x1, y1), inclusive
     unsigned long long* mask;  // [N] subsets containing the splat
     uint32_t* dkey;       // [N] depth key (float bits of z)
+    uint32_t* dkey_lo;    // [N] 16 bits of depth below the float z (depth_fraction)
     uint32_t* vis_pos;    // [N] compaction positions
     uint32_t* skey;       // [N] compacted depth keys   (sort buffer a)
     uint32_t* sid;        // [N] compacted splat ids     (sort buffer a)

@@ -5,7 +5,7 @@ import torch
 from oracle import oracle as O
 
 FWD_FLAGS = O.FLAG_TRUNC | O.FLAG_DEPTH
-PART_FLAGS = O.FLAG_TRUNC | O.FLAG_DEPTH | O.FLAG_SPLIT
+PART_FLAGS = O.FLAG_TRUNC_PART | O.FLAG_DEPTH_PART | O.FLAG_SPLIT
 GRAD_FLAGS = O.FLAG_TRUNC | O.FLAG_DEPTH | O.FLAG_KINK
 
 PIXEL_TOL = 1e-4        # max abs pixel error, float32 path vs float64 oracle
