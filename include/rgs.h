@@ -154,7 +154,8 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
  * Writes partial_C [K,3,H,W] and partial_T [K,H,W] (a subset a ray never meets gets
  * C = 0, T = 1).  If `image` [3,H,W] is non-NULL the partials are also merged in view
  * order (Eq. 5) with the background behind, and T_final [H,W] (nullable) receives the
- * product of all T_k.  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
+ * product of all T_k.  partial_C and partial_T may both be NULL when image is non-NULL:
+ * a forward-only render that keeps the partials on chip (no rgs_render_bwd from it).  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
  * by tile then by the subset's position in rgs_view_order, receives per (tile, subset) the
  * camera depth of the last splat blended before every pixel of the tile had dropped below
  * eps_T in that subset (+inf if that did not happen); rgs_render_bwd uses it to skip
@@ -219,6 +220,86 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
 /* Exponential decay of the position learning rate, 1.6e-4 -> 1.6e-6 in the paper
  * (log-linear between lr_init at step 0 and lr_final at max_steps, then constant). */
 float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_final);
+
+/* ------------------------------------------------------------------ serving
+ * A render server keeps one scene resident (the caller's device parameters, which must
+ * stay allocated while the server lives; their values may change between requests) with
+ * its KD subsets, and renders forward-only requests (Sec. 3.2 and Eq. 5; image only) from
+ * a host-side queue.  The paper has no serving component: this is the deployment loop
+ * around its renderer.
+ *
+ * Batched mode (default).  A host thread forms a batch of up to max_slots queued requests
+ * whenever a lane is free, admitting requests in arrival order while the batch's tile and
+ * instance capacity (set by mem_budget_bytes) has room, and launches the batch as one
+ * captured CUDA graph: one projection pass over all (request, splat) pairs, device-counted
+ * depth and tile sorts, and a persistent blend kernel whose blocks take (request, tile)
+ * work items from a device counter until the batch is done.  With several lanes (each its
+ * own graph, stream and buffers) a batch starts while earlier ones still run, so requests
+ * that arrive while others are on the GPU overlap with them.  A batch that overflows its
+ * instance capacity is re-run with its requests' exact sizes; a request that alone
+ * exceeds a lane fails with RGS_EOVERFLOW.  A request's image does not depend on what
+ * else shares its batch.
+ * Plain mode renders one request at a time, in arrival order, through rgs_render_fwd's
+ * path (the comparison baseline). */
+
+typedef struct {
+    size_t mem_budget_bytes;    /* device bytes for the server's buffers (all lanes) */
+    int max_slots;              /* requests per batch, 1..16 */
+    int lanes;                  /* batches in flight, 1..4 */
+    int plain;                  /* non-zero: plain mode */
+    int max_width, max_height;  /* largest image accepted (1..16384) */
+    int max_queue;              /* queued requests beyond which submit returns RGS_EAGAIN */
+    float inst_per_pixel;       /* first admission estimate of tile instances per pixel (later:
+                                   measured); a low value only costs a re-run of the batch */
+} rgs_serve_config;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled;
+    int64_t batches;            /* launches (batches, or requests in plain mode) */
+    int64_t requeued;           /* requests re-run after their batch overflowed */
+    int64_t instance_capacity;  /* tile instances per lane */
+    double mean_batch;          /* requests per launch */
+} rgs_serve_stats;
+
+/* Defaults: 8 GiB, 8 slots, 2 lanes, batched, 4096x4096, 65536 queued, 16 instances
+ * per pixel. */
+void rgs_serve_default_config(rgs_serve_config* cfg);
+
+/* Device bytes one lane of a batched server with this configuration takes for a capacity
+ * of `instance_capacity` tile instances (pure host arithmetic; mem_budget_bytes and
+ * lanes are ignored).  A lane needs at least 65536 instances. */
+int rgs_serve_lane_bytes(const rgs_kd* kd, const rgs_gaussians* g, const rgs_serve_config* cfg,
+                         int64_t instance_capacity, size_t* bytes);
+
+/* rgs_serve_create_ex with the defaults, mem_budget_bytes and max_slots. */
+int rgs_serve_create(const rgs_kd* kd, const rgs_gaussians* g, const rgs_render_opts* opts, size_t mem_budget_bytes,
+                     int max_slots, rgs_server** out);
+
+/* Allocates the lanes (within the budget), captures their graphs and starts the
+ * scheduler thread on the current device.  kd and g must outlive the server.  Errors:
+ * EINVAL (arguments, a budget too small for one request of max_width x max_height),
+ * ENOMEM, ECUDA. */
+int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_render_opts* opts,
+                        const rgs_serve_config* cfg, rgs_server** out);
+
+/* Queues a render of `cam` into out_image [3,H,W] (device, caller-owned, untouched by the
+ * caller until the request is done).  Never blocks.  *ticket identifies the request.
+ * Errors: EINVAL (camera, image larger than the configured maximum, NULL pointers),
+ * EAGAIN (queue full or server stopping). */
+int rgs_serve_submit(rgs_server* srv, const rgs_camera* cam, float* out_image, uint64_t* ticket);
+
+/* Non-blocking.  *done = 1 once the request has finished, with *latency_ms (nullable) the
+ * host time from submit to the scheduler seeing it complete; the ticket is then retired.
+ * Returns RGS_OK while pending or after success, the request's error (EOVERFLOW, ECUDA,
+ * EAGAIN if cancelled) with *done = 1 if it failed, EINVAL for an unknown ticket. */
+int rgs_serve_poll(rgs_server* srv, uint64_t ticket, int* done, double* latency_ms);
+
+int rgs_serve_stats_read(rgs_server* srv, rgs_serve_stats* out);
+
+/* Stops the scheduler, cancels queued requests and waits at most 10 s for batches on the
+ * GPU.  Returns ETIMEOUT if they did not finish (their buffers are then left allocated
+ * rather than freed under a running kernel).  Never hangs. */
+int rgs_serve_destroy(rgs_server* srv);
 
 /* ------------------------------------------------------------------ tracing
  * rgs_profile_enable(flags): bit 0 turns on per-pass timing: every pass of the library

@@ -12,12 +12,6 @@
 
 #include "rgs_internal.cuh"
 
-// ------------------------------------------------------------------ opaque handles
-struct rgs_kd {
-    rgs::KdBuild b;
-    int device;
-    float trunc_mult;
-};
 
 namespace rgs {
 
@@ -124,6 +118,8 @@ __global__ void gather_key_kernel(const uint32_t* __restrict__ dkey, const uint3
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) key[j] = dkey[id[j]];
 }
+
+}  // namespace
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -241,6 +237,8 @@ void fill_view(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, 
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+namespace {
 
 // Carves the workspace; returns the bytes needed (b may be NULL to only measure).
 size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, RasterBuffers* b) {
@@ -410,7 +408,10 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
 int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                     float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
                     void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters) {
-    if (!partial_C || !partial_T) { set_error("render_fwd: partial maps are required"); return RGS_EINVAL; }
+    if ((!partial_C) != (!partial_T) || (!partial_C && !image)) {
+        set_error("render_fwd: give both partial maps, or neither together with an image (forward only)");
+        return RGS_EINVAL;
+    }
     ViewParams vp;
     TreeParams tp;
     RasterBuffers b;

@@ -275,18 +275,21 @@ __device__ __forceinline__ uint32_t depth_fraction(float zh, float zl) {
 // ------------------------------------------------------------------ forward kernel
 constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are counted by the whole warp
 
+// Projection of splat i (valid: i < n) into one view.  Outputs go to index j of the
+// per-splat arrays of b; the instance and visible-splat totals are added to counters[0..1]
+// and, when non-null, slot_counters[0..1].  Every lane of the warp must call it.
 template <int DEG>
-__global__ void __launch_bounds__(256)
-project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
+__device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t i, bool valid, const ViewParams& vp,
+                                                 const TreeParams& tp, const RasterBuffers& b, int64_t j,
+                                                 unsigned long long* counters, unsigned long long* slot_counters) {
     constexpr int NSH = (DEG + 1) * (DEG + 1);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     // candidate state handed to the counting phase
     bool cand = false;
     float mxh = 0.f, myh = 0.f, l11 = 0.f, l12 = 0.f, l22 = 0.f, alpha = 0.f, rho2 = 0.f, z = 0.f;
     unsigned long long mask = 0;
     int ty0 = 0, ty1 = -1, nsub = 0;
-    if (i < g.n) {
+    if (valid) {
         SplatIn si;
         load_splat(g, i, si);
         float p[3], mxl, myl, zl;
@@ -295,8 +298,14 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         const float smax = fmaxf(si.ls[0], fmaxf(si.ls[1], si.ls[2]));
         const float D = vp.trunc_mult * __expf(smax);
         alpha = 1.f / (1.f + __expf(-si.logit));
-        // A splat contributes nowhere unless z > near and alpha >= alpha_min.
-        if (z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh)) {
+        // A splat contributes nowhere unless z > near and alpha >= alpha_min, nor outside the
+        // ball test's screen ellipse (semi-axes f D / z around the centre; widened by 0.1%
+        // and a pixel against rounding), so splats whose ellipse misses the image skip the
+        // EWA projection.
+        const float bxr = vp.fx * D / z * 1.001f + 1.f, byr = vp.fy * D / z * 1.001f + 1.f;
+        const bool on_screen = mxh + bxr >= 0.f && mxh - bxr <= (float)vp.W && myh + byr >= 0.f &&
+                               myh - byr <= (float)vp.H;
+        if (z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh) && on_screen) {
             Proj P;
             ewa(vp, si, p, P);
             l11 = sqrtf(P.ca);
@@ -327,13 +336,13 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
                 }
                 __half2 lo = __floats2half2_rn(mxl, myl);
                 float lo_bits = __uint_as_float(*reinterpret_cast<uint32_t*>(&lo));
-                b.rec[3 * i] = make_float4(mxh, myh, lo_bits, alpha);
-                b.rec[3 * i + 1] = make_float4(l11, l12, l22, rho2);
-                b.rec[3 * i + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
-                b.rect[i] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
-                b.mask[i] = mask;
-                b.dkey[i] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
-                b.dkey_lo[i] = depth_fraction(z, zl);
+                b.rec[3 * j] = make_float4(mxh, myh, lo_bits, alpha);
+                b.rec[3 * j + 1] = make_float4(l11, l12, l22, rho2);
+                b.rec[3 * j + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
+                b.rect[j] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
+                b.mask[j] = mask;
+                b.dkey[j] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
+                b.dkey_lo[j] = depth_fraction(z, zl);
             }
         }
     }
@@ -363,7 +372,7 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == src) count = acc;
     }
-    if (i < g.n) b.cnt[i] = count;
+    if (valid) b.cnt[j] = count;
     // totals: instances and visible splats
     unsigned long long c64 = count;
     unsigned vis_n = count > 0;
@@ -372,9 +381,41 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
         vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
     }
     if (lane == 0 && (c64 | vis_n)) {
-        atomicAdd(&b.counters[0], c64);
-        atomicAdd(&b.counters[1], (unsigned long long)vis_n);
+        atomicAdd(&counters[0], c64);
+        atomicAdd(&counters[1], (unsigned long long)vis_n);
+        if (slot_counters) {
+            atomicAdd(&slot_counters[0], c64);
+            atomicAdd(&slot_counters[1], (unsigned long long)vis_n);
+        }
     }
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256)
+project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    project_fwd_body<DEG>(g, i, i < g.n, vp, tp, b, i, b.counters, nullptr);
+}
+
+// Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
+// x % kMaxSlots, so the blocks of one splat range run back to back and read its
+// parameters from L2 after the first slot.  Outputs go to index slot * N + i.
+template <int DEG>
+__global__ void __launch_bounds__(256)
+project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                     TreeParams tp, RasterBuffers b, unsigned long long* __restrict__ counters) {
+    const int slot = blockIdx.x % kMaxSlots;
+    if (slot >= hdr->S) return;   // uniform across the block
+    __shared__ ViewParams svp;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&slots[slot].vp);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&svp);
+        for (int w = threadIdx.x; w < (int)(sizeof(ViewParams) / 4); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
+    project_fwd_body<DEG>(g, i, i < g.n, svp, tp, b, (int64_t)slot * g.n + i, counters,
+                          counters + kBatchSlotCounters + 2 * slot);
 }
 
 // ------------------------------------------------------------------ backward kernel
@@ -518,6 +559,19 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
         case 1: project_fwd_kernel<1><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
         case 2: project_fwd_kernel<2><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
         default: project_fwd_kernel<3><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
+    }
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp,
+                         const RasterBuffers& b, unsigned long long* counters, cudaStream_t s) {
+    const unsigned grid = (unsigned)((g.n + 255) / 256) * (unsigned)kMaxSlots;
+    switch (g.sh_degree) {
+        case 0: project_batch_kernel<0><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
+        case 1: project_batch_kernel<1><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
+        case 2: project_batch_kernel<2><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
+        default: project_batch_kernel<3><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
     }
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;

@@ -49,6 +49,61 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // One warp per depth-sorted splat; lanes take the splat's (subset, tile row) items, find
 // the row's tile columns from the footprint (the same arithmetic as the count), and
 // write the row's instances at the positions a warp prefix sum gives them.
+// Instances of one splat (record id, first instance slot `base`), written by the calling
+// warp; global tile indices start at tile_base.
+__device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams& tp, uint32_t id, uint32_t base,
+                                         uint32_t tile_base, const ushort4* __restrict__ rect,
+                                         const unsigned long long* __restrict__ mask, const float4* __restrict__ rec,
+                                         const float* __restrict__ cull, const float2* __restrict__ chunk,
+                                         uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane) {
+    const ushort4 r = rect[id];
+    const unsigned long long m = mask[id];
+    const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+    const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+    const int ty0 = r.y, rows = (int)r.w - (int)r.y + 1;
+    const int nsub = __popcll(m);
+    const int items = nsub * rows;
+    for (int it0 = 0; it0 < items; it0 += 32) {
+        const int it = it0 + lane;
+        int c0 = 1, c1 = 0, ty = 0;
+        uint32_t rank = 0;
+        if (it < items) {
+            int k;
+            item_span(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
+            rank = (uint32_t)vp.rank_of[k];
+        }
+        const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, r2.w);
+        uint32_t incl = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t pos = base + incl - w;
+        const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
+        if (w && !cull) {
+            for (int c = c0; c <= c1; ++c, ++pos) {
+                ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                ival[pos] = id;
+            }
+        } else if (w) {
+            const int nch = cull_nchunk(vp);
+            for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+                const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+                const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
+                if (r2.w > mm.y) continue;
+                const bool all = r2.w <= mm.x;
+                for (int c = lo; c <= hi; ++c) {
+                    if (!all && !keep_tile(cull, vp, ty, c, (int)rank, r2.w)) continue;
+                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                    ival[pos] = id;
+                    ++pos;
+                }
+            }
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
 __global__ void __launch_bounds__(256)
 emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
@@ -57,55 +112,43 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = warp; p < n_vis; p += nwarps) {
+    for (int64_t p = warp; p < n_vis; p += nwarps)
+        emit_one(vp, tp, sorted_ids[p], ioff[p], 0u, rect, mask, rec, cull, chunk, ikey, ival, lane);
+}
+
+// Copies the batch's view parameters into shared memory (the whole block).
+__device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ slots, int S, ViewParams* svp) {
+    constexpr int kWords = (int)(sizeof(ViewParams) / 4);
+    for (int w = threadIdx.x; w < S * kWords; w += blockDim.x) {
+        const int sl = w / kWords, o = w - sl * kWords;
+        reinterpret_cast<uint32_t*>(&svp[sl])[o] = reinterpret_cast<const uint32_t*>(&slots[sl].vp)[o];
+    }
+    __syncthreads();
+}
+
+// Batch emission: sorted ids are slot * N + i, so each warp takes its splat's view from
+// the block's shared copy of the slot table.
+__global__ void __launch_bounds__(256)
+emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
+                  const uint32_t* __restrict__ sorted_ids, int64_t n_cap, int64_t N,
+                  const unsigned long long* __restrict__ counters, const uint32_t* __restrict__ ioff,
+                  const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
+                  const float4* __restrict__ rec, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+    if (counters[2]) return;   // overflow: the batch is discarded
+    __shared__ ViewParams svp[kMaxSlots];
+    __shared__ uint32_t sbase[kMaxSlots];
+    const int S = hdr->S;
+    if ((int)threadIdx.x < S) sbase[threadIdx.x] = hdr->tile_base[threadIdx.x];
+    load_batch_views(slots, S, svp);
+    const unsigned long long nv = counters[1];
+    const int64_t n = nv < (unsigned long long)n_cap ? (int64_t)nv : n_cap;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < n; p += nwarps) {
         const uint32_t id = sorted_ids[p];
-        uint32_t base = ioff[p];
-        const ushort4 r = rect[id];
-        const unsigned long long m = mask[id];
-        const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
-        const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
-        const int ty0 = r.y, rows = (int)r.w - (int)r.y + 1;
-        const int nsub = __popcll(m);
-        const int items = nsub * rows;
-        for (int it0 = 0; it0 < items; it0 += 32) {
-            const int it = it0 + lane;
-            int c0 = 1, c1 = 0, ty = 0;
-            uint32_t rank = 0;
-            if (it < items) {
-                int k;
-                item_span(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
-                rank = (uint32_t)vp.rank_of[k];
-            }
-            const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, r2.w);
-            uint32_t incl = w;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            uint32_t pos = base + incl - w;
-            const uint32_t first = (uint32_t)(ty * vp.tiles_x);
-            if (w && !cull) {
-                for (int c = c0; c <= c1; ++c, ++pos) {
-                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                    ival[pos] = id;
-                }
-            } else if (w) {
-                const int nch = cull_nchunk(vp);
-                for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
-                    const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-                    const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
-                    if (r2.w > mm.y) continue;
-                    const bool all = r2.w <= mm.x;
-                    for (int c = lo; c <= hi; ++c) {
-                        if (!all && !keep_tile(cull, vp, ty, c, (int)rank, r2.w)) continue;
-                        ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                        ival[pos] = id;
-                        ++pos;
-                    }
-                }
-            }
-            base += __shfl_sync(0xffffffffu, incl, 31);
-        }
+        const int slot = (int)(id / (uint64_t)N);
+        emit_one(svp[slot], tp, id, ioff[p], sbase[slot], rect, mask, rec, nullptr, nullptr, ikey, ival, lane);
     }
 }
 
@@ -133,6 +176,17 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint
     uint32_t k = keys[j];
     if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
     if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+}
+
+__global__ void ranges_dev_kernel(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
+                                  int64_t cap, uint2* __restrict__ ranges) {
+    const unsigned long long nv = *n_dev;
+    const int64_t n = nv < (unsigned long long)cap ? (int64_t)nv : cap;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[j];
+        if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
+        if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+    }
 }
 
 // ------------------------------------------------------------------ shared pieces of the blend
@@ -261,19 +315,21 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 }
 
 // ------------------------------------------------------------------ blend forward
+// One tile of the view: `ranges` and `tile_depth` point at the tile's K entries (view
+// rank order); pC/pT (partial maps) and tile_depth may be null.  The whole block calls it.
 template <bool kCount>
-__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
-blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
-                 const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
-                 float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth,
-                 unsigned long long* __restrict__ pairs) {
+__device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
+                                               const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                                               const float4* __restrict__ rec, float* __restrict__ pC,
+                                               float* __restrict__ pT, float* __restrict__ image,
+                                               float* __restrict__ Tfin, float* __restrict__ tile_depth,
+                                               unsigned long long* __restrict__ pairs) {
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ LeafPath lp;
     __shared__ uint32_t sused[kBlendThreads];
     uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0, n_staged = 0, n_used = 0;
-    const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
     thread_pixel(threadIdx.x, lx, ly);
@@ -291,7 +347,7 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
-        const uint2 rg = ranges[(size_t)tile * vp.K + r];
+        const uint2 rg = ranges[r];
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
         bool done = !inside;
         float zsat = __int_as_float(0x7f800000);   // +inf: the subset never saturated the tile
@@ -367,12 +423,14 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 break;
             }
         }
-        if (tile_depth && threadIdx.x == 0) tile_depth[(size_t)tile * vp.K + r] = zsat;
+        if (tile_depth && threadIdx.x == 0) tile_depth[r] = zsat;
         if (inside) {
-            pC[((size_t)k * 3 + 0) * HW + pix] = C0;
-            pC[((size_t)k * 3 + 1) * HW + pix] = C1;
-            pC[((size_t)k * 3 + 2) * HW + pix] = C2;
-            pT[(size_t)k * HW + pix] = T;
+            if (pC) {
+                pC[((size_t)k * 3 + 0) * HW + pix] = C0;
+                pC[((size_t)k * 3 + 1) * HW + pix] = C1;
+                pC[((size_t)k * 3 + 2) * HW + pix] = C2;
+                pT[(size_t)k * HW + pix] = T;
+            }
             img0 = fmaf(C0, Pm, img0);
             img1 = fmaf(C1, Pm, img1);
             img2 = fmaf(C2, Pm, img2);
@@ -393,6 +451,57 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         count_add(pairs + 7, n_strad);
         count_add(pairs + 8, n_staged);
         count_add(pairs + 9, n_used);
+    }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
+blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                 const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
+                 float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth,
+                 unsigned long long* __restrict__ pairs) {
+    const int tile = blockIdx.x;
+    blend_fwd_tile<kCount>(vp, tp, tile, ranges + (size_t)tile * vp.K, ival, rec, pC, pT, image, Tfin,
+                           tile_depth ? tile_depth + (size_t)tile * vp.K : nullptr, pairs);
+}
+
+// Persistent forward blend over the global tiles of a batch: each block takes the next
+// tile from a device counter until all are done; a tile belongs to the last request
+// whose tile_base it reaches.  The request's view is kept in shared memory while
+// consecutive tiles stay in one request.
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
+blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
+                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival, const float4* __restrict__ rec,
+                   unsigned long long* __restrict__ counters) {
+    __shared__ ViewParams svp;
+    __shared__ uint32_t s_tile;
+    __shared__ int s_slot;
+    if (counters[2]) return;   // overflow: the batch is discarded
+    const int S = hdr->S;
+    const uint32_t total = hdr->total_tiles;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = (uint32_t)atomicAdd(&counters[3], 1ull);
+            int sl = 0;
+            while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
+            s_tile = t;
+            s_slot = sl;
+        }
+        __syncthreads();
+        const uint32_t t = s_tile;
+        const int slot = s_slot;
+        if (t >= total) break;
+        if (slot != cur) {
+            constexpr int kWords = (int)(sizeof(ViewParams) / 4);
+            for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+                reinterpret_cast<uint32_t*>(&svp)[w] = reinterpret_cast<const uint32_t*>(&slots[slot].vp)[w];
+            cur = slot;
+            __syncthreads();
+        }
+        blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), ranges + (size_t)t * svp.K, ival, rec,
+                              nullptr, nullptr, slots[slot].image, nullptr, nullptr, nullptr);
+        __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
 
@@ -670,6 +779,33 @@ int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
                                                                image, T_final, tile_depth, nullptr);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
+                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, const unsigned long long* counters,
+                      cudaStream_t s) {
+    emit_batch_kernel<<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect, b.mask,
+                                              b.rec, b.ikey, b.ival);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
+                      cudaStream_t s) {
+    ranges_dev_kernel<<<152 * 8, 256, 0, s>>>(keys, n_dev, cap, ranges);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
+                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    RGS_CUDA_TRY(cudaGetDevice(&dev));
+    RGS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival,
+                                                                                      rec, counters);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

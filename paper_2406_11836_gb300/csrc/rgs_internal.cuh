@@ -53,6 +53,32 @@ struct ViewParams {
     int8_t rank_of[64];        // rank_of[k] = view rank of subset k
 };
 
+// ------------------------------------------------------------------ request batches (serve.cu)
+// A batch renders up to kMaxSlots requests (views of the same resident scene) in one pass
+// of device-counted kernels.  Per-splat arrays are indexed slot * N + i; tile indices are
+// global over the batch: request s owns tiles [tile_base, tile_base + tiles_x * tiles_y).
+constexpr int kMaxSlots = 16;
+
+struct BatchSlot {
+    ViewParams vp;
+    float* image;              // [3, H, W] output of the request
+    uint32_t tile_base;        // first global tile of the request
+    uint32_t pad;
+};
+
+struct BatchHeader {
+    unsigned long long n_total;          // S * N: the projection's output domain
+    int S;                               // requests in the batch
+    uint32_t total_tiles;                // sum of the requests' tiles
+    uint32_t tile_base[kMaxSlots + 1];   // prefix of the requests' tile counts
+};
+
+// Device counters of a batch (uint64): [0] instances, [1] visible (slot, splat) pairs,
+// [2] overflow flag, [3] blend work-queue head, [4] instances to sort (0 on overflow),
+// then (instances, visible) per slot from kBatchSlotCounters.
+constexpr int kBatchSlotCounters = 8;
+constexpr int kBatchCounters = kBatchSlotCounters + 2 * kMaxSlots;
+
 // ------------------------------------------------------------------ tracing
 // Passes timed by the profiler (rgs_profile_*): a pair of CUDA events is recorded on the
 // launching stream around each pass while profiling is on.
@@ -110,6 +136,17 @@ size_t radix_temp_bytes(int64_t n);
 int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int end_bit,
                      void* temp, size_t temp_bytes, cudaStream_t s, bool* in_alt);
 
+// Device-counted variants: the element count is read on the device from *n_dev (clamped
+// to cap, the buffers' capacity), so the launches need no host round trip and can be
+// captured in a CUDA graph.  Fixed temporary sizes.
+size_t scan_dev_temp_bytes();
+int exclusive_scan_dev(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev, int64_t cap, int load,
+                       const uint32_t* gather, void* temp, size_t temp_bytes, cudaStream_t s);
+size_t radix_dev_temp_bytes();
+int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                         const unsigned long long* n_dev, int64_t cap, int end_bit, void* temp, size_t temp_bytes,
+                         cudaStream_t s, bool* in_alt);
+
 // ------------------------------------------------------------------ raster (raster.cu)
 struct RasterBuffers {
     // per splat
@@ -146,6 +183,19 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
                        cudaStream_t s);
 int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
                        const RasterBuffers& b, cudaStream_t s);
+int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp,
+                         const RasterBuffers& b, unsigned long long* counters, cudaStream_t s);
+// Batch emission over the (slot, depth)-sorted visible list (count counters[1]); writes
+// nothing when the overflow flag counters[2] is set.
+int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
+                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, const unsigned long long* counters,
+                      cudaStream_t s);
+int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
+                      cudaStream_t s);
+// Persistent forward blend over the batch's global tiles (fused merge into each slot's
+// image; no partial maps).
+int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
+                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s);
 int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
                 int64_t n_vis, cudaStream_t s);
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
@@ -179,8 +229,25 @@ int kd_build(const rgs_gaussians& g, int L, float trunc_mult, KdBuild* out, cuda
 // Subset lists N_k for the splits already in `out` (out->L, axis, split).
 int kd_subsets(const rgs_gaussians& g, float trunc_mult, KdBuild* out, cudaStream_t s);
 
+// ------------------------------------------------------------------ argument checks and view setup (abi.cu)
+bool aligned(const void* p, size_t a);
+size_t a256(size_t x);
+int check_gaussians(const rgs_gaussians* g);
+int check_camera(const rgs_camera* c);
+int check_opts(const rgs_render_opts* o);
+void view_order_host(const struct ::rgs_kd* kd, const rgs_camera* cam, int32_t* order);
+void fill_view(const struct ::rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+               ViewParams* vp, TreeParams* tp);
+
 // ------------------------------------------------------------------ Adam (adam.cu)
 int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t* seg_off, const float* seg_lr,
                 int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s);
 
 }  // namespace rgs
+
+// ------------------------------------------------------------------ opaque handles
+struct rgs_kd {
+    rgs::KdBuild b;
+    int device;
+    float trunc_mult;
+};

@@ -1,0 +1,765 @@
+// Render server: a resident scene, a host queue of forward-only render requests, and a
+// scheduler thread that packs queued requests into batches and launches each batch as one
+// captured CUDA graph (see the serving section of rgs.h).
+//
+// Batch pipeline (all counts stay on the device, so one graph per lane serves every
+// batch whatever its views, resolutions and splat counts):
+//   slot table H2D -> clear counters and tile ranges -> projection of every (request,
+//   splat) pair -> compaction of the visible pairs -> depth sort (16 low bits, float bits
+//   of z, then request: stable LSD, so the order is (request, depth, index)) -> instance
+//   offsets -> capacity check -> emission with global tile keys -> instance sort ->
+//   tile ranges -> persistent blend over (request, tile) work items -> counters D2H.
+// Each request's arithmetic is that of rgs_render_fwd; a request's records, keys and
+// tiles never mix with another's, so its image is the same alone and in any batch.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "rgs_internal.cuh"
+
+namespace rgs {
+int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
+                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters);
+
+namespace {
+
+static_assert(sizeof(ViewParams) % 4 == 0, "view parameters are copied as 32-bit words");
+
+// ------------------------------------------------------------------ batch kernels
+constexpr int kGridStride = 152 * 8;   // blocks of the grid-stride passes
+
+__device__ __forceinline__ int64_t dev_count(const unsigned long long* n, int64_t cap) {
+    const unsigned long long v = *n;
+    return v < (unsigned long long)cap ? (int64_t)v : cap;
+}
+
+// Visible (request, splat) pairs in index order: (16 low depth bits, pair id).
+__global__ void compact_batch_kernel(const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ pos,
+                                     const uint32_t* __restrict__ dkey_lo, const unsigned long long* __restrict__ n_dev,
+                                     int64_t cap, uint32_t* __restrict__ skey, uint32_t* __restrict__ sid) {
+    const int64_t n = dev_count(n_dev, cap);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (cnt[j] == 0) continue;
+        const uint32_t p = pos[j];
+        skey[p] = dkey_lo[j];
+        sid[p] = (uint32_t)j;
+    }
+}
+
+// key[p] = src[id[p]] (src = float bits of z), or id[p] / N (the request) when src is null.
+__global__ void batch_key_kernel(const uint32_t* __restrict__ src, const uint32_t* __restrict__ id, int64_t N,
+                                 const unsigned long long* __restrict__ n_dev, int64_t cap, uint32_t* __restrict__ key) {
+    const int64_t n = dev_count(n_dev, cap);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        key[p] = src ? src[id[p]] : (uint32_t)(id[p] / (uint64_t)N);
+}
+
+// Overflow check: instances beyond the lane's capacity discard the batch.
+__global__ void check_capacity_kernel(unsigned long long* counters, int64_t inst_cap) {
+    const unsigned long long I = counters[0];
+    const bool over = I > (unsigned long long)inst_cap;
+    counters[2] = over ? 1ull : 0ull;
+    counters[4] = over ? 0ull : I;
+}
+
+// ------------------------------------------------------------------ lanes
+struct LaneBufs {
+    BatchSlot* slots;
+    BatchHeader* hdr;
+    unsigned long long* counters;
+    RasterBuffers b;
+};
+
+// Carves one lane's buffers from `base` (NULL: measure); returns the bytes used.
+size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += a256(bytes);
+        return p;
+    };
+    LaneBufs l;
+    memset(&l, 0, sizeof l);
+    const int64_t P = N * slots;   // (request, splat) pairs
+    l.slots = (BatchSlot*)take(sizeof(BatchSlot) * kMaxSlots);
+    l.hdr = (BatchHeader*)take(sizeof(BatchHeader));
+    l.counters = (unsigned long long*)take(8 * kBatchCounters);
+    RasterBuffers& b = l.b;
+    b.rec = (float4*)take(sizeof(float4) * 3 * P);
+    b.cnt = (uint32_t*)take(4 * P);
+    b.rect = (ushort4*)take(8 * P);
+    b.mask = (unsigned long long*)take(8 * P);
+    b.dkey = (uint32_t*)take(4 * P);
+    b.dkey_lo = (uint32_t*)take(4 * P);
+    b.vis_pos = (uint32_t*)take(4 * P);
+    b.skey = (uint32_t*)take(4 * P);
+    b.sid = (uint32_t*)take(4 * P);
+    b.skey_alt = (uint32_t*)take(4 * P);
+    b.sid_alt = (uint32_t*)take(4 * P);
+    b.ioff = (uint32_t*)take(4 * P);
+    b.ranges = (uint2*)take(sizeof(uint2) * tiles_cap * K);
+    b.ikey = (uint32_t*)take(4 * inst_cap);
+    b.ival = (uint32_t*)take(4 * inst_cap);
+    b.ikey_alt = (uint32_t*)take(4 * inst_cap);
+    b.ival_alt = (uint32_t*)take(4 * inst_cap);
+    b.inst_cap = inst_cap;
+    const size_t tr = radix_dev_temp_bytes(), ts = scan_dev_temp_bytes();
+    b.temp_bytes = tr > ts ? tr : ts;
+    b.temp = take(b.temp_bytes);
+    if (out) *out = l;
+    return off;
+}
+
+int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+// Enqueues the whole batch pipeline of one lane on `s` (captured into the lane's graph).
+int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
+                  const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
+                  unsigned long long* status_host, cudaStream_t s) {
+    const int64_t N = g.n, P = N * slots;
+    const RasterBuffers& b = l.b;
+    unsigned long long* c = l.counters;
+    int rc;
+    RGS_CUDA_TRY(cudaMemcpyAsync(l.hdr, hdr_host, sizeof(BatchHeader), cudaMemcpyHostToDevice, s));
+    RGS_CUDA_TRY(cudaMemcpyAsync(l.slots, slots_host, sizeof(BatchSlot) * slots, cudaMemcpyHostToDevice, s));
+    RGS_CUDA_TRY(cudaMemsetAsync(c, 0, 8 * kBatchCounters, s));
+    RGS_CUDA_TRY(cudaMemsetAsync(b.ranges, 0, sizeof(uint2) * tiles_cap * K, s));
+    if ((rc = launch_project_batch(g, l.slots, l.hdr, tp, b, c, s))) return rc;
+    // compaction in (request, splat) order
+    if ((rc = exclusive_scan_dev(b.cnt, b.vis_pos, &l.hdr->n_total, P, 1, nullptr, b.temp, b.temp_bytes, s)))
+        return rc;
+    compact_batch_kernel<<<kGridStride, 256, 0, s>>>(b.cnt, b.vis_pos, b.dkey_lo, &l.hdr->n_total, P, b.skey, b.sid);
+    RGS_CUDA_LAUNCH_CHECK();
+    // (request, depth, index) order: LSD passes on the low depth bits, the float bits of
+    // z, then the request
+    uint32_t *ka = b.skey, *va = b.sid, *kb = b.skey_alt, *vb = b.sid_alt;
+    auto sort = [&](int bits) -> int {
+        bool alt = false;
+        int r = radix_sort_pairs_dev(ka, va, kb, vb, &c[1], P, bits, b.temp, b.temp_bytes, s, &alt);
+        if (!r && alt) {
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        return r;
+    };
+    if ((rc = sort(16))) return rc;
+    batch_key_kernel<<<kGridStride, 256, 0, s>>>(b.dkey, va, N, &c[1], P, ka);
+    RGS_CUDA_LAUNCH_CHECK();
+    if ((rc = sort(31))) return rc;
+    if (slots > 1) {
+        batch_key_kernel<<<kGridStride, 256, 0, s>>>(nullptr, va, N, &c[1], P, ka);
+        RGS_CUDA_LAUNCH_CHECK();
+        if ((rc = sort(ceil_log2(slots)))) return rc;
+    }
+    const uint32_t* sorted_ids = va;
+    if ((rc = exclusive_scan_dev(b.cnt, b.ioff, &c[1], P, 2, sorted_ids, b.temp, b.temp_bytes, s))) return rc;
+    check_capacity_kernel<<<1, 1, 0, s>>>(c, b.inst_cap);
+    RGS_CUDA_LAUNCH_CHECK();
+    if ((rc = launch_emit_batch(l.slots, l.hdr, tp, b, sorted_ids, P, N, c, s))) return rc;
+    bool alt = false;
+    const int key_bits = ceil_log2(tiles_cap) + L;
+    if ((rc = radix_sort_pairs_dev(b.ikey, b.ival, b.ikey_alt, b.ival_alt, &c[4], b.inst_cap, key_bits, b.temp,
+                                   b.temp_bytes, s, &alt)))
+        return rc;
+    const uint32_t* keys = alt ? b.ikey_alt : b.ikey;
+    const uint32_t* ival = alt ? b.ival_alt : b.ival;
+    if ((rc = launch_ranges_dev(keys, &c[4], b.inst_cap, b.ranges, s))) return rc;
+    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s))) return rc;
+    RGS_CUDA_TRY(cudaMemcpyAsync(status_host, c, 8 * kBatchCounters, cudaMemcpyDeviceToHost, s));
+    return RGS_OK;
+}
+
+// ------------------------------------------------------------------ server state
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+struct Request {
+    uint64_t ticket;
+    rgs_camera cam;
+    ViewParams vp;
+    float* out;
+    int64_t tiles;
+    int64_t pixels;
+    int64_t exact_inst = -1;      // known after a batch holding it overflowed
+    Clock::time_point t_submit;
+    bool done = false;
+    int status = RGS_OK;
+    double latency_ms = 0;
+    char err[160] = {0};
+};
+
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    char* mem = nullptr;
+    LaneBufs bufs;
+    BatchSlot* slots_host = nullptr;     // pinned
+    BatchHeader* hdr_host = nullptr;     // pinned
+    unsigned long long* status_host = nullptr;   // pinned [kBatchCounters]
+    std::vector<Request*> inflight;
+    bool busy = false;
+};
+
+}  // namespace
+}  // namespace rgs
+
+struct rgs_server {
+    const rgs_kd* kd;
+    rgs_gaussians g;
+    rgs_render_opts opts;
+    rgs_serve_config cfg;
+    rgs::TreeParams tp;
+    int device;
+    int K, L;
+    int64_t tiles_cap;      // per lane (batched) / per request (plain)
+    int64_t inst_cap;
+    std::vector<rgs::Lane> lanes;
+    // plain mode
+    void* plain_ws = nullptr;
+    size_t plain_ws_bytes = 0;
+    cudaStream_t plain_stream = nullptr;
+    cudaEvent_t plain_ev = nullptr;
+    // queue and tickets
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<rgs::Request*> queue;
+    std::unordered_map<uint64_t, rgs::Request*> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    bool broken = false;
+    double inst_per_pixel = 16.0;   // running estimate for admission
+    rgs_serve_stats stats;
+    int64_t batched_requests = 0;
+    std::thread worker;
+    bool worker_timed_out = false;
+};
+
+namespace rgs {
+namespace {
+
+void finish(rgs_server* S, Request* r, int status, const char* why) {
+    r->status = status;
+    r->latency_ms = ms_since(r->t_submit);
+    if (why) snprintf(r->err, sizeof r->err, "%s", why);
+    r->done = true;
+    if (status == RGS_OK) ++S->stats.completed;
+    else if (status == RGS_EAGAIN) ++S->stats.cancelled;
+    else ++S->stats.failed;
+}
+
+int64_t est_instances(const rgs_server* S, const Request* r) {
+    if (r->exact_inst >= 0) return r->exact_inst;
+    return (int64_t)(S->inst_per_pixel * 1.25 * (double)r->pixels) + 1024;
+}
+
+// Pops the next batch for a lane (caller holds S->mu).
+void form_batch(rgs_server* S, std::vector<Request*>& batch) {
+    int64_t tiles = 0, inst = 0;
+    while (!S->queue.empty() && (int)batch.size() < S->cfg.max_slots) {
+        Request* r = S->queue.front();
+        const int64_t e = est_instances(S, r);
+        if (!batch.empty() && (tiles + r->tiles > S->tiles_cap || inst + e > S->inst_cap)) break;
+        S->queue.pop_front();
+        tiles += r->tiles;
+        inst += e;
+        batch.push_back(r);
+    }
+}
+
+int launch_lane(rgs_server* S, Lane& ln, std::vector<Request*>& batch) {
+    BatchHeader& h = *ln.hdr_host;
+    memset(&h, 0, sizeof h);
+    h.S = (int)batch.size();
+    h.n_total = (unsigned long long)S->g.n * (unsigned long long)h.S;
+    uint32_t base = 0;
+    for (int s = 0; s < h.S; ++s) {
+        h.tile_base[s] = base;
+        ln.slots_host[s].vp = batch[s]->vp;
+        ln.slots_host[s].image = batch[s]->out;
+        ln.slots_host[s].tile_base = base;
+        base += (uint32_t)batch[s]->tiles;
+    }
+    for (int s = h.S; s <= kMaxSlots; ++s) h.tile_base[s] = base;
+    h.total_tiles = base;
+    RGS_CUDA_TRY(cudaGraphLaunch(ln.exec, ln.stream));
+    RGS_CUDA_TRY(cudaEventRecord(ln.done_ev, ln.stream));
+    ln.inflight = batch;
+    ln.busy = true;
+    ++S->stats.batches;
+    S->batched_requests += h.S;
+    return RGS_OK;
+}
+
+// Lane finished (caller holds S->mu): settle its requests.
+void complete_lane(rgs_server* S, Lane& ln) {
+    const unsigned long long* st = ln.status_host;
+    const bool overflow = st[2] != 0;
+    const int n = (int)ln.inflight.size();
+    if (!overflow) {
+        int64_t inst = 0, pix = 0;
+        for (int s = 0; s < n; ++s) {
+            finish(S, ln.inflight[s], RGS_OK, nullptr);
+            inst += (int64_t)st[kBatchSlotCounters + 2 * s];
+            pix += ln.inflight[s]->pixels;
+        }
+        if (pix > 0) S->inst_per_pixel = 0.8 * S->inst_per_pixel + 0.2 * ((double)inst / (double)pix);
+    } else {
+        // exact sizes are known now: requeue at the front, in order
+        for (int s = n - 1; s >= 0; --s) {
+            Request* r = ln.inflight[s];
+            r->exact_inst = (int64_t)st[kBatchSlotCounters + 2 * s];
+            if (n == 1 || r->exact_inst > S->inst_cap) {
+                char why[160];
+                snprintf(why, sizeof why, "serve: request needs %lld tile instances, a lane holds %lld",
+                         (long long)r->exact_inst, (long long)S->inst_cap);
+                finish(S, r, RGS_EOVERFLOW, why);
+            } else {
+                S->queue.push_front(r);
+                ++S->stats.requeued;
+            }
+        }
+    }
+    ln.inflight.clear();
+    ln.busy = false;
+}
+
+void fail_all(rgs_server* S, const char* why) {
+    for (auto& ln : S->lanes) {
+        for (Request* r : ln.inflight) finish(S, r, RGS_ECUDA, why);
+        ln.inflight.clear();
+    }
+    for (Request* r : S->queue) finish(S, r, RGS_ECUDA, why);
+    S->queue.clear();
+    S->broken = true;
+}
+
+void worker_batched(rgs_server* S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progress = false;
+        for (auto& ln : S->lanes) {
+            if (!ln.busy) continue;
+            const cudaError_t e = cudaEventQuery(ln.done_ev);
+            if (e == cudaSuccess) {
+                complete_lane(S, ln);
+                progress = true;
+            } else if (e != cudaErrorNotReady) {
+                fail_all(S, cudaGetErrorString(e));
+                ln.busy = false;
+            }
+        }
+        if (S->stop) break;
+        if (!S->broken) {
+            for (auto& ln : S->lanes) {
+                if (ln.busy || S->queue.empty()) continue;
+                std::vector<Request*> batch;
+                form_batch(S, batch);
+                if (batch.empty()) break;
+                if (launch_lane(S, ln, batch) != RGS_OK) {
+                    for (Request* r : batch) S->queue.push_front(r);
+                    fail_all(S, "serve: graph launch failed");
+                    break;
+                }
+                progress = true;
+            }
+        }
+        if (!progress) {
+            bool any_busy = false;
+            for (auto& ln : S->lanes) any_busy |= ln.busy;
+            // short naps while batches run; otherwise sleep until a submit or stop
+            if (any_busy) S->cv.wait_for(lk, std::chrono::microseconds(20));
+            else S->cv.wait_for(lk, std::chrono::milliseconds(50));
+        }
+    }
+    // stopping: cancel the queue, wait (bounded) for the lanes
+    for (Request* r : S->queue) finish(S, r, RGS_EAGAIN, "serve: cancelled (server destroyed)");
+    S->queue.clear();
+    const Clock::time_point t0 = Clock::now();
+    for (;;) {
+        bool any = false;
+        for (auto& ln : S->lanes) {
+            if (!ln.busy) continue;
+            const cudaError_t e = cudaEventQuery(ln.done_ev);
+            if (e == cudaErrorNotReady) any = true;
+            else if (e == cudaSuccess) complete_lane(S, ln);
+            else ln.busy = false;
+        }
+        if (!any) break;
+        if (ms_since(t0) > 10000.0) {
+            S->worker_timed_out = true;
+            break;
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+        lk.lock();
+    }
+}
+
+void worker_plain(rgs_server* S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        if (S->stop) break;
+        if (S->queue.empty() || S->broken) {
+            S->cv.wait_for(lk, std::chrono::milliseconds(50));
+            continue;
+        }
+        Request* r = S->queue.front();
+        S->queue.pop_front();
+        ++S->stats.batches;
+        ++S->batched_requests;
+        lk.unlock();
+        unsigned long long counts[2] = {0, 0};
+        prof_suppress(true);
+        int rc = render_fwd_into(S->kd, &S->g, &r->cam, &S->opts, nullptr, nullptr, r->out, nullptr, nullptr,
+                                 S->plain_ws, S->plain_ws_bytes, S->plain_stream, counts);
+        prof_suppress(false);
+        std::string why = rc ? std::string(rgs_last_error()) : std::string();
+        bool timed_out = false;
+        if (rc == RGS_OK) {
+            cudaError_t e = cudaEventRecord(S->plain_ev, S->plain_stream);
+            const Clock::time_point t0 = Clock::now();
+            while (e == cudaSuccess) {
+                e = cudaEventQuery(S->plain_ev);
+                if (e == cudaSuccess) break;
+                if (e != cudaErrorNotReady) break;
+                e = cudaSuccess;
+                if (ms_since(t0) > 10000.0) {
+                    timed_out = true;
+                    break;
+                }
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+            if (timed_out) {
+                rc = RGS_ETIMEOUT;
+                why = "serve: render did not finish within 10 s";
+            } else if (e != cudaSuccess) {
+                rc = RGS_ECUDA;
+                why = cudaGetErrorString(e);
+            }
+        }
+        lk.lock();
+        finish(S, r, rc, rc ? why.c_str() : nullptr);
+        if (rc == RGS_ECUDA || rc == RGS_ETIMEOUT) {
+            fail_all(S, why.c_str());
+            if (timed_out) S->worker_timed_out = true;
+        }
+    }
+    for (Request* r : S->queue) finish(S, r, RGS_EAGAIN, "serve: cancelled (server destroyed)");
+    S->queue.clear();
+}
+
+void worker_main(rgs_server* S) {
+    cudaSetDevice(S->device);
+    if (S->cfg.plain) worker_plain(S);
+    else worker_batched(S);
+}
+
+void free_lane(Lane& ln) {
+    if (ln.exec) cudaGraphExecDestroy(ln.exec);
+    if (ln.done_ev) cudaEventDestroy(ln.done_ev);
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+    if (ln.mem) cudaFree(ln.mem);
+    if (ln.slots_host) cudaFreeHost(ln.slots_host);
+    if (ln.hdr_host) cudaFreeHost(ln.hdr_host);
+    if (ln.status_host) cudaFreeHost(ln.status_host);
+    ln = Lane();
+}
+
+void free_server(rgs_server* S, bool leak_device) {
+    if (!leak_device) {
+        for (auto& ln : S->lanes) free_lane(ln);
+        if (S->plain_ws) cudaFree(S->plain_ws);
+        if (S->plain_ev) cudaEventDestroy(S->plain_ev);
+        if (S->plain_stream) cudaStreamDestroy(S->plain_stream);
+    }
+    for (auto& kv : S->tickets) delete kv.second;
+    delete S;
+}
+
+}  // namespace
+}  // namespace rgs
+
+using namespace rgs;
+
+extern "C" {
+
+void rgs_serve_default_config(rgs_serve_config* cfg) {
+    if (!cfg) return;
+    cfg->mem_budget_bytes = (size_t)8 << 30;
+    cfg->max_slots = 8;
+    cfg->lanes = 2;
+    cfg->plain = 0;
+    cfg->max_width = 4096;
+    cfg->max_height = 4096;
+    cfg->max_queue = 65536;
+    cfg->inst_per_pixel = 16.f;
+}
+
+int rgs_serve_lane_bytes(const rgs_kd* kd, const rgs_gaussians* g, const rgs_serve_config* cfg,
+                         int64_t instance_capacity, size_t* bytes) {
+    int rc;
+    if (!kd || !cfg || !bytes) { set_error("serve_lane_bytes: NULL argument"); return RGS_EINVAL; }
+    if ((rc = check_gaussians(g))) return rc;
+    if (cfg->max_slots < 1 || cfg->max_slots > kMaxSlots || cfg->max_width < 1 || cfg->max_height < 1 ||
+        instance_capacity < 0) {
+        set_error("serve_lane_bytes: invalid configuration");
+        return RGS_EINVAL;
+    }
+    const int64_t max_tiles =
+        (int64_t)((cfg->max_width + kTile - 1) / kTile) * ((cfg->max_height + kTile - 1) / kTile);
+    *bytes = lane_layout(nullptr, g->n, cfg->max_slots, max_tiles * cfg->max_slots, 1 << kd->b.L, instance_capacity,
+                         nullptr);
+    return RGS_OK;
+}
+
+int rgs_serve_create(const rgs_kd* kd, const rgs_gaussians* g, const rgs_render_opts* opts, size_t mem_budget_bytes,
+                     int max_slots, rgs_server** out) {
+    rgs_serve_config cfg;
+    rgs_serve_default_config(&cfg);
+    cfg.mem_budget_bytes = mem_budget_bytes;
+    cfg.max_slots = max_slots;
+    return rgs_serve_create_ex(kd, g, opts, &cfg, out);
+}
+
+int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_render_opts* opts,
+                        const rgs_serve_config* cfg, rgs_server** out) {
+    int rc;
+    if (!out) { set_error("serve_create: NULL out"); return RGS_EINVAL; }
+    *out = nullptr;
+    if (!kd || !cfg) { set_error("serve_create: NULL kd or config"); return RGS_EINVAL; }
+    if ((rc = check_gaussians(g)) || (rc = check_opts(opts))) return rc;
+    if (kd->b.L > kMaxRenderDepth) {
+        set_error("serve_create: KD depth %d > %d", kd->b.L, kMaxRenderDepth);
+        return RGS_EINVAL;
+    }
+    if (cfg->max_slots < 1 || cfg->max_slots > kMaxSlots || cfg->lanes < 1 || cfg->lanes > 4 ||
+        cfg->max_width < 1 || cfg->max_width > 16384 || cfg->max_height < 1 || cfg->max_height > 16384 ||
+        cfg->max_queue < 1 || !(cfg->inst_per_pixel > 0.f)) {
+        set_error("serve_create: need max_slots in [1,%d], lanes in [1,4], max size in [1,16384], max_queue >= 1, "
+                  "inst_per_pixel > 0", kMaxSlots);
+        return RGS_EINVAL;
+    }
+    rgs_server* S = new (std::nothrow) rgs_server();
+    if (!S) { set_error("serve_create: out of host memory"); return RGS_ENOMEM; }
+    S->kd = kd;
+    S->g = *g;
+    S->opts = *opts;
+    S->cfg = *cfg;
+    memset(&S->stats, 0, sizeof S->stats);
+    S->inst_per_pixel = cfg->inst_per_pixel;
+    S->L = kd->b.L;
+    S->K = 1 << kd->b.L;
+    memset(&S->tp, 0, sizeof S->tp);
+    S->tp.L = kd->b.L;
+    for (int j = 0; j < S->K - 1; ++j) {
+        S->tp.axis[j] = kd->b.axis[j];
+        S->tp.split[j] = kd->b.split[j];
+    }
+    auto fail = [&](int code) {
+        free_server(S, false);
+        return code;
+    };
+    if (cudaGetDevice(&S->device) != cudaSuccess) { set_error("serve_create: no CUDA device"); return fail(RGS_ECUDA); }
+    const int64_t max_tiles =
+        (int64_t)((cfg->max_width + kTile - 1) / kTile) * ((cfg->max_height + kTile - 1) / kTile);
+    if (cfg->plain) {
+        // one workspace for rgs_render_fwd's path
+        rgs_camera big;
+        memset(&big, 0, sizeof big);
+        big.viewmat[0] = big.viewmat[5] = big.viewmat[10] = big.viewmat[15] = 1.f;
+        big.fx = big.fy = 1.f;
+        big.width = cfg->max_width;
+        big.height = cfg->max_height;
+        big.near_z = 0.2f;
+        size_t fixed = 0;
+        if ((rc = rgs_render_workspace_size(kd, g, &big, opts, 1 << 20, &fixed))) return fail(rc);
+        if (cfg->mem_budget_bytes < fixed) {
+            set_error("serve_create: budget %zu below the %zu bytes of one %dx%d render", cfg->mem_budget_bytes, fixed,
+                      cfg->max_width, cfg->max_height);
+            return fail(RGS_EINVAL);
+        }
+        S->plain_ws_bytes = cfg->mem_budget_bytes;
+        S->tiles_cap = max_tiles;
+        S->inst_cap = (int64_t)((cfg->mem_budget_bytes - fixed) / 16) + (1 << 20);
+        if (cudaMalloc(&S->plain_ws, S->plain_ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("serve_create: cannot allocate %zu device bytes", S->plain_ws_bytes);
+            return fail(RGS_ENOMEM);
+        }
+        if (cudaStreamCreateWithFlags(&S->plain_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S->plain_ev, cudaEventDisableTiming) != cudaSuccess) {
+            set_error("serve_create: stream/event creation failed");
+            return fail(RGS_ECUDA);
+        }
+    } else {
+        const size_t lane_budget = cfg->mem_budget_bytes / (size_t)cfg->lanes;
+        S->tiles_cap = max_tiles * cfg->max_slots;
+        if (ceil_log2(S->tiles_cap) + S->L > 32) { set_error("serve_create: tile keys exceed 32 bits"); return fail(RGS_EINVAL); }
+        const size_t fixed = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, 0, nullptr);
+        const int64_t min_inst = (int64_t)1 << 16;
+        if (lane_budget < fixed + (size_t)min_inst * 16) {
+            set_error("serve_create: a lane needs at least %zu bytes (%zu given per lane)", fixed + (size_t)min_inst * 16,
+                      lane_budget);
+            return fail(RGS_EINVAL);
+        }
+        int64_t cap = (int64_t)((lane_budget - fixed) / 16);
+        while (cap > min_inst && lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr) > lane_budget)
+            cap -= 64;
+        if (cap > 0xFFFFFFFEll) cap = 0xFFFFFFFEll;
+        S->inst_cap = cap;
+        S->lanes.resize(cfg->lanes);
+        for (auto& ln : S->lanes) {
+            const size_t bytes = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr);
+            if (cudaMalloc(&ln.mem, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("serve_create: cannot allocate %zu device bytes for a lane", bytes);
+                return fail(RGS_ENOMEM);
+            }
+            lane_layout(ln.mem, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, &ln.bufs);
+            if (cudaMallocHost(&ln.slots_host, sizeof(BatchSlot) * kMaxSlots) != cudaSuccess ||
+                cudaMallocHost(&ln.hdr_host, sizeof(BatchHeader)) != cudaSuccess ||
+                cudaMallocHost(&ln.status_host, 8 * kBatchCounters) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ln.done_ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("serve_create: pinned memory, stream or event creation failed");
+                return fail(RGS_ECUDA);
+            }
+            memset(ln.slots_host, 0, sizeof(BatchSlot) * kMaxSlots);
+            memset(ln.hdr_host, 0, sizeof(BatchHeader));
+            // capture the lane's batch pipeline once
+            cudaGraph_t graph = nullptr;
+            RGS_CUDA_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
+            prof_suppress(true);
+            rc = enqueue_batch(S->g, S->tp, S->K, S->L, cfg->max_slots, S->tiles_cap, ln.bufs, ln.slots_host,
+                               ln.hdr_host, ln.status_host, ln.stream);
+            prof_suppress(false);
+            const cudaError_t ec = cudaStreamEndCapture(ln.stream, &graph);
+            if (rc || ec != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                if (!rc) set_error("serve_create: stream capture failed: %s", cudaGetErrorString(ec));
+                return fail(rc ? rc : RGS_ECUDA);
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&ln.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                set_error("serve_create: graph instantiation failed: %s", cudaGetErrorString(ei));
+                return fail(RGS_ECUDA);
+            }
+        }
+    }
+    S->stats.instance_capacity = S->inst_cap;
+    try {
+        S->worker = std::thread(worker_main, S);
+    } catch (...) {
+        set_error("serve_create: cannot start the scheduler thread");
+        return fail(RGS_ENOMEM);
+    }
+    *out = S;
+    return RGS_OK;
+}
+
+int rgs_serve_submit(rgs_server* S, const rgs_camera* cam, float* out_image, uint64_t* ticket) {
+    int rc;
+    if (!S || !out_image || !ticket) { set_error("serve_submit: NULL argument"); return RGS_EINVAL; }
+    if ((rc = check_camera(cam))) return rc;
+    if (cam->width > S->cfg.max_width || cam->height > S->cfg.max_height) {
+        set_error("serve_submit: %dx%d exceeds the server's %dx%d", cam->width, cam->height, S->cfg.max_width,
+                  S->cfg.max_height);
+        return RGS_EINVAL;
+    }
+    Request* r = new (std::nothrow) Request();
+    if (!r) { set_error("serve_submit: out of host memory"); return RGS_ENOMEM; }
+    r->cam = *cam;
+    r->out = out_image;
+    TreeParams tp_unused;
+    fill_view(S->kd, &S->g, cam, &S->opts, &r->vp, &tp_unused);
+    r->tiles = (int64_t)r->vp.tiles_x * r->vp.tiles_y;
+    r->pixels = (int64_t)cam->width * cam->height;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop || S->broken) {
+            delete r;
+            set_error("serve_submit: server is stopping or failed");
+            return RGS_EAGAIN;
+        }
+        if ((int64_t)S->queue.size() >= S->cfg.max_queue) {
+            delete r;
+            set_error("serve_submit: queue full (%d requests)", S->cfg.max_queue);
+            return RGS_EAGAIN;
+        }
+        r->ticket = S->next_ticket++;
+        r->t_submit = Clock::now();
+        S->tickets[r->ticket] = r;
+        S->queue.push_back(r);
+        ++S->stats.submitted;
+        *ticket = r->ticket;
+    }
+    S->cv.notify_one();
+    return RGS_OK;
+}
+
+int rgs_serve_poll(rgs_server* S, uint64_t ticket, int* done, double* latency_ms) {
+    if (!S || !done) { set_error("serve_poll: NULL argument"); return RGS_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) {
+        set_error("serve_poll: unknown ticket %llu", (unsigned long long)ticket);
+        return RGS_EINVAL;
+    }
+    Request* r = it->second;
+    if (!r->done) {
+        *done = 0;
+        return RGS_OK;
+    }
+    *done = 1;
+    if (latency_ms) *latency_ms = r->latency_ms;
+    const int status = r->status;
+    if (status != RGS_OK) set_error("%s", r->err[0] ? r->err : "serve: request failed");
+    S->tickets.erase(it);
+    delete r;
+    return status;
+}
+
+int rgs_serve_stats_read(rgs_server* S, rgs_serve_stats* out) {
+    if (!S || !out) { set_error("serve_stats: NULL argument"); return RGS_EINVAL; }
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    out->mean_batch = S->stats.batches ? (double)S->batched_requests / (double)S->stats.batches : 0.0;
+    return RGS_OK;
+}
+
+int rgs_serve_destroy(rgs_server* S) {
+    if (!S) return RGS_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    const bool timed_out = S->worker_timed_out;
+    free_server(S, timed_out);
+    if (timed_out) {
+        set_error("serve_destroy: work on the GPU did not finish within 10 s; its buffers were left allocated");
+        return RGS_ETIMEOUT;
+    }
+    return RGS_OK;
+}
+
+}  // extern "C"

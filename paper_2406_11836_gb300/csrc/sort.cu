@@ -51,15 +51,15 @@ scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n, int mode, const u
     }
 }
 
-// Exclusive scan of one tile plus the tile's offset.  Items are loaded coalesced into
-// shared memory (padded against bank conflicts), each thread scans 16 consecutive items,
-// and the thread totals are scanned across the block.
-__global__ void __launch_bounds__(kScanThreads)
-scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const uint32_t* __restrict__ gather,
-                 const uint32_t* __restrict__ tile_offsets) {
+// Exclusive scan of the tile [base, base + kScanTile) of the input plus `offset`; returns
+// the tile's total.  Items are loaded coalesced into shared memory (padded against bank
+// conflicts), each thread scans 16 consecutive items, and the thread totals are scanned
+// across the block.  In-place use (in == out) is safe: the tile is read before it is written.
+__device__ __forceinline__ uint32_t scan_tile_body(const uint32_t* in, uint32_t* out, int64_t n, int mode,
+                                                   const uint32_t* __restrict__ gather, int64_t base,
+                                                   uint32_t offset) {
     __shared__ uint32_t sm[kScanTile + kScanTile / 32];
     __shared__ uint32_t warp_tot[kScanThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
     auto pad = [](int i) { return i + (i >> 5); };
     for (int j = 0; j < kScanItems; ++j) {
         int li = j * kScanThreads + threadIdx.x;
@@ -82,8 +82,11 @@ scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const u
     }
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
-    uint32_t wbase = tile_offsets ? tile_offsets[blockIdx.x] : 0u;
-    for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+    uint32_t wbase = offset, total = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        if (w < warp) wbase += warp_tot[w];
+        total += warp_tot[w];
+    }
     uint32_t run = wbase + incl - tsum;
     for (int j = 0; j < kScanItems; ++j) {
         uint32_t x = v[j];
@@ -96,6 +99,15 @@ scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const u
         int64_t i = base + li;
         if (i < n) out[i] = sm[pad(li)];
     }
+    __syncthreads();   // the shared tile is reused by the caller's next tile
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const uint32_t* __restrict__ gather,
+                 const uint32_t* __restrict__ tile_offsets) {
+    scan_tile_body(in, out, n, mode, gather, (int64_t)blockIdx.x * kScanTile,
+                   tile_offsets ? tile_offsets[blockIdx.x] : 0u);
 }
 
 // Per-tile histogram of one 8-bit digit, written digit-major: counts[d * nblocks + b].
@@ -117,22 +129,22 @@ radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, ui
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
 }
 
-// Stable scatter of one tile by one digit.  Warp w owns tile items [w*256, (w+1)*256) and
-// walks them in 8 rounds of 32 lanes, so (round, lane) order is the input order; a
-// per-warp digit counter plus the rank among equal digits of the round gives each key's
-// rank within its warp, the per-digit scan over warps gives its rank within the tile.
-__global__ void __launch_bounds__(kSortThreads, 4)
-radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-                       uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
-                       uint32_t nblocks) {
+// Stable scatter of the tile [base, base + count) (count <= kSortTile) by one digit.
+// Warp w owns tile items [w*256, (w+1)*256) and walks them in 8 rounds of 32 lanes, so
+// (round, lane) order is the input order; a per-warp digit counter plus the rank among
+// equal digits of the round gives each key's rank within its warp, the per-digit scan
+// over warps gives its rank within the tile.  goff[d] (shared) is where the tile's first
+// key of digit d goes; on return it has advanced past the tile's keys of digit d.
+__device__ __forceinline__ void radix_tile_body(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                int64_t base, int count, int shift, uint32_t* goff) {
     __shared__ uint32_t whist[kSortWarps][kRadix];
     __shared__ uint32_t dstart[kRadix];
     __shared__ uint32_t dtot[kRadix];
-    __shared__ uint32_t goff[kRadix];
+    __shared__ uint32_t wsum[kSortWarps];
     __shared__ uint32_t skeys[kSortTile];
     __shared__ uint32_t svals[kSortTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
     __syncthreads();
 
@@ -140,10 +152,10 @@ radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restr
     int dig[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + warp * (kSortItems * 32) + r * 32 + lane;
-        bool ok = i < n;
-        key[r] = ok ? kin[i] : 0u;
-        val[r] = ok ? vin[i] : 0u;
+        const int li = warp * (kSortItems * 32) + r * 32 + lane;
+        const bool ok = li < count;
+        key[r] = ok ? kin[base + li] : 0u;
+        val[r] = ok ? vin[base + li] : 0u;
         dig[r] = ok ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
     }
 #pragma unroll
@@ -165,7 +177,6 @@ radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restr
             run += c;
         }
         dtot[d] = run;
-        goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
     }
     __syncthreads();
     // exclusive scan of the digit totals (kRadix == kSortThreads: one per thread)
@@ -176,7 +187,6 @@ radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restr
             uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        __shared__ uint32_t wsum[kSortWarps];
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
         uint32_t b = 0;
@@ -193,14 +203,107 @@ radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restr
         }
     }
     __syncthreads();
-    int64_t rem = n - base;
-    int count = rem < kSortTile ? (int)rem : kSortTile;
     for (int i = threadIdx.x; i < count; i += kSortThreads) {
         uint32_t k = skeys[i];
         int d = (int)((k >> shift) & (kRadix - 1));
         uint32_t o = goff[d] + (uint32_t)i - dstart[d];
         kout[o] = k;
         vout[o] = svals[i];
+    }
+    __syncthreads();
+    goff[threadIdx.x] += dtot[threadIdx.x];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSortThreads, 4)
+radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                       uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
+                       uint32_t nblocks) {
+    __shared__ uint32_t goff[kRadix];
+    goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int64_t rem = n - base;
+    radix_tile_body(kin, vin, kout, vout, base, rem < kSortTile ? (int)rem : kSortTile, shift, goff);
+}
+
+// ------------------------------------------------------------------ device-counted passes
+// Variants whose element count is read from device memory (a counter written by an
+// earlier kernel on the stream), so that the launches need no host round trip and can
+// be captured in a CUDA graph.  The grid is fixed: block c owns the c-th of kChunks
+// contiguous chunks (whole tiles) of [0, n) and walks its tiles in order, so scans and
+// sorts stay stable.
+constexpr int kChunks = 608;   // 152 SMs x 4 resident blocks
+
+__device__ __forceinline__ void chunk_range(int64_t n, int64_t tile, int64_t& lo, int64_t& hi) {
+    const int64_t tiles = (n + tile - 1) / tile;
+    const int64_t per = (tiles + kChunks - 1) / kChunks;
+    lo = min(n, (int64_t)blockIdx.x * per * tile);
+    hi = min(n, lo + per * tile);
+}
+
+__device__ __forceinline__ int64_t device_count(const unsigned long long* n_dev, int64_t cap) {
+    const unsigned long long v = *n_dev;
+    return v < (unsigned long long)cap ? (int64_t)v : cap;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+dscan_reduce_kernel(const uint32_t* __restrict__ in, const unsigned long long* __restrict__ n_dev, int64_t cap,
+                    int mode, const uint32_t* __restrict__ gather, uint32_t* __restrict__ sums) {
+    int64_t lo, hi;
+    chunk_range(device_count(n_dev, cap), kScanTile, lo, hi);
+    uint32_t acc = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kScanThreads) acc += load_item(in, gather, i, mode);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ uint32_t ws[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+dscan_tile_kernel(const uint32_t* in, uint32_t* out, const unsigned long long* __restrict__ n_dev, int64_t cap,
+                  int mode, const uint32_t* __restrict__ gather, const uint32_t* __restrict__ chunk_offsets) {
+    int64_t lo, hi;
+    const int64_t n = device_count(n_dev, cap);
+    chunk_range(n, kScanTile, lo, hi);
+    uint32_t off = chunk_offsets[blockIdx.x];
+    for (int64_t base = lo; base < hi; base += kScanTile) off += scan_tile_body(in, out, hi, mode, gather, base, off);
+}
+
+__global__ void __launch_bounds__(kSortThreads, 4)
+dradix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev, int64_t cap,
+                      int shift, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t hist[kRadix];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t lo, hi;
+    chunk_range(device_count(n_dev, cap), kSortTile, lo, hi);
+    const int lane = threadIdx.x & 31;
+    for (int64_t b = lo; b < hi; b += kSortThreads) {   // uniform trip count across the block
+        const int64_t i = b + threadIdx.x;
+        const int d = i < hi ? (int)((keys[i] >> shift) & (kRadix - 1)) : kRadix;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < kRadix && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * kChunks + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads, 4)
+dradix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                        uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, int64_t cap,
+                        int shift, const uint32_t* __restrict__ offsets) {
+    __shared__ uint32_t goff[kRadix];
+    goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * kChunks + blockIdx.x];
+    int64_t lo, hi;
+    chunk_range(device_count(n_dev, cap), kSortTile, lo, hi);
+    for (int64_t base = lo; base < hi; base += kSortTile) {
+        const int64_t rem = hi - base;
+        radix_tile_body(kin, vin, kout, vout, base, rem < kSortTile ? (int)rem : kSortTile, shift, goff);
     }
 }
 
@@ -275,6 +378,66 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_
         int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
         if (rc != RGS_OK) return rc;
         radix_downsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, va, kb, vb, n, shift, counts, (uint32_t)nb);
+        RGS_CUDA_LAUNCH_CHECK();
+        uint32_t* t;
+        t = ka; ka = kb; kb = t;
+        t = va; va = vb; vb = t;
+        *in_alt = !*in_alt;
+    }
+    return RGS_OK;
+}
+
+size_t scan_dev_temp_bytes() { return align256((size_t)kChunks * 4) + 256; }
+
+int exclusive_scan_dev(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev, int64_t cap, int load,
+                       const uint32_t* gather, void* temp, size_t temp_bytes, cudaStream_t s) {
+    static_assert(kChunks <= kScanTile, "chunk sums are scanned by one block");
+    if (cap <= 0) return RGS_OK;
+    if (temp_bytes < scan_dev_temp_bytes()) {
+        set_error("scan: temporary buffer too small");
+        return RGS_EOVERFLOW;
+    }
+    uint32_t* sums = (uint32_t*)temp;
+    dscan_reduce_kernel<<<kChunks, kScanThreads, 0, s>>>(in, n_dev, cap, load, gather, sums);
+    RGS_CUDA_LAUNCH_CHECK();
+    scan_tile_kernel<<<1, kScanThreads, 0, s>>>(sums, sums, kChunks, 0, nullptr, nullptr);
+    RGS_CUDA_LAUNCH_CHECK();
+    dscan_tile_kernel<<<kChunks, kScanThreads, 0, s>>>(in, out, n_dev, cap, load, gather, sums);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+size_t radix_dev_temp_bytes() {
+    const int64_t nc = (int64_t)kRadix * kChunks;
+    return align256((size_t)nc * 4) + scan_temp_bytes(nc);
+}
+
+int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                         const unsigned long long* n_dev, int64_t cap, int end_bit, void* temp, size_t temp_bytes,
+                         cudaStream_t s, bool* in_alt) {
+    static_assert(kRadix == kSortThreads, "one digit per thread");
+    *in_alt = false;
+    if (cap <= 1 || end_bit <= 0) return RGS_OK;
+    if (cap > 0xFFFFFFFFll) {
+        set_error("radix sort: capacity %lld exceeds the 32-bit index range", (long long)cap);
+        return RGS_EOVERFLOW;
+    }
+    const int64_t nc = (int64_t)kRadix * kChunks;
+    const size_t cbytes = align256((size_t)nc * 4);
+    if (temp_bytes < radix_dev_temp_bytes()) {
+        set_error("radix sort: temporary buffer too small");
+        return RGS_EOVERFLOW;
+    }
+    uint32_t* counts = (uint32_t*)temp;
+    void* stemp = (char*)temp + cbytes;
+    const size_t sbytes = temp_bytes - cbytes;
+    uint32_t *ka = keys, *va = vals, *kb = keys_alt, *vb = vals_alt;
+    for (int shift = 0; shift < end_bit; shift += kRadixBits) {
+        dradix_upsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, n_dev, cap, shift, counts);
+        RGS_CUDA_LAUNCH_CHECK();
+        int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
+        if (rc != RGS_OK) return rc;
+        dradix_downsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, va, kb, vb, n_dev, cap, shift, counts);
         RGS_CUDA_LAUNCH_CHECK();
         uint32_t* t;
         t = ka; ka = kb; kb = t;

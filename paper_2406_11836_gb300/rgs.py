@@ -45,6 +45,17 @@ class RenderOpts(ctypes.Structure):
                 ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", c_size_t), ("max_slots", c_int), ("lanes", c_int), ("plain", c_int),
+                ("max_width", c_int), ("max_height", c_int), ("max_queue", c_int), ("inst_per_pixel", c_float)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("cancelled", c_int64),
+                ("batches", c_int64), ("requeued", c_int64), ("instance_capacity", c_int64),
+                ("mean_batch", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -85,6 +96,15 @@ def lib():
     L.rgs_profile_stage_name.restype = ctypes.c_char_p
     L.rgs_profile_stage_name.argtypes = [c_int]
     L.rgs_profile_read.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
+    L.rgs_serve_default_config.argtypes = [POINTER(ServeConfig)]
+    L.rgs_serve_default_config.restype = None
+    L.rgs_serve_create_ex.argtypes = [c_void_p, POINTER(Gaussians), POINTER(RenderOpts), POINTER(ServeConfig),
+                                      POINTER(c_void_p)]
+    L.rgs_serve_submit.argtypes = [c_void_p, POINTER(CameraC), c_void_p, POINTER(ctypes.c_uint64)]
+    L.rgs_serve_poll.argtypes = [c_void_p, ctypes.c_uint64, POINTER(c_int), POINTER(ctypes.c_double)]
+    L.rgs_serve_stats_read.argtypes = [c_void_p, POINTER(ServeStats)]
+    L.rgs_serve_lane_bytes.argtypes = [c_void_p, POINTER(Gaussians), POINTER(ServeConfig), c_int64, POINTER(c_size_t)]
+    L.rgs_serve_destroy.argtypes = [c_void_p]
     _lib = L
     return L
 
@@ -235,21 +255,25 @@ def _retry(call, ws: Workspace):
     _check(rc)
 
 
-def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image=True, stream=None, out=None):
-    """Partial maps [K,3,H,W] / [K,H,W] and, if image, the merged image [3,H,W] and T_final."""
+def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image=True, stream=None, out=None,
+               partials=True):
+    """Partial maps [K,3,H,W] / [K,H,W] and, if image, the merged image [3,H,W] and T_final.
+    partials=False renders the image only (forward only, no backward from it)."""
     H, W = int(cam.height), int(cam.width)
     dev = torch.device("cuda", torch.cuda.current_device())
     if out is None:
         tiles = ((H + 15) // 16) * ((W + 15) // 16)
-        out = {"partial_C": torch.empty(kd.K, 3, H, W, device=dev), "partial_T": torch.empty(kd.K, H, W, device=dev),
-               "tile_depth": torch.empty(tiles, kd.K, device=dev)}
-        if image:
+        out = {"tile_depth": torch.empty(tiles, kd.K, device=dev)}
+        if partials:
+            out["partial_C"] = torch.empty(kd.K, 3, H, W, device=dev)
+            out["partial_T"] = torch.empty(kd.K, H, W, device=dev)
+        if image or not partials:
             out["image"] = torch.empty(3, H, W, device=dev)
             out["T_final"] = torch.empty(H, W, device=dev)
     c = camera_c(cam)
     s = _stream(stream)
     _retry(lambda: lib().rgs_render_fwd(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
-                                        _ptr(out["partial_C"]), _ptr(out["partial_T"]), _ptr(out.get("image")),
+                                        _ptr(out.get("partial_C")), _ptr(out.get("partial_T")), _ptr(out.get("image")),
                                         _ptr(out.get("T_final")), _ptr(out.get("tile_depth")), ws.ptr(), ws.nbytes,
                                         s), ws)
     return out
@@ -332,8 +356,97 @@ def profile_read(reset: bool = True) -> dict:
     return {"stages": stages, "counters": dict(zip(PAIR_COUNTERS, (int(c) for c in counters)))}
 
 
+# --------------------------------------------------------------------------- serving
+def serve_config(mem_budget_bytes=8 << 30, max_slots=8, lanes=2, plain=False, max_width=4096, max_height=4096,
+                 max_queue=65536, inst_per_pixel=16.0) -> ServeConfig:
+    cfg = ServeConfig()
+    lib().rgs_serve_default_config(ctypes.byref(cfg))
+    cfg.mem_budget_bytes = int(mem_budget_bytes)
+    cfg.max_slots, cfg.lanes, cfg.plain = int(max_slots), int(lanes), 1 if plain else 0
+    cfg.max_width, cfg.max_height, cfg.max_queue = int(max_width), int(max_height), int(max_queue)
+    cfg.inst_per_pixel = float(inst_per_pixel)
+    return cfg
+
+
+def serve_lane_bytes(kd: KD, g: Gaussians, instance_capacity: int, **cfg_kw) -> int:
+    """Device bytes of one batched lane holding `instance_capacity` tile instances."""
+    cfg = serve_config(**cfg_kw)
+    n = c_size_t()
+    _check(lib().rgs_serve_lane_bytes(kd.handle, ctypes.byref(g), ctypes.byref(cfg), int(instance_capacity),
+                                      ctypes.byref(n)))
+    return int(n.value)
+
+
+class Server:
+    """Render server over a resident scene (rgs_serve_*).  The scene tensors behind `g` and
+    the KD must stay alive while the server does; output images are caller-owned."""
+
+    def __init__(self, kd: KD, g: Gaussians, opts: RenderOpts, mem_budget_bytes: int, max_slots: int = 8,
+                 lanes: int = 2, plain: bool = False, max_width: int = 4096, max_height: int = 4096,
+                 max_queue: int = 65536, inst_per_pixel: float = 16.0, keepalive=None):
+        L = lib()
+        cfg = serve_config(mem_budget_bytes, max_slots, lanes, plain, max_width, max_height, max_queue, inst_per_pixel)
+        self._keep = (kd, g, opts, keepalive)
+        self._g, self._opts = g, opts
+        h = c_void_p()
+        _check(L.rgs_serve_create_ex(kd.handle, ctypes.byref(g), ctypes.byref(opts), ctypes.byref(cfg),
+                                     ctypes.byref(h)))
+        self.handle = h
+        self.outputs = {}
+
+    def submit(self, cam, out) -> int:
+        """Queue a render of cam into out ([3,H,W] float32 cuda tensor); returns the ticket."""
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert tuple(out.shape) == (3, int(cam.height), int(cam.width))
+        c = camera_c(cam)
+        t = ctypes.c_uint64()
+        _check(lib().rgs_serve_submit(self.handle, ctypes.byref(c), _ptr(out), ctypes.byref(t)))
+        self.outputs[t.value] = out
+        return t.value
+
+    def poll(self, ticket):
+        """(done, latency_ms); raises RGSError if the request failed."""
+        done = c_int(0)
+        lat = ctypes.c_double(0.0)
+        rc = lib().rgs_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(lat))
+        if done.value:
+            self.outputs.pop(ticket, None)
+        _check(rc)
+        return bool(done.value), float(lat.value)
+
+    def wait(self, ticket, timeout_s: float = 60.0):
+        """Poll until done (bounded); returns the latency in ms."""
+        import time
+        t0 = time.monotonic()
+        while True:
+            done, lat = self.poll(ticket)
+            if done:
+                return lat
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
+            time.sleep(0.0002)
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(lib().rgs_serve_stats_read(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            h, self.handle = self.handle, None
+            _check(lib().rgs_serve_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_merge_partials", "rgs_merge_partials_bwd",
                "rgs_render_bwd", "rgs_adam_step", "rgs_position_lr", "rgs_profile_enable",
-               "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read")
+               "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
+               "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
+               "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes")

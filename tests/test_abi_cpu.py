@@ -75,3 +75,26 @@ def test_missing_library_fails_loudly(R, monkeypatch):
     monkeypatch.setattr(R, "LIB_PATH", "/nonexistent/librgs.so")
     with pytest.raises(RuntimeError, match="missing"):
         R.lib()
+
+
+def test_serving_arguments_are_rejected(R):
+    lib = R.lib()
+    cfg = R.ServeConfig()
+    lib.rgs_serve_default_config(ctypes.byref(cfg))
+    assert cfg.max_slots == 8 and cfg.lanes == 2 and cfg.plain == 0 and cfg.max_width == 4096
+    out = ctypes.c_void_p()
+    fake = 1 << 20
+    g = R.Gaussians(fake, fake, fake, fake, fake, 10, 3)
+    opts = R.default_opts()
+    # NULL kd, NULL out: rejected before any CUDA call
+    assert lib.rgs_serve_create_ex(None, ctypes.byref(g), ctypes.byref(opts), ctypes.byref(cfg),
+                                   ctypes.byref(out)) == R.RGS_EINVAL
+    assert lib.rgs_serve_create_ex(None, ctypes.byref(g), ctypes.byref(opts), ctypes.byref(cfg), None) == R.RGS_EINVAL
+    cam = R.CameraC()
+    t = ctypes.c_uint64()
+    assert lib.rgs_serve_submit(None, ctypes.byref(cam), ctypes.c_void_p(fake), ctypes.byref(t)) == R.RGS_EINVAL
+    done = ctypes.c_int()
+    assert lib.rgs_serve_poll(None, 1, ctypes.byref(done), None) == R.RGS_EINVAL
+    st = R.ServeStats()
+    assert lib.rgs_serve_stats_read(None, ctypes.byref(st)) == R.RGS_EINVAL
+    assert lib.rgs_serve_destroy(None) == R.RGS_OK
