@@ -50,12 +50,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // the row's tile columns from the footprint (the same arithmetic as the count), and
 // write the row's instances at the positions a warp prefix sum gives them.
 // Instances of one splat (record id, first instance slot `base`), written by the calling
-// warp; global tile indices start at tile_base.
+// warp; global tile indices start at tile_base.  32 (subset, row) items at a time: each
+// lane finds its item's tile columns, a warp prefix sum places the items' runs, and
+// without depth culling the warp then writes the round's contiguous range together
+// (lane l writes positions l, l + 32, ...: coalesced stores), finding each position's
+// item by a forward scan of the run starts.
 __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams& tp, uint32_t id, uint32_t base,
                                          uint32_t tile_base, const ushort4* __restrict__ rect,
                                          const unsigned long long* __restrict__ mask, const float4* __restrict__ rec,
                                          const float* __restrict__ cull, const float2* __restrict__ chunk,
-                                         uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane) {
+                                         uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane,
+                                         uint32_t* s_start, uint32_t* s_key0) {
     const ushort4 r = rect[id];
     const unsigned long long m = mask[id];
     const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
@@ -78,14 +83,21 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        uint32_t pos = base + incl - w;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
-        if (w && !cull) {
-            for (int c = c0; c <= c1; ++c, ++pos) {
-                ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                ival[pos] = id;
+        if (!cull) {
+            s_start[lane] = incl - w;
+            s_key0[lane] = ((first + (uint32_t)c0) << vp.L) | rank;
+            __syncwarp();
+            int cur = 0;
+            for (uint32_t o = (uint32_t)lane; o < total; o += 32) {
+                while (cur < 31 && s_start[cur + 1] <= o) ++cur;   // runs of empty items share a start
+                ikey[base + o] = s_key0[cur] + ((o - s_start[cur]) << vp.L);
+                ival[base + o] = id;
             }
+            __syncwarp();
         } else if (w) {
+            uint32_t pos = base + incl - w;
             const int nch = cull_nchunk(vp);
             for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
                 const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
@@ -100,20 +112,69 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
                 }
             }
         }
-        base += __shfl_sync(0xffffffffu, incl, 31);
+        base += total;
     }
 }
 
+// Instances of one small splat (at most kEmitThreadItems items), written by one thread.
+constexpr int kEmitThreadItems = 4;
+
+__device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreeParams& tp, uint32_t id, uint32_t pos,
+                                            uint32_t tile_base, const Footprint& f, unsigned long long m, int nsub,
+                                            float z, int ty0, int rows, int items, const float* __restrict__ cull,
+                                            const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
+                                            uint32_t* __restrict__ ival) {
+    for (int it = 0; it < items; ++it) {
+        int ty, k, c0, c1;
+        item_span(f, vp, tp, m, nsub, z, ty0, rows, it, ty, k, c0, c1);
+        const uint32_t rank = (uint32_t)vp.rank_of[k];
+        const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
+        for (int c = c0; c <= c1; ++c) {
+            if (cull && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
+            ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+            ival[pos] = id;
+            ++pos;
+        }
+    }
+}
+
+// Emission of the depth-sorted visible splats, 32 per warp: a splat with few (subset,
+// row) items is emitted by its own lane, the others by the whole warp in turn (the same
+// split as the count in the projection).
 __global__ void __launch_bounds__(256)
 emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
             const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
             const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_start[8][32], s_key0[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = warp; p < n_vis; p += nwarps)
-        emit_one(vp, tp, sorted_ids[p], ioff[p], 0u, rect, mask, rec, cull, chunk, ikey, ival, lane);
+    for (int64_t p0 = warp * 32; p0 < n_vis; p0 += nwarps * 32) {
+        const int64_t p = p0 + lane;
+        uint32_t id = 0, base = 0;
+        int items = 0;
+        if (p < n_vis) {
+            id = sorted_ids[p];
+            base = ioff[p];
+            const ushort4 r = rect[id];
+            const unsigned long long m = mask[id];
+            const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
+            items = nsub * rows;
+            if (items <= kEmitThreadItems) {
+                const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+                const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+                emit_thread(vp, tp, id, base, 0u, f, m, nsub, r2.w, r.y, rows, items, cull, chunk, ikey, ival);
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sbase = __shfl_sync(0xffffffffu, base, src);
+            emit_one(vp, tp, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane, s_start[wib], s_key0[wib]);
+        }
+    }
 }
 
 // Copies the batch's view parameters into shared memory (the whole block).
@@ -126,8 +187,8 @@ __device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ s
     __syncthreads();
 }
 
-// Batch emission: sorted ids are slot * N + i, so each warp takes its splat's view from
-// the block's shared copy of the slot table.
+// Batch emission: sorted ids are slot * N + i, so each lane takes its splat's view from
+// the block's shared copy of the slot table; the same thread / warp split as emit_kernel.
 __global__ void __launch_bounds__(256)
 emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
                   const uint32_t* __restrict__ sorted_ids, int64_t n_cap, int64_t N,
@@ -142,13 +203,39 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
     load_batch_views(slots, S, svp);
     const unsigned long long nv = counters[1];
     const int64_t n = nv < (unsigned long long)n_cap ? (int64_t)nv : n_cap;
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t s_start[8][32], s_key0[8][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = warp; p < n; p += nwarps) {
-        const uint32_t id = sorted_ids[p];
-        const int slot = (int)(id / (uint64_t)N);
-        emit_one(svp[slot], tp, id, ioff[p], sbase[slot], rect, mask, rec, nullptr, nullptr, ikey, ival, lane);
+    for (int64_t p0 = warp * 32; p0 < n; p0 += nwarps * 32) {
+        const int64_t p = p0 + lane;
+        uint32_t id = 0, base = 0;
+        int items = 0, slot = 0;
+        if (p < n) {
+            id = sorted_ids[p];
+            base = ioff[p];
+            slot = (int)(id / (uint64_t)N);
+            const ushort4 r = rect[id];
+            const unsigned long long m = mask[id];
+            const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
+            items = nsub * rows;
+            if (items <= kEmitThreadItems) {
+                const ViewParams& vp = svp[slot];
+                const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+                const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+                emit_thread(vp, tp, id, base, sbase[slot], f, m, nsub, r2.w, r.y, rows, items, nullptr, nullptr, ikey,
+                            ival);
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sb = __shfl_sync(0xffffffffu, base, src);
+            const int ss = __shfl_sync(0xffffffffu, slot, src);
+            emit_one(svp[ss], tp, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr, ikey, ival, lane, s_start[wib],
+                     s_key0[wib]);
+        }
     }
 }
 
@@ -254,20 +341,31 @@ __device__ __forceinline__ void thread_pixel(int tid, int& lx, int& ly) {
     ly = ((w >> 1) << 2) | (l >> 3);
 }
 
-struct StagedRec {   // tile-relative record in shared memory (3 x float4)
-    float4 a;        // mx, my, alpha, rho2 (sign: straddles several subsets)
-    float4 b;        // l11, l12, l22, z
-    float4 c;        // r, g, b, (splat id as bits)
+// Tile-relative record in shared memory (3 x float4):
+//   a = (mx, my, l11, l12)    centre relative to the tile origin, conic factor L = [[l11, l12], [0, l22]]
+//   b = (l22, alpha, d2max, rho2)
+//        d2max = min(trunc_mult^2, 2 ln(alpha / alpha_min)): a pixel passes the Mahalanobis
+//        test (d2 <= trunc_mult^2) and the opacity test (alpha exp(-d2/2) >= alpha_min) iff
+//        d2 <= d2max;  rho2 = (D/z)^2 of the ball test, +inf when the ball holds the whole
+//        ellipse d2 <= d2max (the test cannot fail), negated when the splat straddles
+//        subsets (the Eq. 6 test is needed)
+//   c = (r, g, b, z)
+struct StagedRec {
+    float4 a;
+    float4 b;
+    float4 c;
 };
+
+constexpr float kInfF = __builtin_huge_valf();
 
 // Bit w set: the footprint can touch warp w's 8x4 block (one span per 4-row band); for a
 // splat held by several subsets the span is also clipped to the current subset (Eq. 6).
 __device__ __forceinline__ uint32_t block_mask(const StagedRec& r, const ViewParams& vp, const LeafPath& lp, float x0t,
                                                float y0t) {
-    const Footprint f = make_footprint(r.a.x, r.a.y, r.b.x, r.b.y, r.b.z, r.a.z, r.a.w, vp);
-    const bool straddles = r.a.w < 0.f;
+    const Footprint f = make_footprint(r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.b.y, r.b.w, vp);
+    const bool straddles = r.b.w < 0.f;
     SubsetClip clip;
-    if (straddles) make_clip(vp, lp, vp.L, r.b.w, clip);
+    if (straddles) make_clip(vp, lp, vp.L, r.c.w, clip);
     uint32_t m = 0;
 #pragma unroll
     for (int band = 0; band < 4; ++band) {
@@ -283,16 +381,82 @@ __device__ __forceinline__ uint32_t block_mask(const StagedRec& r, const ViewPar
     return m;
 }
 
-__device__ __forceinline__ StagedRec stage_record(const float4* __restrict__ rec, uint32_t id, float x0, float y0) {
-    float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+// True when the ball test's screen ellipse (dx/fx)^2 + (dy/fy)^2 <= rho2 holds the splat's
+// ellipse d2 <= d2max, with 0.1% to spare: the largest value of (dx/fx)^2 + (dy/fy)^2 over
+// the splat's ellipse is d2max times the largest eigenvalue of S Sigma' S, S = diag(1/fx, 1/fy).
+__device__ __forceinline__ bool ball_holds_ellipse(const StagedRec& r, const ViewParams& vp) {
+    const float l11 = r.a.z, l12 = r.a.w, l22 = r.b.x;
+    const float qa = l11 * l11, qb = l11 * l12, qc = fmaf(l12, l12, l22 * l22);
+    const float sd = l11 * l22, idet = 1.f / (sd * sd);
+    const float mxx = qc * idet * vp.ifx * vp.ifx, myy = qa * idet * vp.ify * vp.ify;
+    const float mxy = -qb * idet * vp.ifx * vp.ify;
+    const float h = 0.5f * (mxx + myy), dd = 0.5f * (mxx - myy);
+    const float lmax = h + sqrtf(fmaf(dd, dd, mxy * mxy));
+    return fmaxf(r.b.z, 0.f) * lmax * 1.001f + 1e-30f <= fabsf(r.b.w);
+}
+
+__device__ __forceinline__ StagedRec stage_record(const float4* __restrict__ rec, uint32_t id, float x0, float y0,
+                                                  const ViewParams& vp) {
+    const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
     uint32_t lo_bits = __float_as_uint(r0.z);
     __half2 lo = *reinterpret_cast<__half2*>(&lo_bits);
     float2 lof = __half22float2(lo);
     StagedRec s;
-    s.a = make_float4(__fadd_rn(__fsub_rn(r0.x, x0), lof.x), __fadd_rn(__fsub_rn(r0.y, y0), lof.y), r0.w, r1.w);
-    s.b = make_float4(r1.x, r1.y, r1.z, r2.w);
-    s.c = make_float4(r2.x, r2.y, r2.z, __uint_as_float(id));
+    s.a = make_float4(__fadd_rn(__fsub_rn(r0.x, x0), lof.x), __fadd_rn(__fsub_rn(r0.y, y0), lof.y), r1.x, r1.y);
+    const float d2max = fminf(vp.trunc_mult * vp.trunc_mult, 2.f * logf(r0.w / vp.alpha_min));
+    s.b = make_float4(r1.z, r0.w, d2max, r1.w);
+    s.c = make_float4(r2.x, r2.y, r2.z, r2.w);
     return s;
+}
+
+// Stages record `id` for the current subset (the whole block calls it, one record per
+// thread): its tile-relative form, the mask of warp blocks it can touch, and for a
+// straddling splat the leaf planes that cut the tile (stored in `planes`; their count in
+// mask bits 8-10).  A mask of 0 drops the record.
+__device__ __forceinline__ void stage_for_subset(const float4* __restrict__ rec, uint32_t id, float x0, float y0,
+                                                 const ViewParams& vp, const LeafPath& lp, StagedRec& sr,
+                                                 uint32_t& msk, float4* planes) {
+    sr = stage_record(rec, id, x0, y0, vp);
+    msk = sr.b.z >= 0.f ? block_mask(sr, vp, lp, x0, y0) : 0u;
+    if (sr.b.w < 0.f && msk) {
+        const int nc = classify_planes(vp, lp, sr.c.w, x0 + 0.5f, y0 + 0.5f, planes);
+        if (nc < 0) msk = 0;                        // no pixel of the tile is in this subset
+        else if (nc == 0) sr.b.w = -sr.b.w;         // every pixel is: no per-pixel test
+        else msk |= (uint32_t)nc << 8;
+    }
+    if (msk && ball_holds_ellipse(sr, vp)) sr.b.w = copysignf(kInfF, sr.b.w);
+}
+
+// Compacts, per warp, the staged records whose mask has the warp's bit: wl[0..n) in
+// record order.  Returns n (uniform across the warp).
+__device__ __forceinline__ int warp_list(const uint32_t* smask, int nb, int warp, int lane, uint8_t* wl) {
+    int n = 0;
+    const unsigned lower = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+        const bool hit = c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u);
+        const unsigned bits = __ballot_sync(0xffffffffu, hit);
+        if (hit) wl[n + __popc(bits & lower)] = (uint8_t)(c0 + lane);
+        n += __popc(bits);
+    }
+    __syncwarp();
+    return n;
+}
+
+// The truncation tests of one (pixel, record) pair (Sec. 3.1 and Eq. 6): d2 <= d2max, the
+// ball test unless the ball holds the ellipse, and the subset test for straddling splats.
+// Identical in the forward and the backward, so both take the same decisions.
+__device__ __forceinline__ bool pair_passes(const float4& B, const float4& Cc, float dx, float dy, float d2,
+                                            const float4* planes, uint32_t msk, const ViewParams& vp,
+                                            const LeafPath& lp, float Xc, float Yc) {
+    bool ok = d2 <= B.z;
+    if (B.w != kInfF) {   // uniform across the warp: one record
+        if (fabsf(B.w) != kInfF) {
+            const float bx = dx * vp.ifx, by = dy * vp.ify;
+            ok = ok && fmaf(bx, bx, by * by) <= fabsf(B.w);
+        }
+        if (B.w < 0.f) ok = ok && in_subset(planes, (int)((msk >> 8) & 7u), vp, lp, Cc.w, Xc, Yc);
+    }
+    return ok;
 }
 
 // warp-aggregated pair counters (tracing only)
@@ -315,6 +479,11 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 }
 
 // ------------------------------------------------------------------ blend forward
+// Termination: a pixel whose transmittance is below eps_T at the start of a group of 32
+// entries of its warp's record list is frozen for the rest of the subset (T is kept and
+// set to 0, so later pairs add nothing); the check happens per group only, so the
+// per-pair loop carries no termination logic.  The backward freezes at the same points.
+//
 // One tile of the view: `ranges` and `tile_depth` point at the tile's K entries (view
 // rank order); pC/pT (partial maps) and tile_depth may be null.  The whole block calls it.
 template <bool kCount>
@@ -327,8 +496,12 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
+    __shared__ uint8_t wlist[kBlendThreads / 32][kBlendThreads];
     __shared__ LeafPath lp;
     __shared__ uint32_t sused[kBlendThreads];
+    // per-pixel values touched once per subset live in shared memory (register budget)
+    __shared__ float s_img[4][kBlendThreads];   // merged colour so far and the transmittance in front
+    __shared__ float s_tkeep[kBlendThreads];    // T of a frozen pixel
     uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0, n_staged = 0, n_used = 0;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
@@ -338,31 +511,30 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     const bool inside = px < vp.W && py < vp.H;
     const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
-    const float Xc = (float)px + 0.5f, Yc = (float)py + 0.5f;   // absolute pixel centre (Eq. 6 tests)
-    const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = (size_t)py * vp.W + px;
-    float img0 = 0.f, img1 = 0.f, img2 = 0.f, Pm = 1.f;
+    uint8_t* wl = wlist[warp];
+    const int tid = threadIdx.x;
+    s_img[0][tid] = 0.f;
+    s_img[1][tid] = 0.f;
+    s_img[2][tid] = 0.f;
+    s_img[3][tid] = 1.f;
 
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         const uint2 rg = ranges[r];
-        float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
-        bool done = !inside;
-        float zsat = __int_as_float(0x7f800000);   // +inf: the subset never saturated the tile
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        float T = inside ? 1.f : 0.f;
+        bool frozen = !inside;
+        float zsat = kInfF;   // the subset never saturated the tile
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
             if ((int)threadIdx.x < nb) {
-                StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
-                uint32_t msk = block_mask(sr, vp, lp, x0, y0);
-                if (sr.a.w < 0.f && msk) {
-                    const int nc = classify_planes(vp, lp, sr.b.w, x0 + 0.5f, y0 + 0.5f, splane[threadIdx.x]);
-                    if (nc < 0) msk = 0;                        // no pixel of the tile is in this subset
-                    else if (nc == 0) sr.a.w = -sr.a.w;         // every pixel is: no per-pixel test
-                    else msk |= (uint32_t)nc << 8;
-                }
+                StagedRec sr;
+                uint32_t msk;
+                stage_for_subset(rec, ival[b0 + threadIdx.x], x0, y0, vp, lp, sr, msk, splane[threadIdx.x]);
                 srec[threadIdx.x] = sr;
                 smask[threadIdx.x] = msk;
                 if (kCount) {
@@ -371,58 +543,54 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 }
             }
             __syncthreads();
-            for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
-                unsigned bits = __ballot_sync(0xffffffffu, c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u));
-                while (bits) {
-                    const int j = c0 + __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    // Branch-free body: a pair that fails a test (or a pixel already done)
-                    // gets sigma = 0, which leaves C and T unchanged.  The backward repeats
-                    // this arithmetic exactly.
+            const int n = warp_list(smask, nb, warp, lane, wl);
+            for (int t0 = 0; t0 < n; t0 += 32) {
+                if (!frozen && T < vp.eps_T) {
+                    frozen = true;
+                    s_tkeep[tid] = T;
+                    T = 0.f;
+                }
+                if (__all_sync(0xffffffffu, frozen)) break;
+                const int t1 = min(n, t0 + 32);
+                for (int t = t0; t < t1; ++t) {
+                    const int j = wl[t];
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
+                    const float4 Cc = srec[j].c;
                     const float dx = pcx - A.x, dy = pcy - A.y;
-                    const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
+                    const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    const float bx = dx * vp.ifx, by = dy * vp.ify;
-                    const bool in_ell = d2 <= tm2, in_ball = fmaf(bx, bx, by * by) <= fabsf(A.w);
-                    bool ok = !done && in_ell && in_ball;
-                    bool in_sub = true;
-                    if (A.w < 0.f) {   // uniform across the warp: one record
-                        in_sub = in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
-                        ok = ok && in_sub;
-                    }
+                    const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, x0 + pcx, y0 + pcy);
                     const float G = ex2_approx(d2 * kNegHalfLog2e);
-                    float sig = fminf(A.z * G, vp.alpha_max);
-                    ok = ok && sig >= vp.alpha_min;
-                    if (kCount && !done) {
+                    const float sig = ok ? fminf(B.y * G, vp.alpha_max) : 0.f;
+                    if (kCount && !frozen) {
                         ++n_eval;
-                        n_strad += A.w < 0.f;
-                        n_d2 += !in_ell;
-                        n_ball += in_ell && !in_ball;
-                        n_leaf += in_ell && in_ball && !in_sub;
+                        n_strad += B.w < 0.f;
+                        n_d2 += !(d2 <= B.z);
+                        const bool in_ball = !(fabsf(B.w) != kInfF) ||
+                                             fmaf(dx * vp.ifx, dx * vp.ifx, (dy * vp.ify) * (dy * vp.ify)) <= fabsf(B.w);
+                        n_ball += d2 <= B.z && !in_ball;
+                        n_leaf += d2 <= B.z && in_ball && !ok;
                         n_contrib += ok;
                         if (ok) sused[j] = 1;
                     }
-                    sig = ok ? sig : 0.f;
-                    const float4 Cc = srec[j].c;
                     const float w = sig * T;
                     C0 = fmaf(Cc.x, w, C0);
                     C1 = fmaf(Cc.y, w, C1);
                     C2 = fmaf(Cc.z, w, C2);
                     T = fmaf(-sig, T, T);
-                    done = done || T < vp.eps_T;
                 }
             }
             if (kCount) {
                 __syncthreads();
                 if ((int)threadIdx.x < nb) n_used += sused[threadIdx.x];
             }
-            if (__syncthreads_count(done) == kBlendThreads) {
-                zsat = srec[nb - 1].b.w;   // depth of the last instance staged
+            if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) {
+                zsat = srec[nb - 1].c.w;   // depth of the last instance staged
                 break;
             }
         }
+        if (frozen && inside) T = s_tkeep[tid];
         if (tile_depth && threadIdx.x == 0) tile_depth[r] = zsat;
         if (inside) {
             if (pC) {
@@ -431,16 +599,18 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 pC[((size_t)k * 3 + 2) * HW + pix] = C2;
                 pT[(size_t)k * HW + pix] = T;
             }
-            img0 = fmaf(C0, Pm, img0);
-            img1 = fmaf(C1, Pm, img1);
-            img2 = fmaf(C2, Pm, img2);
-            Pm *= T;
+            const float Pm = s_img[3][tid];
+            s_img[0][tid] = fmaf(C0, Pm, s_img[0][tid]);
+            s_img[1][tid] = fmaf(C1, Pm, s_img[1][tid]);
+            s_img[2][tid] = fmaf(C2, Pm, s_img[2][tid]);
+            s_img[3][tid] = Pm * T;
         }
     }
     if (inside && image) {
-        image[0 * HW + pix] = fmaf(vp.bg[0], Pm, img0);
-        image[1 * HW + pix] = fmaf(vp.bg[1], Pm, img1);
-        image[2 * HW + pix] = fmaf(vp.bg[2], Pm, img2);
+        const float Pm = s_img[3][tid];
+        image[0 * HW + pix] = fmaf(vp.bg[0], Pm, s_img[0][tid]);
+        image[1 * HW + pix] = fmaf(vp.bg[1], Pm, s_img[1][tid]);
+        image[2 * HW + pix] = fmaf(vp.bg[2], Pm, s_img[2][tid]);
         if (Tfin) Tfin[pix] = Pm;
     }
     if (kCount) {
@@ -506,27 +676,51 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
 }
 
 // ------------------------------------------------------------------ blend backward
-__device__ __forceinline__ float warp_sum(float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Sums the 9 values v[0..8] over the 32 lanes of a warp with 12 shuffles (reduce-scatter
+// by halving: at each step a lane keeps part of its values, sends the rest to its partner
+// and adds what it receives).  Returns the total of value index warp_value_index(lane) on
+// every lane (15: none).  Lanes l and l ^ 1 hold the same total.
+__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
+    // 9 -> 5: upper 16 lanes keep values 4..8, lower keep 0..3 (slot 4 padded with 0)
+    const bool u16 = (lane & 16) != 0;
+    float n[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float lo = k < 4 ? v[k] : 0.f, hi = v[4 + k];
+        const float r = __shfl_xor_sync(0xffffffffu, u16 ? lo : hi, 16);
+        n[k] = (u16 ? hi : lo) + r;
+    }
+    // 5 -> 3: upper 8 keep n[2..4], lower keep n[0..1] (slot 2 padded)
+    const bool u8 = (lane & 8) != 0;
+    float m[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = k < 2 ? n[k] : 0.f, hi = n[2 + k];
+        const float r = __shfl_xor_sync(0xffffffffu, u8 ? lo : hi, 8);
+        m[k] = (u8 ? hi : lo) + r;
+    }
+    // 3 -> 2: upper 4 keep m[1..2], lower keep m[0] (slot 1 padded)
+    const bool u4 = (lane & 4) != 0;
+    float p[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float lo = k < 1 ? m[k] : 0.f, hi = m[1 + k];
+        const float r = __shfl_xor_sync(0xffffffffu, u4 ? lo : hi, 4);
+        p[k] = (u4 ? hi : lo) + r;
+    }
+    // 2 -> 1, then the last pair
+    const bool u2 = (lane & 2) != 0;
+    float q = (u2 ? p[1] : p[0]) + __shfl_xor_sync(0xffffffffu, u2 ? p[0] : p[1], 2);
+    return q + __shfl_xor_sync(0xffffffffu, q, 1);
 }
 
-// Sums v[0..15] over the 32 lanes of a warp with 16 shuffles (reduce-scatter by halving):
-// at each step a lane keeps one half of its values, sends the other half to its partner
-// and adds what it receives.  Returns the total of value index (lane >> 1) & 15; both
-// lanes of each pair hold it.
-__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane) {
-#pragma unroll
-    for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
-        const bool upper = (lane & off) != 0;
-#pragma unroll
-        for (int k = 0; k < h; ++k) {
-            const float send = upper ? v[k] : v[k + h];
-            const float keep = upper ? v[k + h] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+// Value index held by a lane after warp_reduce9 (15: a padding slot).  Bits (16, 8, 4, 2)
+// of the lane select, in turn, the kept half of each step.
+__device__ __forceinline__ int warp_value_index(int lane) {
+    // nibble table indexed by (b16 b8 b4 b2): 0,P,1,P,2,P,3,P,4,P,5,P,6,P,7,8
+    constexpr unsigned long long kTable = 0x87F6F5F4F3F2F1F0ull;
+    const int code = (lane >> 1) & 15;
+    return (int)((kTable >> (4 * code)) & 15ull);
 }
 
 __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
@@ -535,7 +729,6 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
                  : "memory");
 }
 
-// dynamic shared memory: s_behind [K][256] floats
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
@@ -545,8 +738,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
+    __shared__ uint32_t sid[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ float sacc[kBlendThreads][9];
+    __shared__ uint8_t wlist[kBlendThreads / 32][kBlendThreads];
     __shared__ LeafPath lp;
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
@@ -559,9 +754,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     const float pcx = lx + 0.5f, pcy = ly + 0.5f;
     const int lane = threadIdx.x & 31;
     const float Xc = (float)px + 0.5f, Yc = (float)py + 0.5f;   // absolute pixel centre (Eq. 6 tests)
-    const float tm2 = vp.trunc_mult * vp.trunc_mult;
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = inside ? (size_t)py * vp.W + px : 0;
+    const int vidx = warp_value_index(lane);
+    uint8_t* wl = wlist[warp];
 
     for (int i = threadIdx.x; i < kBlendThreads * 9; i += kBlendThreads) (&sacc[0][0])[i] = 0.f;
 
@@ -596,76 +792,79 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         }
         const float gC0 = g0 * Pm, gC1 = g1 * Pm, gC2 = g2 * Pm;
         const float gT = Pm * s_behind[r * kBlendThreads + threadIdx.x];
-        const float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
+        float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
         Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         const uint2 rg = ranges[(size_t)tile * vp.K + r];
-        bool active = inside && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
+        const bool active = inside && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
         if (__syncthreads_count(active) == 0) continue;
-        bool done = !active;
-        float T = 1.f, acc = 0.f;   // acc = <gC, A_i>
+        // replay of the forward: the same pairs, the same freeze points (an inactive pixel
+        // is frozen from the start: its gradients are zero)
+        bool frozen = !active;
+        float T = active ? 1.f : 0.f, acc = 0.f;   // acc = <gC, colour accumulated so far>
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
             if ((int)threadIdx.x < nb) {
-                StagedRec sr = stage_record(rec, ival[b0 + threadIdx.x], x0, y0);
-                uint32_t msk = block_mask(sr, vp, lp, x0, y0);
-                if (sr.a.w < 0.f && msk) {
-                    const int nc = classify_planes(vp, lp, sr.b.w, x0 + 0.5f, y0 + 0.5f, splane[threadIdx.x]);
-                    if (nc < 0) msk = 0;                        // no pixel of the tile is in this subset
-                    else if (nc == 0) sr.a.w = -sr.a.w;         // every pixel is: no per-pixel test
-                    else msk |= (uint32_t)nc << 8;
-                }
+                StagedRec sr;
+                uint32_t msk;
+                const uint32_t id = ival[b0 + threadIdx.x];
+                stage_for_subset(rec, id, x0, y0, vp, lp, sr, msk, splane[threadIdx.x]);
                 srec[threadIdx.x] = sr;
                 smask[threadIdx.x] = msk;
+                sid[threadIdx.x] = id;
             }
             __syncthreads();
-            for (int c0 = 0; c0 < nb && !__all_sync(0xffffffffu, done); c0 += 32) {
-                unsigned bits = __ballot_sync(0xffffffffu, c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u));
-                while (bits) {
-                    const int j = c0 + __ffs(bits) - 1;
-                    bits &= bits - 1;
+            const int n = warp_list(smask, nb, warp, lane, wl);
+            for (int t0 = 0; t0 < n; t0 += 32) {
+                if (!frozen && T < vp.eps_T) {
+                    // frozen as in the forward: later pairs get sigma * T = 0, and q = acc
+                    // makes their adjoint vanish too
+                    frozen = true;
+                    T = 0.f;
+                    q = acc;
+                }
+                if (__all_sync(0xffffffffu, frozen)) break;
+                const int t1 = min(n, t0 + 32);
+                for (int t = t0; t < t1; ++t) {
+                    const int j = wl[t];
                     // the forward's arithmetic, then the adjoint of the pair with the same
                     // predicate (a pair that fails gets sigma = 0 and zero gradients)
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
+                    const float4 Cc = srec[j].c;
                     const float dx = pcx - A.x, dy = pcy - A.y;
-                    const float u1 = fmaf(B.x, dx, B.y * dy), u2 = B.z * dy;
+                    const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    const float bx = dx * vp.ifx, by = dy * vp.ify;
-                    bool ok = !done && d2 <= tm2 && fmaf(bx, bx, by * by) <= fabsf(A.w);
-                    if (A.w < 0.f)   // uniform across the warp: one record
-                        ok = ok && in_subset(splane[j], (int)((smask[j] >> 8) & 7u), vp, lp, B.w, Xc, Yc);
+                    const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
                     const float G = ex2_approx(d2 * kNegHalfLog2e);
-                    const float raw = A.z * G;
-                    float sig = fminf(raw, vp.alpha_max);
-                    ok = ok && sig >= vp.alpha_min;
-                    if (kCount && !done) {
+                    const float raw = B.y * G;
+                    const float sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
+                    if (kCount && !frozen) {
                         ++n_eval;
                         n_contrib += ok;
                     }
-                    sig = ok ? sig : 0.f;
-                    const float4 Cc = srec[j].c;
                     const float w = sig * T;
                     const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
                     acc = fmaf(w, grgb, acc);
                     const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
-                    const float gr0 = gC0 * w, gr1 = gC1 * w, gr2 = gC2 * w;
                     const float ds = (ok && raw < vp.alpha_max) ? dsig : 0.f;
-                    const float gal = ds * G;
                     const float gd2 = -0.5f * sig * ds;
-                    const float ga = gd2 * dx * dx, gb = gd2 * 2.f * dx * dy, gc = gd2 * dy * dy;
                     // d(d2)/d(mean) = -2 Q delta, Q delta = L^T (u1, u2)
-                    const float gmx = -2.f * gd2 * (B.x * u1);
-                    const float gmy = -2.f * gd2 * fmaf(B.y, u1, B.z * u2);
+                    float v[9];
+                    v[0] = -2.f * gd2 * (A.z * u1);
+                    v[1] = -2.f * gd2 * fmaf(A.w, u1, B.x * u2);
+                    v[2] = gd2 * dx * dx;
+                    v[3] = gd2 * 2.f * dx * dy;
+                    v[4] = gd2 * dy * dy;
+                    v[5] = ds * G;
+                    v[6] = gC0 * w;
+                    v[7] = gC1 * w;
+                    v[8] = gC2 * w;
                     T = fmaf(-sig, T, T);
-                    done = done || T < vp.eps_T;
-                    const bool contrib = ok;
-                    if (__any_sync(0xffffffffu, contrib)) {
-                        float v[16] = {gmx, gmy, ga, gb, gc, gal, gr0, gr1, gr2, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                        const float tot = warp_reduce16(v, lane);
-                        const int vi = (lane >> 1) & 15;
-                        if ((lane & 1) == 0 && vi < 9) atomicAdd(&sacc[j][vi], tot);
+                    if (__any_sync(0xffffffffu, ok)) {
+                        const float tot = warp_reduce9(v, lane);
+                        if ((lane & 1) == 0 && vidx < 9) atomicAdd(&sacc[j][vidx], tot);
                     }
                 }
             }
@@ -675,15 +874,14 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 bool nz = false;
                 for (int t = 0; t < 9; ++t) nz |= a[t] != 0.f;
                 if (nz) {
-                    const uint32_t id = __float_as_uint(srec[threadIdx.x].c.w);
-                    float4* dst = g2d + 3 * (size_t)id;
+                    float4* dst = g2d + 3 * (size_t)sid[threadIdx.x];
                     red_add_v4(dst, make_float4(a[0], a[1], a[2], a[3]));
                     red_add_v4(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
                     red_add_v4(dst + 2, make_float4(a[8], 0.f, 0.f, 0.f));
                     for (int t = 0; t < 9; ++t) a[t] = 0.f;
                 }
             }
-            if (__syncthreads_count(done) == kBlendThreads) break;
+            if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) break;
         }
     }
     if (kCount) count_pairs(pairs + 2, n_eval, n_contrib);
@@ -746,7 +944,7 @@ __global__ void merge_bwd_kernel(const float* __restrict__ pC, const float* __re
 int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
                 int64_t n_vis, cudaStream_t s) {
     if (n_vis <= 0) return RGS_OK;
-    const int64_t want = (n_vis + 7) / 8;          // one warp per splat
+    const int64_t want = (n_vis + 255) / 256;      // one warp per 32 splats
     unsigned grid = (unsigned)(want < (1 << 20) ? want : (1 << 20));
     emit_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
     RGS_CUDA_LAUNCH_CHECK();
