@@ -203,7 +203,8 @@ def roofline(prof, peaks, peak_src, source, traffic_table):
     out["traffic"] = t["dram_bytes_per_launch"] if t and t.get("source_sha") == source.get(t.get("source")) else None
     out["avg_launch_ms"] = avg_s * 1e3
     out["launches"] = launches
-    out["peak_kind"] = "of " + peak_src
+    out["peak_kind"] = ("derived from unit counts and the measured max SM clock" if out["bound"] == "alu"
+                        else "of " + peak_src)
     return out
 
 
@@ -226,6 +227,8 @@ def _traffic_table():
 
 # --------------------------------------------------------------------------- serving
 def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=24, burst=400, device=None):
+    warm = min(warm, requests // 4)
+    burst = min(burst, requests)
     """Serving on the 5M-splat city scene (K=8): a seeded Poisson stream of mixed-resolution
     requests against the batched server and the plain one-request-per-launch server.
     Latency = host time from submit to completion; Mpix/s = pixels of all requests over the
@@ -277,6 +280,20 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=24, burst=400,
     return res
 
 
+def run_serve_only(args, rank, world, local_rank):
+    """--workload serve: the serving measurement alone (one JSON line)."""
+    import torch
+    from paper_2406_11836_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(local_rank)
+    res = run_serving(requests=args.serve_requests, device=torch.device("cuda", local_rank))
+    if rank == 0:
+        b = res["batched"]
+        print(json.dumps({"metric": "serve Mpix/s (5M Gaussians, K=8, Poisson 200 req/s, mixed resolutions)",
+                          "value": b["mpix_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                          "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "serving": res}), flush=True)
+
+
 # --------------------------------------------------------------------------- arms
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -307,17 +324,19 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- exact replay of the timed steps with the pair counters on (untimed): the counts
     # give the algorithmic work of the timed launches; the state is then restored
-    ck = trainer.checkpoint()
-    rgs.profile_enable(timing=False, counters=True)
-    rgs.profile_read(reset=True)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    torch.cuda.synchronize()
-    counts = rgs.profile_read(reset=True)["counters"]
-    rgs.profile_enable(False, False)
-    trainer.restore(ck)
-    del ck
-    torch.cuda.synchronize()
+    counts = {}
+    if not args.profile_only:
+        ck = trainer.checkpoint()
+        rgs.profile_enable(timing=False, counters=True)
+        rgs.profile_read(reset=True)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        torch.cuda.synchronize()
+        counts = rgs.profile_read(reset=True)["counters"]
+        rgs.profile_enable(False, False)
+        trainer.restore(ck)
+        del ck
+        torch.cuda.synchronize()
 
     # ---- device-timed region (inputs resident in HBM)
     rgs.profile_enable(timing=True, counters=False)
@@ -342,6 +361,12 @@ def run_ours(args, rank, world, local_rank):
     prof["counters"] = dict(counts, kernel_launches=prof["counters"]["kernel_launches"])
     launches_timed = prof["counters"]["kernel_launches"]
 
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "ms_per_step": ms / args.steps,
+                              "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof["stages"].items()
+                                                     if v[1] > 0}}), flush=True)
+        return
     # ---- end to end through the public step API with host inputs
     pinned = [t.cpu().pin_memory() for t in targets]
     dev_target = torch.empty_like(targets[0])
@@ -392,7 +417,7 @@ def run_ours(args, rank, world, local_rank):
     if args.workload == "city" and not args.no_serve and world == 1:
         del trainer, targets, pinned, dev_target
         torch.cuda.empty_cache()
-        line["serving"] = run_serving(device=dev)
+        line["serving"] = run_serving(requests=args.serve_requests, device=dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -431,10 +456,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("city", "object", "tiny", "city-small"), default="city")
+    ap.add_argument("--workload", choices=("city", "object", "tiny", "city-small", "serve"), default="city")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=2200, help="requests of the serving stream")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="warm-up and timed steps only (no counter replay, end-to-end loop, CPU baseline or "
+                         "serving): for launch lists under a profiler; its numbers are not bench values")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -447,7 +476,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "serve":
+        run_serve_only(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
