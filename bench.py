@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd+Adam Mpix/s, 10M Gaussians, 3840x2160, 16 KD subsets"
 WORKLOAD_NAMES = {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x1060-K8", "tiny": "tiny-4k-128px-K2",
-                  "city-small": "city-1M-1920x1080-K16"}
+                  "city-small": "city-1M-1920x1080-K16", "city-100m": "city-100M-3840x2160-K64"}
 UNIT = "Mpix/s"
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -108,6 +108,8 @@ def make_workload(name, device):
         return W.object_1m(device=device)
     if name == "city-small":
         return W.city_10m(device=device, n=1_000_000, width=1920, height=1080, n_views=4)
+    if name == "city-100m":
+        return W.city_100m(device=device)
     return W.tiny(device=device)
 
 
@@ -172,7 +174,7 @@ FLOPS_FWD_CONTRIB = 11
 FLOPS_BWD_CONTRIB = 40
 
 
-def roofline(prof, peaks, peak_src, source, traffic_table):
+def roofline(prof, peaks, peak_src, source, traffic_table, workload=None):
     stages = prof["stages"]
     cnt = prof["counters"]
     cand = {k: v for k, v in stages.items() if v[1] > 0}
@@ -200,7 +202,8 @@ def roofline(prof, peaks, peak_src, source, traffic_table):
         out = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                "frac": achieved / peaks["hbm_gbs"]}
     t = traffic_table.get(dom)
-    out["traffic"] = t["dram_bytes_per_launch"] if t and t.get("source_sha") == source.get(t.get("source")) else None
+    ok = t and t.get("source_sha") == source.get(t.get("source")) and t.get("workload") == workload
+    out["traffic"] = t["dram_bytes_per_launch"] if ok else None
     out["avg_launch_ms"] = avg_s * 1e3
     out["launches"] = launches
     out["peak_kind"] = ("derived from unit counts and the measured max SM clock" if out["bound"] == "alu"
@@ -393,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
     pix_per_step = H * Wd
     value = world * args.steps * pix_per_step / (ms_max / 1e3) / 1e6
     e2e = world * args.steps * pix_per_step / (e2e_ms_max / 1e3) / 1e6
-    rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table())
+    rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table(), WORKLOAD_NAMES[args.workload])
     line = {
         "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -402,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD_NAMES[args.workload],
                    "splats": trainer.n, "width": Wd, "height": H, "subsets": trainer.kd.K, "sh_degree": trainer.sh_degree,
                    "step": "render fwd + L1 loss + render bwd + Adam", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (parameters and Adam state 9.4 GB, instance buffers several GB)"},
+                   "l2": f"inputs larger than L2 (parameters, gradients and Adam state {trainer.n * 59 * 16 / 1e9:.1f} GB, "
+                         "instance buffers several GB)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(targets[0].numel() * 4),
                 "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches_timed),
@@ -456,7 +460,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("city", "object", "tiny", "city-small", "serve"), default="city")
+    ap.add_argument("--workload", choices=("city", "object", "tiny", "city-small", "city-100m", "serve"),
+                    default="city")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
