@@ -296,6 +296,11 @@ int rgs_serve_poll(rgs_server* srv, uint64_t ticket, int* done, double* latency_
 
 int rgs_serve_stats_read(rgs_server* srv, rgs_serve_stats* out);
 
+/* hold != 0: the scheduler starts no new batch (submitted requests wait in the queue;
+ * batches already on the GPU finish).  hold == 0 resumes.  For draining and for
+ * admitting a known set of requests together. */
+int rgs_serve_hold(rgs_server* srv, int hold);
+
 /* Stops the scheduler, cancels queued requests and waits at most 10 s for batches on the
  * GPU.  Returns ETIMEOUT if they did not finish (their buffers are then left allocated
  * rather than freed under a running kernel).  Never hangs. */

@@ -160,8 +160,9 @@ __device__ __forceinline__ bool clip_span(const SubsetClip& c, float ylo, float 
         if (d >= c.n) break;
         const float by = fmaxf(c.B[d] * ylo, c.B[d] * yhi);
         const float rhs = -c.m[d] - c.C[d] - by;       // need A X >= rhs
-        if (c.A[d] > 0.f) xlo = fmaxf(xlo, rhs / c.A[d]);
-        else if (c.A[d] < 0.f) xhi = fminf(xhi, rhs / c.A[d]);
+        // approximate division: its error (a few ulp of X) is far below the margin m / |A|
+        if (c.A[d] > 0.f) xlo = fmaxf(xlo, __fdividef(rhs, c.A[d]));
+        else if (c.A[d] < 0.f) xhi = fminf(xhi, __fdividef(rhs, c.A[d]));
         else if (rhs > 0.f) return false;
     }
     return xlo <= xhi;
@@ -186,15 +187,22 @@ __device__ __forceinline__ void footprint_row_tiles_clipped(const Footprint& f, 
 // its subset k and the tile columns [c0, c1] the footprint touches there, clipped to the
 // subset when the splat is held by several (Eq. 6).  The count in the projection and the
 // emission call this same function on the same record values, so they always agree.
-__device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
-                                          unsigned long long mask, int nsub, float z, int ty0, int rows, int it,
-                                          int& ty, int& k, int& c0, int& c1) {
+// Item `it` of a splat: (subset k, tile row ty), subsets in mask order, rows inner.
+__device__ __forceinline__ void item_locate(unsigned long long mask, int ty0, int rows, int it, int& ty, int& k) {
     const int si = it / rows;
     ty = ty0 + (it - si * rows);
     unsigned long long mm = mask;
     for (int q = 0; q < si; ++q) mm &= mm - 1;
     k = __ffsll((long long)mm) - 1;
-    if (nsub > 1) {
+}
+
+// Tile columns [c0, c1] of the item's row for subset k (clipped to the subset when the
+// splat straddles).  kMulti = 0: the splat is known to lie in one subset (no clipping code
+// is compiled in); 1: it is known to straddle; -1: decided at run time.
+template <int kMulti = -1>
+__device__ __forceinline__ void item_cols(const Footprint& f, const ViewParams& vp, const TreeParams& tp, int k,
+                                          int nsub, float z, int ty, int& c0, int& c1) {
+    if (kMulti == 1 || (kMulti < 0 && nsub > 1)) {
         LeafPath lpk;
         leaf_path(tp, k, lpk);
         SubsetClip clip;
@@ -203,6 +211,14 @@ __device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& 
     } else {
         footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);
     }
+}
+
+template <int kMulti = -1>
+__device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
+                                          unsigned long long mask, int nsub, float z, int ty0, int rows, int it,
+                                          int& ty, int& k, int& c0, int& c1) {
+    item_locate(mask, ty0, rows, it, ty, k);
+    item_cols<kMulti>(f, vp, tp, k, nsub, z, ty, c0, c1);
 }
 
 // Depth culling of the backward's instances: `cull` ([tiles, K] by view rank, nullptr:
@@ -220,16 +236,20 @@ __device__ __forceinline__ bool keep_tile(const float* __restrict__ cull, const 
 
 __device__ __forceinline__ int cull_nchunk(const ViewParams& vp) { return (vp.tiles_x + kCullChunk - 1) / kCullChunk; }
 
+// Entry of the chunk table: per tile row, nch chunks then (index nch) the whole row.
+__device__ __forceinline__ size_t cull_chunk_index(const ViewParams& vp, int ty, int ch, int rank) {
+    return ((size_t)ty * (cull_nchunk(vp) + 1) + ch) * vp.K + rank;
+}
+
 // Number of tiles of [c0, c1] in row ty kept for a splat at depth z in subset `rank`.
 __device__ __forceinline__ uint32_t kept_tiles(const float* __restrict__ cull, const float2* __restrict__ chunk,
                                                const ViewParams& vp, int ty, int c0, int c1, int rank, float z) {
     if (c0 > c1) return 0u;
     if (!cull) return (uint32_t)(c1 - c0 + 1);
-    const int nch = cull_nchunk(vp);
     uint32_t n = 0;
     for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
         const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-        const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
+        const float2 mm = chunk[cull_chunk_index(vp, ty, ch, rank)];
         if (z > mm.y) continue;
         if (z <= mm.x) {
             n += (uint32_t)(hi - lo + 1);
@@ -240,12 +260,27 @@ __device__ __forceinline__ uint32_t kept_tiles(const float* __restrict__ cull, c
     return n;
 }
 
+// rank_of: the view rank of each subset (a copy in shared memory: lanes index it with
+// different subsets).
 __device__ __forceinline__ uint32_t item_tiles(const Footprint& f, const ViewParams& vp, const TreeParams& tp,
-                                               unsigned long long mask, int nsub, float z, int ty0, int rows, int it,
-                                               const float* __restrict__ cull, const float2* __restrict__ chunk) {
+                                               const int8_t* rank_of, unsigned long long mask, int nsub, float z,
+                                               int ty0, int rows, int it, const float* __restrict__ cull,
+                                               const float2* __restrict__ chunk) {
     int ty, k, c0, c1;
     item_span(f, vp, tp, mask, nsub, z, ty0, rows, it, ty, k, c0, c1);
-    return kept_tiles(cull, chunk, vp, ty, c0, c1, vp.rank_of[k], z);
+    return kept_tiles(cull, chunk, vp, ty, c0, c1, rank_of[k], z);
+}
+
+// Block-wide copy of the tree and the view's rank table into shared memory: the per-splat
+// tree walks and per-item leaf paths index them with a different node or subset per lane,
+// which kernel-parameter (constant) memory would serialise.  The whole block calls it.
+__device__ __forceinline__ void stage_tree(const TreeParams& tp, const int8_t* rank_src, TreeParams& stp,
+                                           int8_t* srank) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&tp);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&stp);
+    for (int w = threadIdx.x; w < (int)(sizeof(TreeParams) / 4); w += blockDim.x) dst[w] = src[w];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) srank[k] = rank_src[k];
+    __syncthreads();
 }
 
 }  // namespace rgs

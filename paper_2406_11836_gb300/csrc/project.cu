@@ -142,25 +142,24 @@ __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, flo
 // Subsets holding a splat: leaves of the KD tree whose box, dilated by D in every axis,
 // contains mu (left branch: mu[a] - D < s, right branch: mu[a] + D >= s).  Iterative DFS.
 __device__ __forceinline__ unsigned long long subset_mask(const TreeParams& tp, float mx, float my, float mz, float D) {
-    if (tp.L == 0) return 1ull;
-    unsigned long long mask = 0;
-    int stack[kMaxRenderDepth + 2];
-    int sp = 0;
-    stack[sp++] = 0;
-    const int first_leaf = (1 << tp.L) - 1;
-    while (sp > 0) {
-        int j = stack[--sp];
-        if (j >= first_leaf) {
-            mask |= 1ull << (j - first_leaf);
-            continue;
+    // level by level: `cur` holds the reachable nodes of the level (bit i: node 2^d - 1 + i)
+    unsigned long long cur = 1ull;
+    for (int d = 0; d < tp.L; ++d) {
+        unsigned long long next = 0ull, m = cur;
+        const int first = (1 << d) - 1;
+        while (m) {
+            const int i = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const int j = first + i;
+            const int a = tp.axis[j];
+            const float s = tp.split[j];
+            const float c = a == 0 ? mx : (a == 1 ? my : mz);
+            if (c - D < s) next |= 1ull << (2 * i);
+            if (c + D >= s) next |= 1ull << (2 * i + 1);
         }
-        int a = tp.axis[j];
-        float s = tp.split[j];
-        float c = a == 0 ? mx : (a == 1 ? my : mz);
-        if (c + D >= s) stack[sp++] = 2 * j + 2;
-        if (c - D < s) stack[sp++] = 2 * j + 1;
+        cur = next;
     }
-    return mask;
+    return cur;
 }
 
 struct SplatIn {
@@ -280,8 +279,9 @@ constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are
 // and, when non-null, slot_counters[0..1].  Every lane of the warp must call it.
 template <int DEG>
 __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t i, bool valid, const ViewParams& vp,
-                                                 const TreeParams& tp, const RasterBuffers& b, int64_t j,
-                                                 unsigned long long* counters, unsigned long long* slot_counters) {
+                                                 const TreeParams& tp, const int8_t* rank_of, const RasterBuffers& b,
+                                                 int64_t j, unsigned long long* counters,
+                                                 unsigned long long* slot_counters) {
     constexpr int NSH = (DEG + 1) * (DEG + 1);
     const int lane = threadIdx.x & 31;
     // candidate state handed to the counting phase
@@ -352,7 +352,8 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     uint32_t count = 0;
     if (cand && items <= kWarpCountItems) {
         const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
-        for (int it = 0; it < items; ++it) count += item_tiles(f, vp, tp, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
+        for (int it = 0; it < items; ++it)
+            count += item_tiles(f, vp, tp, rank_of, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
     }
     unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
     while (big) {
@@ -368,7 +369,8 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         const Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
         const int ns = __popcll(m_);
         uint32_t acc = 0;
-        for (int it = lane; it < items_; it += 32) acc += item_tiles(f, vp, tp, m_, ns, z_, t0_, rows_, it, b.cull, b.cull_chunk);
+        for (int it = lane; it < items_; it += 32)
+            acc += item_tiles(f, vp, tp, rank_of, m_, ns, z_, t0_, rows_, it, b.cull, b.cull_chunk);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == src) count = acc;
     }
@@ -391,17 +393,20 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    stage_tree(tp, vp.rank_of, stp, srank);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG>(g, i, i < g.n, vp, tp, b, i, b.counters, nullptr);
+    project_fwd_body<DEG>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
 }
 
 // Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
 // x % kMaxSlots, so the blocks of one splat range run back to back and read its
 // parameters from L2 after the first slot.  Outputs go to index slot * N + i.
 template <int DEG>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
                      TreeParams tp, RasterBuffers b, unsigned long long* __restrict__ counters) {
     const int slot = blockIdx.x % kMaxSlots;
@@ -412,9 +417,11 @@ project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const
         uint32_t* dst = reinterpret_cast<uint32_t*>(&svp);
         for (int w = threadIdx.x; w < (int)(sizeof(ViewParams) / 4); w += blockDim.x) dst[w] = src[w];
     }
-    __syncthreads();
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    stage_tree(tp, slots[slot].vp.rank_of, stp, srank);   // its barrier also publishes svp
     const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG>(g, i, i < g.n, svp, tp, b, (int64_t)slot * g.n + i, counters,
+    project_fwd_body<DEG>(g, i, i < g.n, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
                           counters + kBatchSlotCounters + 2 * slot);
 }
 

@@ -55,8 +55,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // without depth culling the warp then writes the round's contiguous range together
 // (lane l writes positions l, l + 32, ...: coalesced stores), finding each position's
 // item by a forward scan of the run starts.
-__device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams& tp, uint32_t id, uint32_t base,
-                                         uint32_t tile_base, const ushort4* __restrict__ rect,
+template <int kMulti>
+__device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of, uint32_t id,
+                                         uint32_t base, uint32_t tile_base, const ushort4* __restrict__ rect,
                                          const unsigned long long* __restrict__ mask, const float4* __restrict__ rec,
                                          const float* __restrict__ cull, const float2* __restrict__ chunk,
                                          uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane,
@@ -74,8 +75,8 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
         uint32_t rank = 0;
         if (it < items) {
             int k;
-            item_span(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
-            rank = (uint32_t)vp.rank_of[k];
+            item_span<kMulti>(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
+            rank = (uint32_t)rank_of[k];
         }
         const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, r2.w);
         uint32_t incl = w;
@@ -98,10 +99,9 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
             __syncwarp();
         } else if (w) {
             uint32_t pos = base + incl - w;
-            const int nch = cull_nchunk(vp);
             for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
                 const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-                const float2 mm = chunk[((size_t)ty * nch + ch) * vp.K + rank];
+                const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
                 if (r2.w > mm.y) continue;
                 const bool all = r2.w <= mm.x;
                 for (int c = lo; c <= hi; ++c) {
@@ -119,15 +119,17 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
 // Instances of one small splat (at most kEmitThreadItems items), written by one thread.
 constexpr int kEmitThreadItems = 4;
 
-__device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreeParams& tp, uint32_t id, uint32_t pos,
+template <int kMulti>
+__device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of,
+                                            uint32_t id, uint32_t pos,
                                             uint32_t tile_base, const Footprint& f, unsigned long long m, int nsub,
                                             float z, int ty0, int rows, int items, const float* __restrict__ cull,
                                             const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
                                             uint32_t* __restrict__ ival) {
     for (int it = 0; it < items; ++it) {
         int ty, k, c0, c1;
-        item_span(f, vp, tp, m, nsub, z, ty0, rows, it, ty, k, c0, c1);
-        const uint32_t rank = (uint32_t)vp.rank_of[k];
+        item_span<kMulti>(f, vp, tp, m, nsub, z, ty0, rows, it, ty, k, c0, c1);
+        const uint32_t rank = (uint32_t)rank_of[k];
         const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
         for (int c = c0; c <= c1; ++c) {
             if (cull && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
@@ -140,17 +142,28 @@ __device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreePara
 
 // Emission of the depth-sorted visible splats, 32 per warp: a splat with few (subset,
 // row) items is emitted by its own lane, the others by the whole warp in turn (the same
-// split as the count in the projection).
+// split as the count in the projection).  kMulti selects the splats this launch emits:
+// those in one subset (0) or those straddling several (1, with the clipping code); two
+// launches cover all, each compiled for its own register budget.
+template <int kMulti>
 __global__ void __launch_bounds__(256)
 emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
             const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
-            const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+            const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
+            unsigned long long* __restrict__ queue) {
     __shared__ uint32_t s_start[8][32], s_key0[8][32];
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    stage_tree(tp, vp.rank_of, stp, srank);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p0 = warp * 32; p0 < n_vis; p0 += nwarps * 32) {
+    // groups of 32 splats are claimed from a device counter: the near (large) splats come
+    // first in depth order, so the heavy groups start first and spread over all warps
+    for (;;) {
+        unsigned long long gq = 0;
+        if (lane == 0) gq = atomicAdd(queue, 1ull);
+        const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 32;
+        if (p0 >= n_vis) break;
         const int64_t p = p0 + lane;
         uint32_t id = 0, base = 0;
         int items = 0;
@@ -160,11 +173,12 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const ushort4 r = rect[id];
             const unsigned long long m = mask[id];
             const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
-            items = nsub * rows;
-            if (items <= kEmitThreadItems) {
+            items = ((nsub > 1) == (kMulti == 1)) ? nsub * rows : 0;
+            if (items > 0 && items <= kEmitThreadItems) {
                 const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
                 const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
-                emit_thread(vp, tp, id, base, 0u, f, m, nsub, r2.w, r.y, rows, items, cull, chunk, ikey, ival);
+                emit_thread<kMulti>(vp, stp, srank, id, base, 0u, f, m, nsub, r2.w, r.y, rows, items, cull, chunk,
+                                    ikey, ival);
             }
         }
         unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
@@ -172,7 +186,8 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const int src = __ffs(big) - 1;
             big &= big - 1;
             const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sbase = __shfl_sync(0xffffffffu, base, src);
-            emit_one(vp, tp, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane, s_start[wib], s_key0[wib]);
+            emit_one<kMulti>(vp, stp, srank, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
+                             s_start[wib], s_key0[wib]);
         }
     }
 }
@@ -189,10 +204,11 @@ __device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ s
 
 // Batch emission: sorted ids are slot * N + i, so each lane takes its splat's view from
 // the block's shared copy of the slot table; the same thread / warp split as emit_kernel.
+template <int kMulti>
 __global__ void __launch_bounds__(256)
 emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
                   const uint32_t* __restrict__ sorted_ids, int64_t n_cap, int64_t N,
-                  const unsigned long long* __restrict__ counters, const uint32_t* __restrict__ ioff,
+                  unsigned long long* __restrict__ counters, const uint32_t* __restrict__ ioff,
                   const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
                   const float4* __restrict__ rec, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
     if (counters[2]) return;   // overflow: the batch is discarded
@@ -204,10 +220,16 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
     const unsigned long long nv = counters[1];
     const int64_t n = nv < (unsigned long long)n_cap ? (int64_t)nv : n_cap;
     __shared__ uint32_t s_start[8][32], s_key0[8][32];
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank_unused[64];
+    stage_tree(tp, svp[0].rank_of, stp, srank_unused);   // ranks differ per request: svp[slot].rank_of
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p0 = warp * 32; p0 < n; p0 += nwarps * 32) {
+    unsigned long long* queue = &counters[5 + kMulti];   // zeroed with the batch's counters
+    for (;;) {
+        unsigned long long gq = 0;
+        if (lane == 0) gq = atomicAdd(queue, 1ull);
+        const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 32;
+        if (p0 >= n) break;
         const int64_t p = p0 + lane;
         uint32_t id = 0, base = 0;
         int items = 0, slot = 0;
@@ -218,13 +240,13 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             const ushort4 r = rect[id];
             const unsigned long long m = mask[id];
             const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
-            items = nsub * rows;
-            if (items <= kEmitThreadItems) {
+            items = ((nsub > 1) == (kMulti == 1)) ? nsub * rows : 0;
+            if (items > 0 && items <= kEmitThreadItems) {
                 const ViewParams& vp = svp[slot];
                 const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
                 const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
-                emit_thread(vp, tp, id, base, sbase[slot], f, m, nsub, r2.w, r.y, rows, items, nullptr, nullptr, ikey,
-                            ival);
+                emit_thread<kMulti>(vp, stp, vp.rank_of, id, base, sbase[slot], f, m, nsub, r2.w, r.y, rows, items,
+                                    nullptr, nullptr, ikey, ival);
             }
         }
         unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
@@ -233,23 +255,25 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             big &= big - 1;
             const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sb = __shfl_sync(0xffffffffu, base, src);
             const int ss = __shfl_sync(0xffffffffu, slot, src);
-            emit_one(svp[ss], tp, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr, ikey, ival, lane, s_start[wib],
-                     s_key0[wib]);
+            emit_one<kMulti>(svp[ss], stp, svp[ss].rank_of, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr,
+                             ikey, ival, lane, s_start[wib], s_key0[wib]);
         }
     }
 }
 
 // (min, max) of the forward depth table over each run of kCullChunk tiles of a row.
 __global__ void cull_chunk_kernel(ViewParams vp, const float* __restrict__ cull, float2* __restrict__ chunk) {
-    const int nch = cull_nchunk(vp);
+    const int nch = cull_nchunk(vp) + 1;   // the last entry of a row aggregates the whole row
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)vp.tiles_y * nch * vp.K;
     if (i >= total) return;
     const int rank = (int)(i % vp.K);
     const int ch = (int)((i / vp.K) % nch);
     const int ty = (int)(i / ((int64_t)vp.K * nch));
+    const int c_lo = ch == nch - 1 ? 0 : ch * kCullChunk;
+    const int c_hi = ch == nch - 1 ? vp.tiles_x : min(vp.tiles_x, (ch + 1) * kCullChunk);
     float lo = __int_as_float(0x7f800000), hi = -lo;
-    for (int c = ch * kCullChunk; c < min(vp.tiles_x, (ch + 1) * kCullChunk); ++c) {
+    for (int c = c_lo; c < c_hi; ++c) {
         const float d = cull[((size_t)ty * vp.tiles_x + c) * vp.K + rank];
         lo = fminf(lo, d);
         hi = fmaxf(hi, d);
@@ -552,6 +576,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 }
                 if (__all_sync(0xffffffffu, frozen)) break;
                 const int t1 = min(n, t0 + 32);
+                #pragma unroll 2
                 for (int t = t0; t < t1; ++t) {
                     const int j = wl[t];
                     const float4 A = srec[j].a;
@@ -945,14 +970,22 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
                 int64_t n_vis, cudaStream_t s) {
     if (n_vis <= 0) return RGS_OK;
     const int64_t want = (n_vis + 255) / 256;      // one warp per 32 splats
-    unsigned grid = (unsigned)(want < (1 << 20) ? want : (1 << 20));
-    emit_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
+    const int64_t cap = 152 * 16;                  // grid-stride beyond: amortises the tree copy
+    unsigned grid = (unsigned)(want < cap ? want : cap);
+    // work counters: counters[4] and [5] (zeroed with the others at the start of the list build)
+    emit_kernel<0><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
+                                        b.ikey, b.ival, b.counters + 4);
     RGS_CUDA_LAUNCH_CHECK();
+    if (vp.K > 1) {
+        emit_kernel<1><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull,
+                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
     return RGS_OK;
 }
 
 int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s) {
-    const int64_t total = (int64_t)vp.tiles_y * ((vp.tiles_x + kCullChunk - 1) / kCullChunk) * vp.K;
+    const int64_t total = (int64_t)vp.tiles_y * ((vp.tiles_x + kCullChunk - 1) / kCullChunk + 1) * vp.K;
     cull_chunk_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(vp, cull, chunk);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
@@ -982,11 +1015,16 @@ int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
 }
 
 int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
-                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, const unsigned long long* counters,
+                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
                       cudaStream_t s) {
-    emit_batch_kernel<<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect, b.mask,
-                                              b.rec, b.ikey, b.ival);
+    emit_batch_kernel<0><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
+                                                 b.mask, b.rec, b.ikey, b.ival);
     RGS_CUDA_LAUNCH_CHECK();
+    if (tp.L > 0) {
+        emit_batch_kernel<1><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
+                                                     b.mask, b.rec, b.ikey, b.ival);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
     return RGS_OK;
 }
 

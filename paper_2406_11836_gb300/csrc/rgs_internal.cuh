@@ -75,7 +75,8 @@ struct BatchHeader {
 
 // Device counters of a batch (uint64): [0] instances, [1] visible (slot, splat) pairs,
 // [2] overflow flag, [3] blend work-queue head, [4] instances to sort (0 on overflow),
-// then (instances, visible) per slot from kBatchSlotCounters.
+// [5], [6] emission work-queue heads, then (instances, visible) per slot from
+// kBatchSlotCounters.
 constexpr int kBatchSlotCounters = 8;
 constexpr int kBatchCounters = kBatchSlotCounters + 2 * kMaxSlots;
 
@@ -162,12 +163,12 @@ struct RasterBuffers {
     uint32_t* skey_alt;   // [N]                         (sort buffer b)
     uint32_t* sid_alt;    // [N]
     uint32_t* ioff;       // [N] instance offsets in depth order
-    unsigned long long* counters;  // [4]: total instances, visible splats
+    unsigned long long* counters;  // [8]: total instances, visible splats, -, -, emission work queues (2)
     float4* g2d;          // [N * 3] (backward only)
     // per (tile, subset)
     uint2* ranges;        // [tiles * K]
     const float* cull;    // [tiles * K] forward depth table (backward only; nullptr: no culling)
-    float2* cull_chunk;   // [tiles_y * ceil(tiles_x / 16) * K] (min, max) of `cull` over 16-tile chunks
+    float2* cull_chunk;   // [tiles_y * (ceil(tiles_x / 16) + 1) * K] (min, max) of `cull` over 16-tile chunks, then the row
     // per instance
     uint32_t* ikey;
     uint32_t* ival;
@@ -188,7 +189,7 @@ int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const B
 // Batch emission over the (slot, depth)-sorted visible list (count counters[1]); writes
 // nothing when the overflow flag counters[2] is set.
 int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
-                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, const unsigned long long* counters,
+                      const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
                       cudaStream_t s);
 int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
                       cudaStream_t s);

@@ -243,6 +243,7 @@ struct rgs_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     bool broken = false;
+    bool hold = false;
     double inst_per_pixel = 16.0;   // running estimate for admission
     rgs_serve_stats stats;
     int64_t batched_requests = 0;
@@ -365,7 +366,7 @@ void worker_batched(rgs_server* S) {
             }
         }
         if (S->stop) break;
-        if (!S->broken) {
+        if (!S->broken && !S->hold) {
             for (auto& ln : S->lanes) {
                 if (ln.busy || S->queue.empty()) continue;
                 std::vector<Request*> batch;
@@ -415,7 +416,7 @@ void worker_plain(rgs_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         if (S->stop) break;
-        if (S->queue.empty() || S->broken) {
+        if (S->queue.empty() || S->broken || S->hold) {
             S->cv.wait_for(lk, std::chrono::milliseconds(50));
             continue;
         }
@@ -735,6 +736,16 @@ int rgs_serve_poll(rgs_server* S, uint64_t ticket, int* done, double* latency_ms
     S->tickets.erase(it);
     delete r;
     return status;
+}
+
+int rgs_serve_hold(rgs_server* S, int hold) {
+    if (!S) { set_error("serve_hold: NULL server"); return RGS_EINVAL; }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->hold = hold != 0;
+    }
+    S->cv.notify_all();
+    return RGS_OK;
 }
 
 int rgs_serve_stats_read(rgs_server* S, rgs_serve_stats* out) {

@@ -105,6 +105,7 @@ def lib():
     L.rgs_serve_stats_read.argtypes = [c_void_p, POINTER(ServeStats)]
     L.rgs_serve_lane_bytes.argtypes = [c_void_p, POINTER(Gaussians), POINTER(ServeConfig), c_int64, POINTER(c_size_t)]
     L.rgs_serve_destroy.argtypes = [c_void_p]
+    L.rgs_serve_hold.argtypes = [c_void_p, c_int]
     _lib = L
     return L
 
@@ -426,6 +427,10 @@ class Server:
                 raise TimeoutError(f"request {ticket} not done after {timeout_s} s")
             time.sleep(0.0002)
 
+    def hold(self, on: bool = True):
+        """Pause (True) or resume (False) the start of new batches."""
+        _check(lib().rgs_serve_hold(self.handle, 1 if on else 0))
+
     def stats(self) -> dict:
         st = ServeStats()
         _check(lib().rgs_serve_stats_read(self.handle, ctypes.byref(st)))
@@ -449,4 +454,5 @@ ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "
                "rgs_render_bwd", "rgs_adam_step", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
-               "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes")
+               "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",
+               "rgs_serve_hold")

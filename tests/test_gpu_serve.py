@@ -43,12 +43,17 @@ def scene(R):
     return wl, g, kd, cams
 
 
-def _serve(R, scene, cams, **kw):
+def _serve(R, scene, cams, together=True, **kw):
+    """Serve `cams`; with together=True all are queued before the scheduler may start a
+    batch (rgs_serve_hold), so the batching does not depend on host timing."""
     wl, g, kd, _ = scene
     srv = R.Server(kd, g, R.default_opts(), keepalive=wl.scene, **kw)
     outs = [torch.full((3, c.height, c.width), -1.0, device="cuda") for c in cams]
     try:
+        if together:
+            srv.hold(True)
         tickets = [srv.submit(c, o) for c, o in zip(cams, outs)]
+        srv.hold(False)
         lat = [srv.wait(t, timeout_s=120) for t in tickets]
         st = srv.stats()
     finally:
