@@ -297,6 +297,27 @@ def run_serve_only(args, rank, world, local_rank):
                           "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "serving": res}), flush=True)
 
 
+# --------------------------------------------------------------------------- multi-rank host logic
+def shard_cameras(cams, rank, world):
+    """Replicas: rank r renders cameras r, r + world, ... (a rank left without one reuses all)."""
+    return cams[rank::world] or list(cams)
+
+
+def reduce_max(vals, world, device="cpu"):
+    """Element-wise max over ranks (the slowest rank's times); identity for one rank."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_mpix_s(world, steps, pix_per_step, ms_total):
+    """Pixels of every rank's steps over the slowest rank's time, in Mpix/s (weak scaling)."""
+    return world * steps * pix_per_step / (ms_total / 1e3) / 1e6
+
+
 # --------------------------------------------------------------------------- arms
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -310,7 +331,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     wl = make_workload(args.workload, dev)
-    cams = wl.cameras[rank::world] or wl.cameras
+    cams = shard_cameras(wl.cameras, rank, world)
     H, Wd = cams[0].height, cams[0].width
     trainer = Trainer(wl.scene, wl.depth_L, device=dev)
     del wl.scene
@@ -389,13 +410,10 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     print("e2e host ms per step:", [round(x, 1) for x in host_ms], file=sys.stderr)
 
-    t = torch.tensor([ms, e2e_s * 1e3], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], world, dev)
     pix_per_step = H * Wd
-    value = world * args.steps * pix_per_step / (ms_max / 1e3) / 1e6
-    e2e = world * args.steps * pix_per_step / (e2e_ms_max / 1e3) / 1e6
+    value = whole_job_mpix_s(world, args.steps, pix_per_step, ms_max)
+    e2e = whole_job_mpix_s(world, args.steps, pix_per_step, e2e_ms_max)
     rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table(), WORKLOAD_NAMES[args.workload])
     line = {
         "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",
