@@ -162,6 +162,32 @@ __device__ __forceinline__ unsigned long long subset_mask(const TreeParams& tp, 
     return cur;
 }
 
+// The splat's colour before the clamp, raw_c = sum_k sh[k][c] Y_k + 1/2 (coefficients
+// k-major, RGB inner).  kVec: the coefficients are read as float4 (their block is 16-byte
+// aligned); the per-channel accumulation order is the same either way.
+template <int NSH, bool kVec>
+__device__ __forceinline__ void sh_colour(const float* __restrict__ sh, const float* Y, float raw[3]) {
+    raw[0] = raw[1] = raw[2] = 0.5f;
+    if constexpr (kVec) {
+        const float4* s4 = reinterpret_cast<const float4*>(sh);
+#pragma unroll
+        for (int q = 0; q < NSH * 3 / 4; ++q) {
+            const float4 v = __ldg(s4 + q);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int idx = 4 * q + t;
+                raw[idx % 3] = fmaf(e[t], Y[idx / 3], raw[idx % 3]);
+            }
+        }
+    } else {
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int k = 0; k < NSH; ++k) raw[c] = fmaf(sh[3 * k + c], Y[k], raw[c]);
+        }
+    }
+}
+
 struct SplatIn {
     float mu[3], ls[3], q[4], logit;
 };
@@ -277,7 +303,7 @@ constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are
 // Projection of splat i (valid: i < n) into one view.  Outputs go to index j of the
 // per-splat arrays of b; the instance and visible-splat totals are added to counters[0..1]
 // and, when non-null, slot_counters[0..1].  Every lane of the warp must call it.
-template <int DEG>
+template <int DEG, bool kVecSH>
 __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t i, bool valid, const ViewParams& vp,
                                                  const TreeParams& tp, const int8_t* rank_of, const RasterBuffers& b,
                                                  int64_t j, unsigned long long* counters,
@@ -326,14 +352,9 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
                 float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
                 float Y[16];
                 sh_eval<DEG>(dx * inv, dy * inv, dz * inv, Y, nullptr);
-                const float* sh = g.sh + i * NSH * 3;
                 float rgb[3];
-                for (int c = 0; c < 3; ++c) {
-                    float acc = 0.5f;
-#pragma unroll
-                    for (int k = 0; k < NSH; ++k) acc = fmaf(sh[3 * k + c], Y[k], acc);
-                    rgb[c] = fmaxf(acc, 0.f);
-                }
+                sh_colour<NSH, kVecSH>(g.sh + i * NSH * 3, Y, rgb);
+                for (int c = 0; c < 3; ++c) rgb[c] = fmaxf(rgb[c], 0.f);
                 __half2 lo = __floats2half2_rn(mxl, myl);
                 float lo_bits = __uint_as_float(*reinterpret_cast<uint32_t*>(&lo));
                 b.rec[3 * j] = make_float4(mxh, myh, lo_bits, alpha);
@@ -392,20 +413,20 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     }
 }
 
-template <int DEG>
+template <int DEG, bool kVecSH>
 __global__ void __launch_bounds__(256, 3)
 project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
     stage_tree(tp, vp.rank_of, stp, srank);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
+    project_fwd_body<DEG, kVecSH>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
 }
 
 // Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
 // x % kMaxSlots, so the blocks of one splat range run back to back and read its
 // parameters from L2 after the first slot.  Outputs go to index slot * N + i.
-template <int DEG>
+template <int DEG, bool kVecSH>
 __global__ void __launch_bounds__(256, 3)
 project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
                      TreeParams tp, RasterBuffers b, unsigned long long* __restrict__ counters) {
@@ -421,7 +442,7 @@ project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const
     __shared__ int8_t srank[64];
     stage_tree(tp, slots[slot].vp.rank_of, stp, srank);   // its barrier also publishes svp
     const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG>(g, i, i < g.n, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
+    project_fwd_body<DEG, kVecSH>(g, i, i < g.n, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
                           counters + kBatchSlotCounters + 2 * slot);
 }
 
@@ -431,7 +452,7 @@ project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const
 // (J, Rq, S); J and the mean -> camera-space centre -> world centre; Rq -> normalised
 // quaternion -> quaternion; S -> log-scales; alpha -> logit.  Gradients are added to the
 // caller's buffers; one thread owns one splat, so no atomics are needed.
-template <int DEG>
+template <int DEG, bool kVecSH>
 __global__ void __launch_bounds__(128)
 project_bwd_kernel(rgs_gaussians g, rgs_gaussian_grads gr, ViewParams vp, const float4* __restrict__ g2d) {
     constexpr int NSH = (DEG + 1) * (DEG + 1);
@@ -466,19 +487,40 @@ project_bwd_kernel(rgs_gaussians g, rgs_gaussian_grads gr, ViewParams vp, const 
         const float* sh = g.sh + i * NSH * 3;
         float* gsh = gr.sh + i * NSH * 3;
         float gd[3] = {0.f, 0.f, 0.f};
-        for (int c = 0; c < 3; ++c) {
-            float raw = 0.5f;
+        float raw[3], gcol[3];
+        sh_colour<NSH, kVecSH>(sh, Y, raw);
+        for (int c = 0; c < 3; ++c) gcol[c] = raw[c] > 0.f ? g_rgb[c] : 0.f;   // clamp at 0: no gradient
+        if constexpr (kVecSH) {
+            const float4* s4 = reinterpret_cast<const float4*>(sh);
+            float4* g4 = reinterpret_cast<float4*>(gsh);
 #pragma unroll
-            for (int k = 0; k < NSH; ++k) raw = fmaf(sh[3 * k + c], Y[k], raw);
-            if (!(raw > 0.f)) continue;
-            float gcol = g_rgb[c];
+            for (int q = 0; q < NSH * 3 / 4; ++q) {
+                const float4 v = __ldg(s4 + q);
+                float4 gv = g4[q];
+                const float e[4] = {v.x, v.y, v.z, v.w};
+                float* ge[4] = {&gv.x, &gv.y, &gv.z, &gv.w};
 #pragma unroll
-            for (int k = 0; k < NSH; ++k) {
-                gsh[3 * k + c] += gcol * Y[k];
-                float w = gcol * sh[3 * k + c];
-                gd[0] = fmaf(w, dY[k].x, gd[0]);
-                gd[1] = fmaf(w, dY[k].y, gd[1]);
-                gd[2] = fmaf(w, dY[k].z, gd[2]);
+                for (int t = 0; t < 4; ++t) {
+                    const int idx = 4 * q + t, c = idx % 3, k = idx / 3;
+                    *ge[t] += gcol[c] * Y[k];
+                    const float w = gcol[c] * e[t];
+                    gd[0] = fmaf(w, dY[k].x, gd[0]);
+                    gd[1] = fmaf(w, dY[k].y, gd[1]);
+                    gd[2] = fmaf(w, dY[k].z, gd[2]);
+                }
+                g4[q] = gv;
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                if (!(raw[c] > 0.f)) continue;
+#pragma unroll
+                for (int k = 0; k < NSH; ++k) {
+                    gsh[3 * k + c] += gcol[c] * Y[k];
+                    const float w = gcol[c] * sh[3 * k + c];
+                    gd[0] = fmaf(w, dY[k].x, gd[0]);
+                    gd[1] = fmaf(w, dY[k].y, gd[1]);
+                    gd[2] = fmaf(w, dY[k].z, gd[2]);
+                }
             }
         }
         float dd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
@@ -558,15 +600,30 @@ project_bwd_kernel(rgs_gaussians g, rgs_gaussian_grads gr, ViewParams vp, const 
 
 }  // namespace
 
+// Float4 reads of the SH block need it 16-byte aligned: the base pointer aligned and a
+// per-splat stride that is a multiple of 16 bytes (degrees 1 and 3).
+static bool vec_sh(const rgs_gaussians& g, const float* gsh = nullptr) {
+    const bool stride_ok = g.sh_degree == 1 || g.sh_degree == 3;
+    return stride_ok && ((uintptr_t)g.sh % 16 == 0) && (!gsh || (uintptr_t)gsh % 16 == 0);
+}
+
+#define RGS_DISPATCH_SH(DEG_EXPR, VEC_EXPR, LAUNCH)                     \
+    do {                                                                \
+        const bool _vec = (VEC_EXPR);                                   \
+        switch (DEG_EXPR) {                                             \
+            case 0: { constexpr int D = 0; constexpr bool V = false; LAUNCH; } break; \
+            case 1: if (_vec) { constexpr int D = 1; constexpr bool V = true; LAUNCH; } \
+                    else { constexpr int D = 1; constexpr bool V = false; LAUNCH; } break; \
+            case 2: { constexpr int D = 2; constexpr bool V = false; LAUNCH; } break; \
+            default: if (_vec) { constexpr int D = 3; constexpr bool V = true; LAUNCH; } \
+                     else { constexpr int D = 3; constexpr bool V = false; LAUNCH; } break; \
+        }                                                               \
+    } while (0)
+
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s) {
     unsigned grid = (unsigned)((g.n + 255) / 256);
-    switch (g.sh_degree) {
-        case 0: project_fwd_kernel<0><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
-        case 1: project_fwd_kernel<1><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
-        case 2: project_fwd_kernel<2><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
-        default: project_fwd_kernel<3><<<grid, 256, 0, s>>>(g, vp, tp, b); break;
-    }
+    RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V><<<grid, 256, 0, s>>>(g, vp, tp, b)));
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -574,12 +631,8 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
 int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp,
                          const RasterBuffers& b, unsigned long long* counters, cudaStream_t s) {
     const unsigned grid = (unsigned)((g.n + 255) / 256) * (unsigned)kMaxSlots;
-    switch (g.sh_degree) {
-        case 0: project_batch_kernel<0><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
-        case 1: project_batch_kernel<1><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
-        case 2: project_batch_kernel<2><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
-        default: project_batch_kernel<3><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters); break;
-    }
+    RGS_DISPATCH_SH(g.sh_degree, vec_sh(g),
+                    (project_batch_kernel<D, V><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters)));
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -587,12 +640,8 @@ int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const B
 int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
                        const RasterBuffers& b, cudaStream_t s) {
     unsigned grid = (unsigned)((g.n + 127) / 128);
-    switch (g.sh_degree) {
-        case 0: project_bwd_kernel<0><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
-        case 1: project_bwd_kernel<1><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
-        case 2: project_bwd_kernel<2><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
-        default: project_bwd_kernel<3><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d); break;
-    }
+    RGS_DISPATCH_SH(g.sh_degree, vec_sh(g, gr.sh),
+                    (project_bwd_kernel<D, V><<<grid, 128, 0, s>>>(g, gr, vp, b.g2d)));
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
