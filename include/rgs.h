@@ -155,7 +155,10 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
  * C = 0, T = 1).  If `image` [3,H,W] is non-NULL the partials are also merged in view
  * order (Eq. 5) with the background behind, and T_final [H,W] (nullable) receives the
  * product of all T_k.  partial_C and partial_T may both be NULL when image is non-NULL:
- * a forward-only render that keeps the partials on chip (no rgs_render_bwd from it).  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
+ * a forward-only render that keeps the partials on chip (no rgs_render_bwd from it); it
+ * also stops a pixel at the first subset whose transmittance in front (the merge's
+ * prod_{m<r} T_{o_m}) is below eps_T, which changes the image by less than eps_T times the
+ * largest colour (T_final is then that transmittance rather than the full product).  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
  * by tile then by the subset's position in rgs_view_order, receives per (tile, subset) the
  * camera depth of the last splat blended before every pixel of the tile had dropped below
  * eps_T in that subset (+inf if that did not happen); rgs_render_bwd uses it to skip

@@ -544,13 +544,22 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     s_img[2][tid] = 0.f;
     s_img[3][tid] = 1.f;
 
+    // Without partial maps only the image is wanted: a pixel whose transmittance in front of
+    // subset k (the merge's P) is below eps_T skips k and every later subset (they change its
+    // colour by less than eps_T max(rgb)), and a tile with no such pixel left skips the subset.
+    const bool image_only = pC == nullptr;
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
-        if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         const uint2 rg = ranges[r];
+        const bool live = inside && !(image_only && s_img[3][tid] < vp.eps_T);
+        if (image_only && __syncthreads_count(live) == 0) {
+            if (tile_depth && threadIdx.x == 0) tile_depth[r] = kInfF;
+            continue;
+        }
+        if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         float C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        float T = inside ? 1.f : 0.f;
-        bool frozen = !inside;
+        float T = live ? 1.f : 0.f;
+        bool frozen = !live;
         float zsat = kInfF;   // the subset never saturated the tile
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
@@ -615,7 +624,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 break;
             }
         }
-        if (frozen && inside) T = s_tkeep[tid];
+        if (frozen && inside) T = live ? s_tkeep[tid] : 1.f;
         if (tile_depth && threadIdx.x == 0) tile_depth[r] = zsat;
         if (inside) {
             if (pC) {
