@@ -229,7 +229,7 @@ def _traffic_table():
 
 
 # --------------------------------------------------------------------------- serving
-def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=24, burst=400, device=None):
+def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400, device=None, lanes=4, max_slots=4):
     warm = min(warm, requests // 4)
     burst = min(burst, requests)
     """Serving on the 5M-splat city scene (K=8): a seeded Poisson stream of mixed-resolution
@@ -248,7 +248,7 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=24, burst=400,
     outs = {(w, h): [torch.empty(3, h, w, device=device) for _ in range(ring)] for (w, h) in W.RESOLUTIONS}
     res = {}
     for mode in ("batched", "plain"):
-        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, max_slots=8, lanes=2,
+        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, max_slots=max_slots, lanes=lanes,
                          plain=(mode == "plain"), keepalive=wl.scene)
         for (w, h), bufs in outs.items():     # warm every resolution once
             srv.wait(srv.submit(W.look_at((6.0, 6.0, 5.0), (0, 0, 0), w, h), bufs[0]))
@@ -278,7 +278,7 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=24, burst=400,
     res["config"] = {"workload": "serve-5M-K8", "splats": int(g.n), "subsets": kd.K,
                      "arrivals": f"Poisson {rate_hz:g} req/s, {requests} requests ({warm} warm-up)",
                      "resolutions": [f"{w}x{h}" for w, h in W.RESOLUTIONS], "budget_gb": budget_gb,
-                     "max_slots": 8, "lanes": 2,
+                     "max_slots": max_slots, "lanes": lanes,
                      "offered_mpix_s": rate_hz * float(np.mean([w * h for w, h in W.RESOLUTIONS])) / 1e6}
     return res
 
