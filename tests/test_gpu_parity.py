@@ -382,3 +382,26 @@ def test_backward_depth_culling_changes_nothing(R):
     assert c_cut == c_full
     for a, b in zip(cut, full):
         assert rel_l2(a.double().cpu().numpy(), b.double().cpu().numpy()) <= 1e-5
+
+
+def test_image_only_render_stops_at_negligible_front_transmittance(R):
+    """A render without partial maps stops a pixel at the first subset whose transmittance in
+    front is below eps_T: its image stays within eps_T * K * max colour of the full render's
+    and of the oracle's (a dense scene so that many pixels reach that point)."""
+    scene = W.uniform_cube_scene(20_000, seed=31, log_scale_mean=-2.5, sh_degree=1)
+    cam = W.look_at((0.0, -3.0, 0.4), (0.0, 0.0, 0.0), 96, 80)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 3)
+    ws = R.Workspace()
+    full = R.render_fwd(kd, R.scene_c(dev), cam, R.default_opts(), ws)
+    img_only = R.render_fwd(kd, R.scene_c(dev), cam, R.default_opts(), ws, partials=False)
+    torch.cuda.synchronize()
+    a, b = full["image"], img_only["image"]
+    cmax = max(1.0, float(a.abs().max()))
+    assert float((a - b).abs().max()) <= 1e-6 * 8 * cmax + 1e-7
+    assert float((full["T_final"] < 1e-6).float().mean()) > 0.2   # the stop was exercised
+    pix = W.sample_pixels(cam.width, cam.height, 600, seed=5)
+    flat = O.render(scene, cam, oracle_opts(), pix=pix)
+    ok = (flat["flags"] & FWD_FLAGS) == 0
+    assert ok.mean() >= 1 - MAX_FLAGGED
+    assert np.abs(image_at(b, pix) - flat["C"])[ok].max() <= PIXEL_TOL

@@ -180,3 +180,30 @@ def test_submit_validation_and_destroy_with_pending(R, scene):
         srv.submit(c, o)
     srv.close()          # cancels what is queued, waits (bounded) for what runs
     torch.cuda.synchronize()
+
+
+def test_edge_sizes_and_a_single_subset_scene(R):
+    """1x1 and odd-sized requests, and a scene with one KD subset (K = 1), through the
+    batched server: each equal to rgs_render_fwd's image of the same view."""
+    wl = W.serving_5m(device="cuda", n=30_000)
+    g = R.scene_c(wl.scene)
+    for L in (0, 2):
+        kd = R.kd_partition(wl.scene, L)
+        cams = [W.look_at((6.0, -5.0, 4.0), (0, 0, 0), w, h) for (w, h) in ((1, 1), (17, 9), (33, 65), (16, 16))]
+        srv = R.Server(kd, g, R.default_opts(), 2 << 30, max_slots=4, lanes=1, max_width=64, max_height=128,
+                       keepalive=wl.scene)
+        outs = [torch.full((3, c.height, c.width), -1.0, device="cuda") for c in cams]
+        try:
+            srv.hold(True)
+            ts = [srv.submit(c, o) for c, o in zip(cams, outs)]
+            srv.hold(False)
+            for t in ts:
+                srv.wait(t, timeout_s=60)
+        finally:
+            srv.close()
+        torch.cuda.synchronize()
+        ws = R.Workspace()
+        for c, o in zip(cams, outs):
+            ref = R.render_fwd(kd, g, c, R.default_opts(), ws, partials=False)["image"]
+            torch.cuda.synchronize()
+            assert torch.equal(ref, o), (L, c.width, c.height)
