@@ -236,9 +236,9 @@ __device__ __forceinline__ bool keep_tile(const float* __restrict__ cull, const 
 
 __device__ __forceinline__ int cull_nchunk(const ViewParams& vp) { return (vp.tiles_x + kCullChunk - 1) / kCullChunk; }
 
-// Entry of the chunk table: per tile row, nch chunks then (index nch) the whole row.
+// Entry of the chunk table for chunk ch of tile row ty in subset `rank`.
 __device__ __forceinline__ size_t cull_chunk_index(const ViewParams& vp, int ty, int ch, int rank) {
-    return ((size_t)ty * (cull_nchunk(vp) + 1) + ch) * vp.K + rank;
+    return ((size_t)ty * cull_nchunk(vp) + ch) * vp.K + rank;
 }
 
 // Number of tiles of [c0, c1] in row ty kept for a splat at depth z in subset `rank`.

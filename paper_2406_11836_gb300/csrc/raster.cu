@@ -263,15 +263,14 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
 
 // (min, max) of the forward depth table over each run of kCullChunk tiles of a row.
 __global__ void cull_chunk_kernel(ViewParams vp, const float* __restrict__ cull, float2* __restrict__ chunk) {
-    const int nch = cull_nchunk(vp) + 1;   // the last entry of a row aggregates the whole row
+    const int nch = cull_nchunk(vp);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)vp.tiles_y * nch * vp.K;
     if (i >= total) return;
     const int rank = (int)(i % vp.K);
     const int ch = (int)((i / vp.K) % nch);
     const int ty = (int)(i / ((int64_t)vp.K * nch));
-    const int c_lo = ch == nch - 1 ? 0 : ch * kCullChunk;
-    const int c_hi = ch == nch - 1 ? vp.tiles_x : min(vp.tiles_x, (ch + 1) * kCullChunk);
+    const int c_lo = ch * kCullChunk, c_hi = min(vp.tiles_x, (ch + 1) * kCullChunk);
     float lo = __int_as_float(0x7f800000), hi = -lo;
     for (int c = c_lo; c < c_hi; ++c) {
         const float d = cull[((size_t)ty * vp.tiles_x + c) * vp.K + rank];
@@ -994,7 +993,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
 }
 
 int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s) {
-    const int64_t total = (int64_t)vp.tiles_y * ((vp.tiles_x + kCullChunk - 1) / kCullChunk + 1) * vp.K;
+    const int64_t total = (int64_t)vp.tiles_y * ((vp.tiles_x + kCullChunk - 1) / kCullChunk) * vp.K;
     cull_chunk_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(vp, cull, chunk);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;

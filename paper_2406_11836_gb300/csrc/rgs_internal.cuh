@@ -168,7 +168,7 @@ struct RasterBuffers {
     // per (tile, subset)
     uint2* ranges;        // [tiles * K]
     const float* cull;    // [tiles * K] forward depth table (backward only; nullptr: no culling)
-    float2* cull_chunk;   // [tiles_y * (ceil(tiles_x / 16) + 1) * K] (min, max) of `cull` over 16-tile chunks, then the row
+    float2* cull_chunk;   // [tiles_y * ceil(tiles_x / 16) * K] (min, max) of `cull` over 16-tile chunks
     // per instance
     uint32_t* ikey;
     uint32_t* ival;
