@@ -110,21 +110,57 @@ scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n, int mode, const u
                    tile_offsets ? tile_offsets[blockIdx.x] : 0u);
 }
 
-// Per-tile histogram of one 8-bit digit, written digit-major: counts[d * nblocks + b].
+// A block of the host-counted passes owns kBlockTiles consecutive sort tiles, so the
+// digit-major count table (read and written with a stride of the block count) stays small.
+constexpr int kBlockTiles = 8;
+constexpr int kBlockItems = kSortTile * kBlockTiles;   // 16384
+
+// Adds the digits of keys [lo, hi) to the shared histogram: a thread takes 8 consecutive
+// keys per round (two 16-byte loads when `vec` and lo is a multiple of 8) and adds each
+// run of equal digits with one shared atomic (the later passes see keys already ordered
+// by their low digits, whose high digits repeat).  The whole block calls it.
+__device__ __forceinline__ void hist_runs(const uint32_t* __restrict__ keys, int64_t lo, int64_t hi, int shift, bool vec,
+                                          uint32_t* hist) {
+    for (int64_t b = lo; b < hi; b += kSortThreads * 8) {   // uniform trip count across the block
+        const int64_t i0 = b + (int64_t)threadIdx.x * 8;
+        uint32_t k[8];
+        if (vec && i0 + 8 <= hi) {
+            const uint4 x = *reinterpret_cast<const uint4*>(keys + i0);
+            const uint4 y = *reinterpret_cast<const uint4*>(keys + i0 + 4);
+            k[0] = x.x; k[1] = x.y; k[2] = x.z; k[3] = x.w; k[4] = y.x; k[5] = y.y; k[6] = y.z; k[7] = y.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) k[j] = i0 + j < hi ? keys[i0 + j] : 0u;
+        }
+        const int m = hi - i0 < 8 ? (int)(hi - i0) : 8;   // may be <= 0 past the end
+        if (m > 0) {
+            uint32_t cur = (k[0] >> shift) & (kRadix - 1), run = 1;
+#pragma unroll
+            for (int j = 1; j < 8; ++j) {
+                if (j >= m) break;
+                const uint32_t d = (k[j] >> shift) & (kRadix - 1);
+                if (d != cur) {
+                    atomicAdd(&hist[cur], run);
+                    cur = d;
+                    run = 0;
+                }
+                ++run;
+            }
+            atomicAdd(&hist[cur], run);
+        }
+    }
+}
+
+// Histogram of one 8-bit digit over the block's range, written digit-major:
+// counts[d * nblocks + b].
 __global__ void __launch_bounds__(kSortThreads, 4)
 radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
-                     uint32_t nblocks) {
+                     uint32_t nblocks, bool vec) {
     __shared__ uint32_t hist[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) hist[d] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const int lane = threadIdx.x & 31;
-    for (int j = 0; j < kSortItems; ++j) {
-        int64_t i = base + (int64_t)j * kSortThreads + threadIdx.x;
-        int d = i < n ? (int)((keys[i] >> shift) & (kRadix - 1)) : kRadix;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < kRadix && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&hist[d], (uint32_t)__popc(peers));
-    }
+    const int64_t lo = (int64_t)blockIdx.x * kBlockItems;
+    hist_runs(keys, lo, min(n, lo + kBlockItems), shift, vec, hist);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
 }
@@ -135,9 +171,24 @@ radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, ui
 // equal digits of the round gives each key's rank within its warp, the per-digit scan
 // over warps gives its rank within the tile.  goff[d] (shared) is where the tile's first
 // key of digit d goes; on return it has advanced past the tile's keys of digit d.
-__device__ __forceinline__ void radix_tile_body(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                int64_t base, int count, int shift, uint32_t* goff) {
+// This thread's items of the tile [base, base + count) in the order radix_rank_scatter
+// expects them.
+__device__ __forceinline__ void radix_tile_load(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                int64_t base, int count, uint32_t (&key)[kSortItems],
+                                                uint32_t (&val)[kSortItems]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int li = warp * (kSortItems * 32) + r * 32 + lane;
+        const bool ok = li < count;
+        key[r] = ok ? kin[base + li] : 0u;
+        val[r] = ok ? vin[base + li] : 0u;
+    }
+}
+
+__device__ __forceinline__ void radix_rank_scatter(const uint32_t (&key)[kSortItems], const uint32_t (&val)[kSortItems],
+                                                   uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                   int count, int shift, uint32_t* goff) {
     __shared__ uint32_t whist[kSortWarps][kRadix];
     __shared__ uint32_t dstart[kRadix];
     __shared__ uint32_t dtot[kRadix];
@@ -148,15 +199,12 @@ __device__ __forceinline__ void radix_tile_body(const uint32_t* __restrict__ kin
     for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&whist[0][0])[i] = 0;
     __syncthreads();
 
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    uint32_t rank[kSortItems];
     int dig[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int li = warp * (kSortItems * 32) + r * 32 + lane;
-        const bool ok = li < count;
-        key[r] = ok ? kin[base + li] : 0u;
-        val[r] = ok ? vin[base + li] : 0u;
-        dig[r] = ok ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
+        dig[r] = li < count ? (int)((key[r] >> shift) & (kRadix - 1)) : kRadix;
     }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
@@ -215,15 +263,26 @@ __device__ __forceinline__ void radix_tile_body(const uint32_t* __restrict__ kin
     __syncthreads();
 }
 
+__device__ __forceinline__ void radix_tile_body(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                int64_t base, int count, int shift, uint32_t* goff) {
+    uint32_t key[kSortItems], val[kSortItems];
+    radix_tile_load(kin, vin, base, count, key, val);
+    radix_rank_scatter(key, val, kout, vout, count, shift, goff);
+}
+
 __global__ void __launch_bounds__(kSortThreads, 4)
 radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                        uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
                        uint32_t nblocks) {
     __shared__ uint32_t goff[kRadix];
     goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const int64_t rem = n - base;
-    radix_tile_body(kin, vin, kout, vout, base, rem < kSortTile ? (int)rem : kSortTile, shift, goff);
+    const int64_t lo = (int64_t)blockIdx.x * kBlockItems;
+    const int64_t hi = min(n, lo + kBlockItems);
+    for (int64_t base = lo; base < hi; base += kSortTile) {   // tiles in order: stable
+        const int64_t rem = hi - base;
+        radix_tile_body(kin, vin, kout, vout, base, rem < kSortTile ? (int)rem : kSortTile, shift, goff);
+    }
 }
 
 // ------------------------------------------------------------------ device-counted passes
@@ -282,13 +341,7 @@ dradix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long lon
     __syncthreads();
     int64_t lo, hi;
     chunk_range(device_count(n_dev, cap), kSortTile, lo, hi);
-    const int lane = threadIdx.x & 31;
-    for (int64_t b = lo; b < hi; b += kSortThreads) {   // uniform trip count across the block
-        const int64_t i = b + threadIdx.x;
-        const int d = i < hi ? (int)((keys[i] >> shift) & (kRadix - 1)) : kRadix;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < kRadix && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&hist[d], (uint32_t)__popc(peers));
-    }
+    hist_runs(keys, lo, hi, shift, ((uintptr_t)keys & 15) == 0, hist);
     __syncthreads();
     counts[(int64_t)threadIdx.x * kChunks + blockIdx.x] = hist[threadIdx.x];
 }
@@ -348,7 +401,7 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int load, c
 }
 
 size_t radix_temp_bytes(int64_t n) {
-    int64_t nb = cdiv(n > 0 ? n : 1, kSortTile);
+    int64_t nb = cdiv(n > 0 ? n : 1, kBlockItems);
     int64_t nc = nb * kRadix;
     return align256((size_t)nc * 4) + scan_temp_bytes(nc);
 }
@@ -361,7 +414,7 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_
         set_error("radix sort: %lld elements exceed the 32-bit index range", (long long)n);
         return RGS_EOVERFLOW;
     }
-    int64_t nb = cdiv(n, kSortTile);
+    int64_t nb = cdiv(n, kBlockItems);
     int64_t nc = nb * kRadix;
     size_t cbytes = align256((size_t)nc * 4);
     if (temp_bytes < cbytes + scan_temp_bytes(nc)) {
@@ -373,7 +426,8 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_
     size_t sbytes = temp_bytes - cbytes;
     uint32_t *ka = keys, *va = vals, *kb = keys_alt, *vb = vals_alt;
     for (int shift = 0; shift < end_bit; shift += kRadixBits) {
-        radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb);
+        radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb,
+                                                                   ((uintptr_t)ka & 15) == 0);
         RGS_CUDA_LAUNCH_CHECK();
         int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
         if (rc != RGS_OK) return rc;
