@@ -280,12 +280,29 @@ __global__ void cull_chunk_kernel(ViewParams vp, const float* __restrict__ cull,
     chunk[i] = make_float2(lo, hi);
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    uint32_t k = keys[j];
-    if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
-    if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+// Run boundaries of the sorted keys: a thread takes 4 consecutive keys per round (one
+// 16-byte load when `vec`) and their right neighbour; grid-stride over a resident grid.
+__global__ void __launch_bounds__(256)
+ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, bool vec, uint2* __restrict__ ranges) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; j0 < n; j0 += stride) {
+        uint32_t k[5];
+        if (vec && j0 + 4 <= n) {
+            const uint4 v = *reinterpret_cast<const uint4*>(keys + j0);
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+            for (int q = 0; q < 4; ++q) k[q] = j0 + q < n ? keys[j0 + q] : 0u;
+        }
+        k[4] = j0 + 4 < n ? keys[j0 + 4] : 0u;
+        const uint32_t prev = j0 > 0 ? keys[j0 - 1] : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t j = j0 + q;
+            if (j >= n) break;
+            if (j == 0 || (q == 0 ? prev : k[q - 1]) != k[q]) ranges[k[q]].x = (uint32_t)j;
+            if (j == n - 1 || k[q + 1] != k[q]) ranges[k[q]].y = (uint32_t)(j + 1);
+        }
+    }
 }
 
 __global__ void ranges_dev_kernel(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
@@ -1002,7 +1019,9 @@ int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, c
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s) {
     RGS_CUDA_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s));
     if (n <= 0) return RGS_OK;
-    ranges_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, ranges);
+    const int64_t want = (n + 1023) / 1024;
+    ranges_kernel<<<(unsigned)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(keys, n, ((uintptr_t)keys & 15) == 0,
+                                                                            ranges);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
