@@ -5,9 +5,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "rgs_internal.cuh"
@@ -111,6 +113,8 @@ __global__ void compact_kernel(const uint32_t* __restrict__ cnt, const uint32_t*
     skey[p] = dkey_lo[i];
     sid[p] = (uint32_t)i;
 }
+
+__global__ void store_u64_kernel(unsigned long long* p, unsigned long long v) { *p = v; }
 
 // key[j] = dkey[id[j]]: the float bits of z in the order of the first (low-bits) pass.
 __global__ void gather_key_kernel(const uint32_t* __restrict__ dkey, const uint32_t* __restrict__ id, int64_t n,
@@ -250,6 +254,7 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     };
     RasterBuffers t;
     memset(&t, 0, sizeof t);
+    t.header = (unsigned long long*)take(256);
     t.rec = (float4*)take(sizeof(float4) * 3 * N);
     t.g2d = (float4*)take(sizeof(float4) * 3 * N);
     t.cnt = (uint32_t*)take(4 * N);
@@ -279,6 +284,62 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     return off;
 }
 
+// The buffers of a workspace of ws_bytes, with the largest instance capacity that fits.
+void carve_workspace(void* workspace, size_t ws_bytes, int64_t N, int64_t tiles, int K, RasterBuffers* b) {
+    int64_t lo = 0, hi = (int64_t)(ws_bytes / 16) + 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2;
+        if (layout(nullptr, N, tiles, K, mid, nullptr) <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    layout((char*)workspace, N, tiles, K, lo, b);
+}
+
+// ------------------------------------------------------------------ lists kept for the backward
+// A forward with partial maps leaves in its workspace the records, the sorted instance
+// payloads and the (tile, subset) ranges cut back to what it staged.  The backward of that
+// same render replays exactly these lists, so when rgs_render_bwd gets the same workspace
+// with the arguments of that forward it skips re-deriving them.  The host keeps, per
+// workspace, the forward's arguments and a nonce that the forward also wrote into the
+// workspace header; the backward takes the shortcut only when both match (anything that
+// overwrote the header in between makes it re-derive the lists).
+struct ListStamp {
+    const rgs_kd* kd;
+    rgs_gaussians g;
+    rgs_camera cam;
+    rgs_render_opts opts;
+    const float* pC;
+    const float* pT;
+    size_t ws_bytes;
+    bool alt;           // payloads in ival_alt
+    int64_t I;          // instances
+    unsigned long long nonce;
+};
+std::mutex g_stamp_mu;
+std::unordered_map<const void*, ListStamp> g_stamps;
+std::atomic<unsigned long long> g_nonce_counter{0};
+
+unsigned long long next_nonce() {
+    // splitmix64 of a per-process base and a counter: distinct per forward, never 0
+    static const unsigned long long base = (unsigned long long)(uintptr_t)&g_nonce_counter ^
+                                           ((unsigned long long)std::chrono::steady_clock::now().time_since_epoch().count()
+                                            << 1);
+    unsigned long long z = base + 0x9E3779B97F4A7C15ull * (g_nonce_counter.fetch_add(1) + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z ? z : 1;
+}
+
+bool same_gaussians(const rgs_gaussians& a, const rgs_gaussians& b) {
+    return a.means == b.means && a.log_scales == b.log_scales && a.quats == b.quats &&
+           a.opacity_logits == b.opacity_logits && a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree;
+}
+
+void stamp_erase(const void* ws) {
+    std::lock_guard<std::mutex> lk(g_stamp_mu);
+    g_stamps.erase(ws);
+}
+
 struct PinnedCounters {
     unsigned long long* h = nullptr;
     ~PinnedCounters() {
@@ -292,7 +353,8 @@ thread_local PinnedCounters g_pinned;
 // payloads in blend order.
 int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                 void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
-                const uint32_t** sorted_ival, const float* cull, unsigned long long* host_counters = nullptr) {
+                const uint32_t** sorted_ival, const float* cull, unsigned long long* host_counters = nullptr,
+                int64_t* n_inst = nullptr) {
     int rc;
     if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
     if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
@@ -311,13 +373,7 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         return RGS_EOVERFLOW;
     }
     if (!aligned(workspace, 256)) { set_error("render: workspace must be 256-byte aligned"); return RGS_EINVAL; }
-    // the instance capacity that fits the workspace
-    int64_t lo = 0, hi = (int64_t)(ws_bytes / 16) + 1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi + 1) / 2;
-        if (layout(nullptr, N, tiles, vp->K, mid, nullptr) <= ws_bytes) lo = mid; else hi = mid - 1;
-    }
-    layout((char*)workspace, N, tiles, vp->K, lo, b);
+    carve_workspace(workspace, ws_bytes, N, tiles, vp->K, b);
     b->cull = cull;
     if (cull) {
         rc = launch_cull_chunks(*vp, cull, b->cull_chunk, s);
@@ -339,6 +395,7 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
     RGS_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t I = (int64_t)hc[0];
     const int64_t n_vis = (int64_t)hc[1];
+    if (n_inst) *n_inst = I;
     if (I > 0xFFFFFFFFll - 1) {
         set_error("render: %lld tile instances exceed the 32-bit instance index", (long long)I);
         return RGS_EOVERFLOW;
@@ -407,7 +464,8 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
 
 int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                     float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters) {
+                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters,
+                    bool keep_lists) {
     if ((!partial_C) != (!partial_T) || (!partial_C && !image)) {
         set_error("render_fwd: give both partial maps, or neither together with an image (forward only)");
         return RGS_EINVAL;
@@ -416,10 +474,77 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
     TreeParams tp;
     RasterBuffers b;
     const uint32_t* ival = nullptr;
-    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, host_counters);
+    int64_t I = 0;
+    if (keep_lists) stamp_erase(workspace);   // its lists are about to be replaced
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, host_counters, &I);
     if (rc) return rc;
-    ProfScope ps(ST_BLEND_FWD, s);
-    return launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s);
+    const bool keep = keep_lists && partial_C != nullptr;   // a backward may follow
+    {
+        ProfScope ps(ST_BLEND_FWD, s);
+        rc = launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s, keep);
+        if (rc) return rc;
+    }
+    if (keep) {
+        ListStamp st;
+        st.kd = kd;
+        st.g = *g;
+        st.cam = *cam;
+        st.opts = *opts;
+        st.pC = partial_C;
+        st.pT = partial_T;
+        st.ws_bytes = ws_bytes;
+        st.alt = ival == b.ival_alt;
+        st.I = I;
+        st.nonce = next_nonce();
+        store_u64_kernel<<<1, 1, 0, s>>>(b.header, st.nonce);
+        RGS_CUDA_LAUNCH_CHECK();
+        std::lock_guard<std::mutex> lk(g_stamp_mu);
+        g_stamps[workspace] = st;
+    }
+    return RGS_OK;
+}
+
+// The backward of the forward whose lists `workspace` holds, if the arguments are that
+// forward's: replays its lists (no projection, sorting or emission).  Returns 1 when it
+// does not apply (the caller re-derives the lists), else a status.
+int render_bwd_reuse(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                     const float* partial_C, const float* partial_T, const float* dL_dimage,
+                     const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, cudaStream_t s) {
+    ListStamp st;
+    {
+        std::lock_guard<std::mutex> lk(g_stamp_mu);
+        auto it = g_stamps.find(workspace);
+        if (it == g_stamps.end()) return 1;
+        st = it->second;
+    }
+    if (st.kd != kd || !same_gaussians(st.g, *g) || memcmp(&st.cam, cam, sizeof *cam) != 0 ||
+        memcmp(&st.opts, opts, sizeof *opts) != 0 || st.pC != partial_C || st.pT != partial_T ||
+        st.ws_bytes != ws_bytes)
+        return 1;
+    ViewParams vp;
+    TreeParams tp;
+    fill_view(kd, g, cam, opts, &vp, &tp);
+    RasterBuffers b;
+    carve_workspace(workspace, ws_bytes, g->n, (int64_t)vp.tiles_x * vp.tiles_y, vp.K, &b);
+    if (st.I > b.inst_cap) return 1;
+    unsigned long long* hc = g_pinned.h;
+    if (!hc) {
+        RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
+        hc = g_pinned.h;
+    }
+    RGS_CUDA_TRY(cudaMemcpyAsync(hc, b.header, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    RGS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hc[0] != st.nonce) return 1;   // the workspace was overwritten since
+    const uint32_t* ival = st.alt ? b.ival_alt : b.ival;
+    int rc;
+    {
+        ProfScope ps(ST_BLEND_BWD, s);
+        RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
+        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, st.I, g->n, s);
+        if (rc) return rc;
+    }
+    ProfScope ps(ST_PROJECT_BWD, s);
+    return launch_project_bwd(*g, *grads, vp, b, s);
 }
 
 }  // namespace rgs
@@ -581,16 +706,24 @@ int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* c
     }
     if (!aligned(grads->quats, 16)) { set_error("render_bwd: grads->quats must be 16-byte aligned"); return RGS_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    int rc;
+    if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
+    if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
+    rc = render_bwd_reuse(kd, g, cam, opts, partial_C, partial_T, dL_dimage, grads, workspace, ws_bytes, s);
+    if (rc != 1) return rc;
+    // re-derive the lists (depth-culled by tile_depth when given)
+    stamp_erase(workspace);
     ViewParams vp;
     TreeParams tp;
     RasterBuffers b;
     const uint32_t* ival = nullptr;
-    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, tile_depth);
+    int64_t I = 0;
+    rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, tile_depth, nullptr, &I);
     if (rc) return rc;
     {
         ProfScope ps(ST_BLEND_BWD, s);
         RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
-        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, s);
+        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, I, g->n, s);
         if (rc) return rc;
     }
     ProfScope ps(ST_PROJECT_BWD, s);

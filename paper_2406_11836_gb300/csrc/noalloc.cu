@@ -60,7 +60,7 @@ extern "C" int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, 
     unsigned long long counts[2] = {0, 0};   // host copy of the instance counts (no pinned buffer)
     rgs::prof_suppress(true);                // tracing would create CUDA events
     const int rc = rgs::render_fwd_into(kd, g, cam, opts, partial_C, partial_T, image, T_final, tile_depth, scratch,
-                                        kScratchBytes, (cudaStream_t)stream, counts);
+                                        kScratchBytes, (cudaStream_t)stream, counts, false);
     rgs::prof_suppress(false);
     if (rc == RGS_EOVERFLOW) {
         const size_t need = rgs_last_required_workspace();

@@ -526,13 +526,17 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 //
 // One tile of the view: `ranges` and `tile_depth` point at the tile's K entries (view
 // rank order); pC/pT (partial maps) and tile_depth may be null.  The whole block calls it.
+//
+// ends (nullable, the tile's K ranges again): where a subset saturated the tile, the
+// range's end is moved back to the end of the last batch staged, so that a backward
+// replaying these lists stops where the forward did.
 template <bool kCount>
 __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
-                                               const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                                               const uint2* ranges, const uint32_t* __restrict__ ival,
                                                const float4* __restrict__ rec, float* __restrict__ pC,
                                                float* __restrict__ pT, float* __restrict__ image,
                                                float* __restrict__ Tfin, float* __restrict__ tile_depth,
-                                               unsigned long long* __restrict__ pairs) {
+                                               uint2* ends, unsigned long long* __restrict__ pairs) {
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -577,6 +581,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         float T = live ? 1.f : 0.f;
         bool frozen = !live;
         float zsat = kInfF;   // the subset never saturated the tile
+        uint32_t send = rg.y;  // end of the last batch staged
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
@@ -637,11 +642,13 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
             }
             if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) {
                 zsat = srec[nb - 1].c.w;   // depth of the last instance staged
+                send = b0 + (uint32_t)nb;
                 break;
             }
         }
         if (frozen && inside) T = live ? s_tkeep[tid] : 1.f;
         if (tile_depth && threadIdx.x == 0) tile_depth[r] = zsat;
+        if (ends && threadIdx.x == 0 && send != rg.y) ends[r].y = send;
         if (inside) {
             if (pC) {
                 pC[((size_t)k * 3 + 0) * HW + pix] = C0;
@@ -676,13 +683,14 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
 
 template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
-blend_fwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
-                 float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth,
+                 float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth, bool record_ends,
                  unsigned long long* __restrict__ pairs) {
     const int tile = blockIdx.x;
-    blend_fwd_tile<kCount>(vp, tp, tile, ranges + (size_t)tile * vp.K, ival, rec, pC, pT, image, Tfin,
-                           tile_depth ? tile_depth + (size_t)tile * vp.K : nullptr, pairs);
+    uint2* tr = ranges + (size_t)tile * vp.K;
+    blend_fwd_tile<kCount>(vp, tp, tile, tr, ival, rec, pC, pT, image, Tfin,
+                           tile_depth ? tile_depth + (size_t)tile * vp.K : nullptr, record_ends ? tr : nullptr, pairs);
 }
 
 // Persistent forward blend over the global tiles of a batch: each block takes the next
@@ -720,7 +728,7 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
             __syncthreads();
         }
         blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), ranges + (size_t)t * svp.K, ival, rec,
-                              nullptr, nullptr, slots[slot].image, nullptr, nullptr, nullptr);
+                              nullptr, nullptr, slots[slot].image, nullptr, nullptr, nullptr, nullptr);
         __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
@@ -783,7 +791,8 @@ template <bool kCount>
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
-                 const float* __restrict__ gI, float4* __restrict__ g2d, unsigned long long* __restrict__ pairs) {
+                 const float* __restrict__ gI, float4* __restrict__ g2d, uint32_t n_inst, uint32_t n_splats,
+                 unsigned long long* __restrict__ pairs) {
     extern __shared__ float s_behind[];
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ StagedRec srec[kBlendThreads];
@@ -845,7 +854,9 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
         Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
-        const uint2 rg = ranges[(size_t)tile * vp.K + r];
+        uint2 rg = ranges[(size_t)tile * vp.K + r];
+        rg.y = min(rg.y, n_inst);   // lists handed over from a forward: never read past them
+        rg.x = min(rg.x, rg.y);
         const bool active = inside && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
         if (__syncthreads_count(active) == 0) continue;
         // replay of the forward: the same pairs, the same freeze points (an inactive pixel
@@ -858,8 +869,14 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             if ((int)threadIdx.x < nb) {
                 StagedRec sr;
                 uint32_t msk;
-                const uint32_t id = ival[b0 + threadIdx.x];
-                stage_for_subset(rec, id, x0, y0, vp, lp, sr, msk, splane[threadIdx.x]);
+                uint32_t id = ival[b0 + threadIdx.x];
+                if (id < n_splats) {
+                    stage_for_subset(rec, id, x0, y0, vp, lp, sr, msk, splane[threadIdx.x]);
+                } else {   // not a splat: touches no pixel
+                    id = 0;
+                    msk = 0u;
+                    sr.a = sr.b = sr.c = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 srec[threadIdx.x] = sr;
                 smask[threadIdx.x] = msk;
                 sid[threadIdx.x] = id;
@@ -1028,15 +1045,15 @@ int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_rang
 
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool record_ends) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
     unsigned long long* pairs = prof_pair_counters();
     if (pairs)
         blend_fwd_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
-                                                              T_final, tile_depth, pairs);
+                                                              T_final, tile_depth, record_ends, pairs);
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                               image, T_final, tile_depth, nullptr);
+                                                               image, T_final, tile_depth, record_ends, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -1074,7 +1091,8 @@ int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tre
 }
 
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     const float* partial_C, const float* partial_T, const float* dL_dimage, cudaStream_t s) {
+                     const float* partial_C, const float* partial_T, const float* dL_dimage, int64_t n_inst,
+                     int64_t n_splats, cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
     size_t smem = sizeof(float) * (size_t)vp.K * kBlendThreads;
     static bool attr_set = false;
@@ -1086,10 +1104,12 @@ int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
     unsigned long long* pairs = prof_pair_counters();
     if (pairs)
         blend_bwd_kernel<true><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                                 dL_dimage, b.g2d, pairs);
+                                                                 dL_dimage, b.g2d, (uint32_t)n_inst,
+                                                                 (uint32_t)n_splats, pairs);
     else
         blend_bwd_kernel<false><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                                  dL_dimage, b.g2d, nullptr);
+                                                                  dL_dimage, b.g2d, (uint32_t)n_inst,
+                                                                  (uint32_t)n_splats, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -169,6 +169,7 @@ struct RasterBuffers {
     uint2* ranges;        // [tiles * K]
     const float* cull;    // [tiles * K] forward depth table (backward only; nullptr: no culling)
     float2* cull_chunk;   // [tiles_y * ceil(tiles_x / 16) * K] (min, max) of `cull` over 16-tile chunks
+    unsigned long long* header;   // [32] workspace header: [0] the nonce of the forward whose lists it holds
     // per instance
     uint32_t* ikey;
     uint32_t* ival;
@@ -201,11 +202,16 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
                 int64_t n_vis, cudaStream_t s);
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
 int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s);
+// record_ends: where a subset saturates a tile, b.ranges' end is moved back to the end of
+// the last batch the blend staged (the prefix a backward has to replay).
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                     cudaStream_t s);
+                     cudaStream_t s, bool record_ends = false);
+// n_inst: instances in ival (ranges are clamped to it); n_splats: records in b.rec (other
+// payloads are skipped).
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     const float* partial_C, const float* partial_T, const float* dL_dimage, cudaStream_t s);
+                     const float* partial_C, const float* partial_T, const float* dL_dimage, int64_t n_inst,
+                     int64_t n_splats, cudaStream_t s);
 int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
                  float* image, float* T_out, cudaStream_t s);
 int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
@@ -213,9 +219,12 @@ int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int
 
 // Forward render into a caller-given workspace.  host_counters (2 x uint64, nullable)
 // receives the instance and visible-splat counts; NULL uses a pinned buffer of the library.
+// keep_lists: with partial maps, register the workspace's lists for the backward of this
+// render (a host-side table entry; false for callers that must not allocate).
 int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                     float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters);
+                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters,
+                    bool keep_lists = true);
 
 // ------------------------------------------------------------------ KD (kd.cu)
 struct KdBuild {

@@ -25,9 +25,6 @@
 #include "rgs_internal.cuh"
 
 namespace rgs {
-int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                    float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                    void* workspace, size_t ws_bytes, cudaStream_t s, unsigned long long* host_counters);
 
 namespace {
 

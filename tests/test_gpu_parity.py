@@ -366,11 +366,13 @@ def test_backward_depth_culling_changes_nothing(R):
     assert torch.isfinite(td).sum() > 0          # some (tile, subset) saturated
     dL = torch.randn(3, 112, 160, device="cuda") * 1e-3
 
+    ws_b = R.Workspace()   # not the forward's workspace: the backward re-derives its lists
+
     def grads(tile_depth):
         gr = tuple(torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh))
         R.profile_enable(timing=False, counters=True)
         R.profile_read(reset=True)
-        R.render_bwd(kd, g, cam, opts, out["partial_C"], out["partial_T"], dL, gr, ws, tile_depth=tile_depth)
+        R.render_bwd(kd, g, cam, opts, out["partial_C"], out["partial_T"], dL, gr, ws_b, tile_depth=tile_depth)
         torch.cuda.synchronize()
         c = R.profile_read(reset=True)["counters"]
         R.profile_enable(False, False)
@@ -405,3 +407,61 @@ def test_image_only_render_stops_at_negligible_front_transmittance(R):
     ok = (flat["flags"] & FWD_FLAGS) == 0
     assert ok.mean() >= 1 - MAX_FLAGGED
     assert np.abs(image_at(b, pix) - flat["C"])[ok].max() <= PIXEL_TOL
+
+
+def test_backward_replays_the_forward_lists(R):
+    """Given the forward's workspace and arguments, the backward replays the forward's lists
+    (cut back to what the forward staged) instead of re-deriving them: no instances are
+    binned, the gradients equal those of a backward that re-derives its lists (up to the
+    order of atomic additions).  A later forward into the workspace, or anything that
+    overwrote its header, sends the backward back to re-deriving."""
+    scene = W.uniform_cube_scene(30_000, seed=53, log_scale_mean=-2.6, sh_degree=3)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, 3)
+    cam = W.look_at((0.2, -2.6, 0.3), (0, 0, 0), 150, 104)
+    cam2 = W.look_at((2.4, 0.5, 0.8), (0, 0, 0), 150, 104)
+    opts = R.default_opts()
+    g = R.scene_c(dev)
+    dL = torch.randn(3, 104, 150, device="cuda") * 1e-3
+
+    def bwd(out, ws):
+        gr = tuple(torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh))
+        R.profile_enable(timing=False, counters=True)
+        R.profile_read(reset=True)
+        R.render_bwd(kd, g, cam, opts, out["partial_C"], out["partial_T"], dL, gr, ws, tile_depth=out["tile_depth"])
+        torch.cuda.synchronize()
+        c = R.profile_read(reset=True)["counters"]
+        R.profile_enable(False, False)
+        return [t.double().cpu().numpy() for t in gr], c
+
+    ws = R.Workspace()
+    out = R.render_fwd(kd, g, cam, opts, ws)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out["tile_depth"]).sum() > 0        # some runs are cut back
+    fast, c_fast = bwd(out, ws)
+    full, c_full = bwd(out, R.Workspace())
+    assert c_fast["instances"] == 0 and c_full["instances"] > 0
+    assert c_fast["bwd_contrib"] == c_full["bwd_contrib"]
+    for a, b in zip(fast, full):
+        assert rel_l2(a, b) <= 1e-5
+    again, c_again = bwd(out, ws)                             # the lists are still there
+    assert c_again["instances"] == 0
+    for a, b in zip(again, fast):
+        assert rel_l2(a, b) <= 1e-5
+
+    # another forward into the same workspace: the first render's backward re-derives
+    R.render_fwd(kd, g, cam2, opts, ws)
+    torch.cuda.synchronize()
+    other, c_other = bwd(out, ws)
+    assert c_other["instances"] > 0
+    for a, b in zip(other, full):
+        assert rel_l2(a, b) <= 1e-5
+
+    # a forward, then its workspace header overwritten: re-derive
+    out = R.render_fwd(kd, g, cam, opts, ws)
+    torch.cuda.synchronize()
+    ws.buf[:256].zero_()
+    hdr, c_hdr = bwd(out, ws)
+    assert c_hdr["instances"] > 0
+    for a, b in zip(hdr, full):
+        assert rel_l2(a, b) <= 1e-5
