@@ -199,13 +199,17 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
 
 /* Backward of rgs_render_fwd with the merge (the "backward process" of Sec. 3.4): routes
  * dL/dimage [3,H,W] through Eq. 5 to each subset's (C_k, T_k), replays each subset's blend
- * from the stored partials (re-deriving the per-tile lists rather than storing them),
- * and pulls the per-splat 2D gradients back through the projection.  Gradients are
- * accumulated into `grads` (same shapes as the parameters; the caller zeroes them).  A
- * splat shared by several subsets accumulates into its single parameter slot.
- * partial_C/partial_T (and tile_depth when non-NULL) must be the ones rgs_render_fwd wrote
- * for the same inputs; with tile_depth the re-derived lists omit the splats lying behind
- * a (tile, subset) the forward had already saturated, which changes no result.
+ * from the stored partials, and pulls the per-splat 2D gradients back through the
+ * projection.  Gradients are accumulated into `grads` (same shapes as the parameters; the
+ * caller zeroes them).  A splat shared by several subsets accumulates into its single
+ * parameter slot.  partial_C/partial_T (and tile_depth when non-NULL) must be the ones
+ * rgs_render_fwd wrote for the same inputs.
+ * The per-tile lists: when `workspace` (same pointer and size) still holds the lists of
+ * the rgs_render_fwd call that wrote partial_C/partial_T with these kd, g, cam and opts
+ * (no render into that workspace since; the forward stamps it), they are replayed as the
+ * forward left them, cut back to what it staged, and nothing is re-derived.  Otherwise
+ * they are re-derived; with tile_depth they then omit the splats lying behind a (tile,
+ * subset) the forward had already saturated.  Neither changes a result.
  * Synchronises once with `stream`.  Errors as rgs_render_fwd. */
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                    const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
