@@ -224,6 +224,15 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
                   const float* seg_lr_host, int nseg, float beta1, float beta2, float eps, int step, int zero_grad,
                   void* stream);
 
+/* rgs_adam_step with one segment split periodically: inside segment `pseg`, an element
+ * whose offset from the segment start is below `head` modulo `period` takes `head_lr`
+ * instead of seg_lr_host[pseg].  For the SH block [N, (d+1)^2, 3] of splats (period
+ * 3 (d+1)^2, head 3) that gives the degree-0 coefficients of every splat their own rate.
+ * 0 <= pseg < nseg, period >= 1, 0 <= head <= period; otherwise as rgs_adam_step. */
+int rgs_adam_step_periodic(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,
+                           const float* seg_lr_host, int nseg, int pseg, int64_t period, int64_t head, float head_lr,
+                           float beta1, float beta2, float eps, int step, int zero_grad, void* stream);
+
 /* Exponential decay of the position learning rate, 1.6e-4 -> 1.6e-6 in the paper
  * (log-linear between lr_init at step 0 and lr_final at max_steps, then constant). */
 float rgs_position_lr(int64_t step, int64_t max_steps, float lr_init, float lr_final);

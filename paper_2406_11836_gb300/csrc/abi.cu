@@ -756,8 +756,19 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
 int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,
                   const float* seg_lr_host, int nseg, float beta1, float beta2, float eps, int step, int zero_grad,
                   void* stream) {
+    return rgs_adam_step_periodic(param, grad, m, v, n, seg_offsets_host, seg_lr_host, nseg, -1, 1, 0, 0.f, beta1,
+                                  beta2, eps, step, zero_grad, stream);
+}
+
+int rgs_adam_step_periodic(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,
+                           const float* seg_lr_host, int nseg, int pseg, int64_t period, int64_t head, float head_lr,
+                           float beta1, float beta2, float eps, int step, int zero_grad, void* stream) {
     if (!param || !grad || !m || !v || n < 1 || !seg_offsets_host || !seg_lr_host || nseg < 1 || nseg > 16 || step < 1) {
         set_error("adam_step: invalid argument");
+        return RGS_EINVAL;
+    }
+    if (pseg >= nseg || (pseg >= 0 && (period < 1 || head < 0 || head > period))) {
+        set_error("adam_step: periodic rule needs 0 <= pseg < nseg, period >= 1, 0 <= head <= period");
         return RGS_EINVAL;
     }
     if (!aligned(param, 16) || !aligned(grad, 16) || !aligned(m, 16) || !aligned(v, 16)) {
@@ -772,7 +783,7 @@ int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, cons
     float bc2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
     ProfScope ps(ST_ADAM, (cudaStream_t)stream);
     return launch_adam(param, grad, m, v, n, seg_offsets_host, seg_lr_host, nseg, beta1, beta2, eps, bc1, bc2,
-                       zero_grad, (cudaStream_t)stream);
+                       zero_grad, (cudaStream_t)stream, pseg < 0 ? -1 : pseg, pseg < 0 ? 1 : period, head, head_lr);
 }
 
 int rgs_profile_enable(int flags) {

@@ -11,12 +11,26 @@ struct AdamSegs {
     int64_t off[17];
     float lr[16];
     int nseg;
+    // optional periodic rule inside segment pseg (-1: none): an element whose offset from
+    // the segment start is below `head` modulo `period` takes head_lr (the degree-0 SH
+    // coefficients of every splat in a [N, (d+1)^2, 3] block)
+    int pseg;
+    int64_t period, head;
+    float head_lr;
 };
 
-__device__ __forceinline__ float seg_lr(const AdamSegs& s, int64_t i) {
+__device__ __forceinline__ int seg_of(const AdamSegs& s, int64_t i) {
     int q = 0;
     while (q + 1 < s.nseg && i >= s.off[q + 1]) ++q;
-    return s.lr[q];
+    return q;
+}
+
+__device__ __forceinline__ float seg_lr(const AdamSegs& s, int64_t i) { return s.lr[seg_of(s, i)]; }
+
+// Rate of element i whose position in the period is pos (valid when segment pseg holds i).
+__device__ __forceinline__ float elem_lr(const AdamSegs& s, int64_t i, int64_t pos) {
+    const int q = seg_of(s, i);
+    return (q == s.pseg && pos < s.head) ? s.head_lr : s.lr[q];
 }
 
 __device__ __forceinline__ void adam1(float& p, float g, float& m, float& v, float lr, float b1, float b2, float eps,
@@ -35,11 +49,32 @@ adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
     float4* g4 = reinterpret_cast<float4*>(g);
     float4* m4 = reinterpret_cast<float4*>(m);
     float4* v4 = reinterpret_cast<float4*>(v);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    // position of element 4 i in the period of the periodic segment, carried along the
+    // grid-stride loop (one 64-bit remainder per thread, then additions)
+    const int64_t i_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool periodic = segs.pseg >= 0;
+    const int64_t per = periodic ? segs.period : 1;
+    const int64_t step_mod = (4 * stride) % per;
+    int64_t r = (((4 * i_first - (periodic ? segs.off[segs.pseg] : 0)) % per) + per) % per;
+    for (int64_t i = i_first; i < n4; i += stride) {
         float4 P = p4[i], G = g4[i], M = m4[i], V = v4[i];
         const int64_t e = 4 * i;
-        float l0 = seg_lr(segs, e), l3 = seg_lr(segs, e + 3);
-        float l1 = l0 == l3 ? l0 : seg_lr(segs, e + 1), l2 = l0 == l3 ? l0 : seg_lr(segs, e + 2);
+        float l0, l1, l2, l3;
+        if (periodic) {
+            const int64_t r1 = r + 1 >= per ? r + 1 - per : r + 1, r2 = r1 + 1 >= per ? r1 + 1 - per : r1 + 1,
+                          r3 = r2 + 1 >= per ? r2 + 1 - per : r2 + 1;
+            l0 = elem_lr(segs, e, r);
+            l1 = elem_lr(segs, e + 1, r1);
+            l2 = elem_lr(segs, e + 2, r2);
+            l3 = elem_lr(segs, e + 3, r3);
+            r += step_mod;
+            if (r >= per) r -= per;
+        } else {
+            l0 = seg_lr(segs, e);
+            l3 = seg_lr(segs, e + 3);
+            l1 = l0 == l3 ? l0 : seg_lr(segs, e + 1);
+            l2 = l0 == l3 ? l0 : seg_lr(segs, e + 2);
+        }
         adam1(P.x, G.x, M.x, V.x, l0, b1, b2, eps, bc1, bc2);
         adam1(P.y, G.y, M.y, V.y, l1, b1, b2, eps, bc1, bc2);
         adam1(P.z, G.z, M.z, V.z, l2, b1, b2, eps, bc1, bc2);
@@ -53,7 +88,9 @@ adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
         float P = p[t], M = m[t], V = v[t];
-        adam1(P, g[t], M, V, seg_lr(segs, t), b1, b2, eps, bc1, bc2);
+        const float lt = periodic ? elem_lr(segs, t, (((t - segs.off[segs.pseg]) % per) + per) % per)
+                                  : seg_lr(segs, t);
+        adam1(P, g[t], M, V, lt, b1, b2, eps, bc1, bc2);
         p[t] = P;
         m[t] = M;
         v[t] = V;
@@ -64,9 +101,14 @@ adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
 }  // namespace
 
 int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t* seg_off, const float* seg_lr_h,
-                int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s) {
+                int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s,
+                int pseg, int64_t period, int64_t head, float head_lr) {
     AdamSegs segs;
     segs.nseg = nseg;
+    segs.pseg = pseg;
+    segs.period = period;
+    segs.head = head;
+    segs.head_lr = head_lr;
     for (int q = 0; q <= nseg; ++q) segs.off[q] = seg_off[q];
     for (int q = 0; q < nseg; ++q) segs.lr[q] = seg_lr_h[q];
     int dev = 0, sms = 152;

@@ -250,8 +250,11 @@ void fill_view(const struct ::rgs_kd* kd, const rgs_gaussians* g, const rgs_came
                ViewParams* vp, TreeParams* tp);
 
 // ------------------------------------------------------------------ Adam (adam.cu)
+// pseg >= 0: inside segment pseg, elements whose offset from the segment start is below
+// `head` modulo `period` take head_lr.
 int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t* seg_off, const float* seg_lr,
-                int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s);
+                int nseg, float b1, float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s,
+                int pseg = -1, int64_t period = 1, int64_t head = 0, float head_lr = 0.f);
 
 }  // namespace rgs
 

@@ -89,13 +89,9 @@ class Trainer:
             self.p[name] = self.flat[a:b].view(shapes[name])
             self.g[name] = self.grad[a:b].view(shapes[name])
             self.p[name].copy_(src[name].reshape(shapes[name]).to(device))
-        # Adam segments: quats, means, log_scales, opacity, sh dc, sh rest
-        sh0 = int(offs[4])
-        self.seg = [0, int(offs[1]), int(offs[2]), int(offs[3]), int(offs[4])]
-        if self.nsh > 1:
-            self.seg += [sh0 + 3 * n, total]
-        else:
-            self.seg += [total]
+        # Adam segments: quats, means, log_scales, opacity, sh; inside the sh block [N, nsh, 3]
+        # the degree-0 coefficients of every splat (3 of each 3 nsh) take the dc rate
+        self.seg = [0, int(offs[1]), int(offs[2]), int(offs[3]), int(offs[4]), total]
         self.max_steps = max_steps
         self.step_count = 0
         self.opts = opts if opts is not None else rgs.default_opts()
@@ -111,11 +107,13 @@ class Trainer:
         return (g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"])
 
     def lrs(self, step):
-        lrs = [self.LR["quats"], rgs.position_lr(step, self.max_steps), self.LR["log_scales"],
-               self.LR["opacity_logits"], self.LR["sh_dc"]]
-        if self.nsh > 1:
-            lrs.append(self.LR["sh_rest"])
-        return lrs
+        sh = self.LR["sh_rest"] if self.nsh > 1 else self.LR["sh_dc"]
+        return [self.LR["quats"], rgs.position_lr(step, self.max_steps), self.LR["log_scales"],
+                self.LR["opacity_logits"], sh]
+
+    def sh_periodic(self):
+        """The Adam rule giving the degree-0 SH coefficients of every splat the dc rate."""
+        return (4, 3 * self.nsh, 3, self.LR["sh_dc"]) if self.nsh > 1 else None
 
     def repartition(self, depth_L: int | None = None):
         """Re-run the KD partition on the current centres (Sec. 3.4: repeated after a set
@@ -164,5 +162,5 @@ class Trainer:
                        tile_depth=out["tile_depth"])
         self.step_count += 1
         rgs.adam_step(self.flat, self.grad, self.m, self.v, self.seg, self.lrs(self.step_count), self.step_count,
-                      zero_grad=True)
+                      zero_grad=True, periodic=self.sh_periodic())
         return loss

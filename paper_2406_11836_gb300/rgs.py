@@ -91,6 +91,9 @@ def lib():
                                          c_void_p, c_void_p, c_void_p, c_void_p]
     L.rgs_adam_step.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int, c_float,
                                 c_float, c_float, c_int, c_int, c_void_p]
+    L.rgs_adam_step_periodic.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int,
+                                         c_int, c_int64, c_int64, c_float, c_float, c_float, c_float, c_int, c_int,
+                                         c_void_p]
     L.rgs_default_opts.argtypes = [POINTER(RenderOpts)]
     L.rgs_profile_enable.argtypes = [c_int]
     L.rgs_profile_stage_name.restype = ctypes.c_char_p
@@ -320,12 +323,17 @@ def merge_partials_bwd(partial_C, partial_T, order, dL_dimage, dL_dT=None, bg=(0
 
 
 def adam_step(param, grad, m, v, seg_offsets, seg_lr, step, beta1=0.9, beta2=0.999, eps=1e-15, zero_grad=True,
-              stream=None):
+              stream=None, periodic=None):
+    """One Adam step over flat buffers split into segments with their own rates.
+    periodic = (segment, period, head, head_lr): inside that segment, elements whose offset
+    from its start is below `head` modulo `period` take head_lr."""
     offs = np.asarray(seg_offsets, np.int64)
     lrs = np.asarray(seg_lr, np.float32)
-    _check(lib().rgs_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()),
-                               c_void_p(offs.ctypes.data), c_void_p(lrs.ctypes.data), len(lrs), float(beta1),
-                               float(beta2), float(eps), int(step), 1 if zero_grad else 0, _stream(stream)))
+    pseg, period, head, head_lr = periodic if periodic is not None else (-1, 1, 0, 0.0)
+    _check(lib().rgs_adam_step_periodic(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), int(param.numel()),
+                                        c_void_p(offs.ctypes.data), c_void_p(lrs.ctypes.data), len(lrs), int(pseg),
+                                        int(period), int(head), float(head_lr), float(beta1), float(beta2),
+                                        float(eps), int(step), 1 if zero_grad else 0, _stream(stream)))
 
 
 def position_lr(step, max_steps, lr_init=1.6e-4, lr_final=1.6e-6) -> float:
@@ -451,7 +459,7 @@ class Server:
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_merge_partials", "rgs_merge_partials_bwd",
-               "rgs_render_bwd", "rgs_adam_step", "rgs_position_lr", "rgs_profile_enable",
+               "rgs_render_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
                "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",

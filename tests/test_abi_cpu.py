@@ -64,6 +64,14 @@ def test_invalid_arguments_are_rejected(R):
     # NULL kd handle
     assert lib.rgs_render_workspace_size(None, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), 0,
                                          ctypes.byref(nbytes)) == R.RGS_EINVAL
+    # periodic Adam rule: its segment must exist, the period be positive
+    offs = (ctypes.c_int64 * 3)(0, 8, 16)
+    rates = (ctypes.c_float * 2)(1e-3, 1e-4)
+    for pseg, period, head in ((2, 4, 1), (1, 0, 0), (1, 4, 5)):
+        assert lib.rgs_adam_step_periodic(ctypes.c_void_p(fake), ctypes.c_void_p(fake), ctypes.c_void_p(fake),
+                                          ctypes.c_void_p(fake), 16, offs, rates, 2, pseg, period, head,
+                                          ctypes.c_float(1e-2), ctypes.c_float(0.9), ctypes.c_float(0.999),
+                                          ctypes.c_float(1e-15), 1, 1, None) == R.RGS_EINVAL
     # view order needs a handle; merge needs buffers
     assert lib.rgs_merge_partials(None, None, None, 0, 1, 1, None, None, None, None) == R.RGS_EINVAL
     assert lib.rgs_adam_step(None, None, None, None, 0, None, None, 0, ctypes.c_float(0.9), ctypes.c_float(0.999),

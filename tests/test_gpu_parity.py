@@ -297,6 +297,32 @@ def test_adam_step_matches_oracle(R):
     assert abs(R.position_lr(30000, 60000) - 1.6e-5) < 1e-10
 
 
+def test_adam_periodic_rates_match_oracle(R):
+    """The periodic rule: inside one segment an SH-like block [N, 16, 3], the 3 degree-0
+    coefficients of each splat take their own rate (per-element rates for the oracle come
+    from that definition); a grid-stride loop long enough to wrap the period many times."""
+    r = np.random.default_rng(1)
+    nspl, nsh = 3001, 16
+    head_n = 1001                       # a segment in front, so the block starts off a period boundary
+    n = head_n + nspl * 3 * nsh
+    p = r.normal(size=n).astype(np.float32)
+    segs, lrs = [0, head_n, n], [1e-3, 2.5e-3 / 20]
+    dc_lr = 2.5e-3
+    off = np.arange(n) - head_n
+    lr_el = np.where(off < 0, lrs[0], np.where(off % (3 * nsh) < 3, dc_lr, lrs[1]))
+    pd = torch.tensor(p, device="cuda")
+    md = torch.zeros(n, device="cuda")
+    vd = torch.zeros(n, device="cuda")
+    po, mo, vo = p.astype(np.float64), np.zeros(n), np.zeros(n)
+    for step in (1, 2):
+        g = r.normal(size=n).astype(np.float32)
+        R.adam_step(pd, torch.tensor(g, device="cuda"), md, vd, segs, lrs, step, eps=1e-15,
+                    periodic=(1, 3 * nsh, 3, dc_lr))
+        po, mo, vo = O.adam_step(po, g, mo, vo, step, lr=lr_el)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(pd.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+
+
 # --------------------------------------------------------------------------- partitions from given planes
 def test_kd_from_splits_matches_partition_and_random_trees_render_flat(R):
     scene = W.uniform_cube_scene(4000, seed=31, log_scale_mean=-3.0, sh_degree=1)
