@@ -20,8 +20,11 @@
 // is then replayed front to back from its stored partials: recomputing sigma and T
 // exactly as the forward did, with A_i the colour accumulated up to and including pair i,
 //   dC_k/dsigma_i = T_i c_i - (C_k - A_i)/(1 - sigma_i),   dT_k/dsigma_i = -T_k/(1 - sigma_i).
-// Per-splat 2D gradients are reduced across the warp with shuffles, across the CTA in
-// shared memory, and added to global memory with one vector reduction per float4.
+// A warp takes its record list 8 entries at a time: each lane replays its pixel and leaves
+// two scalars per pair in shared memory, then each lane sums one record over one row of
+// the warp's pixels and four lanes combine the rows.  Per-splat 2D gradients are summed
+// across the CTA in shared memory and added to global memory with one vector reduction
+// per float4.
 #include <cuda_fp16.h>
 
 #include "footprint.cuh"
@@ -36,6 +39,10 @@ constexpr int kBlendThreads = kTilePixels;  // 256
 #define RGS_BLEND_MIN_BLOCKS 3
 #endif
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -0.5 * log2(e)
+// The backward handles a warp's record list in stretches of kBwdSub entries: pixel by pixel,
+// then record by record (rows padded to kBwdSubPad floats: conflict-free in both phases).
+constexpr int kBwdSub = 8;
+constexpr int kBwdSubPad = kBwdSub + 1;
 
 // exp(-d2/2) as 2^(d2 * -0.5 log2 e) on the SFU (ex2.approx, ~2 ulp); the forward and
 // the backward call the same function, so the backward sees the forward's sigma exactly.
@@ -734,53 +741,7 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
 }
 
 // ------------------------------------------------------------------ blend backward
-// Sums the 9 values v[0..8] over the 32 lanes of a warp with 12 shuffles (reduce-scatter
-// by halving: at each step a lane keeps part of its values, sends the rest to its partner
-// and adds what it receives).  Returns the total of value index warp_value_index(lane) on
-// every lane (15: none).  Lanes l and l ^ 1 hold the same total.
-__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
-    // 9 -> 5: upper 16 lanes keep values 4..8, lower keep 0..3 (slot 4 padded with 0)
-    const bool u16 = (lane & 16) != 0;
-    float n[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const float lo = k < 4 ? v[k] : 0.f, hi = v[4 + k];
-        const float r = __shfl_xor_sync(0xffffffffu, u16 ? lo : hi, 16);
-        n[k] = (u16 ? hi : lo) + r;
-    }
-    // 5 -> 3: upper 8 keep n[2..4], lower keep n[0..1] (slot 2 padded)
-    const bool u8 = (lane & 8) != 0;
-    float m[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float lo = k < 2 ? n[k] : 0.f, hi = n[2 + k];
-        const float r = __shfl_xor_sync(0xffffffffu, u8 ? lo : hi, 8);
-        m[k] = (u8 ? hi : lo) + r;
-    }
-    // 3 -> 2: upper 4 keep m[1..2], lower keep m[0] (slot 1 padded)
-    const bool u4 = (lane & 4) != 0;
-    float p[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float lo = k < 1 ? m[k] : 0.f, hi = m[1 + k];
-        const float r = __shfl_xor_sync(0xffffffffu, u4 ? lo : hi, 4);
-        p[k] = (u4 ? hi : lo) + r;
-    }
-    // 2 -> 1, then the last pair
-    const bool u2 = (lane & 2) != 0;
-    float q = (u2 ? p[1] : p[0]) + __shfl_xor_sync(0xffffffffu, u2 ? p[0] : p[1], 2);
-    return q + __shfl_xor_sync(0xffffffffu, q, 1);
-}
-
-// Value index held by a lane after warp_reduce9 (15: a padding slot).  Bits (16, 8, 4, 2)
-// of the lane select, in turn, the kept half of each step.
-__device__ __forceinline__ int warp_value_index(int lane) {
-    // nibble table indexed by (b16 b8 b4 b2): 0,P,1,P,2,P,3,P,4,P,5,P,6,P,7,8
-    constexpr unsigned long long kTable = 0x87F6F5F4F3F2F1F0ull;
-    const int code = (lane >> 1) & 15;
-    return (int)((kTable >> (4 * code)) & 15ull);
-}
-
+// Adds a float4 into global memory with one vector reduction.
 __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
                  "f"(v.w)
@@ -793,15 +754,20 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                  const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
                  const float* __restrict__ gI, float4* __restrict__ g2d, uint32_t n_inst, uint32_t n_splats,
                  unsigned long long* __restrict__ pairs) {
-    extern __shared__ float s_behind[];
+    // <g, S_r> of this pixel for every rank: private to the thread, in local memory (cached),
+    // so that shared memory does not grow with K
+    float behind_r[1 << kMaxRenderDepth];
     uint32_t n_eval = 0, n_contrib = 0;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
-    __shared__ uint32_t sid[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
     __shared__ float sacc[kBlendThreads][9];
     __shared__ uint8_t wlist[kBlendThreads / 32][kBlendThreads];
     __shared__ LeafPath lp;
+    // per warp, the (pixel, entry) scalars of the current stretch of kBwdSub list entries
+    __shared__ float sh_h[kBlendThreads / 32][32 * kBwdSubPad];   // sigma dL/dsigma
+    __shared__ float sh_w[kBlendThreads / 32][32 * kBwdSubPad];   // sigma T
+    __shared__ float s_gc[kBlendThreads][3];                        // dL/dC_k of each pixel
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
@@ -815,8 +781,8 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     const float Xc = (float)px + 0.5f, Yc = (float)py + 0.5f;   // absolute pixel centre (Eq. 6 tests)
     const size_t HW = (size_t)vp.W * vp.H;
     const size_t pix = inside ? (size_t)py * vp.W + px : 0;
-    const int vidx = warp_value_index(lane);
     uint8_t* wl = wlist[warp];
+    const int wx0 = (warp & 1) << 3, wy0 = (warp >> 1) << 2;   // the warp's 8x4 block in the tile
 
     for (int i = threadIdx.x; i < kBlendThreads * 9; i += kBlendThreads) (&sacc[0][0])[i] = 0.f;
 
@@ -830,7 +796,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     {
         float behind = g0 * vp.bg[0] + g1 * vp.bg[1] + g2 * vp.bg[2];
         for (int r = vp.K - 1; r >= 0; --r) {
-            s_behind[r * kBlendThreads + threadIdx.x] = behind;
+            behind_r[r] = behind;
             if (inside) {
                 const int k = vp.order[r];
                 float c0 = pC[((size_t)k * 3 + 0) * HW + pix], c1 = pC[((size_t)k * 3 + 1) * HW + pix],
@@ -850,7 +816,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             Tk = pT[(size_t)k * HW + pix];
         }
         const float gC0 = g0 * Pm, gC1 = g1 * Pm, gC2 = g2 * Pm;
-        const float gT = Pm * s_behind[r * kBlendThreads + threadIdx.x];
+        const float gT = Pm * behind_r[r];
+        s_gc[threadIdx.x][0] = gC0;   // read by the lanes of this warp after the next barrier
+        s_gc[threadIdx.x][1] = gC1;
+        s_gc[threadIdx.x][2] = gC2;
         float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
         Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
@@ -879,7 +848,6 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 }
                 srec[threadIdx.x] = sr;
                 smask[threadIdx.x] = msk;
-                sid[threadIdx.x] = id;
             }
             __syncthreads();
             const int n = warp_list(smask, nb, warp, lane, wl);
@@ -893,46 +861,97 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 }
                 if (__all_sync(0xffffffffu, frozen)) break;
                 const int t1 = min(n, t0 + 32);
-                for (int t = t0; t < t1; ++t) {
-                    const int j = wl[t];
-                    // the forward's arithmetic, then the adjoint of the pair with the same
-                    // predicate (a pair that fails gets sigma = 0 and zero gradients)
-                    const float4 A = srec[j].a;
-                    const float4 B = srec[j].b;
-                    const float4 Cc = srec[j].c;
-                    const float dx = pcx - A.x, dy = pcy - A.y;
-                    const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
-                    const float d2 = fmaf(u1, u1, u2 * u2);
-                    const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
-                    const float G = ex2_approx(d2 * kNegHalfLog2e);
-                    const float raw = B.y * G;
-                    const float sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
-                    if (kCount && !frozen) {
-                        ++n_eval;
-                        n_contrib += ok;
+                for (int s0 = t0; s0 < t1; s0 += kBwdSub) {
+                    const int s1 = min(t1, s0 + kBwdSub);
+                    // phase 1, pixel by pixel: the forward's arithmetic, then the adjoint of
+                    // the pair with the same predicate (a pair that fails gets sigma = 0 and
+                    // zero gradients); two scalars per (pixel, entry) go to shared memory
+                    bool any = false;
+                    for (int t = s0; t < s1; ++t) {
+                        const int j = wl[t];
+                        const float4 A = srec[j].a;
+                        const float4 B = srec[j].b;
+                        const float4 Cc = srec[j].c;
+                        const float dx = pcx - A.x, dy = pcy - A.y;
+                        const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
+                        const float d2 = fmaf(u1, u1, u2 * u2);
+                        const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
+                        const float G = ex2_approx(d2 * kNegHalfLog2e);
+                        const float raw = B.y * G;
+                        const float sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
+                        if (kCount && !frozen) {
+                            ++n_eval;
+                            n_contrib += ok;
+                        }
+                        const float w = sig * T;
+                        const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
+                        acc = fmaf(w, grgb, acc);
+                        const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
+                        const float h = (ok && raw < vp.alpha_max) ? sig * dsig : 0.f;   // sigma dL/dsigma
+                        sh_h[warp][lane * kBwdSubPad + (t - s0)] = h;
+                        sh_w[warp][lane * kBwdSubPad + (t - s0)] = w;
+                        any |= (h != 0.f) | (w != 0.f);
+                        T = fmaf(-sig, T, T);
                     }
-                    const float w = sig * T;
-                    const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
-                    acc = fmaf(w, grgb, acc);
-                    const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
-                    const float ds = (ok && raw < vp.alpha_max) ? dsig : 0.f;
-                    const float gd2 = -0.5f * sig * ds;
-                    // d(d2)/d(mean) = -2 Q delta, Q delta = L^T (u1, u2)
-                    float v[9];
-                    v[0] = -2.f * gd2 * (A.z * u1);
-                    v[1] = -2.f * gd2 * fmaf(A.w, u1, B.x * u2);
-                    v[2] = gd2 * dx * dx;
-                    v[3] = gd2 * 2.f * dx * dy;
-                    v[4] = gd2 * dy * dy;
-                    v[5] = ds * G;
-                    v[6] = gC0 * w;
-                    v[7] = gC1 * w;
-                    v[8] = gC2 * w;
-                    T = fmaf(-sig, T, T);
-                    if (__any_sync(0xffffffffu, ok)) {
-                        const float tot = warp_reduce9(v, lane);
-                        if ((lane & 1) == 0 && vidx < 9) atomicAdd(&sacc[j][vidx], tot);
+                    if (!__any_sync(0xffffffffu, any)) continue;   // a frozen or empty stretch
+                    __syncwarp();
+                    // phase 2, record by record: lane (row g of the warp's block, entry e)
+                    // sums the 8 pixels of row g.  With delta = (dx, dy) from the centre,
+                    // u = L delta, h = sigma dL/dsigma, the pair's 2D gradients are
+                    //   mean: h L^T u,  conic: -h/2 (dx^2, 2 dx dy, dy^2),  alpha: h / alpha,
+                    //   colour: dL/dC_k sigma T,
+                    // and dy is the same on a row, so three running sums over dx do.
+                    const int g = lane >> 3, e = lane & 7;
+                    float o[9];
+                    int jr = 0;
+                    if (s0 + e < s1) {
+                        jr = wl[s0 + e];
+                        const float4 A = srec[jr].a;
+                        const float4 B = srec[jr].b;
+                        const float dy = ((float)(wy0 + g) + 0.5f) - A.y;
+                        const float dx0 = ((float)wx0 + 0.5f) - A.x;
+                        float Sh = 0.f, Shx = 0.f, Shxx = 0.f, Sw0 = 0.f, Sw1 = 0.f, Sw2 = 0.f;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int p = g * 8 + i;
+                            const float h = sh_h[warp][p * kBwdSubPad + e], w = sh_w[warp][p * kBwdSubPad + e];
+                            const float dx = dx0 + (float)i;
+                            const float hdx = h * dx;
+                            Sh += h;
+                            Shx += hdx;
+                            Shxx = fmaf(hdx, dx, Shxx);
+                            const float* gc = s_gc[warp * 32 + p];
+                            Sw0 = fmaf(gc[0], w, Sw0);
+                            Sw1 = fmaf(gc[1], w, Sw1);
+                            Sw2 = fmaf(gc[2], w, Sw2);
+                        }
+                        const float shu1 = fmaf(A.z, Shx, A.w * dy * Sh);   // row sum of h u1
+                        o[0] = A.z * shu1;
+                        o[1] = fmaf(A.w, shu1, B.x * B.x * dy * Sh);
+                        o[2] = -0.5f * Shxx;
+                        o[3] = -dy * Shx;
+                        o[4] = -0.5f * dy * dy * Sh;
+                        o[5] = __fdividef(Sh, B.y);
+                        o[6] = Sw0;
+                        o[7] = Sw1;
+                        o[8] = Sw2;
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) o[c] = 0.f;
                     }
+                    // the four rows of an entry: lanes e, e + 8, e + 16, e + 24
+                    bool nz = false;
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        o[c] += __shfl_xor_sync(0xffffffffu, o[c], 8);
+                        o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
+                        nz |= o[c] != 0.f;
+                    }
+                    if (g == 0 && s0 + e < s1 && nz) {
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) atomicAdd(&sacc[jr][c], o[c]);
+                    }
+                    __syncwarp();
                 }
             }
             __syncthreads();
@@ -940,8 +959,9 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 float* a = sacc[threadIdx.x];
                 bool nz = false;
                 for (int t = 0; t < 9; ++t) nz |= a[t] != 0.f;
-                if (nz) {
-                    float4* dst = g2d + 3 * (size_t)sid[threadIdx.x];
+                const uint32_t id = ival[b0 + threadIdx.x];
+                if (nz && id < n_splats) {
+                    float4* dst = g2d + 3 * (size_t)id;
                     red_add_v4(dst, make_float4(a[0], a[1], a[2], a[3]));
                     red_add_v4(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
                     red_add_v4(dst + 2, make_float4(a[8], 0.f, 0.f, 0.f));
@@ -1094,11 +1114,14 @@ int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
                      const float* partial_C, const float* partial_T, const float* dL_dimage, int64_t n_inst,
                      int64_t n_splats, cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
-    size_t smem = sizeof(float) * (size_t)vp.K * kBlendThreads;
+    const size_t smem = 0;
     static bool attr_set = false;
     if (!attr_set) {
-        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        // about 58 KB per CTA: three CTAs per SM need most of the carveout as shared memory
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
         attr_set = true;
     }
     unsigned long long* pairs = prof_pair_counters();
