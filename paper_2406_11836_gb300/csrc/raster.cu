@@ -41,7 +41,7 @@ constexpr int kBlendThreads = kTilePixels;  // 256
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -0.5 * log2(e)
 // The backward handles a warp's record list in stretches of kBwdSub entries: pixel by pixel,
 // then record by record (rows padded to kBwdSubPad floats: conflict-free in both phases).
-constexpr int kBwdSub = 8;
+constexpr int kBwdSub = 16;
 constexpr int kBwdSubPad = kBwdSub + 1;
 
 // exp(-d2/2) as 2^(d2 * -0.5 log2 e) on the SFU (ex2.approx, ~2 ulp); the forward and
@@ -890,60 +890,60 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                         const float h = (ok && raw < vp.alpha_max) ? sig * dsig : 0.f;   // sigma dL/dsigma
                         sh_h[warp][lane * kBwdSubPad + (t - s0)] = h;
                         sh_w[warp][lane * kBwdSubPad + (t - s0)] = w;
-                        any |= (h != 0.f) | (w != 0.f);
+                        any |= ok;   // a pair that fails has h = w = 0
                         T = fmaf(-sig, T, T);
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;   // a frozen or empty stretch
                     __syncwarp();
-                    // phase 2, record by record: lane (row g of the warp's block, entry e)
-                    // sums the 8 pixels of row g.  With delta = (dx, dy) from the centre,
-                    // u = L delta, h = sigma dL/dsigma, the pair's 2D gradients are
+                    // phase 2, record by record: lane (half g of the warp's block, entry e)
+                    // sums rows 2g and 2g + 1 (8 pixels each).  With delta = (dx, dy) from the
+                    // centre, u = L delta, h = sigma dL/dsigma, the pair's 2D gradients are
                     //   mean: h L^T u,  conic: -h/2 (dx^2, 2 dx dy, dy^2),  alpha: h / alpha,
                     //   colour: dL/dC_k sigma T,
-                    // and dy is the same on a row, so three running sums over dx do.
-                    const int g = lane >> 3, e = lane & 7;
+                    // and dy is the same on a row, so three running sums in dx per row do.
+                    const int g = lane >> 4, e = lane & 15;
                     float o[9];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) o[c] = 0.f;
                     int jr = 0;
                     if (s0 + e < s1) {
                         jr = wl[s0 + e];
                         const float4 A = srec[jr].a;
                         const float4 B = srec[jr].b;
-                        const float dy = ((float)(wy0 + g) + 0.5f) - A.y;
                         const float dx0 = ((float)wx0 + 0.5f) - A.x;
-                        float Sh = 0.f, Shx = 0.f, Shxx = 0.f, Sw0 = 0.f, Sw1 = 0.f, Sw2 = 0.f;
+                        float Sh_all = 0.f;
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int p = g * 8 + i;
-                            const float h = sh_h[warp][p * kBwdSubPad + e], w = sh_w[warp][p * kBwdSubPad + e];
-                            const float dx = dx0 + (float)i;
-                            const float hdx = h * dx;
-                            Sh += h;
-                            Shx += hdx;
-                            Shxx = fmaf(hdx, dx, Shxx);
-                            const float* gc = s_gc[warp * 32 + p];
-                            Sw0 = fmaf(gc[0], w, Sw0);
-                            Sw1 = fmaf(gc[1], w, Sw1);
-                            Sw2 = fmaf(gc[2], w, Sw2);
+                        for (int row = 2 * g; row < 2 * g + 2; ++row) {
+                            const float dy = ((float)(wy0 + row) + 0.5f) - A.y;
+                            float Sh = 0.f, Shx = 0.f, Shxx = 0.f;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int p = row * 8 + i;
+                                const float h = sh_h[warp][p * kBwdSubPad + e], w = sh_w[warp][p * kBwdSubPad + e];
+                                const float dx = dx0 + (float)i;
+                                const float hdx = h * dx;
+                                Sh += h;
+                                Shx += hdx;
+                                Shxx = fmaf(hdx, dx, Shxx);
+                                const float* gc = s_gc[warp * 32 + p];
+                                o[6] = fmaf(gc[0], w, o[6]);
+                                o[7] = fmaf(gc[1], w, o[7]);
+                                o[8] = fmaf(gc[2], w, o[8]);
+                            }
+                            const float shu1 = fmaf(A.z, Shx, A.w * dy * Sh);   // row sum of h u1
+                            o[0] = fmaf(A.z, shu1, o[0]);
+                            o[1] += fmaf(A.w, shu1, B.x * B.x * dy * Sh);
+                            o[2] = fmaf(-0.5f, Shxx, o[2]);
+                            o[3] = fmaf(-dy, Shx, o[3]);
+                            o[4] = fmaf(-0.5f * dy * dy, Sh, o[4]);
+                            Sh_all += Sh;
                         }
-                        const float shu1 = fmaf(A.z, Shx, A.w * dy * Sh);   // row sum of h u1
-                        o[0] = A.z * shu1;
-                        o[1] = fmaf(A.w, shu1, B.x * B.x * dy * Sh);
-                        o[2] = -0.5f * Shxx;
-                        o[3] = -dy * Shx;
-                        o[4] = -0.5f * dy * dy * Sh;
-                        o[5] = __fdividef(Sh, B.y);
-                        o[6] = Sw0;
-                        o[7] = Sw1;
-                        o[8] = Sw2;
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 9; ++c) o[c] = 0.f;
+                        o[5] = __fdividef(Sh_all, B.y);
                     }
-                    // the four rows of an entry: lanes e, e + 8, e + 16, e + 24
+                    // the two halves of an entry: lanes e and e + 16
                     bool nz = false;
 #pragma unroll
                     for (int c = 0; c < 9; ++c) {
-                        o[c] += __shfl_xor_sync(0xffffffffu, o[c], 8);
                         o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
                         nz |= o[c] != 0.f;
                     }
