@@ -271,6 +271,8 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.counters = (unsigned long long*)take(64);
     t.ranges = (uint2*)take(sizeof(uint2) * tiles * K);
     t.cull_chunk = (float2*)take(sizeof(float2) * (size_t)tiles * K / 16 + sizeof(float2) * 2048 * K);
+    t.clip_plane = (float4*)take(sizeof(float4) * kClipTable);
+    t.clip_margin = (float*)take(sizeof(float) * kClipTable);
     t.ikey = (uint32_t*)take(4 * inst_cap);
     t.ival = (uint32_t*)take(4 * inst_cap);
     t.ikey_alt = (uint32_t*)take(4 * inst_cap);
@@ -375,6 +377,9 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
     if (!aligned(workspace, 256)) { set_error("render: workspace must be 256-byte aligned"); return RGS_EINVAL; }
     carve_workspace(workspace, ws_bytes, N, tiles, vp->K, b);
     b->cull = cull;
+    vp->set_clip(b->clip_plane, b->clip_margin);
+    rc = launch_clip_table(*vp, *tp, s);
+    if (rc) return rc;
     if (cull) {
         rc = launch_cull_chunks(*vp, cull, b->cull_chunk, s);
         if (rc) return rc;
@@ -526,6 +531,7 @@ int render_bwd_reuse(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera*
     fill_view(kd, g, cam, opts, &vp, &tp);
     RasterBuffers b;
     carve_workspace(workspace, ws_bytes, g->n, (int64_t)vp.tiles_x * vp.tiles_y, vp.K, &b);
+    vp.set_clip(b.clip_plane, b.clip_margin);   // the forward's table, still in the workspace
     if (st.I > b.inst_cap) return 1;
     unsigned long long* hc = g_pinned.h;
     if (!hc) {

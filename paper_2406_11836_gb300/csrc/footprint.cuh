@@ -152,6 +152,26 @@ __device__ __forceinline__ void make_clip(const ViewParams& vp, const LeafPath& 
     }
 }
 
+// The same half-planes from the view's plane templates: for subset k and level d of its
+// leaf path, tab (tA, tB, tG, tC) and margin m0 with the branch sign folded in, so that
+// the plane at depth z is (z tA) X + (z tB) Y + (z tG + tC) >= 0 with margin m0 + 4e-5 z.
+// No tree walk and no per-axis selection per item: the count and the emission call this
+// on the same inputs, so they agree.
+__device__ __forceinline__ void make_clip_tab(const ViewParams& vp, int k, int L, float z, SubsetClip& c) {
+    c.n = L;
+    const float4* t = vp.clip_plane() + k * L;
+    const float* tm = vp.clip_margin() + k * L;
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= L) break;
+        const float4 q = __ldg(t + d);
+        c.A[d] = z * q.x;
+        c.B[d] = z * q.y;
+        c.C[d] = fmaf(z, q.z, q.w);
+        c.m[d] = fmaf(4e-5f, z, __ldg(tm + d));
+    }
+}
+
 // Narrow [xlo, xhi] (absolute pixel-centre X) to the X where, for some Y in [ylo, yhi],
 // every half-plane holds within its margin.  Returns false if nothing is left.
 __device__ __forceinline__ bool clip_span(const SubsetClip& c, float ylo, float yhi, float& xlo, float& xhi) {
@@ -203,10 +223,8 @@ template <int kMulti = -1>
 __device__ __forceinline__ void item_cols(const Footprint& f, const ViewParams& vp, const TreeParams& tp, int k,
                                           int nsub, float z, int ty, int& c0, int& c1) {
     if (kMulti == 1 || (kMulti < 0 && nsub > 1)) {
-        LeafPath lpk;
-        leaf_path(tp, k, lpk);
         SubsetClip clip;
-        make_clip(vp, lpk, tp.L, z, clip);
+        make_clip_tab(vp, k, tp.L, z, clip);
         footprint_row_tiles_clipped(f, vp, ty, &clip, c0, c1);
     } else {
         footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);

@@ -620,6 +620,64 @@ static bool vec_sh(const rgs_gaussians& g, const float* gsh = nullptr) {
         }                                                               \
     } while (0)
 
+namespace {
+
+// ------------------------------------------------------------------ plane templates (Eq. 6)
+// Entry i = k L + d of a view's table: the half-plane that level d of leaf k's path puts on
+// the image for a splat at depth z, as (z tA) X + (z tB) Y + (z tG + tC) >= 0 with the
+// branch's sign folded in (x_i[a] - s = A X + B Y + C along the node's axis a; see
+// plane_coeffs), and the clip margin's depth-independent part.
+__device__ __forceinline__ void clip_entry(const ViewParams& vp, const TreeParams& tp, int i, float4* plane,
+                                           float* margin) {
+    const int L = tp.L;
+    const int k = i / L, d = i - k * L;
+    int node = 0;
+    for (int dd = 0; dd < d; ++dd) node = 2 * node + 1 + ((k >> (L - 1 - dd)) & 1);
+    const int right = (k >> (L - 1 - d)) & 1;
+    const int a = tp.axis[node];
+    const float s = tp.split[node];
+    const float sg = right ? 1.f : -1.f;
+    const float Ra = vp.R[a], Rb = vp.R[3 + a], Rc = vp.R[6 + a];
+    const float oa = vp.o[a];
+    const float gam = Rc - Ra * vp.cx * vp.ifx - Rb * vp.cy * vp.ify;
+    plane[i] = make_float4(sg * Ra * vp.ifx, sg * Rb * vp.ify, sg * gam, sg * (oa - s));
+    margin[i] = 1e-5f * (fabsf(oa) + fabsf(s)) + 1e-6f;
+}
+
+__global__ void clip_table_kernel(ViewParams vp, TreeParams tp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1 << tp.L) * tp.L) return;
+    clip_entry(vp, tp, i, const_cast<float4*>(vp.clip_plane()), const_cast<float*>(vp.clip_margin()));
+}
+
+// One table per request of a batch: blockIdx.y is the slot.
+__global__ void clip_table_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                                        TreeParams tp) {
+    const int sl = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= hdr->S || i >= (1 << tp.L) * tp.L) return;
+    const ViewParams& vp = slots[sl].vp;
+    clip_entry(vp, tp, i, const_cast<float4*>(vp.clip_plane()), const_cast<float*>(vp.clip_margin()));
+}
+
+}  // namespace
+
+int launch_clip_table(const ViewParams& vp, const TreeParams& tp, cudaStream_t s) {
+    const int n = (1 << tp.L) * tp.L;
+    if (n == 0) return RGS_OK;
+    clip_table_kernel<<<(n + 127) / 128, 128, 0, s>>>(vp, tp);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_clip_table_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, cudaStream_t s) {
+    const int n = (1 << tp.L) * tp.L;
+    if (n == 0) return RGS_OK;
+    clip_table_batch_kernel<<<dim3((n + 127) / 128, kMaxSlots), 128, 0, s>>>(slots, hdr, tp);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s) {
     unsigned grid = (unsigned)((g.n + 255) / 256);

@@ -51,7 +51,24 @@ struct ViewParams {
     int tile_bits;             // bits of the tile index in an instance key
     int8_t order[64];          // order[r]  = subset at view rank r
     int8_t rank_of[64];        // rank_of[k] = view rank of subset k
+    // per-view plane templates of the KD leaves (see clip_table_kernel), [K * L] each:
+    // device addresses, kept as 32-bit halves so that the struct stays 4-byte aligned (the
+    // kernels' parameter layout, and with it their code, does not change)
+    uint32_t clip_addr[4];
+    __host__ __device__ const float4* clip_plane() const {
+        return reinterpret_cast<const float4*>(((uint64_t)clip_addr[1] << 32) | clip_addr[0]);
+    }
+    __host__ __device__ const float* clip_margin() const {
+        return reinterpret_cast<const float*>(((uint64_t)clip_addr[3] << 32) | clip_addr[2]);
+    }
+    __host__ void set_clip(const float4* plane, const float* margin) {
+        clip_addr[0] = (uint32_t)(uintptr_t)plane;
+        clip_addr[1] = (uint32_t)((uint64_t)(uintptr_t)plane >> 32);
+        clip_addr[2] = (uint32_t)(uintptr_t)margin;
+        clip_addr[3] = (uint32_t)((uint64_t)(uintptr_t)margin >> 32);
+    }
 };
+constexpr int kClipTable = 64 * kMaxRenderDepth;   // entries of one view's plane-template table
 
 // ------------------------------------------------------------------ request batches (serve.cu)
 // A batch renders up to kMaxSlots requests (views of the same resident scene) in one pass
@@ -169,6 +186,8 @@ struct RasterBuffers {
     uint2* ranges;        // [tiles * K]
     const float* cull;    // [tiles * K] forward depth table (backward only; nullptr: no culling)
     float2* cull_chunk;   // [tiles_y * ceil(tiles_x / 16) * K] (min, max) of `cull` over 16-tile chunks
+    float4* clip_plane;   // [kClipTable] the view's plane templates (ViewParams::clip_plane())
+    float* clip_margin;   // [kClipTable]
     unsigned long long* header;   // [32] workspace header: [0] the nonce of the forward whose lists it holds
     // per instance
     uint32_t* ikey;
@@ -183,6 +202,10 @@ struct RasterBuffers {
 
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s);
+// Fills vp.clip_plane / vp.clip_margin (device) for one view, or for every slot of a batch
+// (each slot's view carries its own table pointers).
+int launch_clip_table(const ViewParams& vp, const TreeParams& tp, cudaStream_t s);
+int launch_clip_table_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, cudaStream_t s);
 int launch_project_bwd(const rgs_gaussians& g, const rgs_gaussian_grads& gr, const ViewParams& vp,
                        const RasterBuffers& b, cudaStream_t s);
 int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp,

@@ -72,6 +72,8 @@ struct LaneBufs {
     BatchSlot* slots;
     BatchHeader* hdr;
     unsigned long long* counters;
+    float4* clip_plane;    // [kMaxSlots * kClipTable]: each request's plane templates
+    float* clip_margin;    // [kMaxSlots * kClipTable]
     RasterBuffers b;
 };
 
@@ -89,6 +91,8 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     l.slots = (BatchSlot*)take(sizeof(BatchSlot) * kMaxSlots);
     l.hdr = (BatchHeader*)take(sizeof(BatchHeader));
     l.counters = (unsigned long long*)take(8 * kBatchCounters);
+    l.clip_plane = (float4*)take(sizeof(float4) * kMaxSlots * kClipTable);
+    l.clip_margin = (float*)take(sizeof(float) * kMaxSlots * kClipTable);
     RasterBuffers& b = l.b;
     b.rec = (float4*)take(sizeof(float4) * 3 * P);
     b.cnt = (uint32_t*)take(4 * P);
@@ -133,6 +137,7 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
     RGS_CUDA_TRY(cudaMemcpyAsync(l.slots, slots_host, sizeof(BatchSlot) * slots, cudaMemcpyHostToDevice, s));
     RGS_CUDA_TRY(cudaMemsetAsync(c, 0, 8 * kBatchCounters, s));
     RGS_CUDA_TRY(cudaMemsetAsync(b.ranges, 0, sizeof(uint2) * tiles_cap * K, s));
+    if ((rc = launch_clip_table_batch(l.slots, l.hdr, tp, s))) return rc;
     if ((rc = launch_project_batch(g, l.slots, l.hdr, tp, b, c, s))) return rc;
     // compaction in (request, splat) order
     if ((rc = exclusive_scan_dev(b.cnt, b.vis_pos, &l.hdr->n_total, P, 1, nullptr, b.temp, b.temp_bytes, s)))
@@ -289,6 +294,8 @@ int launch_lane(rgs_server* S, Lane& ln, std::vector<Request*>& batch) {
     for (int s = 0; s < h.S; ++s) {
         h.tile_base[s] = base;
         ln.slots_host[s].vp = batch[s]->vp;
+        ln.slots_host[s].vp.set_clip(ln.bufs.clip_plane + (size_t)s * kClipTable,
+                                     ln.bufs.clip_margin + (size_t)s * kClipTable);
         ln.slots_host[s].image = batch[s]->out;
         ln.slots_host[s].tile_base = base;
         base += (uint32_t)batch[s]->tiles;
