@@ -1,7 +1,8 @@
 // Fused Adam step over a flat parameter buffer (Sec. 4 implementation details: the
 // position learning rate decays exponentially; every parameter group has its own rate).
-// One pass reads p, g, m, v and writes p, m, v (and optionally a zeroed g) with 16-byte
-// vector accesses: 28 (32) bytes per parameter, so the kernel is bound by HBM bandwidth.
+// One pass reads p, g, m, v and writes p, m, v (and optionally zeroes the non-zero parts
+// of g) with 16-byte vector accesses: 28 (up to 32) bytes per parameter, so the kernel is
+// bound by HBM bandwidth.
 #include "rgs_internal.cuh"
 
 namespace rgs {
@@ -82,7 +83,9 @@ adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
         p4[i] = P;
         m4[i] = M;
         v4[i] = V;
-        if (zero_grad) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // most splats of a view get no gradient: skip storing zeros over zeros
+        if (zero_grad && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f))
+            g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // scalar tail
     const int64_t t = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
