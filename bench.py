@@ -394,8 +394,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the public step API with host inputs
     pinned = [t.cpu().pin_memory() for t in targets]
     dev_target = torch.empty_like(targets[0])
-    dev_target.copy_(pinned[0], non_blocking=True)          # one untimed pass warms the loss path
-    float(trainer.step(cams[0], dev_target, return_loss=True).item())
+    for j in range(max(len(cams), args.warmup)):           # untimed passes warm the loss path on every view
+        dev_target.copy_(pinned[j % len(cams)], non_blocking=True)
+        float(trainer.step(cams[j % len(cams)], dev_target, return_loss=True).item())
     torch.cuda.synchronize()
     host_ms = []
     t0 = time.perf_counter()
