@@ -332,13 +332,14 @@ int rgs_serve_destroy(rgs_server* srv);
  * others fail (slower; keep it off where time is measured).  Process-wide.
  * rgs_profile_read synchronises with the recorded events and writes, per stage index
  * 0..rgs_profile_num_stages()-1, the accumulated milliseconds (ms_host) and pass counts
- * (launches_host), and counters_host[13] = {fwd pairs evaluated, fwd pairs contributing,
+ * (launches_host), and counters_host[14] = {fwd pairs evaluated, fwd pairs contributing,
  * bwd pairs evaluated, bwd pairs contributing, tile instances, visible splats, kernel
  * launches of the library (counted whether or not profiling is on), fwd pairs failing the
  * Mahalanobis test, failing the ball test, failing the Eq. 6 subset test, fwd pairs
  * evaluated for splats held by several subsets, fwd instances staged before their tile's
- * pixels were all done, fwd instances contributing to at least one pixel}, summed since
- * the last reset.  Any
+ * pixels were all done, fwd instances contributing to at least one pixel, fwd warp passes
+ * over one record-list entry (pairs evaluated / (32 x passes): the share of a warp's lanes
+ * whose pixel is still blending)}, summed since the last reset.  Any
  * output pointer may be NULL.  reset != 0 clears the sums. */
 int rgs_profile_enable(int flags);
 int rgs_profile_num_stages(void);

@@ -495,14 +495,10 @@ __device__ __forceinline__ int warp_list(const uint32_t* smask, int nb, int warp
 __device__ __forceinline__ bool pair_passes(const float4& B, const float4& Cc, float dx, float dy, float d2,
                                             const float4* planes, uint32_t msk, const ViewParams& vp,
                                             const LeafPath& lp, float Xc, float Yc) {
-    bool ok = d2 <= B.z;
-    if (B.w != kInfF) {   // uniform across the warp: one record
-        if (fabsf(B.w) != kInfF) {
-            const float bx = dx * vp.ifx, by = dy * vp.ify;
-            ok = ok && fmaf(bx, bx, by * by) <= fabsf(B.w);
-        }
-        if (B.w < 0.f) ok = ok && in_subset(planes, (int)((msk >> 8) & 7u), vp, lp, Cc.w, Xc, Yc);
-    }
+    // the ball test without a branch: |rho2| is +inf when the ball holds the ellipse
+    const float bx = dx * vp.ifx, by = dy * vp.ify;
+    bool ok = (d2 <= B.z) & (fmaf(bx, bx, by * by) <= fabsf(B.w));
+    if (B.w < 0.f) ok = ok && in_subset(planes, (int)((msk >> 8) & 7u), vp, lp, Cc.w, Xc, Yc);   // warp-uniform
     return ok;
 }
 
@@ -554,6 +550,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     __shared__ float s_img[4][kBlendThreads];   // merged colour so far and the transmittance in front
     __shared__ float s_tkeep[kBlendThreads];    // T of a frozen pixel
     uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0, n_staged = 0, n_used = 0;
+    uint32_t n_iter = 0;   // warp passes over one list entry (lane 0 counts)
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
     thread_pixel(threadIdx.x, lx, ly);
@@ -615,6 +612,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 const int t1 = min(n, t0 + 32);
                 #pragma unroll 2
                 for (int t = t0; t < t1; ++t) {
+                    if (kCount && lane == 0) ++n_iter;
                     const int j = wl[t];
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
@@ -684,6 +682,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         count_add(pairs + 6, n_leaf);
         count_add(pairs + 7, n_strad);
         count_add(pairs + 8, n_staged);
+        count_add(pairs + 10, n_iter);
         count_add(pairs + 9, n_used);
     }
 }
