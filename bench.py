@@ -399,6 +399,8 @@ def run_ours(args, rank, world, local_rank):
         float(trainer.step(cams[j % len(cams)], dev_target, return_loss=True).item())
     torch.cuda.synchronize()
     host_ms = []
+    e2e_clocks = ClockSampler(local_rank)
+    e2e_clocks.start()
     t0 = time.perf_counter()
     for i in range(args.steps):
         ts = time.perf_counter()
@@ -409,6 +411,7 @@ def run_ours(args, rank, world, local_rank):
         host_ms.append((time.perf_counter() - ts) * 1e3)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    e2e_clk = e2e_clocks.stop()
     print("e2e host ms per step:", [round(x, 1) for x in host_ms], file=sys.stderr)
 
     ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], world, dev)
@@ -427,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 (parameters, gradients and Adam state {trainer.n * 59 * 16 / 1e9:.1f} GB, "
                          "instance buffers several GB)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(targets[0].numel() * 4),
-                "d2h_bytes_per_step": 4},
+                "d2h_bytes_per_step": 4, "clocks": e2e_clk},
         "gpu_launches": int(launches_timed),
         "roofline": rl,
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof["stages"].items() if v[1] > 0},
