@@ -2,9 +2,9 @@
 
 ``RetinaGSRender`` wraps the C ABI: its forward renders every subset's partial colour and
 transmittance and merges them (Eq. 3-5); its backward routes dL/dimage through the merge
-to each subset, replays each subset's blend from the stored partials with the per-tile
-lists re-derived, and pulls the 2D gradients back to means, scales, rotations, opacity and
-SH.  ``Trainer`` runs the full step (render, L1 loss, backward, Adam with the position
+to each subset, replays each subset's blend from the stored partials over the forward's
+per-tile lists (kept in the render's workspace), and pulls the 2D gradients back to means,
+scales, rotations, opacity and SH.  ``Trainer`` runs the full step (render, L1 loss, backward, Adam with the position
 learning-rate decay of Sec. 4) on flat parameter buffers without extra copies.
 """
 from __future__ import annotations
