@@ -319,6 +319,20 @@ def whole_job_mpix_s(world, steps, pix_per_step, ms_total):
 
 
 # --------------------------------------------------------------------------- arms
+def partition_report(trainer) -> dict:
+    """Subset balance of the median KD partition the step ran with, against a fixed grid of
+    the same depth (untimed; the analogue of the paper's subset-balance table)."""
+    from paper_2406_11836_gb300 import partition as Pt
+    from paper_2406_11836_gb300 import workloads as W
+    p = trainer.p
+    scene = W.Scene(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"], trainer.sh_degree)
+    keys = ("owned_max_over_mean", "owned_min_over_mean", "members_max_over_mean", "overlap")
+    med = Pt.balance(trainer.kd, p["means"])
+    grid = Pt.balance(Pt.kd_grid(scene, trainer.kd.L), p["means"])
+    return {"subsets": med["subsets"], "median_kd": {k: round(med[k], 4) for k in keys},
+            "fixed_grid": {k: round(grid[k], 4) for k in keys}}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -437,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
         "counters_per_step": {k: v / args.steps for k, v in prof["counters"].items()},
         "clocks": clk,
     }
+    if rank == 0:
+        line["partition"] = partition_report(trainer)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_host = make_workload(args.workload, "cpu")
         line["cpu_baseline"] = oracle_step_estimate(wl_host, budget_s=args.cpu_budget)

@@ -67,7 +67,7 @@ class Trainer:
     LR = {"quats": 1e-3, "log_scales": 5e-3, "opacity_logits": 5e-2, "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20}
 
     def __init__(self, scene, depth_L: int, opts: rgs.RenderOpts | None = None, max_steps: int = 60000,
-                 device="cuda"):
+                 device="cuda", repartition_every: int = 0):
         n = scene.n
         self.n = n
         self.sh_degree = scene.sh_degree
@@ -93,6 +93,9 @@ class Trainer:
         # the degree-0 coefficients of every splat (3 of each 3 nsh) take the dc rate
         self.seg = [0, int(offs[1]), int(offs[2]), int(offs[3]), int(offs[4]), total]
         self.max_steps = max_steps
+        # Sec. 3.4: the partition is re-run on the current centres every so many steps
+        # (0: never); the planes change, the parameters and moments do not
+        self.repartition_every = int(repartition_every)
         self.step_count = 0
         self.opts = opts if opts is not None else rgs.default_opts()
         self.ws = rgs.Workspace(device)
@@ -163,4 +166,6 @@ class Trainer:
         self.step_count += 1
         rgs.adam_step(self.flat, self.grad, self.m, self.v, self.seg, self.lrs(self.step_count), self.step_count,
                       zero_grad=True, periodic=self.sh_periodic())
+        if self.repartition_every and self.step_count % self.repartition_every == 0:
+            self.repartition()
         return loss
