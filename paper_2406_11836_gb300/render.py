@@ -152,17 +152,34 @@ class Trainer:
     def load(self, path: str):
         self.restore(torch.load(path, map_location="cpu"))
 
-    def step(self, cam, target: torch.Tensor, return_loss: bool = True):
-        """One training step: forward, L1 loss against `target` [3,H,W], backward, Adam.
-        Returns the loss as a 0-d tensor (left on the device)."""
-        g = self.gaussians()
+    def _accumulate(self, g, cam, target: torch.Tensor, weight: float, return_loss: bool):
+        """Forward, L1 loss (scaled by weight) and backward of one view, adding its gradients
+        to the gradient buffer; the backward follows its own forward, so it replays the
+        forward's lists."""
         out = rgs.render_fwd(self.kd, g, cam, self.opts, self.ws, image=True)
         img = out["image"]
         diff = img - target
         loss = diff.abs().mean() if return_loss else None
-        dL = torch.sign(diff).div_(float(diff.numel()))
+        dL = torch.sign(diff).div_(float(diff.numel()) / weight)
         rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws,
                        tile_depth=out["tile_depth"])
+        return loss
+
+    def step(self, cam, target: torch.Tensor, return_loss: bool = True):
+        """One training step: forward, L1 loss against `target` [3,H,W], backward, Adam.
+        Returns the loss as a 0-d tensor (left on the device)."""
+        loss = self._accumulate(self.gaussians(), cam, target, 1.0, return_loss)
+        return self._update(loss)
+
+    def step_batch(self, cams, targets, return_loss: bool = True):
+        """One training step on several views: the mean of their L1 losses, its gradient
+        summed over the views' backwards, then one Adam step.  Returns the mean loss."""
+        g = self.gaussians()
+        w = 1.0 / len(cams)
+        losses = [self._accumulate(g, c, t, w, return_loss) for c, t in zip(cams, targets)]
+        return self._update(torch.stack(losses).mean() if return_loss else None)
+
+    def _update(self, loss):
         self.step_count += 1
         rgs.adam_step(self.flat, self.grad, self.m, self.v, self.seg, self.lrs(self.step_count), self.step_count,
                       zero_grad=True, periodic=self.sh_periodic())
