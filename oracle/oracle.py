@@ -75,12 +75,13 @@ class Opts:
     bg: tuple = (0.0, 0.0, 0.0)
     flag_rel: float = 3e-6      # relative rounding margin of the truncation/plane ambiguity flags (~50 fp32 ulp)
     flag_depth_rel: float = 1e-11  # relative margin for two contributors at (nearly) equal depth
+    foot: bool = False          # x_i = foot of the perpendicular from u_i onto the ray (comparison reading)
 
     def vec(self) -> np.ndarray:
         f = lambda v: float(np.float32(v))
         return np.array([f(self.trunc_mult), f(self.eps_T), f(self.alpha_min), f(self.alpha_max),
                          f(self.dilation), f(self.bg[0]), f(self.bg[1]), f(self.bg[2]), self.flag_rel,
-                         self.flag_depth_rel], np.float64)
+                         self.flag_depth_rel, 1.0 if self.foot else 0.0], np.float64)
 
 
 def cam_vec(cam) -> np.ndarray:
@@ -221,7 +222,9 @@ def render(scene, cam, opts: Opts = Opts(), pix=None, hier=False, L=0, axis=None
     hier=False: flat blending, Eq. 2, over every splat that passes the truncation tests,
     in depth order.  hier=True: Eq. 3-4 per subset of the KD tree (axis, split) with the
     indicator of Eq. 6, merged by Eq. 5 in the order each ray crosses the subspaces.
-    Returns C [P,3] (background included), T [P], flags [P], ncontrib [P] and, in
+    With opts.foot, x_i is the foot of the perpendicular from the splat centre onto the
+    pixel ray (Sec. 3.2, printed reading) and the contributors are ordered by its ray
+    parameter.  Returns C [P,3] (background included), T [P], flags [P], ncontrib [P] and, in
     hierarchical mode, partC [P,K,3], partT [P,K], order [P,K]."""
     s = _Scene(scene)
     p = _pix(cam, pix)

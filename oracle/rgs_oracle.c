@@ -23,7 +23,11 @@
  *                 centre, ties by ascending splat index.
  *   x_i           the point of pixel ray l at camera depth z_i, o + z_i * R^T r_p with
  *                 r_p = ((px+0.5-cx)/fx, (py+0.5-cy)/fy, 1); the printed formula of Sec. 3.2
- *                 does not lie on the ray.
+ *                 does not lie on the ray.  With the `foot` option x_i is instead the foot
+ *                 of the perpendicular from u_i onto the ray, o + (d^T (u_i - o)) d for the
+ *                 unit direction d, and the contributors of each ray are ordered by that
+ *                 ray parameter (ties by splat index); the ball test is taken at the foot.
+ *                 A comparison mode: the adjoint supports the depth-plane reading only.
  *   o_l           per ray: the subspaces the ray crosses, ordered by the ray parameter at
  *                 which it enters them (slab test).  This is computed per ray here; the
  *                 CUDA path uses one near-child-first KD traversal per view instead.
@@ -75,6 +79,7 @@ typedef struct {
 
 typedef struct {
     double trunc_mult, eps_T, alpha_min, alpha_max, dilation, bg[3], flag_rel, flag_depth_rel;
+    int foot;               /* 1: x_i is the foot of the perpendicular (comparison reading) */
 } opt_t;
 
 typedef struct {
@@ -99,6 +104,7 @@ static void read_opt(const double* o, opt_t* opt) {
     opt->dilation = o[4]; opt->bg[0] = o[5]; opt->bg[1] = o[6]; opt->bg[2] = o[7];
     opt->flag_rel = o[8];
     opt->flag_depth_rel = o[9];
+    opt->foot = o[10] != 0.0;
 }
 
 /* ------------------------------------------------------------------ real SH, degree <= 3
@@ -274,6 +280,7 @@ static void project_one(const scene_t* sc, int64_t i, const cam_t* cam, const op
 typedef struct {
     int64_t id;
     double z, sigma, G, d2, dx, dy, x[3];   /* x = x_i, the ray point at depth z_i */
+    double zs;                               /* size of the terms that sum to z (depth flag margin) */
     int clamped;                             /* alpha*G >= alpha_max */
     double amb;                              /* max_t q_t / margin_t of the decision */
     int mark;                                /* 1: truncation ambiguous, 2: at a clamp's kink */
@@ -305,12 +312,33 @@ static int eval_pair(const proj_t* P, int64_t id, const cam_t* cam, const opt_t*
     double q2 = ball - P->D * P->D, m2 = e * P->D * P->D;
     double q3 = opt->alpha_min - sigma, m3 = e * opt->alpha_min * (2.0 + d2 * (1.0 + sqrt(P->cond)));
     double r1 = q1 / m1, r2 = q2 / m2, r3 = q3 / m3;
-    double amb = r1 > r2 ? r1 : r2;
-    if (r3 > amb) amb = r3;
     out->id = id; out->z = z; out->sigma = sigma; out->G = G; out->d2 = d2; out->dx = dx; out->dy = dy;
     out->clamped = raw >= opt->alpha_max;
-    out->amb = amb;
+    out->zs = P->zscale;
     for (int j = 0; j < 3; ++j) out->x[j] = cam->o[j] + z * dray[j];
+    if (opt->foot) {
+        /* Comparison reading of Sec. 3.2: x_i = o + (d^T (u_i - o)) d with d the unit
+         * direction of the pixel ray, the foot of the perpendicular from the centre u_i
+         * onto the ray.  The contributors are then ordered by that ray parameter t, the
+         * ball test measures |x_i - u_i| at the foot, and Eq. 6 tests the foot. */
+        double dn = sqrt(dray[0] * dray[0] + dray[1] * dray[1] + dray[2] * dray[2]);
+        double dh[3] = {dray[0] / dn, dray[1] / dn, dray[2] / dn};
+        double u_o[3] = {P->vnorm * P->dir[0], P->vnorm * P->dir[1], P->vnorm * P->dir[2]};   /* u_i - o */
+        double t = dh[0] * u_o[0] + dh[1] * u_o[1] + dh[2] * u_o[2];
+        double perp = 0;
+        for (int j = 0; j < 3; ++j) {
+            double e = t * dh[j] - u_o[j];            /* x_i - u_i */
+            perp += e * e;
+            out->x[j] = cam->o[j] + t * dh[j];
+        }
+        q2 = perp - P->D * P->D;
+        r2 = q2 / m2;
+        out->z = t;
+        out->zs = P->zscale > P->vnorm ? P->zscale : P->vnorm;
+    }
+    double amb = r1 > r2 ? r1 : r2;
+    if (r3 > amb) amb = r3;
+    out->amb = amb;
     return q1 <= 0 && q2 <= 0 && q3 <= 0;
 }
 
@@ -641,8 +669,8 @@ static int gather_pixel(const proj_t* P, const double* bb, int64_t n, const cam_
         if (j + 1 < out->n) {
             const pair_t* b = &out->v[j + 1];
             /* margin relative to z and to the size of the terms that sum to z */
-            double zs = b->z > P[a->id].zscale ? b->z : P[a->id].zscale;
-            if (P[b->id].zscale > zs) zs = P[b->id].zscale;
+            double zs = b->z > a->zs ? b->z : a->zs;
+            if (b->zs > zs) zs = b->zs;
             if (b->z - a->z <= opt->flag_depth_rel * zs) {
                 double dc = 0;
                 for (int ch = 0; ch < 3; ++ch) {
@@ -874,6 +902,7 @@ int or_adjoint(int64_t n, const double* means, const double* log_scales, const d
                double* g2d_out) {
     cam_t cam; opt_t opt;
     read_cam(camv, &cam); read_opt(optv, &opt);
+    if (opt.foot) return -3;   /* the adjoint is of the depth-plane reading only */
     scene_t sc = make_scene(n, means, log_scales, quats, logits, sh, deg);
     proj_t* P = project_all(&sc, &cam, &opt);
     if (!P) return -2;

@@ -416,6 +416,138 @@ def test_ray_order_matches_dense_sampling():
         assert sorted(order.tolist()) == list(range(1 << L))
 
 
+# --------------------------------------------------------------------------- foot reading of x_i
+# The comparison reading of Sec. 3.2: x_i is the foot of the perpendicular from the splat
+# centre onto the pixel ray and each ray's contributors are ordered by its ray parameter.
+FOOT = O.Opts(foot=True)
+
+
+def _ray(cam, px, py):
+    """Camera centre and unit world direction of the ray through pixel centre (px, py)."""
+    V = np.asarray(cam.viewmat, np.float32).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    d = V[:3, :3].T @ np.array([(px + 0.5 - cx) / fx, (py + 0.5 - cy) / fy, 1.0])
+    return -V[:3, :3].T @ V[:3, 3], d / np.linalg.norm(d)
+
+
+def _closest_on_ray(o, d, mu):
+    """(t, distance) of the point of the ray o + t d nearest to mu, by a bounded scalar
+    minimisation of the distance (not the projection formula)."""
+    from scipy.optimize import minimize_scalar
+    f = lambda t: float(np.sum((o + t * d - mu) ** 2))
+    span = float(np.linalg.norm(mu - o)) * 2 + 1.0
+    res = minimize_scalar(f, bounds=(-span, span), method="bounded", options={"xatol": 1e-12})
+    return res.x, math.sqrt(max(res.fun, 0.0))
+
+
+def test_foot_equals_depth_plane_on_a_ray_through_every_centre():
+    """Centres on one pixel's ray: there the foot is the centre itself, as is the ray point
+    at the centre's depth, so both readings give that pixel the same colour."""
+    cam = W.look_at((0.4, -3.0, 0.6), (0, 0, 0), 48, 40)
+    px, py = 30, 13
+    o, d = _ray(cam, px, py)
+    lam = np.array([2.2, 2.9, 3.1, 3.6, 4.4])
+    splats = [(np.float32(o + l * d).astype(np.float32), np.full(3, -2.6, np.float32),
+               np.array([0.9, 0.1, -0.3, 0.2], np.float32), np.float32(0.4 + 0.3 * j),
+               np.array([0.2 * j, 0.9 - 0.15 * j, 0.5], np.float32)) for j, l in enumerate(lam)]
+    sc = _scene_of(splats[::-1])
+    pix = [py * cam.width + px]
+    a = O.render(sc, cam, pix=pix)
+    b = O.render(sc, cam, FOOT, pix=pix)
+    assert a["ncontrib"][0] == len(lam) and b["ncontrib"][0] == len(lam)
+    np.testing.assert_allclose(b["C"], a["C"], atol=1e-12)
+    np.testing.assert_allclose(b["T"], a["T"], atol=1e-12)
+
+
+def test_foot_ball_region_matches_minimised_distance():
+    """Small, opaque, isotropic splats whose screen ellipse (with the dilation) holds the
+    ball: a pixel counts a splat iff the ray passes within D of its centre, the distance
+    found by minimising along the ray.  The depth-plane reading accepts fewer pixels."""
+    cam = W.axis_camera((0.0, 0.0, -3.0), 64, 64)
+    r = np.random.default_rng(3)
+    n = 10
+    xy = r.uniform(-1.3, 1.3, (n, 2))
+    splats = [_iso_splat(float(r.uniform(-0.3, 0.3)), 0.05, 6.0, [0.3, 0.3, 0.3], x=float(a), y=float(b))
+              for a, b in xy]
+    sc = _scene_of(splats)
+    foot = O.render(sc, cam, FOOT)
+    plane = O.render(sc, cam)
+    proj = O.project(sc, cam)
+    D = proj["D"]
+    expect = np.zeros(cam.width * cam.height, np.int64)
+    near_edge = np.zeros(cam.width * cam.height, bool)
+    for q in range(cam.width * cam.height):
+        px, py = q % cam.width, q // cam.width
+        o, d = _ray(cam, px, py)
+        for i in range(n):
+            dx = px + 0.5 - proj["mean_x"][i]
+            dy = py + 0.5 - proj["mean_y"][i]
+            if dx * dx + dy * dy > 400:            # far outside every footprint
+                continue
+            _, dist = _closest_on_ray(o, d, sc.means[i].astype(np.float64))
+            if abs(dist - D[i]) < 1e-6 * D[i]:
+                near_edge[q] = True
+            if dist <= D[i]:
+                expect[q] += 1
+                # precondition: the ellipse d^2 <= 9 holds every pixel of the ball
+                d2 = proj["conic_a"][i] * dx * dx + 2 * proj["conic_b"][i] * dx * dy + proj["conic_c"][i] * dy * dy
+                assert d2 <= 9.0 * (1 - 1e-3)
+    ok = ~near_edge
+    np.testing.assert_array_equal(foot["ncontrib"][ok], expect[ok])
+    assert np.all(foot["ncontrib"] >= plane["ncontrib"])
+    assert (foot["ncontrib"] > plane["ncontrib"]).sum() >= 10
+    assert expect.sum() > 200
+
+
+def test_foot_order_follows_the_ray_parameter():
+    """Two overlapping splats whose order along the ray flips inside the overlap: the foot
+    reading composites them in the order of the minimised ray parameter, the depth-plane
+    reading always puts the nearer centre first."""
+    cam = W.axis_camera((0.0, 0.0, -3.0), 64, 64)
+    A = _iso_splat(0.0, 0.2, 2.0, [0.9, 0.1, 0.1], x=-0.3)
+    B = _iso_splat(0.02, 0.2, 2.0, [0.1, 0.1, 0.9], x=0.3)
+    both = O.render(_scene_of([A, B]), cam, FOOT)
+    sA = 1 - O.render(_scene_of([A]), cam, FOOT)["T"]
+    sB = 1 - O.render(_scene_of([B]), cam, FOOT)["T"]
+    c0 = 0.5 / math.sqrt(math.pi)
+    cA = np.array([c0 * float(np.float32(v)) + 0.5 for v in (0.9, 0.1, 0.1)])
+    cB = np.array([c0 * float(np.float32(v)) + 0.5 for v in (0.1, 0.1, 0.9)])
+    flips = 0
+    for q in np.nonzero((sA > 0.02) & (sB > 0.02))[0]:
+        o, d = _ray(cam, q % cam.width, q // cam.width)
+        tA, _ = _closest_on_ray(o, d, np.array(A[0], np.float64))
+        tB, _ = _closest_on_ray(o, d, np.array(B[0], np.float64))
+        if abs(tA - tB) < 1e-6:
+            continue
+        if tA < tB:
+            expect = sA[q] * cA + sB[q] * (1 - sA[q]) * cB
+        else:
+            expect = sB[q] * cB + sA[q] * (1 - sB[q]) * cA
+            flips += 1
+        np.testing.assert_allclose(both["C"][q], expect, atol=1e-12)
+    assert flips >= 5
+    plane = O.render(_scene_of([A, B]), cam)
+    assert np.abs(plane["C"] - both["C"]).max() > 1e-3
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_foot_hierarchical_equals_flat(L, seed):
+    """The appendix's equivalence holds for the foot reading too: the foot lies on the ray,
+    so every convex subspace holds one interval of the ray parameter."""
+    r = np.random.default_rng(200 + seed)
+    sc = rand_scene(96, 40 + seed, log_scale=(-2.0, 0.4), deg=2 if seed else 0)
+    axis, split = _random_tree(L, r)
+    cam = W.look_at((0.6, -2.6, 0.9), (0, 0, 0), 32, 32)
+    flat = O.render(sc, cam, FOOT)
+    hier = O.render(sc, cam, FOOT, hier=True, L=L, axis=axis, split=split)
+    np.testing.assert_allclose(hier["C"], flat["C"], atol=1e-12)
+    np.testing.assert_allclose(hier["T"], flat["T"], atol=1e-12)
+    assert flat["ncontrib"].sum() > 200
+    assert ((hier["partT"] < 1).any(axis=0)).sum() >= 2
+    assert np.abs(flat["C"] - O.render(sc, cam)["C"]).max() > 1e-4   # the readings differ here
+
+
 # --------------------------------------------------------------------------- adjoint vs FD
 def _loss(sc, cam, w, opts):
     return float(np.sum(O.render(sc, cam, opts)["C"] * w))
