@@ -333,6 +333,64 @@ def partition_report(trainer) -> dict:
             "fixed_grid": {k: round(grid[k], 4) for k in keys}}
 
 
+def foot_reading_report(trainer, cams) -> dict:
+    """Cost of the perpendicular-foot reading of x_i (Sec. 3.2) against the depth-plane
+    reading the step uses: the forward with partial maps over every view, each timed with
+    CUDA events (untimed warm-up pass first), then once more with per-stage timing.  The
+    foot forward sorts every (tile, subset) run by a per-tile bound of the foot's ray
+    parameter and restores each pixel's order in a 64-entry buffer; `overflow` counts the
+    contributors that buffer blended early (0: exact order)."""
+    import torch
+    from paper_2406_11836_gb300 import rgs
+    g = trainer.gaussians()
+    opts = trainer.opts
+    kd = trainer.kd
+    dev = trainer.flat.device
+    H, Wd = cams[0].height, cams[0].width
+    tiles = ((H + 15) // 16) * ((Wd + 15) // 16)
+    out = {"partial_C": torch.empty(kd.K, 3, H, Wd, device=dev), "partial_T": torch.empty(kd.K, H, Wd, device=dev),
+           "image": torch.empty(3, H, Wd, device=dev), "T_final": torch.empty(H, Wd, device=dev),
+           "tile_depth": torch.empty(tiles, kd.K, device=dev)}
+    foot_out = {k: out[k] for k in ("partial_C", "partial_T", "image", "T_final")}
+    ws = trainer.ws
+    stream = torch.cuda.current_stream()
+
+    def plane(c):
+        rgs.render_fwd(kd, g, c, opts, ws, out=out)
+        return 0
+
+    def foot(c):
+        return rgs.render_fwd_foot(kd, g, c, opts, ws, out=foot_out)["overflow"]
+
+    res = {}
+    for name, fn in (("depth_plane", plane), ("foot", foot)):
+        for c in cams:
+            fn(c)
+        torch.cuda.synchronize()
+        ms, over = [], 0
+        for c in cams:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            over += fn(c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rgs.profile_enable(timing=True, counters=False)
+        rgs.profile_read(reset=True)
+        for c in cams:
+            fn(c)
+        torch.cuda.synchronize()
+        prof = rgs.profile_read(reset=True)
+        rgs.profile_enable(False, False)
+        res[name] = {"forward_ms": round(float(np.mean(ms)), 3),
+                     "stages_ms": {k: round(v[0] / len(cams), 3) for k, v in prof["stages"].items() if v[1] > 0}}
+        if name == "foot":
+            res[name]["overflow_per_view"] = over / len(cams)
+    res["views"] = len(cams)
+    res["foot_over_depth_plane"] = round(res["foot"]["forward_ms"] / res["depth_plane"]["forward_ms"], 3)
+    return res
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -453,6 +511,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0:
         line["partition"] = partition_report(trainer)
+    if rank == 0 and world == 1 and not args.no_foot:
+        line["foot_reading"] = foot_reading_report(trainer, cams)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_host = make_workload(args.workload, "cpu")
         line["cpu_baseline"] = oracle_step_estimate(wl_host, budget_s=args.cpu_budget)
@@ -503,6 +563,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-foot", action="store_true", help="skip the foot-reading forward comparison")
     ap.add_argument("--serve-requests", type=int, default=2200, help="requests of the serving stream")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and timed steps only (no counter replay, end-to-end loop, CPU baseline or "

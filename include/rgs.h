@@ -184,6 +184,25 @@ int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, const rgs_c
                            const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
                            float* T_final, float* tile_depth, void* stream);
 
+/* Forward render under the other reading of the intersection point in Sec. 3.2 (a
+ * comparison mode, forward only): x_i is the foot of the perpendicular from the centre u_i
+ * onto the pixel ray, o + (d^T (u_i - o)) d for the unit ray direction d.  The ball test
+ * |x_i - u_i| <= D_i and the indicator of Eq. 6 are taken at the foot, and each ray's
+ * contributors are blended in the order of the foot's ray parameter, which differs from
+ * pixel to pixel (ties in list order).  The foot lies on the ray, so Eq. 5 still merges
+ * the partials exactly.  The instances of each (tile, subset) are sorted by a lower bound
+ * of that parameter over the tile, and each pixel holds up to 64 accepted contributors in
+ * a buffer ordered by the parameter, blending one once the next instance's bound shows
+ * that nothing later can precede it.  The order is exact unless that buffer overflows;
+ * *overflow_host (nullable; reading it synchronises with `stream`) receives the number of
+ * contributors blended early because it was full.  Arguments, outputs, eps_T stopping and
+ * errors as rgs_render_fwd, without tile_depth; the workspace needs 8 more bytes per
+ * instance and 16 per splat (EOVERFLOW reports the size).  rgs_render_bwd does not accept
+ * its partials: they are not the depth-plane reading's. */
+int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                        const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
+                        float* T_final, void* workspace, size_t ws_bytes, uint64_t* overflow_host, void* stream);
+
 /* Eq. 5 over caller-owned partial maps: image = sum_r C_{o_r} prod_{m<r} T_{o_m} +
  * bg * prod_m T_m.  order_dev [K] int32 (device) lists the subsets front to back.
  * partial_C [K,3,H,W], partial_T [K,H,W], image [3,H,W], T_out [H,W] (nullable). */

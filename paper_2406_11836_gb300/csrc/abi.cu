@@ -245,7 +245,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 namespace {
 
 // Carves the workspace; returns the bytes needed (b may be NULL to only measure).
-size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, RasterBuffers* b) {
+size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, RasterBuffers* b, bool foot = false) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -277,6 +277,11 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.ival = (uint32_t*)take(4 * inst_cap);
     t.ikey_alt = (uint32_t*)take(4 * inst_cap);
     t.ival_alt = (uint32_t*)take(4 * inst_cap);
+    if (foot) {   // the foot reading's ball radii and its bound sort
+        t.foot_side = (float4*)take(16 * N);
+        t.fkey = (uint32_t*)take(4 * inst_cap);
+        t.fidx = (uint32_t*)take(4 * inst_cap);
+    }
     t.inst_cap = inst_cap;
     size_t tb = radix_temp_bytes(N > inst_cap ? N : inst_cap);
     size_t sb = scan_temp_bytes(N);
@@ -287,13 +292,14 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
 }
 
 // The buffers of a workspace of ws_bytes, with the largest instance capacity that fits.
-void carve_workspace(void* workspace, size_t ws_bytes, int64_t N, int64_t tiles, int K, RasterBuffers* b) {
+void carve_workspace(void* workspace, size_t ws_bytes, int64_t N, int64_t tiles, int K, RasterBuffers* b,
+                     bool foot = false) {
     int64_t lo = 0, hi = (int64_t)(ws_bytes / 16) + 1;
     while (lo < hi) {
         int64_t mid = (lo + hi + 1) / 2;
-        if (layout(nullptr, N, tiles, K, mid, nullptr) <= ws_bytes) lo = mid; else hi = mid - 1;
+        if (layout(nullptr, N, tiles, K, mid, nullptr, foot) <= ws_bytes) lo = mid; else hi = mid - 1;
     }
-    layout((char*)workspace, N, tiles, K, lo, b);
+    layout((char*)workspace, N, tiles, K, lo, b, foot);
 }
 
 // ------------------------------------------------------------------ lists kept for the backward
@@ -356,7 +362,7 @@ thread_local PinnedCounters g_pinned;
 int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                 void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
                 const uint32_t** sorted_ival, const float* cull, unsigned long long* host_counters = nullptr,
-                int64_t* n_inst = nullptr) {
+                int64_t* n_inst = nullptr, bool foot = false) {
     int rc;
     if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
     if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
@@ -365,17 +371,18 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         return RGS_EINVAL;
     }
     fill_view(kd, g, cam, opts, vp, tp);
+    vp->foot = foot ? 1 : 0;
     const int64_t N = g->n;
     const int64_t tiles = (int64_t)vp->tiles_x * vp->tiles_y;
     if (vp->tile_bits + vp->L > 32) { set_error("render: tile index and subset rank exceed 32 key bits"); return RGS_EINVAL; }
-    size_t fixed = layout(nullptr, N, tiles, vp->K, 0, nullptr);
+    size_t fixed = layout(nullptr, N, tiles, vp->K, 0, nullptr, foot);
     if (!workspace || ws_bytes < fixed) {
-        set_required_workspace(layout(nullptr, N, tiles, vp->K, 1 << 20, nullptr));
+        set_required_workspace(layout(nullptr, N, tiles, vp->K, 1 << 20, nullptr, foot));
         set_error("render: workspace of %zu bytes is smaller than the %zu needed before binning", ws_bytes, fixed);
         return RGS_EOVERFLOW;
     }
     if (!aligned(workspace, 256)) { set_error("render: workspace must be 256-byte aligned"); return RGS_EINVAL; }
-    carve_workspace(workspace, ws_bytes, N, tiles, vp->K, b);
+    carve_workspace(workspace, ws_bytes, N, tiles, vp->K, b, foot);
     b->cull = cull;
     vp->set_clip(b->clip_plane, b->clip_margin);
     rc = launch_clip_table(*vp, *tp, s);
@@ -406,7 +413,7 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         return RGS_EOVERFLOW;
     }
     if (I > b->inst_cap) {
-        set_required_workspace(layout(nullptr, N, tiles, vp->K, I, nullptr));
+        set_required_workspace(layout(nullptr, N, tiles, vp->K, I, nullptr, foot));
         set_error("render: %lld tile instances need a larger workspace", (long long)I);
         return RGS_EOVERFLOW;
     }
@@ -452,14 +459,22 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         rc = launch_emit(*vp, *tp, *b, sorted_ids, n_vis, s);
         if (rc) return rc;
     }
-    {
+    const uint32_t* keys = nullptr;
+    if (foot) {
+        // per (tile, subset) run, ascending bound of the foot's ray parameter over the tile
         ProfScope ps(ST_INST_SORT, s);
-        rc = radix_sort_pairs(b->ikey, b->ival, b->ikey_alt, b->ival_alt, I, vp->tile_bits + vp->L, b->temp,
-                              b->temp_bytes, s, &alt);
+        rc = launch_foot_order(*vp, *b, I, s, &keys, sorted_ival);
         if (rc) return rc;
+    } else {
+        {
+            ProfScope ps(ST_INST_SORT, s);
+            rc = radix_sort_pairs(b->ikey, b->ival, b->ikey_alt, b->ival_alt, I, vp->tile_bits + vp->L, b->temp,
+                                  b->temp_bytes, s, &alt);
+            if (rc) return rc;
+        }
+        keys = alt ? b->ikey_alt : b->ikey;
+        *sorted_ival = alt ? b->ival_alt : b->ival;
     }
-    const uint32_t* keys = alt ? b->ikey_alt : b->ikey;
-    *sorted_ival = alt ? b->ival_alt : b->ival;
     ProfScope ps(ST_RANGES, s);
     rc = launch_ranges(keys, I, b->ranges, tiles * vp->K, s);
     return rc;
@@ -700,6 +715,40 @@ int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* c
                    void* workspace, size_t ws_bytes, void* stream) {
     return render_fwd_into(kd, g, cam, opts, partial_C, partial_T, image, T_final, tile_depth, workspace, ws_bytes,
                            (cudaStream_t)stream, nullptr);
+}
+
+int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                        const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
+                        float* T_final, void* workspace, size_t ws_bytes, uint64_t* overflow_host, void* stream) {
+    if ((!partial_C) != (!partial_T) || (!partial_C && !image)) {
+        set_error("render_fwd_foot: give both partial maps, or neither together with an image");
+        return RGS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    stamp_erase(workspace);   // its lists are about to be replaced
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int64_t I = 0;
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, nullptr, &I, true);
+    if (rc) return rc;
+    // the overflow counter: word 6 of the workspace counter block (unused by the lists)
+    unsigned long long* over = b.counters + 6;
+    RGS_CUDA_TRY(cudaMemsetAsync(over, 0, 8, s));
+    {
+        ProfScope ps(ST_BLEND_FWD, s);
+        rc = launch_blend_foot(vp, tp, b, ival, partial_C, partial_T, image, T_final, over, s);
+        if (rc) return rc;
+    }
+    if (overflow_host) {
+        if (!g_pinned.h) RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
+        unsigned long long* h = g_pinned.h;
+        RGS_CUDA_TRY(cudaMemcpyAsync(h + 6, over, 8, cudaMemcpyDeviceToHost, s));
+        RGS_CUDA_TRY(cudaStreamSynchronize(s));
+        *overflow_host = (uint64_t)h[6];
+    }
+    return RGS_OK;
 }
 
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,

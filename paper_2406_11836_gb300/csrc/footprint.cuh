@@ -19,8 +19,16 @@ struct Footprint {
     float bx, by;            // ball half-extents (pixels)
     float rho2;              // (D/z)^2 with margin
     float ystar;             // y offset of the ellipse's rightmost point
+    float zr;                // foot reading: half-width of the foot's depth interval (0: depth plane)
     bool empty;
 };
+
+// Foot reading: a foot that passes the ball test lies within D of the centre, so its
+// camera depth lies within D of z.  D = z sqrt(rho2) from the ball radius rho2 = (D/z)^2,
+// widened by 0.1%; the count and the emission evaluate this on the same stored values.
+__device__ __forceinline__ float foot_depth_radius(float z, float rho2_ball) {
+    return __fmul_rn(__fmul_rn(z, __fsqrt_rn(rho2_ball)), 1.001f);
+}
 
 __device__ __forceinline__ Footprint make_footprint(float mxh, float myh, float l11, float l12, float l22, float alpha,
                                                     float rho2_signed, const ViewParams& vp) {
@@ -45,6 +53,7 @@ __device__ __forceinline__ Footprint make_footprint(float mxh, float myh, float 
     const float rb = sqrtf(f.rho2);
     f.bx = vp.fx * rb;
     f.by = vp.fy * rb;
+    f.zr = 0.f;
     return f;
 }
 
@@ -188,6 +197,64 @@ __device__ __forceinline__ bool clip_span(const SubsetClip& c, float ylo, float 
     return xlo <= xhi;
 }
 
+// The same narrowing for a point anywhere on the pixel ray between depths za and zb
+// (0 < za < zb): the point's coordinate along a split axis is affine in its depth, so a
+// half-plane holds somewhere in between iff it holds at za or at zb; per plane the looser
+// of the two half-lines (both point the same way, the slope having the sign of the depth)
+// is kept.  Reads the view's plane templates for subset k directly.
+__device__ __forceinline__ bool clip_span_depths(const ViewParams& vp, int k, int L, float za, float zb, float ylo,
+                                                 float yhi, float& xlo, float& xhi) {
+    const float4* t = vp.clip_plane() + k * L;
+    const float* tm = vp.clip_margin() + k * L;
+    const float inf = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= L) break;
+        const float4 q = __ldg(t + d);
+        const float m0 = __ldg(tm + d);
+        float lo = inf, hi = -inf;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float z = e ? zb : za;
+            const float A = z * q.x, B = z * q.y, C = fmaf(z, q.z, q.w), m = fmaf(4e-5f, z, m0);
+            const float rhs = -m - C - fmaxf(B * ylo, B * yhi);   // need A X >= rhs
+            if (A > 0.f) {
+                lo = fminf(lo, __fdividef(rhs, A));
+                hi = inf;
+            } else if (A < 0.f) {
+                hi = fmaxf(hi, __fdividef(rhs, A));
+                lo = -inf;
+            } else if (rhs <= 0.f) {
+                lo = -inf;
+                hi = inf;
+            }
+        }
+        xlo = fmaxf(xlo, lo);
+        xhi = fminf(xhi, hi);
+    }
+    return xlo <= xhi;
+}
+
+// Foot reading: the camera depth of the foot for pixel centres in [X0, X1] x [Y0, Y1] is
+// z (1 + r_x u_x + r_y u_y) / (1 + r_x^2 + r_y^2), u the projected centre in normalised
+// units; bounded by the extremes of the linear numerator and of the quadratic denominator
+// over the rectangle, intersected with [z - zr, z + zr] and widened by 1e-4.  Returns
+// false when the range reaches the camera (then nothing is clipped).
+__device__ __forceinline__ bool foot_depth_range(const Footprint& f, const ViewParams& vp, float z, float X0, float X1,
+                                                 float Y0, float Y1, float& za, float& zb) {
+    const float ux = (f.cx - vp.cx) * vp.ifx, uy = (f.cy - vp.cy) * vp.ify;
+    const float rx0 = (X0 - vp.cx) * vp.ifx, rx1 = (X1 - vp.cx) * vp.ifx;
+    const float ry0 = (Y0 - vp.cy) * vp.ify, ry1 = (Y1 - vp.cy) * vp.ify;
+    const float nlo = 1.f + fminf(rx0 * ux, rx1 * ux) + fminf(ry0 * uy, ry1 * uy);
+    const float nhi = 1.f + fmaxf(rx0 * ux, rx1 * ux) + fmaxf(ry0 * uy, ry1 * uy);
+    const float qhi = 1.f + fmaxf(rx0 * rx0, rx1 * rx1) + fmaxf(ry0 * ry0, ry1 * ry1);
+    const float qlo = 1.f + (rx0 * rx1 <= 0.f ? 0.f : fminf(rx0 * rx0, rx1 * rx1)) +
+                      (ry0 * ry1 <= 0.f ? 0.f : fminf(ry0 * ry0, ry1 * ry1));
+    za = fmaxf(z - f.zr, z * nlo / qhi) * (1.f - 1e-4f);
+    zb = fminf(z + f.zr, z * nhi / qlo) * (1.f + 1e-4f);
+    return nlo > 0.f && za > 0.f && za <= zb;
+}
+
 // Tile columns [c0, c1] of tile row ty touched by the footprint restricted to subset clip
 // `c` (c == nullptr: no restriction).
 __device__ __forceinline__ void footprint_row_tiles_clipped(const Footprint& f, const ViewParams& vp, int ty,
@@ -223,6 +290,26 @@ template <int kMulti = -1>
 __device__ __forceinline__ void item_cols(const Footprint& f, const ViewParams& vp, const TreeParams& tp, int k,
                                           int nsub, float z, int ty, int& c0, int& c1) {
     if (kMulti == 1 || (kMulti < 0 && nsub > 1)) {
+        if (f.zr > 0.f) {
+            // foot reading: clip with the foot's depth range over the row's span, twice (the
+            // second time over the narrowed span); nothing is clipped where that range
+            // reaches the camera
+            footprint_row_tiles_clipped(f, vp, ty, nullptr, c0, c1);
+            const float Ylo = (float)(ty * kTile) + 0.5f, Yhi = (float)(ty * kTile) + (kTile - 0.5f);
+            for (int pass = 0; pass < 2 && c0 <= c1; ++pass) {
+                float X0 = (float)(c0 * kTile) + 0.5f, X1 = (float)(c1 * kTile) + (kTile - 0.5f);
+                float za, zb;
+                if (!foot_depth_range(f, vp, z, X0, X1, Ylo, Yhi, za, zb)) break;
+                if (!clip_span_depths(vp, k, tp.L, za, zb, Ylo, Yhi, X0, X1)) {
+                    c0 = 1;
+                    c1 = 0;
+                    return;
+                }
+                c0 = max(c0, (int)floorf(ceilf(X0 - 0.5f) * (1.f / kTile)));
+                c1 = min(c1, (int)floorf(floorf(X1 - 0.5f) * (1.f / kTile)));
+            }
+            return;
+        }
         SubsetClip clip;
         make_clip_tab(vp, k, tp.L, z, clip);
         footprint_row_tiles_clipped(f, vp, ty, &clip, c0, c1);

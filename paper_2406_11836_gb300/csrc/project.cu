@@ -18,41 +18,12 @@
 // so no cancellation occurs for elongated splats.  Everything else is plain fp32.
 #include <cuda_fp16.h>
 
+#include "eft.cuh"
 #include "footprint.cuh"
 #include "rgs_internal.cuh"
 
 namespace rgs {
 namespace {
-
-// ------------------------------------------------------------------ error-free transformations
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
-// a0*b0 + a1*b1 + a2*b2 + c as hi + lo (Ogita-Rump-Oishi Dot2 style)
-__device__ __forceinline__ void dot3_plus(float a0, float b0, float a1, float b1, float a2, float b2, float c,
-                                          float& hi, float& lo) {
-    float s, e, p, q, t;
-    two_prod(a0, b0, s, e);
-    two_prod(a1, b1, p, q);
-    two_sum(s, p, s, t);
-    e = __fadd_rn(e, __fadd_rn(q, t));
-    two_prod(a2, b2, p, q);
-    two_sum(s, p, s, t);
-    e = __fadd_rn(e, __fadd_rn(q, t));
-    two_sum(s, c, s, t);
-    e = __fadd_rn(e, t);
-    fast_two_sum(s, e, hi, lo);
-}
 
 // ------------------------------------------------------------------ real SH basis, degree <= 3
 // Real spherical harmonics with the Condon-Shortley phase: for m != 0,
@@ -302,8 +273,9 @@ constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are
 
 // Projection of splat i (valid: i < n) into one view.  Outputs go to index j of the
 // per-splat arrays of b; the instance and visible-splat totals are added to counters[0..1]
-// and, when non-null, slot_counters[0..1].  Every lane of the warp must call it.
-template <int DEG, bool kVecSH>
+// and, when non-null, slot_counters[0..1].  Every lane of the warp must call it.  kFoot:
+// the foot reading of x_i (its ball region, side array and depth interval).
+template <int DEG, bool kVecSH, bool kFoot = false>
 __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t i, bool valid, const ViewParams& vp,
                                                  const TreeParams& tp, const int8_t* rank_of, const RasterBuffers& b,
                                                  int64_t j, unsigned long long* counters,
@@ -312,7 +284,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     const int lane = threadIdx.x & 31;
     // candidate state handed to the counting phase
     bool cand = false;
-    float mxh = 0.f, myh = 0.f, l11 = 0.f, l12 = 0.f, l22 = 0.f, alpha = 0.f, rho2 = 0.f, z = 0.f;
+    float mxh = 0.f, myh = 0.f, l11 = 0.f, l12 = 0.f, l22 = 0.f, alpha = 0.f, rho2 = 0.f, z = 0.f, zr = 0.f;
     unsigned long long mask = 0;
     int ty0 = 0, ty1 = -1, nsub = 0;
     if (valid) {
@@ -328,7 +300,24 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         // ball test's screen ellipse (semi-axes f D / z around the centre; widened by 0.1%
         // and a pixel against rounding), so splats whose ellipse misses the image skip the
         // EWA projection.
-        const float bxr = vp.fx * D / z * 1.001f + 1.f, byr = vp.fy * D / z * 1.001f + 1.f;
+        float rball = D / z;   // ball radius in normalised image units
+        if (kFoot) {
+            // foot reading: the rays passing within D of the centre form a cone of half-angle
+            // al = asin(D / |p|) around p, whose axis makes th with the optical axis.  A
+            // direction within al of p lands within al / cos^2(th + al) of the projected
+            // centre (the gnomonic map stretches arcs by at most 1 / cos^2 of their polar
+            // angle), so that disc, widened by 1%, bounds every pixel the ball test accepts;
+            // from th + al = 89 degrees on it is taken as unbounded.
+            const float pxy2 = fmaf(p[0], p[0], p[1] * p[1]);
+            const float pr2 = fmaf(z, z, pxy2);
+            rball = __int_as_float(0x7f800000);
+            if (D * D < pr2) {
+                // cos(th + al) = (z sqrt(|p|^2 - D^2) - sqrt(x^2 + y^2) D) / |p|^2
+                const float c = (z * sqrtf(pr2 - D * D) - sqrtf(pxy2) * D) / pr2;
+                if (c > 0.0175f) rball = asinf(D * rsqrtf(pr2)) / (c * c) * 1.01f + 1e-7f;
+            }
+        }
+        const float bxr = vp.fx * rball * 1.001f + 1.f, byr = vp.fy * rball * 1.001f + 1.f;
         const bool on_screen = mxh + bxr >= 0.f && mxh - bxr <= (float)vp.W && myh + byr >= 0.f &&
                                myh - byr <= (float)vp.H;
         if (z > vp.near_z && alpha >= vp.alpha_min && isfinite(mxh) && isfinite(myh) && on_screen) {
@@ -340,7 +329,11 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
             const float rb = D / z;                   // ball radius in normalised image units
             mask = subset_mask(tp, si.mu[0], si.mu[1], si.mu[2], D);
             nsub = __popcll(mask);
-            rho2 = nsub > 1 ? -(rb * rb) : rb * rb;
+            // foot reading: the record carries the disc bounding the foot's ball region
+            // (footprints, counts and emission use it as they use the depth plane's ball),
+            // and the ball radius itself moves to a side array for the per-pixel test
+            rho2 = nsub > 1 ? -(rball * rball) : rball * rball;
+            if (kFoot) zr = foot_depth_radius(z, rb * rb);
             if (isfinite(P.det) && P.det > 0.f && isfinite(l11) && isfinite(l22)) {
                 const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
                 footprint_tile_rows(f, vp, ty0, ty1);
@@ -360,6 +353,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
                 b.rec[3 * j] = make_float4(mxh, myh, lo_bits, alpha);
                 b.rec[3 * j + 1] = make_float4(l11, l12, l22, rho2);
                 b.rec[3 * j + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
+                if (kFoot) b.foot_side[j] = make_float4(rb * rb, zl, mxl, myl);
                 b.rect[j] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
                 b.mask[j] = mask;
                 b.dkey[j] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
@@ -372,7 +366,8 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     const int items = cand ? nsub * rows : 0;
     uint32_t count = 0;
     if (cand && items <= kWarpCountItems) {
-        const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
+        Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
+        f.zr = zr;
         for (int it = 0; it < items; ++it)
             count += item_tiles(f, vp, tp, rank_of, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
     }
@@ -387,7 +382,8 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         const unsigned long long m_ = __shfl_sync(0xffffffffu, mask, src);
         const int t0_ = __shfl_sync(0xffffffffu, ty0, src), rows_ = __shfl_sync(0xffffffffu, rows, src);
         const int items_ = __shfl_sync(0xffffffffu, items, src);
-        const Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
+        Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
+        f.zr = __shfl_sync(0xffffffffu, zr, src);
         const int ns = __popcll(m_);
         uint32_t acc = 0;
         for (int it = lane; it < items_; it += 32)
@@ -413,14 +409,14 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     }
 }
 
-template <int DEG, bool kVecSH>
+template <int DEG, bool kVecSH, bool kFoot>
 __global__ void __launch_bounds__(256, 3)
 project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b) {
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
     stage_tree(tp, vp.rank_of, stp, srank);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG, kVecSH>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
+    project_fwd_body<DEG, kVecSH, kFoot>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
 }
 
 // Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
@@ -681,7 +677,10 @@ int launch_clip_table_batch(const BatchSlot* slots, const BatchHeader* hdr, cons
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s) {
     unsigned grid = (unsigned)((g.n + 255) / 256);
-    RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V><<<grid, 256, 0, s>>>(g, vp, tp, b)));
+    if (vp.foot)
+        RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V, true><<<grid, 256, 0, s>>>(g, vp, tp, b)));
+    else
+        RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V, false><<<grid, 256, 0, s>>>(g, vp, tp, b)));
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

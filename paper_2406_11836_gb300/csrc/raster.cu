@@ -27,6 +27,7 @@
 // per float4.
 #include <cuda_fp16.h>
 
+#include "eft.cuh"
 #include "footprint.cuh"
 #include "rgs_internal.cuh"
 
@@ -68,11 +69,12 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
                                          const unsigned long long* __restrict__ mask, const float4* __restrict__ rec,
                                          const float* __restrict__ cull, const float2* __restrict__ chunk,
                                          uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane,
-                                         uint32_t* s_start, uint32_t* s_key0) {
+                                         uint32_t* s_start, uint32_t* s_key0, const float4* __restrict__ foot_side) {
     const ushort4 r = rect[id];
     const unsigned long long m = mask[id];
     const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
-    const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+    Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+    if (kMulti == 1 && foot_side) f.zr = foot_depth_radius(r2.w, foot_side[id].x);
     const int ty0 = r.y, rows = (int)r.w - (int)r.y + 1;
     const int nsub = __popcll(m);
     const int items = nsub * rows;
@@ -158,7 +160,7 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
             const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
             const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-            unsigned long long* __restrict__ queue) {
+            unsigned long long* __restrict__ queue, const float4* __restrict__ foot_side) {
     __shared__ uint32_t s_start[8][32], s_key0[8][32];
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
@@ -183,7 +185,8 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             items = ((nsub > 1) == (kMulti == 1)) ? nsub * rows : 0;
             if (items > 0 && items <= kEmitThreadItems) {
                 const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
-                const Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+                Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+                if (kMulti == 1 && foot_side) f.zr = foot_depth_radius(r2.w, foot_side[id].x);
                 emit_thread<kMulti>(vp, stp, srank, id, base, 0u, f, m, nsub, r2.w, r.y, rows, items, cull, chunk,
                                     ikey, ival);
             }
@@ -194,7 +197,7 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             big &= big - 1;
             const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sbase = __shfl_sync(0xffffffffu, base, src);
             emit_one<kMulti>(vp, stp, srank, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
-                             s_start[wib], s_key0[wib]);
+                             s_start[wib], s_key0[wib], foot_side);
         }
     }
 }
@@ -263,7 +266,7 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             const uint32_t sid_ = __shfl_sync(0xffffffffu, id, src), sb = __shfl_sync(0xffffffffu, base, src);
             const int ss = __shfl_sync(0xffffffffu, slot, src);
             emit_one<kMulti>(svp[ss], stp, svp[ss].rank_of, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr,
-                             ikey, ival, lane, s_start[wib], s_key0[wib]);
+                             ikey, ival, lane, s_start[wib], s_key0[wib], nullptr);
         }
     }
 }
@@ -739,6 +742,381 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
     }
 }
 
+// ------------------------------------------------------------------ foot reading (forward only)
+// Under the comparison reading of Sec. 3.2, x_i is the foot of the perpendicular from the
+// centre onto the pixel ray, and a ray's contributors are ordered by the foot's ray
+// parameter t.  For pixel centre (X, Y) and a splat at depth z with projected centre
+// (mx, my), with a = X - cx, c = Y - cy, b = mx - cx, d = my - cy and k = fx^2 / fy^2,
+//   s(p) = fx^2 |r_p| t = z (fx^2 + a b + k c d),       r_p = (a / fx, c / fy, 1),
+// an order key free of the roundings of 1/fx (a, c and fx^2 + ... are nearly exact), so
+// that the fp32 key errs by about 1e-7 of its size.  The order changes from pixel to
+// pixel.  The instances of a (tile, subset) run are sorted by a lower bound of s over the
+// tile; each pixel keeps the contributors it has accepted in a small buffer ordered by s
+// and blends one only when the next instance's bound shows that nothing later can come
+// before it.  Exact unless the buffer overflows (counted); then its nearest entry is
+// blended early.
+constexpr int kFootPend = 64;   // pending contributors per pixel (power of two)
+
+// fx^2 and k = fx^2 / fy^2 of the key, rounded the same way wherever they are used.
+__device__ __forceinline__ float2 foot_scale(const ViewParams& vp) {
+    const float fx2 = __fmul_rn(vp.fx, vp.fx);
+    return make_float2(fx2, __fdiv_rn(fx2, __fmul_rn(vp.fy, vp.fy)));
+}
+
+// Lower bound of s over the pixel centres [px0, px1] x [py0, py1] for a splat with
+// projected centre (mx, my) at depth z, less a margin (1e-5 of the size of its terms) far
+// above the fp32 error of the per-pixel s.
+__device__ __forceinline__ float foot_bound_px(float mx, float my, float z, int px0, int px1, int py0, int py1,
+                                               const ViewParams& vp) {
+    const float2 sc = foot_scale(vp);
+    const float b = __fsub_rn(mx, vp.cx), d = __fsub_rn(my, vp.cy);
+    const float a0 = __fsub_rn((float)px0 + 0.5f, vp.cx), a1 = __fsub_rn((float)px1 + 0.5f, vp.cx);
+    const float c0 = __fmul_rn(__fsub_rn((float)py0 + 0.5f, vp.cy), sc.y);
+    const float c1 = __fmul_rn(__fsub_rn((float)py1 + 0.5f, vp.cy), sc.y);
+    const float ax = fminf(__fmul_rn(a0, b), __fmul_rn(a1, b));
+    const float ay = fminf(__fmul_rn(c0, d), __fmul_rn(c1, d));
+    const float q = __fadd_rn(__fadd_rn(sc.x, ax), ay);
+    const float size = __fmul_rn(z, __fadd_rn(__fadd_rn(sc.x, fabsf(ax)), fabsf(ay)));
+    return __fsub_rn(__fmul_rn(z, q), __fmul_rn(size, 1e-5f));
+}
+
+// The bound over the pixels of tile (tx, ty) inside the image: the sort key of an
+// instance.  The key kernel and the blend evaluate it on the same record values with
+// explicit roundings, so the blend sees the bounds the sort used.
+__device__ __forceinline__ float foot_bound(float mx, float my, float z, int tx, int ty, const ViewParams& vp) {
+    return foot_bound_px(mx, my, z, tx * kTile, min(tx * kTile + kTile - 1, vp.W - 1), ty * kTile,
+                         min(ty * kTile + kTile - 1, vp.H - 1), vp);
+}
+
+// Warp blocks of the tile that a staged record can touch under the foot reading: per
+// 4-row band the footprint's span, clipped for a straddling splat to subset k over the
+// foot's depth range in that band (the count's and emission's rule at band resolution).
+__device__ __forceinline__ uint32_t foot_block_mask(const StagedRec& r, const ViewParams& vp, int k, float zr,
+                                                    float x0t, float y0t) {
+    Footprint f = make_footprint(r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.b.y, fabsf(r.b.w), vp);
+    f.zr = zr;
+    const bool straddles = r.b.w < 0.f;
+    uint32_t m = 0;
+#pragma unroll
+    for (int band = 0; band < 4; ++band) {
+        float x0, x1;
+        const float ylo = (float)(4 * band) + 0.5f - f.cy, yhi = (float)(4 * band) + 3.5f - f.cy;
+        if (!footprint_span(f, vp, ylo, yhi, x0, x1)) continue;
+        float X0 = f.cx + x0 + x0t, X1 = f.cx + x1 + x0t;          // absolute pixel-centre X
+        if (straddles) {
+            const float Ylo = ylo + f.cy + y0t, Yhi = yhi + f.cy + y0t;
+            Footprint fa = f;   // absolute centre for the depth range
+            fa.cx = f.cx + x0t;
+            fa.cy = f.cy + y0t;
+            float za, zb;
+            if (foot_depth_range(fa, vp, r.c.w, fmaxf(X0, x0t + 0.5f), fminf(X1, x0t + 15.5f), Ylo, Yhi, za, zb) &&
+                !clip_span_depths(vp, k, vp.L, za, zb, Ylo, Yhi, X0, X1))
+                continue;
+        }
+        const float pl = ceilf(X0 - x0t - 0.5f), ph = floorf(X1 - x0t - 0.5f);   // tile pixel columns
+        if (pl <= 7.f && ph >= 0.f) m |= 1u << (2 * band);
+        if (pl <= 15.f && ph >= 8.f) m |= 1u << (2 * band + 1);
+    }
+    return m;
+}
+
+// Float bits mapped so that unsigned order is float order (negative bounds included).
+__device__ __forceinline__ uint32_t ordered_bits(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Per instance: the bound of its (splat, tile) and its position, for the first sort pass.
+__global__ void foot_keys_kernel(ViewParams vp, const uint32_t* __restrict__ ikey, const uint32_t* __restrict__ ival,
+                                 int64_t n, const float4* __restrict__ rec, uint32_t* __restrict__ fkey,
+                                 uint32_t* __restrict__ fidx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t tile = ikey[i] >> vp.L;
+        const int ty = (int)(tile / (uint32_t)vp.tiles_x), tx = (int)(tile - (uint32_t)ty * vp.tiles_x);
+        const uint32_t id = ival[i];
+        const float4 r0 = rec[3 * (size_t)id];
+        const float z = rec[3 * (size_t)id + 2].w;
+        fkey[i] = ordered_bits(foot_bound(r0.x, r0.y, z, tx, ty, vp));
+        fidx[i] = (uint32_t)i;
+    }
+}
+
+// (tile, subset) keys and payloads in the order of the bound sort.
+__global__ void foot_gather_kernel(const uint32_t* __restrict__ idx, int64_t n, const uint32_t* __restrict__ ikey,
+                                   const uint32_t* __restrict__ ival, uint32_t* __restrict__ k2,
+                                   uint32_t* __restrict__ v2) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = idx[j];
+        k2[j] = ikey[i];
+        v2[j] = ival[i];
+    }
+}
+
+// Eq. 6 at the foot: x = o + zf R^T r_p, with zf = s / (fx^2 |r_p|^2) the foot's camera
+// depth and g = R^T r_p; right of a node iff x[a] >= split (the half-open rule).  Every leaf
+// tests a node with the same arithmetic, so the decisions of two leaves are complementary.
+__device__ __forceinline__ bool in_subset_foot(const LeafPath& lp, int L, float zf, float g0, float g1, float g2,
+                                               const ViewParams& vp) {
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < kMaxRenderDepth; ++d) {
+        if (d >= L) break;
+        const int ar = lp.axis_right[d];
+        const int a = ar & 3;
+        const float ga = a == 0 ? g0 : (a == 1 ? g1 : g2);
+        const float oa = a == 0 ? vp.o[0] : (a == 1 ? vp.o[1] : vp.o[2]);
+        const float xa = fmaf(zf, ga, oa);
+        ok = ok && ((ar >> 2) ? (xa >= lp.split[d]) : (xa < lp.split[d]));
+    }
+    return ok;
+}
+
+// One pixel's pending contributors: a ring of kFootPend entries in ascending key (the
+// float pair s + sl, equal keys in arrival order) starting at `head`, `n` of them; head,
+// n and the head's s (`hs`, +inf when empty) stay in registers.  An entry keeps the splat
+// id, and its colour is read back from the record when it is blended.
+struct FootPending {
+    float s[kFootPend], sl[kFootPend], sig[kFootPend];
+    uint32_t id[kFootPend];
+};
+
+__device__ __forceinline__ void foot_pop(FootPending& P, const float4* __restrict__ rec, int& head, int& n, float& hs,
+                                         float& C0, float& C1, float& C2, float& T) {
+    const int q = head;
+    const float4 c = rec[3 * (size_t)P.id[q] + 2];
+    const float w = P.sig[q] * T;
+    C0 = fmaf(c.x, w, C0);
+    C1 = fmaf(c.y, w, C1);
+    C2 = fmaf(c.z, w, C2);
+    T = fmaf(-P.sig[q], T, T);
+    head = (q + 1) & (kFootPend - 1);
+    --n;
+    hs = n > 0 ? P.s[head] : kInfF;
+}
+
+__device__ __forceinline__ void foot_insert(FootPending& P, const float4* __restrict__ rec, int& head, int& n,
+                                            float& hs, float s, float sl, float sig, uint32_t id, float& C0,
+                                            float& C1, float& C2, float& T, uint32_t& n_over) {
+    if (n == kFootPend) {
+        foot_pop(P, rec, head, n, hs, C0, C1, C2, T);
+        ++n_over;
+    }
+    int i = n;
+    while (i > 0) {
+        const int prev = (head + i - 1) & (kFootPend - 1);
+        if (P.s[prev] < s || (P.s[prev] == s && P.sl[prev] <= sl)) break;
+        const int to = (head + i) & (kFootPend - 1);
+        P.s[to] = P.s[prev];
+        P.sl[to] = P.sl[prev];
+        P.sig[to] = P.sig[prev];
+        P.id[to] = P.id[prev];
+        --i;
+    }
+    const int at = (head + i) & (kFootPend - 1);
+    P.s[at] = s;
+    P.sl[at] = sl;
+    P.sig[at] = sig;
+    P.id[at] = id;
+    ++n;
+    if (i == 0) hs = s;
+}
+
+// Forward blend of one tile under the foot reading: the structure of the depth-plane
+// forward (subsets in view order, batches staged in shared memory, per-warp lists,
+// freezing below eps_T, the merge of Eq. 5 in shared memory), with the per-pixel order
+// restored through the pending buffer.  A contributor's key s = z (fx^2 + a b + k c d) is
+// carried as a float pair (b = mx - cx, d = my - cy and z from the projection's float
+// pairs; a and, for square pixels, k c exact), so that the order is exact to about 1e-12
+// of the key.  `over` counts buffer overflows.
+__global__ void __launch_bounds__(kBlendThreads, 2)
+blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges_all, const uint32_t* __restrict__ ival,
+                  const float4* __restrict__ rec, const float4* __restrict__ side, float* __restrict__ pC,
+                  float* __restrict__ pT, float* __restrict__ image, float* __restrict__ Tfin,
+                  unsigned long long* __restrict__ over) {
+    __shared__ StagedRec srec[kBlendThreads];
+    __shared__ uint32_t smask[kBlendThreads];
+    __shared__ float sbound[kBlendThreads];
+    __shared__ float4 skey[kBlendThreads];     // (b hi, b lo, d hi, d lo)
+    __shared__ float2 sextra[kBlendThreads];   // ((D/z)^2, z lo)
+    __shared__ uint32_t sid[kBlendThreads];
+    __shared__ float4 sctr[kBlendThreads];     // (mx, my, z, -): inputs of the warp-block bounds
+    // per warp and list entry: a lower bound of s, over the warp's 8x4 block, for that
+    // entry and every later one (the suffix minimum of the entries' block bounds, capped
+    // by the tile bound of the batch's last record, below every later batch)
+    __shared__ float wthr[kBlendThreads / 32][kBlendThreads];
+    __shared__ uint8_t wlist[kBlendThreads / 32][kBlendThreads];
+    __shared__ LeafPath lp;
+    __shared__ float s_img[4][kBlendThreads];
+    __shared__ float s_tkeep[kBlendThreads];
+    const int tile = blockIdx.x;
+    const uint2* ranges = ranges_all + (size_t)tile * vp.K;
+    const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
+    int lx, ly;
+    thread_pixel(threadIdx.x, lx, ly);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = txi * kTile + lx, py = tyi * kTile + ly;
+    const bool inside = px < vp.W && py < vp.H;
+    const float x0 = (float)(txi * kTile), y0 = (float)(tyi * kTile);
+    const float pcx = lx + 0.5f, pcy = ly + 0.5f;
+    const size_t HW = (size_t)vp.W * vp.H;
+    const size_t pix = (size_t)py * vp.W + px;
+    const int tid = threadIdx.x;
+    // per-pixel ray: a = X - cx and k c (key units), fx^2 as a float pair, r_p, |r_p|^2
+    // and g = R^T r_p
+    const float2 sc = foot_scale(vp);
+    float Fh, Fl;
+    two_prod(vp.fx, vp.fx, Fh, Fl);
+    const float pa = (float)px + 0.5f - vp.cx, pc = ((float)py + 0.5f - vp.cy) * sc.y;
+    const float rx = ((float)px + 0.5f - vp.cx) * vp.ifx, ry = ((float)py + 0.5f - vp.cy) * vp.ify;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, 1.f));
+    const float izf = 1.f / (sc.x * r2);   // foot depth = s / (fx^2 |r_p|^2)
+    const float g0 = fmaf(vp.R[0], rx, fmaf(vp.R[3], ry, vp.R[6]));
+    const float g1 = fmaf(vp.R[1], rx, fmaf(vp.R[4], ry, vp.R[7]));
+    const float g2 = fmaf(vp.R[2], rx, fmaf(vp.R[5], ry, vp.R[8]));
+    uint8_t* wl = wlist[warp];
+    // the warp's 8x4 pixel block, clipped to the image (an empty block gives no entries)
+    const int bx0 = txi * kTile + ((warp & 1) << 3), by0 = tyi * kTile + ((warp >> 1) << 2);
+    uint32_t n_over = 0;
+    FootPending P;
+    s_img[0][tid] = 0.f;
+    s_img[1][tid] = 0.f;
+    s_img[2][tid] = 0.f;
+    s_img[3][tid] = 1.f;
+    const bool image_only = pC == nullptr;
+    for (int r = 0; r < vp.K; ++r) {
+        const int k = vp.order[r];
+        const uint2 rg = ranges[r];
+        const bool live = inside && !(image_only && s_img[3][tid] < vp.eps_T);
+        if (image_only && __syncthreads_count(live) == 0) continue;
+        if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        float T = live ? 1.f : 0.f;
+        bool frozen = !live;
+        int ph = 0, pn = 0;
+        float hs = kInfF;
+        for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
+            const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
+            __syncthreads();
+            if ((int)threadIdx.x < nb) {
+                const uint32_t id = ival[b0 + threadIdx.x];
+                StagedRec sr = stage_record(rec, id, x0, y0, vp);
+                const float4 r0 = rec[3 * (size_t)id];
+                const float4 sd = side[id];
+                smask[threadIdx.x] =
+                    sr.b.z >= 0.f ? foot_block_mask(sr, vp, k, foot_depth_radius(sr.c.w, sd.x), x0, y0) : 0u;
+                srec[threadIdx.x] = sr;
+                sbound[threadIdx.x] = foot_bound(r0.x, r0.y, sr.c.w, txi, tyi, vp);
+                sctr[threadIdx.x] = make_float4(r0.x, r0.y, sr.c.w, 0.f);
+                float bh, bl, dh, dl;
+                two_sum(r0.x, -vp.cx, bh, bl);
+                two_sum(r0.y, -vp.cy, dh, dl);
+                skey[threadIdx.x] = make_float4(bh, __fadd_rn(bl, sd.z), dh, __fadd_rn(dl, sd.w));
+                sextra[threadIdx.x] = make_float2(sd.x, sd.y);
+                sid[threadIdx.x] = id;
+            }
+            __syncthreads();
+            const int n = warp_list(smask, nb, warp, lane, wl);
+            {
+                // block bounds of the warp's entries, then their suffix minimum, back to front
+                const float cap = sbound[nb - 1];
+                float carry = cap;
+                for (int c = ((n - 1) >> 5) << 5; c >= 0; c -= 32) {
+                    const int t = c + lane;
+                    float v = kInfF;
+                    if (t < n) {
+                        const float4 m = sctr[wl[t]];
+                        v = fmaxf(foot_bound_px(m.x, m.y, m.z, bx0, bx0 + 7, by0, by0 + 3, vp), sbound[wl[t]]);
+                    }
+                    // suffix minimum within the chunk (lanes above hold later entries)
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float w = __shfl_down_sync(0xffffffffu, v, o);
+                        if (lane + o < 32) v = fminf(v, w);
+                    }
+                    v = fminf(v, carry);
+                    if (t < n) wthr[warp][t] = v;
+                    carry = __shfl_sync(0xffffffffu, v, 0);
+                }
+                __syncwarp();
+            }
+            for (int t0 = 0; t0 < n; t0 += 32) {
+                if (!frozen && T < vp.eps_T) {
+                    frozen = true;
+                    s_tkeep[tid] = T;
+                    T = 0.f;
+                    pn = 0;
+                    hs = kInfF;
+                }
+                if (__all_sync(0xffffffffu, frozen)) break;
+                const int t1 = min(n, t0 + 32);
+                for (int t = t0; t < t1; ++t) {
+                    const int j = wl[t];
+                    const float bound = wthr[warp][t];
+                    // nothing from here on can come before a pending key below this bound
+                    while (hs < bound) foot_pop(P, rec, ph, pn, hs, C0, C1, C2, T);
+                    const float4 A = srec[j].a;
+                    const float4 B = srec[j].b;
+                    const float4 Cc = srec[j].c;
+                    const float4 Kb = skey[j];
+                    const float2 ex = sextra[j];
+                    const float dx = pcx - A.x, dy = pcy - A.y;
+                    const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
+                    const float d2 = fmaf(u1, u1, u2 * u2);
+                    const float ux = Kb.x * vp.ifx, uy = Kb.z * vp.ify;
+                    const float bx = dx * vp.ifx, by = dy * vp.ify;
+                    const float cr = fmaf(ux, by, -uy * bx);
+                    // the ball test at the foot: |x_i - u_i|^2 / z^2 = (bx^2 + by^2 + cr^2) / |r_p|^2
+                    bool ok = (d2 <= B.z) & (fmaf(bx, bx, fmaf(by, by, cr * cr)) <= ex.x * r2);
+                    if (B.w < 0.f) {   // warp-uniform: Eq. 6 at the foot, with the key in one float
+                        const float s1 = Cc.w * fmaf(pa, Kb.x, fmaf(pc, Kb.z, sc.x));
+                        ok = ok && in_subset_foot(lp, vp.L, s1 * izf, g0, g1, g2, vp);
+                    }
+                    if (ok && !frozen) {
+                        // s = z (fx^2 + a b + k c d) as a float pair
+                        float p1, e1, p2, e2, q1, t1, q2, t2, Sh, Sl, kh, kl;
+                        two_prod(pa, Kb.x, p1, e1);
+                        e1 = __fmaf_rn(pa, Kb.y, e1);
+                        two_prod(pc, Kb.z, p2, e2);
+                        e2 = __fmaf_rn(pc, Kb.w, e2);
+                        two_sum(Fh, p1, q1, t1);
+                        two_sum(q1, p2, q2, t2);
+                        fast_two_sum(q2, __fadd_rn(__fadd_rn(__fadd_rn(t1, t2), __fadd_rn(e1, e2)), Fl), Sh, Sl);
+                        two_prod(Cc.w, Sh, kh, kl);
+                        kl = __fmaf_rn(Cc.w, Sl, __fmaf_rn(ex.y, Sh, kl));
+                        fast_two_sum(kh, kl, kh, kl);
+                        const float G = ex2_approx(d2 * kNegHalfLog2e);
+                        const float sig = fminf(B.y * G, vp.alpha_max);
+                        foot_insert(P, rec, ph, pn, hs, kh, kl, sig, sid[j], C0, C1, C2, T, n_over);
+                    }
+                }
+            }
+            if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) break;
+        }
+        while (pn > 0) foot_pop(P, rec, ph, pn, hs, C0, C1, C2, T);
+        if (frozen && inside) T = live ? s_tkeep[tid] : 1.f;
+        if (inside) {
+            if (pC) {
+                pC[((size_t)k * 3 + 0) * HW + pix] = C0;
+                pC[((size_t)k * 3 + 1) * HW + pix] = C1;
+                pC[((size_t)k * 3 + 2) * HW + pix] = C2;
+                pT[(size_t)k * HW + pix] = T;
+            }
+            const float Pm = s_img[3][tid];
+            s_img[0][tid] = fmaf(C0, Pm, s_img[0][tid]);
+            s_img[1][tid] = fmaf(C1, Pm, s_img[1][tid]);
+            s_img[2][tid] = fmaf(C2, Pm, s_img[2][tid]);
+            s_img[3][tid] = Pm * T;
+        }
+    }
+    if (inside && image) {
+        const float Pm = s_img[3][tid];
+        image[0 * HW + pix] = fmaf(vp.bg[0], Pm, s_img[0][tid]);
+        image[1 * HW + pix] = fmaf(vp.bg[1], Pm, s_img[1][tid]);
+        image[2 * HW + pix] = fmaf(vp.bg[2], Pm, s_img[2][tid]);
+        if (Tfin) Tfin[pix] = Pm;
+    }
+    count_add(over, n_over);
+}
+
 // ------------------------------------------------------------------ blend backward
 // Adds a float4 into global memory with one vector reduction.
 __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
@@ -1035,11 +1413,13 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     unsigned grid = (unsigned)(want < cap ? want : cap);
     // work counters: counters[4] and [5] (zeroed with the others at the start of the list build)
     emit_kernel<0><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
-                                        b.ikey, b.ival, b.counters + 4);
+                                        b.ikey, b.ival, b.counters + 4, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     if (vp.K > 1) {
+        // foot reading: straddlers are clipped over the foot's depth interval (side array)
         emit_kernel<1><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull,
-                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5);
+                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5,
+                                            vp.foot ? b.foot_side : nullptr);
         RGS_CUDA_LAUNCH_CHECK();
     }
     return RGS_OK;
@@ -1073,6 +1453,44 @@ int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
                                                                image, T_final, tile_depth, record_ends, nullptr);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_foot_order(const ViewParams& vp, const RasterBuffers& b, int64_t I, cudaStream_t s,
+                      const uint32_t** keys_out, const uint32_t** vals_out) {
+    if (I <= 0) {
+        *keys_out = b.ikey;
+        *vals_out = b.ival;
+        return RGS_OK;
+    }
+    const int64_t want = (I + 255) / 256;
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    foot_keys_kernel<<<grid, 256, 0, s>>>(vp, b.ikey, b.ival, I, b.rec, b.fkey, b.fidx);
+    RGS_CUDA_LAUNCH_CHECK();
+    // LSD: the bound first, then stably the (tile, subset) key
+    bool alt = false;
+    int rc = radix_sort_pairs(b.fkey, b.fidx, b.ikey_alt, b.ival_alt, I, 32, b.temp, b.temp_bytes, s, &alt);
+    if (rc) return rc;
+    const uint32_t* idx = alt ? b.ival_alt : b.fidx;
+    uint32_t* k2 = alt ? b.fkey : b.ikey_alt;
+    uint32_t* v2 = alt ? b.fidx : b.ival_alt;
+    foot_gather_kernel<<<grid, 256, 0, s>>>(idx, I, b.ikey, b.ival, k2, v2);
+    RGS_CUDA_LAUNCH_CHECK();
+    bool alt2 = false;
+    rc = radix_sort_pairs(k2, v2, b.ikey, b.ival, I, vp.tile_bits + vp.L, b.temp, b.temp_bytes, s, &alt2);
+    if (rc) return rc;
+    *keys_out = alt2 ? b.ikey : k2;
+    *vals_out = alt2 ? b.ival : v2;
+    return RGS_OK;
+}
+
+int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                      float* partial_C, float* partial_T, float* image, float* T_final,
+                      unsigned long long* over, cudaStream_t s) {
+    unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
+    blend_foot_kernel<<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, b.foot_side, partial_C, partial_T,
+                                                     image, T_final, over);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

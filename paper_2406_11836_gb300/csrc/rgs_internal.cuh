@@ -67,6 +67,9 @@ struct ViewParams {
         clip_addr[2] = (uint32_t)(uintptr_t)margin;
         clip_addr[3] = (uint32_t)((uint64_t)(uintptr_t)margin >> 32);
     }
+    // 1: x_i is the foot of the perpendicular from the centre onto the pixel ray (the
+    // comparison reading of Sec. 3.2, forward only); 0: the ray point at the splat's depth
+    int foot;
 };
 constexpr int kClipTable = 64 * kMaxRenderDepth;   // entries of one view's plane-template table
 
@@ -189,6 +192,11 @@ struct RasterBuffers {
     float4* clip_plane;   // [kClipTable] the view's plane templates (ViewParams::clip_plane())
     float* clip_margin;   // [kClipTable]
     unsigned long long* header;   // [32] workspace header: [0] the nonce of the forward whose lists it holds
+    // foot reading only (nullptr otherwise)
+    float4* foot_side;    // [N] ((D/z)^2, z lo, mx lo, my lo): the ball radius (the record carries +-inf so
+                          // that no footprint uses it) and the low parts of the depth and centre
+    uint32_t* fkey;       // [inst_cap] order-preserving bits of the per-(splat, tile) ray-parameter bound
+    uint32_t* fidx;       // [inst_cap] instance positions
     // per instance
     uint32_t* ikey;
     uint32_t* ival;
@@ -230,6 +238,14 @@ int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, c
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
                      cudaStream_t s, bool record_ends = false);
+// Foot reading (forward only): orders the emitted instances by (tile, subset, bound of
+// the foot's ray parameter over the tile) and returns the sorted keys and payloads.
+int launch_foot_order(const ViewParams& vp, const RasterBuffers& b, int64_t I, cudaStream_t s,
+                      const uint32_t** keys_out, const uint32_t** vals_out);
+// Foot-reading forward blend; `over` (device, zeroed by the caller) counts pending-buffer overflows.
+int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                      float* partial_C, float* partial_T, float* image, float* T_final,
+                      unsigned long long* over, cudaStream_t s);
 // n_inst: instances in ival (ranges are clamped to it); n_splats: records in b.rec (other
 // payloads are skipped).
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,

@@ -83,6 +83,9 @@ def lib():
                                             c_int64, POINTER(c_size_t)]
     L.rgs_render_fwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]
+    L.rgs_render_fwd_foot.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, POINTER(ctypes.c_uint64),
+                                      c_void_p]
     L.rgs_render_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                  c_void_p, c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_merge_partials.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
@@ -283,6 +286,29 @@ def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image
     return out
 
 
+def render_fwd_foot(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, partials=True, stream=None,
+                    out=None):
+    """Forward render under the perpendicular-foot reading of x_i (Sec. 3.2; comparison
+    mode, no backward): like render_fwd, plus "overflow", the number of contributors the
+    per-pixel order buffer had to blend early (0: the per-pixel order is exact)."""
+    H, W = int(cam.height), int(cam.width)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        out = {"image": torch.empty(3, H, W, device=dev), "T_final": torch.empty(H, W, device=dev)}
+        if partials:
+            out["partial_C"] = torch.empty(kd.K, 3, H, W, device=dev)
+            out["partial_T"] = torch.empty(kd.K, H, W, device=dev)
+    c = camera_c(cam)
+    s = _stream(stream)
+    over = ctypes.c_uint64(0)
+    _retry(lambda: lib().rgs_render_fwd_foot(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
+                                             _ptr(out.get("partial_C")), _ptr(out.get("partial_T")),
+                                             _ptr(out.get("image")), _ptr(out.get("T_final")), ws.ptr(), ws.nbytes,
+                                             ctypes.byref(over), s), ws)
+    out["overflow"] = int(over.value)
+    return out
+
+
 def render_bwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, partial_C, partial_T, dL_dimage, grads, ws: Workspace,
                stream=None, tile_depth=None):
     """Accumulate dL/d(params) into grads = (means, log_scales, quats, opacity_logits, sh) tensors.
@@ -458,7 +484,7 @@ class Server:
 
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
-               "rgs_render_workspace_size", "rgs_render_fwd", "rgs_merge_partials", "rgs_merge_partials_bwd",
+               "rgs_render_workspace_size", "rgs_render_fwd", "rgs_render_fwd_foot", "rgs_merge_partials", "rgs_merge_partials_bwd",
                "rgs_render_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",

@@ -72,6 +72,14 @@ def test_invalid_arguments_are_rejected(R):
                                           ctypes.c_void_p(fake), 16, offs, rates, 2, pseg, period, head,
                                           ctypes.c_float(1e-2), ctypes.c_float(0.9), ctypes.c_float(0.999),
                                           ctypes.c_float(1e-15), 1, 1, None) == R.RGS_EINVAL
+    # foot-reading forward: no output at all, then a NULL kd handle
+    over = ctypes.c_uint64()
+    assert lib.rgs_render_fwd_foot(None, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), None, None, None,
+                                   None, None, 0, ctypes.byref(over), None) == R.RGS_EINVAL
+    assert lib.rgs_render_fwd_foot(None, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), None, None,
+                                   ctypes.c_void_p(fake), None, ctypes.c_void_p(fake), 1 << 20, ctypes.byref(over),
+                                   None) == R.RGS_EINVAL
+    assert b"kd" in lib.rgs_last_error()
     # view order needs a handle; merge needs buffers
     assert lib.rgs_merge_partials(None, None, None, 0, 1, 1, None, None, None, None) == R.RGS_EINVAL
     assert lib.rgs_adam_step(None, None, None, None, 0, None, None, 0, ctypes.c_float(0.9), ctypes.c_float(0.999),

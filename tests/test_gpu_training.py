@@ -35,8 +35,13 @@ def test_one_view_batch_is_the_one_view_step(R):
     lb = b.step_batch([cam], [target])
     torch.cuda.synchronize()
     assert torch.equal(la, lb)
-    # the 2D gradients are summed with atomics, so the two updates agree to rounding
-    assert float((a.flat - b.flat).abs().max()) <= 1e-6
+    # the 2D gradients are summed with atomics, so the first moments (0.1 g) agree to rounding
+    assert rel_l2(a.m.double().cpu().numpy(), b.m.double().cpu().numpy()) <= 1e-5
+    # Adam's first update is lr g / (|g| + eps): only where g itself is at the rounding level
+    # of those sums may the two updates differ by more than rounding
+    d = (a.flat - b.flat).abs()
+    big = d > 1e-6
+    assert bool((a.m[big].abs() <= 1e-6 * float(a.m.abs().max())).all())
     assert a.step_count == b.step_count == 1
 
 
