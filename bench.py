@@ -383,7 +383,8 @@ def foot_reading_report(trainer, cams) -> dict:
         prof = rgs.profile_read(reset=True)
         rgs.profile_enable(False, False)
         res[name] = {"forward_ms": round(float(np.mean(ms)), 3),
-                     "stages_ms": {k: round(v[0] / len(cams), 3) for k, v in prof["stages"].items() if v[1] > 0}}
+                     "stages_ms": {k: round(v[0] / len(cams), 3) for k, v in prof["stages"].items() if v[1] > 0},
+                     "instances_per_view": prof["counters"]["instances"] / len(cams)}
         if name == "foot":
             res[name]["overflow_per_view"] = over / len(cams)
     res["views"] = len(cams)
