@@ -879,7 +879,7 @@ int rgs_profile_read(double* ms_host, int64_t* launches_host, int64_t* counters_
         counters_host[4] = g_prof.host_counts[0];
         counters_host[5] = g_prof.host_counts[1];
         counters_host[6] = g_launches.load();
-        for (int i = 0; i < 7; ++i) counters_host[7 + i] = (int64_t)pairs[4 + i];
+        for (int i = 0; i < 9; ++i) counters_host[7 + i] = (int64_t)pairs[4 + i];
     }
     if (reset) {
         for (int i = 0; i < ST_COUNT; ++i) {

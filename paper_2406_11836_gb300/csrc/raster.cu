@@ -554,6 +554,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     __shared__ float s_tkeep[kBlendThreads];    // T of a frozen pixel
     uint32_t n_eval = 0, n_contrib = 0, n_d2 = 0, n_ball = 0, n_leaf = 0, n_strad = 0, n_staged = 0, n_used = 0;
     uint32_t n_iter = 0;   // warp passes over one list entry (lane 0 counts)
+    uint32_t n_behind = 0; // pairs evaluated where the merged front transmittance is below eps_T
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
     thread_pixel(threadIdx.x, lx, ly);
@@ -589,6 +590,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         bool frozen = !live;
         float zsat = kInfF;   // the subset never saturated the tile
         uint32_t send = rg.y;  // end of the last batch staged
+        const bool behind_front = kCount && s_img[3][tid] < vp.eps_T;
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
@@ -628,6 +630,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                     const float sig = ok ? fminf(B.y * G, vp.alpha_max) : 0.f;
                     if (kCount && !frozen) {
                         ++n_eval;
+                        n_behind += behind_front;
                         n_strad += B.w < 0.f;
                         n_d2 += !(d2 <= B.z);
                         const bool in_ball = !(fabsf(B.w) != kInfF) ||
@@ -687,6 +690,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         count_add(pairs + 8, n_staged);
         count_add(pairs + 10, n_iter);
         count_add(pairs + 9, n_used);
+        count_add(pairs + 11, n_behind);
     }
 }
 
@@ -1134,7 +1138,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     // <g, S_r> of this pixel for every rank: private to the thread, in local memory (cached),
     // so that shared memory does not grow with K
     float behind_r[1 << kMaxRenderDepth];
-    uint32_t n_eval = 0, n_contrib = 0;
+    uint32_t n_eval = 0, n_contrib = 0, n_iter = 0;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -1198,12 +1202,16 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         s_gc[threadIdx.x][1] = gC1;
         s_gc[threadIdx.x][2] = gC2;
         float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
+        // a pixel whose transmittance in front of this subset is below eps_T gets gradients
+        // scaled by less than eps_T from it: the subset is skipped there, as an image-only
+        // forward skips it
+        const bool front_open = Pm >= vp.eps_T;
         Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         uint2 rg = ranges[(size_t)tile * vp.K + r];
         rg.y = min(rg.y, n_inst);   // lists handed over from a forward: never read past them
         rg.x = min(rg.x, rg.y);
-        const bool active = inside && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
+        const bool active = inside && front_open && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
         if (__syncthreads_count(active) == 0) continue;
         // replay of the forward: the same pairs, the same freeze points (an inactive pixel
         // is frozen from the start: its gradients are zero)
@@ -1245,6 +1253,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                     // zero gradients); two scalars per (pixel, entry) go to shared memory
                     bool any = false;
                     for (int t = s0; t < s1; ++t) {
+                        if (kCount && lane == 0) ++n_iter;
                         const int j = wl[t];
                         const float4 A = srec[j].a;
                         const float4 B = srec[j].b;
@@ -1348,7 +1357,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) break;
         }
     }
-    if (kCount) count_pairs(pairs + 2, n_eval, n_contrib);
+    if (kCount) {
+        count_pairs(pairs + 2, n_eval, n_contrib);
+        count_add(pairs + 12, n_iter);
+    }
 }
 
 // ------------------------------------------------------------------ standalone merge (Eq. 5)

@@ -374,7 +374,7 @@ def profile_enable(timing: bool = True, counters: bool = False):
 
 PAIR_COUNTERS = ("fwd_pairs", "fwd_contrib", "bwd_pairs", "bwd_contrib", "instances", "visible", "kernel_launches",
                  "fwd_fail_d2", "fwd_fail_ball", "fwd_fail_subset", "fwd_pairs_straddling", "fwd_instances_staged",
-                 "fwd_instances_used", "fwd_warp_iterations")
+                 "fwd_instances_used", "fwd_warp_iterations", "fwd_pairs_behind_front", "bwd_warp_iterations")
 
 
 def profile_read(reset: bool = True) -> dict:
