@@ -35,7 +35,7 @@ WORKLOAD_NAMES = {"city": "city-10M-3840x2160-K16", "object": "object-1M-1600x10
                   "city-small": "city-1M-1920x1080-K16", "city-100m": "city-100M-3840x2160-K64"}
 UNIT = "Mpix/s"
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
+MUFU_PER_SM_CLK = 16     # ex2 results per SM per clock (the SFU rate)
 
 
 def _peaks():
@@ -164,50 +164,91 @@ def oracle_step_estimate(wl, budget_s=20.0, cam_index=0, threads=None):
 
 
 # --------------------------------------------------------------------------- roofline of the dominant kernel
-# Algorithmic FP32 operations per (pixel, splat) pair of the blend kernels (an FMA counts 2):
-#   every evaluated pair: offset (2), Cholesky-factored Mahalanobis distance (7), ball test (5)      = 14
-#   forward, contributing pair: exponent scale, alpha*G, weight, colour FMAs (6), transmittance FMA (2) = 11
-#   backward, contributing pair: the forward's 11 plus the adjoint (colour dot 5, prefix 2, dsigma 5,
-#   colour grads 3, alpha 1, d2 grad 2, conic grads 7, mean grads 7) minus the colour FMAs     = ~40
+# Algorithmic work per (pixel, splat) pair of the blend kernels, as the method counts it:
+#   forward:  ~30 FP32 operations + 1 ex2 per evaluated pair (Mahalanobis distance through the
+#             conic, the truncation tests, alpha, weight, colour and transmittance updates)
+#   backward: ~70 FP32 operations + 1 ex2 per evaluated pair (the forward's replay plus the
+#             adjoint of sigma and the 2D mean, conic, opacity and colour gradients)
+# and per instance / pixel the bytes each must move (records once per staged instance, the
+# partial maps, dL/dC, the per-splat 2D gradients).  The kernel's own finer count (an FMA as
+# two operations: 14 per evaluated pair, +11 forward / +40 backward per contributing pair) is
+# reported beside it.
+FLOPS_PER_PAIR = {"blend_fwd": 30, "blend_bwd": 70}
 FLOPS_EVAL = 14
-FLOPS_FWD_CONTRIB = 11
-FLOPS_BWD_CONTRIB = 40
+FLOPS_CONTRIB = {"blend_fwd": 11, "blend_bwd": 40}
 
 
-def roofline(prof, peaks, peak_src, source, traffic_table, workload=None):
+def sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def stage_roofline(name, ms, launches, cnt, peaks, peak_src, geom):
+    """Roofline of one pass: min-time bound = max(bytes / HBM peak, FP32 ops / FP32 peak,
+    ex2 / SFU peak) over its launches; frac = bound / measured time."""
+    avg_s = ms / 1e3 / launches
+    sms = geom["sms"]
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6          # FLOP/s
+    mufu_peak = sms * MUFU_PER_SM_CLK * clock_mhz * 1e6                 # ex2/s
+    hbm = peaks["hbm_gbs"] * 1e9
+    HW, K = geom["pixels"], geom["K"]
+    per = lambda key: cnt.get(key, 0) / max(launches, 1)               # per launch
+    flops = mufu = 0.0
+    own = None
+    if name == "blend_fwd":
+        P = per("fwd_pairs")
+        flops, mufu = FLOPS_PER_PAIR[name] * P, P
+        byts = 36 * per("fwd_instances_staged") + 16 * K * HW + 16 * HW
+        own = FLOPS_EVAL * P + FLOPS_CONTRIB[name] * per("fwd_contrib")
+    elif name == "blend_bwd":
+        P = per("bwd_pairs")
+        flops, mufu = FLOPS_PER_PAIR[name] * P, P
+        # the backward replays the lists the forward staged
+        byts = 12 * HW + 32 * K * HW + 36 * per("fwd_instances_staged") + 36 * per("visible")
+        own = FLOPS_EVAL * P + FLOPS_CONTRIB[name] * per("bwd_contrib")
+    else:
+        I, Nv = per("instances"), per("visible")
+        byts = {"instance_sort": 24 * I, "depth_sort": 24 * Nv, "emit": 8 * I, "ranges": 4 * I,
+                "project": 44 * geom["N"] + 192 * Nv + 76 * Nv, "project_bwd": 48 * Nv + 236 * Nv * 2,
+                "adam": 28 * geom["params"]}.get(name, 0.0)
+    t_hbm, t_fp32, t_mufu = byts / hbm, flops / fp32_peak, mufu / mufu_peak
+    t_min = max(t_hbm, t_fp32, t_mufu)
+    if t_fp32 >= t_hbm and t_fp32 >= t_mufu and flops > 0:
+        out = {"kernel": name, "bound": "alu", "achieved": flops / avg_s / 1e12, "peak": fp32_peak / 1e12,
+               "unit": "TFLOP/s", "frac": t_min / avg_s,
+               "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz (derived)",
+               "peak_kind": "derived from unit counts and the measured max SM clock"}
+    else:
+        out = {"kernel": name, "bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": peaks["hbm_gbs"],
+               "unit": "GB/s", "frac": t_min / avg_s, "peak_kind": "of " + peak_src}
+    out.update({"algorithmic_bytes": byts, "algorithmic_flops": flops, "ex2": mufu,
+                "bound_ms": {"hbm": t_hbm * 1e3, "fp32": t_fp32 * 1e3, "sfu": t_mufu * 1e3},
+                "avg_launch_ms": avg_s * 1e3, "launches": launches})
+    if own is not None:
+        out["own_count_tflops"] = own / avg_s / 1e12
+    if name == "instance_sort":
+        out["implementation_bytes"] = 20 * I * geom.get("sort_passes", 3)
+    return out
+
+
+def roofline(prof, peaks, peak_src, source, traffic_table, geom, workload=None):
     stages = prof["stages"]
     cnt = prof["counters"]
     cand = {k: v for k, v in stages.items() if v[1] > 0}
     dom = max(cand, key=lambda k: cand[k][0])
-    ms, launches = cand[dom]
-    avg_s = ms / 1e3 / launches
-    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12     # TFLOP/s
-    if dom in ("blend_fwd", "blend_bwd"):
-        if dom == "blend_fwd":
-            flops = FLOPS_EVAL * cnt["fwd_pairs"] + FLOPS_FWD_CONTRIB * cnt["fwd_contrib"]
-        else:
-            flops = FLOPS_EVAL * cnt["bwd_pairs"] + FLOPS_BWD_CONTRIB * cnt["bwd_contrib"]
-        achieved = flops / launches / avg_s / 1e12
-        out = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-               "frac": achieved / fp32_peak,
-               "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz (derived)"}
-    else:
-        # bandwidth-bound passes: algorithmic bytes per launch
-        I = cnt["instances"] / max(launches, 1)
-        Nv = cnt["visible"] / max(launches, 1)
-        per = {"instance_sort": 60 * I, "depth_sort": 80 * Nv, "emit": 8 * I, "ranges": 4 * I}
-        byts = per.get(dom, 0.0)
-        achieved = byts / avg_s / 1e9
-        out = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-               "frac": achieved / peaks["hbm_gbs"]}
+    out = stage_roofline(dom, cand[dom][0], cand[dom][1], cnt, peaks, peak_src, geom)
     t = traffic_table.get(dom)
     ok = t and t.get("source_sha") == source.get(t.get("source")) and t.get("workload") == workload
     out["traffic"] = t["dram_bytes_per_launch"] if ok else None
-    out["avg_launch_ms"] = avg_s * 1e3
-    out["launches"] = launches
-    out["peak_kind"] = ("derived from unit counts and the measured max SM clock" if out["bound"] == "alu"
-                        else "of " + peak_src)
+    # the next passes by time, same arithmetic (context for the dominant one)
+    others = sorted(cand, key=lambda k: -cand[k][0])[1:4]
+    out["next"] = {k: {kk: v for kk, v in stage_roofline(k, cand[k][0], cand[k][1], cnt, peaks, peak_src, geom).items()
+                       if kk in ("bound", "achieved", "unit", "frac", "avg_launch_ms")} for k in others}
+    for k in others:
+        tk = traffic_table.get(k)
+        if tk and tk.get("source_sha") == source.get(tk.get("source")) and tk.get("workload") == workload:
+            out["next"][k]["traffic"] = tk["dram_bytes_per_launch"]
     return out
 
 
@@ -247,9 +288,14 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400,
     ring = 32   # output buffers per resolution, reused round robin
     outs = {(w, h): [torch.empty(3, h, w, device=device) for _ in range(ring)] for (w, h) in W.RESOLUTIONS}
     res = {}
-    for mode in ("batched", "plain"):
-        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, max_slots=max_slots, lanes=lanes,
-                         plain=(mode == "plain"), keepalive=wl.scene)
+    # batched: `lanes` concurrent lanes of up to `max_slots` requests per batch; lanes_only: the
+    # same lanes with one request per batch (concurrency without batching); plain: one request
+    # at a time through the render entry point
+    modes = {"batched": dict(max_slots=max_slots, lanes=lanes, plain=False),
+             "lanes_only": dict(max_slots=1, lanes=lanes, plain=False),
+             "plain": dict(max_slots=max_slots, lanes=lanes, plain=True)}
+    for mode, kw in modes.items():
+        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, keepalive=wl.scene, **kw)
         for (w, h), bufs in outs.items():     # warm every resolution once
             srv.wait(srv.submit(W.look_at((6.0, 6.0, 5.0), (0, 0, 0), w, h), bufs[0]))
         tickets = []
@@ -270,10 +316,14 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400,
         for t in bt:
             srv.wait(t, timeout_s=600)
         sat = sum(c.width * c.height for _, c in sub) / (time.perf_counter() - t1) / 1e6
+        st2 = srv.stats()
         srv.close()
+        sat_batches = max(st2["batches"] - st["batches"], 1)
         res[mode] = {"p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
                      "mean_ms": float(L.mean()), "mpix_s": pix / span / 1e6, "saturation_mpix_s": sat,
-                     "requests_measured": int(len(L)), "mean_batch": st["mean_batch"], "requeued": st["requeued"]}
+                     "requests_measured": int(len(L)), "mean_batch": st["mean_batch"],
+                     "saturation_mean_batch": (st2["completed"] - st["completed"]) / sat_batches,
+                     "requeued": st2["requeued"], "max_slots": kw["max_slots"], "lanes": 1 if kw["plain"] else lanes}
     torch.cuda.synchronize()
     res["config"] = {"workload": "serve-5M-K8", "splats": int(g.n), "subsets": kd.K,
                      "arrivals": f"Poisson {rate_hz:g} req/s, {requests} requests ({warm} warm-up)",
@@ -392,6 +442,122 @@ def foot_reading_report(trainer, cams) -> dict:
     return res
 
 
+def sort_passes(L, H, W):
+    """Radix passes of the (tile, subset) instance sort: 8-bit digits over the key's bits."""
+    tiles = ((H + 15) // 16) * ((W + 15) // 16)
+    bits = max(0, (tiles - 1).bit_length()) + L
+    return -(-bits // 8)
+
+
+def variant_report(trainer, cams, targets, args) -> dict:
+    """Untimed-for-the-headline comparisons on the same views (CUDA events on the launching
+    stream, after a warm-up pass over every view):
+      exact_partials: the step with every subset blended on every ray it meets (the partial
+                      maps are the whole Eq. 3-4), against the headline's occlusion culling;
+      backward_flat / backward_subsets: the step with the other backward form than the
+                      headline's (flat: image-only forward and one replay of each pixel's
+                      concatenated list; subsets: partial maps and the merge adjoint);
+      bwd_recompute:  the backward with a workspace that does not hold the forward's lists,
+                      so it re-derives them (projection, binning, sorting) with the forward's
+                      per-(tile, subset) depth table culling splats behind saturated tiles."""
+    import torch
+    from paper_2406_11836_gb300 import rgs
+    stream = torch.cuda.current_stream()
+    n = max(len(cams), 4)
+    res = {}
+
+    def timed(fn):
+        for i in range(len(cams)):
+            fn(i)
+        torch.cuda.synchronize()
+        rgs.profile_enable(timing=True, counters=False)
+        rgs.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n):
+            fn(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = rgs.profile_read(reset=True)
+        rgs.profile_enable(False, False)
+        return e0.elapsed_time(e1) / n, {k: round(v[0] / n, 3) for k, v in prof["stages"].items() if v[1] > 0}
+
+    step = lambda i: trainer.step(cams[i % len(cams)], targets[i % len(cams)], return_loss=False)
+    saved, saved_bwd = trainer.opts, trainer.backward
+    trainer.opts, trainer.backward = rgs.default_opts(cull_occluded=0), "subsets"
+    ms, st = timed(step)
+    res["exact_partials"] = {"ms_per_step": round(ms, 3), "stages_ms": st}
+    # the other backward form than the headline's, same culled forward
+    trainer.opts = saved
+    trainer.backward = "flat" if saved_bwd == "subsets" else "subsets"
+    ms, st = timed(step)
+    res[f"backward_{trainer.backward}"] = {"ms_per_step": round(ms, 3), "stages_ms": st}
+    trainer.backward = saved_bwd
+
+    g = trainer.gaussians()
+    ws2 = rgs.Workspace(trainer.flat.device)
+    outs = {}
+
+    def fwd(i):
+        c = cams[i % len(cams)]
+        outs[i % len(cams)] = rgs.render_fwd(trainer.kd, g, c, trainer.opts, trainer.ws, image=True)
+
+    def bwd(i):
+        c = cams[i % len(cams)]
+        o = outs[i % len(cams)]
+        dL = torch.sign(o["image"] - targets[i % len(cams)]).div_(float(o["image"].numel()))
+        rgs.render_bwd(trainer.kd, g, c, trainer.opts, o["partial_C"], o["partial_T"], dL, trainer.grads(), ws2,
+                       tile_depth=o["tile_depth"])
+
+    rec = []
+    rgs.profile_read(reset=True)
+    for rep in range(2):   # a pass to warm up, then the timed one
+        for i in range(len(cams)):
+            fwd(i)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            rgs.profile_enable(timing=rep == 1, counters=False)
+            e0.record(stream)
+            bwd(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rgs.profile_enable(False, False)
+            if rep == 1:
+                rec.append(e0.elapsed_time(e1))
+    prof = rgs.profile_read(reset=True)
+    trainer.grad.zero_()
+    res["bwd_recompute"] = {"bwd_ms": round(float(np.mean(rec)), 3),
+                            "stages_ms": {k: round(v[0] / len(cams), 3) for k, v in prof["stages"].items() if v[1] > 0},
+                            "instances_per_view": prof["counters"]["instances"] / len(cams)}
+    del outs, ws2
+    torch.cuda.empty_cache()
+    return res
+
+
+class OracleOneThread:
+    """The oracle's step estimate with one host thread, in a fresh interpreter with
+    OMP_NUM_THREADS=1 that touches no GPU; started at the beginning of the run so that its
+    CPU time (about two minutes on the city workload) overlaps the GPU measurements."""
+
+    def __init__(self, workload, budget_s=10.0):
+        code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+                "wl = bench.make_workload(%r, 'cpu'); "
+                "print(json.dumps(bench.oracle_step_estimate(wl, budget_s=%r, threads=1)))"
+                % (ROOT, workload, budget_s))
+        env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+        self.proc = subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                     text=True, env=env)
+
+    def result(self, timeout_s=600) -> dict:
+        try:
+            out, _ = self.proc.communicate(timeout=timeout_s)
+            d = json.loads(out.strip().splitlines()[-1])
+            return {"value": d["value"], "unit": d["unit"], "cores": 1, "sample": d["sample"]}
+        except Exception as e:   # reported, never fatal
+            self.proc.kill()
+            return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -401,6 +567,8 @@ def run_ours(args, rank, world, local_rank):
     from paper_2406_11836_gb300 import workloads as W
     from paper_2406_11836_gb300.render import Trainer
 
+    one_thread = (OracleOneThread(args.workload, budget_s=args.cpu_budget / 2)
+                  if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.profile_only else None)
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     wl = make_workload(args.workload, dev)
@@ -491,7 +659,9 @@ def run_ours(args, rank, world, local_rank):
     pix_per_step = H * Wd
     value = whole_job_mpix_s(world, args.steps, pix_per_step, ms_max)
     e2e = whole_job_mpix_s(world, args.steps, pix_per_step, e2e_ms_max)
-    rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table(), WORKLOAD_NAMES[args.workload])
+    geom = {"sms": sm_count(), "pixels": H * Wd, "K": trainer.kd.K, "N": trainer.n, "params": int(trainer.flat.numel()),
+            "sort_passes": sort_passes(trainer.kd.L, H, Wd)}
+    rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table(), geom, WORKLOAD_NAMES[args.workload])
     line = {
         "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -512,11 +682,14 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0:
         line["partition"] = partition_report(trainer)
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["variants"] = variant_report(trainer, cams, targets, args)
     if rank == 0 and world == 1 and not args.no_foot:
         line["foot_reading"] = foot_reading_report(trainer, cams)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_host = make_workload(args.workload, "cpu")
         line["cpu_baseline"] = oracle_step_estimate(wl_host, budget_s=args.cpu_budget)
+        line["cpu_baseline"]["one_thread"] = one_thread.result() if one_thread else None
     if args.workload == "city" and not args.no_serve and world == 1:
         del trainer, targets, pinned, dev_target
         torch.cuda.empty_cache()
@@ -565,6 +738,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-foot", action="store_true", help="skip the foot-reading forward comparison")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the exact-partials step and the recomputing backward comparisons")
     ap.add_argument("--serve-requests", type=int, default=2200, help="requests of the serving stream")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and timed steps only (no counter replay, end-to-end loop, CPU baseline or "

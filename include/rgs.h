@@ -84,6 +84,12 @@ typedef struct {
     float alpha_max;              /* 0.99: sigma clamp */
     float dilation;               /* 0.3: added to the diagonal of the 2D covariance */
     float bg[3];                  /* background colour behind every ray (merge only) */
+    int cull_occluded;            /* 0: every subset is blended on every ray it meets (its
+                                     partials are the whole Eq. 3-4).  1: a subset is not
+                                     blended on a ray whose transmittance in front of it (the
+                                     merge's prod_{m<r} T_{o_m}, Eq. 5) is below eps_T; its
+                                     partials there are C = 0, T = 1.  The merged image moves
+                                     by less than eps_T times the largest colour. */
 } rgs_render_opts;
 
 typedef struct rgs_kd rgs_kd;          /* KD partition: splits, leaf boxes, subset lists */
@@ -156,13 +162,17 @@ int rgs_render_workspace_size(const rgs_kd* kd, const rgs_gaussians* g, const rg
  * order (Eq. 5) with the background behind, and T_final [H,W] (nullable) receives the
  * product of all T_k.  partial_C and partial_T may both be NULL when image is non-NULL:
  * a forward-only render that keeps the partials on chip (no rgs_render_bwd from it); it
- * also stops a pixel at the first subset whose transmittance in front (the merge's
- * prod_{m<r} T_{o_m}) is below eps_T, which changes the image by less than eps_T times the
- * largest colour (T_final is then that transmittance rather than the full product).  tile_depth (nullable) [ceil(H/16) * ceil(W/16), K] float, indexed
- * by tile then by the subset's position in rgs_view_order, receives per (tile, subset) the
- * camera depth of the last splat blended before every pixel of the tile had dropped below
- * eps_T in that subset (+inf if that did not happen); rgs_render_bwd uses it to skip
- * splats that cannot matter.  Synchronises once with `stream` to size the instance buffers.
+ * always culls as opts->cull_occluded = 1 does: a pixel stops at the first subset whose
+ * transmittance in front (the merge's prod_{m<r} T_{o_m}) is below eps_T, which changes
+ * the image by less than eps_T times the largest colour (T_final is then that
+ * transmittance rather than the full product).  With partial maps and cull_occluded = 1
+ * the culled (pixel, subset) partials are C = 0, T = 1.  tile_depth (nullable)
+ * [ceil(H/16) * ceil(W/16), K] float, indexed by tile then by the subset's position in
+ * rgs_view_order, receives per (tile, subset) the camera depth of the last splat blended
+ * before every pixel of the tile had dropped below eps_T in that subset (+inf if that did
+ * not happen, -inf if culling left no pixel of the tile to blend); rgs_render_bwd uses it
+ * to skip splats that cannot matter.  Synchronises once with `stream` to size the
+ * instance buffers.
  * Errors: EINVAL (shapes, sh_degree, tile != 16, L > 6 for rendering, non-finite camera,
  * misaligned pointers), EOVERFLOW (workspace too small; required size via
  * rgs_last_required_workspace()), ECUDA. */
@@ -171,15 +181,21 @@ int rgs_render_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* c
                    void* workspace, size_t ws_bytes, void* stream);
 
 /* rgs_render_fwd for callers that cannot allocate device memory (the paper has no
- * counterpart: this is a deployment variant).  Same arguments and results as
- * rgs_render_fwd minus the workspace, which comes from a fixed 64 MiB device array
- * inside the library; nothing is allocated.
+ * counterpart: this is a deployment variant), such as a real-time thread that must not
+ * block in the allocator or a host program that hands all device memory out from its own
+ * pool.  Same arguments and results as rgs_render_fwd minus the workspace, which comes
+ * from a fixed 64 MiB device array inside the library; nothing is allocated.  Like
+ * rgs_render_fwd it synchronises `stream` once, after the projection, to size the
+ * instance buffers.
  * The first call on a device looks the array up (make it before any stream capture);
- * every GPU that loads the library holds the array until exit.  All calls share it:
- * calls that overlap on the GPU race and must be serialised by the caller.  A render
- * whose workspace exceeds the array returns RGS_EOVERFLOW with the needed size in
- * rgs_last_error() (roughly 150 bytes per splat plus 16 per tile instance).  Tracing
- * records no events for this call. */
+ * every GPU that loads the library holds the array until exit.  All calls share it and
+ * it keeps the last call's contents (the render clears what must start at zero): calls
+ * that overlap on the GPU race and must be serialised by the caller.  A render whose
+ * workspace exceeds the array (roughly 150 bytes per splat plus 16 per tile instance)
+ * returns RGS_EOVERFLOW; rgs_last_error() gives the render's reason (before binning: the
+ * bytes needed for the splats; after binning: the instance count) and
+ * rgs_last_required_workspace() the bytes needed (exact after binning; before binning an
+ * estimate that assumes 2^20 instances).  Tracing records no events for this call. */
 int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
                            const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
                            float* T_final, float* tile_depth, void* stream);
@@ -223,16 +239,39 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
  * caller zeroes them).  A splat shared by several subsets accumulates into its single
  * parameter slot.  partial_C/partial_T (and tile_depth when non-NULL) must be the ones
  * rgs_render_fwd wrote for the same inputs.
+ * A pixel whose transmittance in front of a subset (the merge's prod_{m<r} T_{o_m}) is
+ * below eps_T takes no gradient from that subset or any behind it (they would be scaled by
+ * less than eps_T).
  * The per-tile lists: when `workspace` (same pointer and size) still holds the lists of
  * the rgs_render_fwd call that wrote partial_C/partial_T with these kd, g, cam and opts
  * (no render into that workspace since; the forward stamps it), they are replayed as the
  * forward left them, cut back to what it staged, and nothing is re-derived.  Otherwise
  * they are re-derived; with tile_depth they then omit the splats lying behind a (tile,
  * subset) the forward had already saturated.  Neither changes a result.
+ * The library recognises "these g" by the parameter POINTERS (and n, sh_degree), not by
+ * their contents: the parameters must not change between the forward and its backward
+ * (an in-place update with the same pointers would replay lists built for the old values
+ * and give wrong gradients).  To back-propagate through changed parameters, render again.
  * Synchronises once with `stream`.  Errors as rgs_render_fwd. */
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                    const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
                    const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream);
+
+/* Backward of a render through the flat form (an alternative to rgs_render_bwd): Eq. 5
+ * equals flat blending (Eq. 2) exactly (the paper's appendix proof), so the gradients of
+ * the merged image can be taken over each pixel's concatenated list (the subsets in view
+ * order, each in depth order) in ONE front-to-back replay with the global transmittance:
+ * dL/dsigma_i = T_i <g, c_i> - <g, C - A_i> / (1 - sigma_i), C the image (background
+ * included), A_i the colour blended up to and including pair i.  Needs only the image the
+ * forward wrote (rgs_render_fwd with or without partial maps: `image` [3,H,W]) and
+ * dL_dimage; no partial maps are read or needed.  It replays the forward's own decisions:
+ * each subset from T = 1 with its freeze points, the transmittance in front of it rebuilt
+ * from the subset ends, a subset skipped where that is below eps_T.  Lists, tile_depth,
+ * accumulation into `grads`, the parameter-pointer rule and errors as rgs_render_bwd (the
+ * lists are replayed when `workspace` holds those of the forward that wrote `image`). */
+int rgs_render_bwd_flat(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                        const float* image, const float* dL_dimage, const float* tile_depth,
+                        const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ Adam (Sec. 4 details)
  * One Adam step over a flat parameter buffer split into `nseg` contiguous segments, each
@@ -351,14 +390,16 @@ int rgs_serve_destroy(rgs_server* srv);
  * others fail (slower; keep it off where time is measured).  Process-wide.
  * rgs_profile_read synchronises with the recorded events and writes, per stage index
  * 0..rgs_profile_num_stages()-1, the accumulated milliseconds (ms_host) and pass counts
- * (launches_host), and counters_host[14] = {fwd pairs evaluated, fwd pairs contributing,
+ * (launches_host), and counters_host[16] = {fwd pairs evaluated, fwd pairs contributing,
  * bwd pairs evaluated, bwd pairs contributing, tile instances, visible splats, kernel
  * launches of the library (counted whether or not profiling is on), fwd pairs failing the
  * Mahalanobis test, failing the ball test, failing the Eq. 6 subset test, fwd pairs
  * evaluated for splats held by several subsets, fwd instances staged before their tile's
  * pixels were all done, fwd instances contributing to at least one pixel, fwd warp passes
  * over one record-list entry (pairs evaluated / (32 x passes): the share of a warp's lanes
- * whose pixel is still blending)}, summed since the last reset.  Any
+ * whose pixel is still blending), fwd pairs evaluated where the merged transmittance in
+ * front of their subset is below eps_T, bwd warp passes over one record-list entry},
+ * summed since the last reset.  Any
  * output pointer may be NULL.  reset != 0 clears the sums. */
 int rgs_profile_enable(int flags);
 int rgs_profile_num_stages(void);

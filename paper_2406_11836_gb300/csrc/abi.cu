@@ -168,6 +168,10 @@ int check_opts(const rgs_render_opts* o) {
         set_error("opts: need trunc_mult > 0, 0 < alpha_min < alpha_max < 1, eps_T >= 0, dilation >= 0");
         return RGS_EINVAL;
     }
+    if (o->cull_occluded != 0 && o->cull_occluded != 1) {
+        set_error("opts: cull_occluded must be 0 or 1");
+        return RGS_EINVAL;
+    }
     return RGS_OK;
 }
 
@@ -219,6 +223,7 @@ void fill_view(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, 
     vp->trunc_mult = opts->trunc_mult; vp->eps_T = opts->eps_T;
     vp->alpha_min = opts->alpha_min; vp->alpha_max = opts->alpha_max; vp->dilation = opts->dilation;
     for (int c = 0; c < 3; ++c) vp->bg[c] = opts->bg[c];
+    vp->cull_occluded = opts->cull_occluded;
     vp->L = kd->b.L;
     vp->K = 1 << kd->b.L;
     vp->sh_degree = g ? g->sh_degree : 0;
@@ -317,6 +322,7 @@ struct ListStamp {
     rgs_render_opts opts;
     const float* pC;
     const float* pT;
+    const float* image;
     size_t ws_bytes;
     bool alt;           // payloads in ival_alt
     int64_t I;          // instances
@@ -498,7 +504,7 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
     if (keep_lists) stamp_erase(workspace);   // its lists are about to be replaced
     int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, host_counters, &I);
     if (rc) return rc;
-    const bool keep = keep_lists && partial_C != nullptr;   // a backward may follow
+    const bool keep = keep_lists && (partial_C != nullptr || image != nullptr);   // a backward may follow
     {
         ProfScope ps(ST_BLEND_FWD, s);
         rc = launch_blend_fwd(vp, tp, b, ival, partial_C, partial_T, image, T_final, tile_depth, s, keep);
@@ -512,6 +518,7 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
         st.opts = *opts;
         st.pC = partial_C;
         st.pT = partial_T;
+        st.image = image;
         st.ws_bytes = ws_bytes;
         st.alt = ival == b.ival_alt;
         st.I = I;
@@ -526,9 +533,10 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
 
 // The backward of the forward whose lists `workspace` holds, if the arguments are that
 // forward's: replays its lists (no projection, sorting or emission).  Returns 1 when it
-// does not apply (the caller re-derives the lists), else a status.
+// does not apply (the caller re-derives the lists), else a status.  image != nullptr: the
+// flat form (the forward's image must be the one given; its partial maps are not read).
 int render_bwd_reuse(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
-                     const float* partial_C, const float* partial_T, const float* dL_dimage,
+                     const float* partial_C, const float* partial_T, const float* image, const float* dL_dimage,
                      const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, cudaStream_t s) {
     ListStamp st;
     {
@@ -537,9 +545,9 @@ int render_bwd_reuse(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera*
         if (it == g_stamps.end()) return 1;
         st = it->second;
     }
+    const bool same_maps = image ? st.image == image : (st.pC == partial_C && st.pT == partial_T);
     if (st.kd != kd || !same_gaussians(st.g, *g) || memcmp(&st.cam, cam, sizeof *cam) != 0 ||
-        memcmp(&st.opts, opts, sizeof *opts) != 0 || st.pC != partial_C || st.pT != partial_T ||
-        st.ws_bytes != ws_bytes)
+        memcmp(&st.opts, opts, sizeof *opts) != 0 || !same_maps || st.ws_bytes != ws_bytes)
         return 1;
     ViewParams vp;
     TreeParams tp;
@@ -561,7 +569,43 @@ int render_bwd_reuse(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera*
     {
         ProfScope ps(ST_BLEND_BWD, s);
         RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
-        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, st.I, g->n, s);
+        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, image, dL_dimage, st.I, g->n, s);
+        if (rc) return rc;
+    }
+    ProfScope ps(ST_PROJECT_BWD, s);
+    return launch_project_bwd(*g, *grads, vp, b, s);
+}
+
+// Both backward forms: replay the forward's lists if the workspace holds them, else
+// re-derive them (depth-culled by tile_depth when given).
+int render_bwd_any(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                   const float* partial_C, const float* partial_T, const float* image, const float* dL_dimage,
+                   const float* tile_depth, const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes,
+                   cudaStream_t s) {
+    if (!dL_dimage || !grads || !grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits ||
+        !grads->sh) {
+        set_error("render_bwd: NULL argument");
+        return RGS_EINVAL;
+    }
+    if (!aligned(grads->quats, 16)) { set_error("render_bwd: grads->quats must be 16-byte aligned"); return RGS_EINVAL; }
+    int rc;
+    if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
+    if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
+    rc = render_bwd_reuse(kd, g, cam, opts, partial_C, partial_T, image, dL_dimage, grads, workspace, ws_bytes, s);
+    if (rc != 1) return rc;
+    // re-derive the lists (depth-culled by tile_depth when given)
+    stamp_erase(workspace);
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int64_t I = 0;
+    rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, tile_depth, nullptr, &I);
+    if (rc) return rc;
+    {
+        ProfScope ps(ST_BLEND_BWD, s);
+        RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
+        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, image, dL_dimage, I, g->n, s);
         if (rc) return rc;
     }
     ProfScope ps(ST_PROJECT_BWD, s);
@@ -587,6 +631,7 @@ void rgs_default_opts(rgs_render_opts* o) {
     o->alpha_max = 0.99f;
     o->dilation = 0.3f;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.f;
+    o->cull_occluded = 0;
 }
 
 int rgs_kd_partition(const rgs_gaussians* g, int depth_L, float trunc_mult, rgs_kd** out, void* stream) {
@@ -754,35 +799,23 @@ int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_came
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                    const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
                    const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream) {
-    if (!partial_C || !partial_T || !dL_dimage || !grads || !grads->means || !grads->log_scales || !grads->quats ||
-        !grads->opacity_logits || !grads->sh) {
-        set_error("render_bwd: NULL argument");
+    if (!partial_C || !partial_T) {
+        set_error("render_bwd: NULL partial maps");
         return RGS_EINVAL;
     }
-    if (!aligned(grads->quats, 16)) { set_error("render_bwd: grads->quats must be 16-byte aligned"); return RGS_EINVAL; }
-    cudaStream_t s = (cudaStream_t)stream;
-    int rc;
-    if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
-    if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
-    rc = render_bwd_reuse(kd, g, cam, opts, partial_C, partial_T, dL_dimage, grads, workspace, ws_bytes, s);
-    if (rc != 1) return rc;
-    // re-derive the lists (depth-culled by tile_depth when given)
-    stamp_erase(workspace);
-    ViewParams vp;
-    TreeParams tp;
-    RasterBuffers b;
-    const uint32_t* ival = nullptr;
-    int64_t I = 0;
-    rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, tile_depth, nullptr, &I);
-    if (rc) return rc;
-    {
-        ProfScope ps(ST_BLEND_BWD, s);
-        RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
-        rc = launch_blend_bwd(vp, tp, b, ival, partial_C, partial_T, dL_dimage, I, g->n, s);
-        if (rc) return rc;
+    return render_bwd_any(kd, g, cam, opts, partial_C, partial_T, nullptr, dL_dimage, tile_depth, grads, workspace,
+                          ws_bytes, (cudaStream_t)stream);
+}
+
+int rgs_render_bwd_flat(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
+                        const float* image, const float* dL_dimage, const float* tile_depth,
+                        const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream) {
+    if (!image) {
+        set_error("render_bwd_flat: NULL image");
+        return RGS_EINVAL;
     }
-    ProfScope ps(ST_PROJECT_BWD, s);
-    return launch_project_bwd(*g, *grads, vp, b, s);
+    return render_bwd_any(kd, g, cam, opts, nullptr, nullptr, image, dL_dimage, tile_depth, grads, workspace, ws_bytes,
+                          (cudaStream_t)stream);
 }
 
 int rgs_merge_partials(const float* partial_C, const float* partial_T, const int32_t* order_dev, int K, int H, int W,

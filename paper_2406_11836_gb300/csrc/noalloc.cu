@@ -1,11 +1,13 @@
 // Forward render for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) around a render: a
-// real-time thread that must not block on the allocator, a host program that hands all
-// device memory out from its own pool, code that runs between the start and the end of
-// a stream capture.  rgs_render_fwd_noalloc serves them: it does the same work as
-// rgs_render_fwd but takes its workspace from a fixed array in this file instead of
-// from the caller, and allocates nothing itself.
+// real-time thread that must not block on the allocator (cudaMalloc can take a lock and
+// wait for the device), or a host program that hands all device memory out from its own
+// pool and so has none left to give a render.  rgs_render_fwd_noalloc serves them: it
+// does the same work as rgs_render_fwd but takes its workspace from a fixed array in
+// this file instead of from the caller, and allocates nothing itself.  Like
+// rgs_render_fwd it synchronises its stream once, after the projection, to size the
+// instance buffers.
 //
 // The array (kScratchBytes) is a file-scope __device__ variable: every GPU that loads the
 // library holds it until the process exits.  In host code its name is only a host-side
@@ -15,6 +17,7 @@
 // previous call's contents: the render clears what has to start at zero (counters, tile
 // ranges) itself, and calls that overlap on the GPU (several streams, several host
 // threads) race on the array — serialise them.
+#include <cstdio>
 #include <mutex>
 
 #include "rgs_internal.cuh"
@@ -58,14 +61,17 @@ extern "C" int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, 
         scratch = g_scratch_ptr[dev];
     }
     unsigned long long counts[2] = {0, 0};   // host copy of the instance counts (no pinned buffer)
+    rgs::set_required_workspace(0);          // set again only when the scratch is what was too small
     rgs::prof_suppress(true);                // tracing would create CUDA events
     const int rc = rgs::render_fwd_into(kd, g, cam, opts, partial_C, partial_T, image, T_final, tile_depth, scratch,
                                         kScratchBytes, (cudaStream_t)stream, counts, false);
     rgs::prof_suppress(false);
-    if (rc == RGS_EOVERFLOW) {
-        const size_t need = rgs_last_required_workspace();
-        rgs::set_error("render_fwd_noalloc: this render needs %zu bytes of scratch, more than the fixed %zu "
-                       "(use rgs_render_fwd with a caller workspace)", need, kScratchBytes);
+    if (rc == RGS_EOVERFLOW && rgs_last_required_workspace() > kScratchBytes) {
+        // keep the render's own reason (before or after binning) and say what to do
+        char why[384];
+        snprintf(why, sizeof why, "%s", rgs_last_error());
+        rgs::set_error("render_fwd_noalloc: the fixed scratch of %zu bytes is too small (%s); "
+                       "use rgs_render_fwd with a caller workspace", kScratchBytes, why);
     }
     return rc;
 }

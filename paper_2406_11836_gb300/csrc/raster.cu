@@ -572,16 +572,25 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     s_img[2][tid] = 0.f;
     s_img[3][tid] = 1.f;
 
-    // Without partial maps only the image is wanted: a pixel whose transmittance in front of
-    // subset k (the merge's P) is below eps_T skips k and every later subset (they change its
-    // colour by less than eps_T max(rgb)), and a tile with no such pixel left skips the subset.
-    const bool image_only = pC == nullptr;
+    // Culling (always without partial maps, where only the image is wanted; with them when
+    // the options ask for it): a pixel whose transmittance in front of subset k (the merge's
+    // P) is below eps_T skips k and every later subset (they change its colour by less than
+    // eps_T max(rgb); its partials there stay C = 0, T = 1), and a tile with no pixel left
+    // skips the subset.
+    const bool cull = pC == nullptr || vp.cull_occluded != 0;
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         const uint2 rg = ranges[r];
-        const bool live = inside && !(image_only && s_img[3][tid] < vp.eps_T);
-        if (image_only && __syncthreads_count(live) == 0) {
-            if (tile_depth && threadIdx.x == 0) tile_depth[r] = kInfF;
+        const bool live = inside && !(cull && s_img[3][tid] < vp.eps_T);
+        if (cull && __syncthreads_count(live) == 0) {
+            if (tile_depth && threadIdx.x == 0) tile_depth[r] = -kInfF;   // nothing blended, nothing needed
+            if (ends && threadIdx.x == 0) ends[r].y = rg.x;                 // nothing for a backward to replay
+            if (inside && pC) {
+                pC[((size_t)k * 3 + 0) * HW + pix] = 0.f;
+                pC[((size_t)k * 3 + 1) * HW + pix] = 0.f;
+                pC[((size_t)k * 3 + 2) * HW + pix] = 0.f;
+                pT[(size_t)k * HW + pix] = 1.f;
+            }
             continue;
         }
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
@@ -986,12 +995,20 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
     s_img[1][tid] = 0.f;
     s_img[2][tid] = 0.f;
     s_img[3][tid] = 1.f;
-    const bool image_only = pC == nullptr;
+    const bool cull = pC == nullptr || vp.cull_occluded != 0;   // as in blend_fwd_tile
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         const uint2 rg = ranges[r];
-        const bool live = inside && !(image_only && s_img[3][tid] < vp.eps_T);
-        if (image_only && __syncthreads_count(live) == 0) continue;
+        const bool live = inside && !(cull && s_img[3][tid] < vp.eps_T);
+        if (cull && __syncthreads_count(live) == 0) {
+            if (inside && pC) {
+                pC[((size_t)k * 3 + 0) * HW + pix] = 0.f;
+                pC[((size_t)k * 3 + 1) * HW + pix] = 0.f;
+                pC[((size_t)k * 3 + 2) * HW + pix] = 0.f;
+                pT[(size_t)k * HW + pix] = 1.f;
+            }
+            continue;
+        }
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         float C0 = 0.f, C1 = 0.f, C2 = 0.f;
         float T = live ? 1.f : 0.f;
@@ -1129,15 +1146,22 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
                  : "memory");
 }
 
-template <bool kCount>
+// kFlat = false: the adjoint of Eq. 5 and each subset's replay from its stored partials
+// (pC, pT; `img` unused).  kFlat = true: the adjoint of the flat form (Eq. 2, which Eq. 5
+// equals exactly: appendix proof) from the merged image alone (`img`; pC, pT unused): one
+// front-to-back replay of the tile's concatenated subset-ordered list per pixel, with the
+// transmittance in front of each subset (P) rebuilt from the replayed subset ends, and
+// dL/dsigma_i = T_i <g, c_i> - <g, C - A_i> / (1 - sigma_i) where C is the image and A_i the
+// colour blended up to and including pair i (both global).
+template <bool kCount, bool kFlat>
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
-                 const float* __restrict__ gI, float4* __restrict__ g2d, uint32_t n_inst, uint32_t n_splats,
-                 unsigned long long* __restrict__ pairs) {
+                 const float* __restrict__ img, const float* __restrict__ gI, float4* __restrict__ g2d,
+                 uint32_t n_inst, uint32_t n_splats, unsigned long long* __restrict__ pairs) {
     // <g, S_r> of this pixel for every rank: private to the thread, in local memory (cached),
-    // so that shared memory does not grow with K
-    float behind_r[1 << kMaxRenderDepth];
+    // so that shared memory does not grow with K (the flat form needs none)
+    float behind_r[kFlat ? 1 : 1 << kMaxRenderDepth];
     uint32_t n_eval = 0, n_contrib = 0, n_iter = 0;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
@@ -1174,7 +1198,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         g1 = gI[1 * HW + pix];
         g2 = gI[2 * HW + pix];
     }
-    {
+    if (!kFlat) {
         float behind = g0 * vp.bg[0] + g1 * vp.bg[1] + g2 * vp.bg[2];
         for (int r = vp.K - 1; r >= 0; --r) {
             behind_r[r] = behind;
@@ -1186,37 +1210,54 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             }
         }
     }
+    // flat form: <g, C> of the whole pixel, and the colour blended so far (acc) carried over
+    // subsets
+    const float qflat = kFlat && inside ? g0 * img[0 * HW + pix] + g1 * img[1 * HW + pix] + g2 * img[2 * HW + pix]
+                                        : 0.f;
+    float acc = 0.f;   // <gC, colour blended so far> (per subset; over all subsets in the flat form)
     float Pm = 1.f;
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         float Ck0 = 0.f, Ck1 = 0.f, Ck2 = 0.f, Tk = 1.f;
-        if (inside) {
+        if (!kFlat && inside) {
             Ck0 = pC[((size_t)k * 3 + 0) * HW + pix];
             Ck1 = pC[((size_t)k * 3 + 1) * HW + pix];
             Ck2 = pC[((size_t)k * 3 + 2) * HW + pix];
             Tk = pT[(size_t)k * HW + pix];
         }
         const float gC0 = g0 * Pm, gC1 = g1 * Pm, gC2 = g2 * Pm;
-        const float gT = Pm * behind_r[r];
         s_gc[threadIdx.x][0] = gC0;   // read by the lanes of this warp after the next barrier
         s_gc[threadIdx.x][1] = gC1;
         s_gc[threadIdx.x][2] = gC2;
-        float q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
+        // q - acc = <g, colour behind the current pair> (times P for the per-subset form)
+        float q;
+        if (kFlat) {
+            q = qflat;
+        } else {
+            const float gT = Pm * behind_r[r];
+            q = gC0 * Ck0 + gC1 * Ck1 + gC2 * Ck2 + gT * Tk;
+            acc = 0.f;
+        }
         // a pixel whose transmittance in front of this subset is below eps_T gets gradients
         // scaled by less than eps_T from it: the subset is skipped there, as an image-only
         // forward skips it
         const bool front_open = Pm >= vp.eps_T;
-        Pm *= Tk;
+        if (!kFlat) Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
         uint2 rg = ranges[(size_t)tile * vp.K + r];
         rg.y = min(rg.y, n_inst);   // lists handed over from a forward: never read past them
         rg.x = min(rg.x, rg.y);
-        const bool active = inside && front_open && (gC0 != 0.f || gC1 != 0.f || gC2 != 0.f || gT != 0.f);
-        if (__syncthreads_count(active) == 0) continue;
+        const bool active = inside && front_open && (g0 != 0.f || g1 != 0.f || g2 != 0.f);
+        // an inactive pixel stays inactive for every later subset (P only falls): nothing of
+        // the tile is left to replay once all are
+        if (__syncthreads_count(active) == 0) break;
         // replay of the forward: the same pairs, the same freeze points (an inactive pixel
-        // is frozen from the start: its gradients are zero)
+        // is frozen from the start, with q = acc: its pairs get zero gradients)
         bool frozen = !active;
-        float T = active ? 1.f : 0.f, acc = 0.f;   // acc = <gC, colour accumulated so far>
+        float T = active ? 1.f : 0.f;
+        float Tkeep = 1.f;     // transmittance of the subset where the pixel froze (flat form)
+        const float qkeep = q;
+        if (!active) q = acc;
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
@@ -1241,6 +1282,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                     // frozen as in the forward: later pairs get sigma * T = 0, and q = acc
                     // makes their adjoint vanish too
                     frozen = true;
+                    Tkeep = T;
                     T = 0.f;
                     q = acc;
                 }
@@ -1355,6 +1397,11 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                 }
             }
             if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) break;
+        }
+        if (kFlat && active) {
+            // the subset's end transmittance, as the forward stored it: P in front of the next
+            Pm *= frozen ? Tkeep : T;
+            q = qkeep;   // undo a freeze's q = acc: later subsets see the whole pixel again
         }
     }
     if (kCount) {
@@ -1540,28 +1587,40 @@ int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tre
 }
 
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     const float* partial_C, const float* partial_T, const float* dL_dimage, int64_t n_inst,
-                     int64_t n_splats, cudaStream_t s) {
+                     const float* partial_C, const float* partial_T, const float* image, const float* dL_dimage,
+                     int64_t n_inst, int64_t n_splats, cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
     const size_t smem = 0;
     static bool attr_set = false;
     if (!attr_set) {
         // about 58 KB per CTA: three CTAs per SM need most of the carveout as shared memory
-        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           cudaSharedmemCarveoutMaxShared));
-        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_kernel<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           cudaSharedmemCarveoutMaxShared));
         attr_set = true;
     }
     unsigned long long* pairs = prof_pair_counters();
-    if (pairs)
-        blend_bwd_kernel<true><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                                 dL_dimage, b.g2d, (uint32_t)n_inst,
-                                                                 (uint32_t)n_splats, pairs);
+    const bool flat = image != nullptr;
+    const uint32_t ni = (uint32_t)n_inst, ns = (uint32_t)n_splats;
+    if (flat && pairs)
+        blend_bwd_kernel<true, true><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, nullptr, nullptr,
+                                                                       image, dL_dimage, b.g2d, ni, ns, pairs);
+    else if (flat)
+        blend_bwd_kernel<false, true><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, nullptr, nullptr,
+                                                                        image, dL_dimage, b.g2d, ni, ns, nullptr);
+    else if (pairs)
+        blend_bwd_kernel<true, false><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C,
+                                                                        partial_T, nullptr, dL_dimage, b.g2d, ni, ns,
+                                                                        pairs);
     else
-        blend_bwd_kernel<false><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                                  dL_dimage, b.g2d, (uint32_t)n_inst,
-                                                                  (uint32_t)n_splats, nullptr);
+        blend_bwd_kernel<false, false><<<grid, kBlendThreads, smem, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C,
+                                                                         partial_T, nullptr, dL_dimage, b.g2d, ni, ns,
+                                                                         nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

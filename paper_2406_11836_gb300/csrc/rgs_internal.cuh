@@ -70,6 +70,9 @@ struct ViewParams {
     // 1: x_i is the foot of the perpendicular from the centre onto the pixel ray (the
     // comparison reading of Sec. 3.2, forward only); 0: the ray point at the splat's depth
     int foot;
+    // 1: a subset is not blended on a ray whose merged transmittance in front of it is
+    // below eps_T (rgs_render_opts::cull_occluded)
+    int cull_occluded;
 };
 constexpr int kClipTable = 64 * kMaxRenderDepth;   // entries of one view's plane-template table
 
@@ -247,10 +250,11 @@ int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBu
                       float* partial_C, float* partial_T, float* image, float* T_final,
                       unsigned long long* over, cudaStream_t s);
 // n_inst: instances in ival (ranges are clamped to it); n_splats: records in b.rec (other
-// payloads are skipped).
+// payloads are skipped).  image != nullptr: the flat form (from the merged image; the
+// partial maps are not read), else the per-subset form from the partial maps.
 int launch_blend_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
-                     const float* partial_C, const float* partial_T, const float* dL_dimage, int64_t n_inst,
-                     int64_t n_splats, cudaStream_t s);
+                     const float* partial_C, const float* partial_T, const float* image, const float* dL_dimage,
+                     int64_t n_inst, int64_t n_splats, cudaStream_t s);
 int launch_merge(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],
                  float* image, float* T_out, cudaStream_t s);
 int launch_merge_bwd(const float* pC, const float* pT, const int32_t* order, int K, int H, int W, const float bg[3],

@@ -67,7 +67,7 @@ class Trainer:
     LR = {"quats": 1e-3, "log_scales": 5e-3, "opacity_logits": 5e-2, "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20}
 
     def __init__(self, scene, depth_L: int, opts: rgs.RenderOpts | None = None, max_steps: int = 60000,
-                 device="cuda", repartition_every: int = 0):
+                 device="cuda", repartition_every: int = 0, cull_occluded: bool = True, backward: str = "flat"):
         n = scene.n
         self.n = n
         self.sh_degree = scene.sh_degree
@@ -97,7 +97,18 @@ class Trainer:
         # (0: never); the planes change, the parameters and moments do not
         self.repartition_every = int(repartition_every)
         self.step_count = 0
-        self.opts = opts if opts is not None else rgs.default_opts()
+        # by default a subset is not blended on rays already saturated in front of it
+        # (rgs_render_opts.cull_occluded): the image moves by less than eps_T max(rgb), and
+        # the backward skips those rays anyway
+        self.opts = opts if opts is not None else rgs.default_opts(cull_occluded=1 if cull_occluded else 0)
+        # "flat" (default, the faster on the city workload): the forward writes the image
+        # only and the backward replays each pixel's concatenated list once
+        # (rgs_render_bwd_flat, exact by the equality of Eq. 5 and Eq. 2); "subsets": the
+        # forward writes the partial maps and the backward routes dL/dimage through the
+        # merge to each subset (rgs_render_bwd)
+        if backward not in ("subsets", "flat"):
+            raise ValueError(f"backward must be 'subsets' or 'flat', not {backward!r}")
+        self.backward = backward
         self.ws = rgs.Workspace(device)
         self.kd = rgs.kd_partition(self.gaussians(), depth_L, float(self.opts.trunc_mult))
 
@@ -156,13 +167,18 @@ class Trainer:
         """Forward, L1 loss (scaled by weight) and backward of one view, adding its gradients
         to the gradient buffer; the backward follows its own forward, so it replays the
         forward's lists."""
-        out = rgs.render_fwd(self.kd, g, cam, self.opts, self.ws, image=True)
+        flat = self.backward == "flat"
+        out = rgs.render_fwd(self.kd, g, cam, self.opts, self.ws, image=True, partials=not flat)
         img = out["image"]
         diff = img - target
         loss = diff.abs().mean() if return_loss else None
         dL = torch.sign(diff).div_(float(diff.numel()) / weight)
-        rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws,
-                       tile_depth=out["tile_depth"])
+        if flat:
+            rgs.render_bwd_flat(self.kd, g, cam, self.opts, img, dL, self.grads(), self.ws,
+                                tile_depth=out["tile_depth"])
+        else:
+            rgs.render_bwd(self.kd, g, cam, self.opts, out["partial_C"], out["partial_T"], dL, self.grads(), self.ws,
+                           tile_depth=out["tile_depth"])
         return loss
 
     def step(self, cam, target: torch.Tensor, return_loss: bool = True):

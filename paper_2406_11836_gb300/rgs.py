@@ -42,7 +42,7 @@ class CameraC(ctypes.Structure):
 
 class RenderOpts(ctypes.Structure):
     _fields_ = [("tile", c_int), ("trunc_mult", c_float), ("eps_T", c_float), ("alpha_min", c_float),
-                ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3)]
+                ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3), ("cull_occluded", c_int)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -88,6 +88,8 @@ def lib():
                                       c_void_p]
     L.rgs_render_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                  c_void_p, c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
+    L.rgs_render_bwd_flat.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
+                                      c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_merge_partials.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_void_p]
     L.rgs_merge_partials_bwd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -265,7 +267,7 @@ def _retry(call, ws: Workspace):
 def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image=True, stream=None, out=None,
                partials=True):
     """Partial maps [K,3,H,W] / [K,H,W] and, if image, the merged image [3,H,W] and T_final.
-    partials=False renders the image only (forward only, no backward from it)."""
+    partials=False renders the image only (its backward: render_bwd_flat)."""
     H, W = int(cam.height), int(cam.width)
     dev = torch.device("cuda", torch.cuda.current_device())
     if out is None:
@@ -364,6 +366,20 @@ def adam_step(param, grad, m, v, seg_offsets, seg_lr, step, beta1=0.9, beta2=0.9
 
 def position_lr(step, max_steps, lr_init=1.6e-4, lr_final=1.6e-6) -> float:
     return float(lib().rgs_position_lr(int(step), int(max_steps), float(lr_init), float(lr_final)))
+
+
+def render_bwd_flat(kd: KD, g: Gaussians, cam, opts: RenderOpts, image, dL_dimage, grads, ws: Workspace,
+                    stream=None, tile_depth=None):
+    """Flat-form backward (one front-to-back replay per pixel over the concatenated subset
+    lists, from the forward's image; no partial maps).  Accumulates into grads like
+    render_bwd."""
+    gg = GaussianGrads(*(_ptr(t) for t in grads))
+    c = camera_c(cam)
+    s = _stream(stream)
+    dL = dL_dimage.contiguous()
+    _retry(lambda: lib().rgs_render_bwd_flat(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
+                                             _ptr(image), _ptr(dL), _ptr(tile_depth), ctypes.byref(gg), ws.ptr(),
+                                             ws.nbytes, s), ws)
 
 
 # --------------------------------------------------------------------------- tracing
@@ -485,7 +501,7 @@ class Server:
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_render_fwd_foot", "rgs_merge_partials", "rgs_merge_partials_bwd",
-               "rgs_render_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
+               "rgs_render_bwd", "rgs_render_bwd_flat", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
                "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",

@@ -18,7 +18,8 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import FWD_FLAGS, MAX_FLAGGED, PART_FLAGS, PIXEL_TOL, image_at, oracle_opts, partials_at
+from _helpers import (FWD_FLAGS, MAX_FLAGGED, PART_FLAGS, PART_MAX_FLAGGED, PIXEL_TOL, image_at, oracle_opts,
+                      partials_at)
 from oracle import oracle as O
 from paper_2406_11836_gb300 import workloads as W
 
@@ -46,7 +47,8 @@ def foot_opts(opts=None, eps_T=0.0):
     return o
 
 
-def _check_foot(R, scene, cam, L, pix=None, opts=None, partials=True, differ=True, max_flagged=MAX_FLAGGED):
+def _check_foot(R, scene, cam, L, pix=None, opts=None, partials=True, differ=True, max_flagged=MAX_FLAGGED,
+                part_cap=PART_MAX_FLAGGED):
     dev = scene.to("cuda")
     kd = R.kd_partition(dev, L)
     opts = opts if opts is not None else R.default_opts()
@@ -56,10 +58,11 @@ def _check_foot(R, scene, cam, L, pix=None, opts=None, partials=True, differ=Tru
     assert out["overflow"] == 0
     pix = np.arange(cam.width * cam.height) if pix is None else pix
     flat = O.render(scene, cam, foot_opts(opts), pix=pix)
+    # the foot's order key is a float pair good to ~1e-12 and its ball test differs from the
+    # depth plane's: pixels the oracle flags as ambiguous are left out (at most 0.1%)
     ok = (flat["flags"] & FWD_FLAGS) == 0
     assert ok.mean() >= 1 - max_flagged, ok.mean()
-    got = image_at(out["image"], pix)
-    err = np.abs(got - flat["C"])[ok].max()
+    err = np.abs(image_at(out["image"], pix) - flat["C"])[ok].max()
     assert err <= PIXEL_TOL, err
     if partials:
         terr = np.abs(out["T_final"].reshape(-1).double().cpu().numpy()[pix] - flat["T"])[ok].max()
@@ -68,6 +71,7 @@ def _check_foot(R, scene, cam, L, pix=None, opts=None, partials=True, differ=Tru
         hier = O.render(scene, cam, foot_opts(opts, eps_T=float(np.float32(1e-6))), pix=pix, hier=True, L=L,
                         axis=axis, split=split)
         okp = (hier["flags"] & PART_FLAGS) == 0
+        assert okp.mean() >= 1 - part_cap, okp.mean()
         pc, pt = partials_at(out["partial_C"], out["partial_T"], pix)
         perr = max(np.abs(pc - hier["partC"])[okp].max(), np.abs(pt - hier["partT"])[okp].max())
         assert perr <= PIXEL_TOL, perr
@@ -138,7 +142,8 @@ def test_foot_edge_cases(R):
     one = W.uniform_cube_scene(1, seed=2, log_scale_mean=-1.0)
     _check_foot(R, one, W.axis_camera((0.0, 0.0, -3.0), 1, 1), 0, opts=opts, differ=False)
     _check_foot(R, W.uniform_cube_scene(500, seed=5, log_scale_mean=-2.0),
-                W.axis_camera((0.1, 0.0, -2.5), 7, 5, fov_x_deg=10.0), 3, differ=False)
+                W.axis_camera((0.1, 0.0, -2.5), 7, 5, fov_x_deg=10.0), 3, differ=False, max_flagged=0.1,
+                part_cap=1.0)   # 35 rays along a split plane: a few are at a plane or a threshold
 
 
 def test_foot_rejects_missing_outputs(R):
@@ -161,10 +166,10 @@ def test_foot_fullsize_sampled(R, name, view, n_pix, max_flagged, max_over):
     8 subsets; 10M at 3840x2160 with 16): the whole frame on the GPU, a seeded sample of
     pixels in the oracle.  In the city view the foot's ball test, which accepts more rays
     than the depth plane's, leaves ~1.1% of the sampled pixels with a pair at a truncation
-    threshold (0.8% for the depth-plane reading): up to 1.5% may be excluded.  The city's
-    clusters put more than 64 contributors within one bound window on some pixels: the
-    order buffer blends ~0.06 contributors per pixel early there (counted; at most 0.1
-    allowed), and the sampled pixels still agree with the exact order to 1e-4."""
+    threshold: up to 1.5% may be left out there.  The city's clusters put more than 64
+    contributors within one bound window on some pixels: the order buffer blends some
+    contributors early there (counted; at most 0.1 per pixel allowed), and the sampled
+    pixels must still agree with the exact order to 1e-4."""
     wl = getattr(W, name)(device="cuda")
     cam = wl.cameras[view]
     kd = R.kd_partition(wl.scene, wl.depth_L)

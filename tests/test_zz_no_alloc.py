@@ -1,8 +1,9 @@
 """rgs_render_fwd_noalloc: the forward render for callers that cannot allocate device
-memory (for example a real-time thread or a host program that hands out all device
-memory from its own pool).  It must give the same partial maps, image and depth table as
-rgs_render_fwd, on consecutive calls that reuse its fixed scratch array, and refuse a
-render that does not fit that array.  This file is collected last on purpose."""
+memory (for example a real-time thread that must not block in the allocator, or a host
+program that hands out all device memory from its own pool).  It must give the same
+partial maps, image and depth table as rgs_render_fwd, on consecutive calls that reuse
+its fixed scratch array, and refuse a render that does not fit that array, before or
+after binning, leaving the next render correct.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -46,28 +47,53 @@ def _noalloc(R, kd, g, cam, opts):
     return rc, out
 
 
-def test_noalloc_matches_render_fwd_on_consecutive_calls(R):
+def _small_scene(R):
     scene = W.uniform_cube_scene(6000, seed=61, log_scale_mean=-3.0, sh_degree=2)
     dev = scene.to("cuda")
-    kd = R.kd_partition(dev, 2)
-    g = R.scene_c(dev)
+    return R.kd_partition(dev, 2), R.scene_c(dev), dev
+
+
+def _check_against_render_fwd(R, kd, g, cam, opts):
+    rc, got = _noalloc(R, kd, g, cam, opts)
+    assert rc == R.RGS_OK, R.lib().rgs_last_error()
+    ref = R.render_fwd(kd, g, cam, opts, R.Workspace())
+    torch.cuda.synchronize()
+    for key in ("partial_C", "partial_T", "image", "T_final"):
+        assert torch.isfinite(got[key]).all(), key
+        assert (got[key] - ref[key]).abs().max().item() <= TOL, key
+    assert torch.equal(got["tile_depth"], ref["tile_depth"])
+
+
+def test_noalloc_matches_render_fwd_on_consecutive_calls(R):
+    kd, g, _dev = _small_scene(R)
     opts = R.default_opts()
     cams = [W.look_at((0.3, -2.7, 0.4), (0, 0, 0), 120, 90), W.look_at((-1.5, 1.8, 1.2), (0.1, 0, 0), 100, 75)]
     for cam in cams:                                  # two calls in a row share the scratch array
-        rc, got = _noalloc(R, kd, g, cam, opts)
-        assert rc == R.RGS_OK, R.lib().rgs_last_error()
-        ref = R.render_fwd(kd, g, cam, opts, R.Workspace())
-        torch.cuda.synchronize()
-        for key in ("partial_C", "partial_T", "image", "T_final"):
-            assert torch.isfinite(got[key]).all(), key
-            assert (got[key] - ref[key]).abs().max().item() <= TOL, key
-        assert torch.equal(got["tile_depth"], ref["tile_depth"])
+        _check_against_render_fwd(R, kd, g, cam, opts)
 
 
 def test_noalloc_rejects_a_render_beyond_its_scratch(R):
+    """Before binning: the splats alone do not fit the array."""
     scene = W.uniform_cube_scene(600_000, seed=62, log_scale_mean=-3.0)
     dev = scene.to("cuda")
     kd = R.kd_partition(dev, 1)
     rc, _ = _noalloc(R, kd, R.scene_c(dev), W.axis_camera((0.0, 0.0, -3.0), 64, 64), R.default_opts())
     assert rc == R.RGS_EOVERFLOW
-    assert b"more than the fixed" in R.lib().rgs_last_error()
+    err = R.lib().rgs_last_error()
+    assert b"fixed scratch" in err and b"before binning" in err, err
+    assert R.lib().rgs_last_required_workspace() > 64 << 20
+
+
+def test_noalloc_rejects_too_many_instances_then_renders_correctly(R):
+    """After binning: the splats fit, their tile instances do not.  The refused call has
+    already projected into the shared array; the next call must not see its leftovers."""
+    big = W.uniform_cube_scene(200_000, seed=63, log_scale_mean=-1.2)
+    bdev = big.to("cuda")
+    bkd = R.kd_partition(bdev, 1)
+    rc, _ = _noalloc(R, bkd, R.scene_c(bdev), W.axis_camera((0.0, 0.0, -3.0), 1024, 1024), R.default_opts())
+    assert rc == R.RGS_EOVERFLOW
+    err = R.lib().rgs_last_error()
+    assert b"fixed scratch" in err and b"tile instances" in err, err
+    assert R.lib().rgs_last_required_workspace() > 64 << 20
+    kd, g, _dev = _small_scene(R)
+    _check_against_render_fwd(R, kd, g, W.look_at((0.3, -2.7, 0.4), (0, 0, 0), 120, 90), R.default_opts())
