@@ -1172,7 +1172,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     // per warp, the (pixel, entry) scalars of the current stretch of kBwdSub list entries
     __shared__ float sh_h[kBlendThreads / 32][32 * kBwdSubPad];   // sigma dL/dsigma
     __shared__ float sh_w[kBlendThreads / 32][32 * kBwdSubPad];   // sigma T
-    __shared__ float s_gc[kBlendThreads][3];                        // dL/dC_k of each pixel
+    __shared__ float4 s_gc[kBlendThreads];                          // dL/dC_k of each pixel (w unused)
     const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
@@ -1226,9 +1226,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
             Tk = pT[(size_t)k * HW + pix];
         }
         const float gC0 = g0 * Pm, gC1 = g1 * Pm, gC2 = g2 * Pm;
-        s_gc[threadIdx.x][0] = gC0;   // read by the lanes of this warp after the next barrier
-        s_gc[threadIdx.x][1] = gC1;
-        s_gc[threadIdx.x][2] = gC2;
+        s_gc[threadIdx.x] = make_float4(gC0, gC1, gC2, 0.f);   // read by this warp's lanes after the next barrier
         // q - acc = <g, colour behind the current pair> (times P for the per-subset form)
         float q;
         if (kFlat) {
@@ -1353,10 +1351,10 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
                                 Sh += h;
                                 Shx += hdx;
                                 Shxx = fmaf(hdx, dx, Shxx);
-                                const float* gc = s_gc[warp * 32 + p];
-                                o[6] = fmaf(gc[0], w, o[6]);
-                                o[7] = fmaf(gc[1], w, o[7]);
-                                o[8] = fmaf(gc[2], w, o[8]);
+                                const float4 gc = s_gc[warp * 32 + p];
+                                o[6] = fmaf(gc.x, w, o[6]);
+                                o[7] = fmaf(gc.y, w, o[7]);
+                                o[8] = fmaf(gc.z, w, o[8]);
                             }
                             const float shu1 = fmaf(A.z, Shx, A.w * dy * Sh);   // row sum of h u1
                             o[0] = fmaf(A.z, shu1, o[0]);
