@@ -534,6 +534,40 @@ def variant_report(trainer, cams, targets, args) -> dict:
     return res
 
 
+def batch_report(device, B=4, steps=6) -> dict:
+    """Training steps over B views per step (the object 1M workload: 1M splats, 1600x1060,
+    8 subsets, SH degree 3): Trainer.step_batch through one batched launch sequence
+    (rgs_render_batch_fwd/bwd) against the same steps view by view.  CUDA events on the
+    launching stream around `steps` steps after two warm-up steps, each mode on a fresh
+    trainer from the same scene."""
+    import torch
+    from paper_2406_11836_gb300 import workloads as W
+    from paper_2406_11836_gb300.render import Trainer
+    wl = W.object_1m(device=device)
+    cams = wl.cameras[:B]
+    targets = [W.target_image(c.width, c.height, seed=2000 + i, device=device) for i, c in enumerate(cams)]
+    stream = torch.cuda.current_stream()
+    res = {"workload": "object-1M-1600x1060-K8", "views_per_step": B, "steps": steps}
+    for mode in ("sequential", "batched"):
+        tr = Trainer(wl.scene, wl.depth_L, device=device, batched_views=(mode == "batched"))
+        for _ in range(2):
+            tr.step_batch(cams, targets, return_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            tr.step_batch(cams, targets, return_loss=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        pix = sum(c.width * c.height for c in cams)
+        res[mode] = {"ms_per_step": round(ms, 3), "mpix_s": round(pix / (ms / 1e3) / 1e6, 1)}
+        del tr
+        torch.cuda.empty_cache()
+    res["batched_over_sequential"] = round(res["batched"]["mpix_s"] / res["sequential"]["mpix_s"], 3)
+    return res
+
+
 class OracleOneThread:
     """The oracle's step estimate with one host thread, in a fresh interpreter with
     OMP_NUM_THREADS=1 that touches no GPU; started at the beginning of the run so that its
@@ -686,6 +720,8 @@ def run_ours(args, rank, world, local_rank):
         line["variants"] = variant_report(trainer, cams, targets, args)
     if rank == 0 and world == 1 and not args.no_foot:
         line["foot_reading"] = foot_reading_report(trainer, cams)
+    if rank == 0 and world == 1 and not args.no_batches and args.workload == "city":
+        line["view_batches"] = batch_report(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_host = make_workload(args.workload, "cpu")
         line["cpu_baseline"] = oracle_step_estimate(wl_host, budget_s=args.cpu_budget)
@@ -738,6 +774,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-foot", action="store_true", help="skip the foot-reading forward comparison")
+    ap.add_argument("--no-batches", action="store_true",
+                    help="skip the batched multi-view training comparison (object 1M workload)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the exact-partials step and the recomputing backward comparisons")
     ap.add_argument("--serve-requests", type=int, default=2200, help="requests of the serving stream")

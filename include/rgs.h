@@ -219,6 +219,34 @@ int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_came
                         const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
                         float* T_final, void* workspace, size_t ws_bytes, uint64_t* overflow_host, void* stream);
 
+/* Training on several views of one scene per step (Sec. 4 trains with a batch size per
+ * step), through one launch sequence instead of one per view.
+ * rgs_render_batch_fwd renders B views (1 <= B <= 16; cams[B] host array, images a host
+ * array of B device pointers, images[b] [3,H_b,W_b]; views may differ in size) with the
+ * arithmetic of the image-only rgs_render_fwd (merge of the partials per pixel, culling
+ * behind a saturated front): one projection of every (view, splat) pair, one depth sort,
+ * emission with keys over the batch's tiles, one instance sort and one persistent blend
+ * over all views' tiles, every count kept on the device.  A view's image equals its
+ * image-only rgs_render_fwd image bit for bit.  The lists stay in `workspace` for
+ * rgs_render_batch_bwd.  Synchronises once with `stream` (to read the instance count).
+ * Errors: EINVAL (arguments as rgs_render_fwd, B out of range, tile keys of the batch beyond
+ * 32 bits), EOVERFLOW (workspace too small: rgs_last_required_workspace() gives the bytes,
+ * exact when the instances did not fit, an estimate before binning), ECUDA.
+ * rgs_render_batch_bwd: the flat backward (as rgs_render_bwd_flat) of every view of that
+ * forward in one persistent launch, then each view's 2D gradients pulled back through its
+ * projection; accumulates into `grads` (same shapes as the parameters; the caller zeroes
+ * them).  dL_dimages: host array of B device pointers [3,H_b,W_b].  When `workspace` (same
+ * pointer and size) no longer holds the lists of the forward with these arguments, the
+ * forward is run again first (re-deriving the lists; the images are rewritten with the
+ * same values).  Parameters are recognised by their pointers: they must not change between
+ * the forward and its backward.  Synchronises with `stream`.  Errors as the forward. */
+int rgs_render_batch_fwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cams, int B,
+                         const rgs_render_opts* opts, float* const* images, void* workspace, size_t ws_bytes,
+                         void* stream);
+int rgs_render_batch_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cams, int B,
+                         const rgs_render_opts* opts, float* const* images, const float* const* dL_dimages,
+                         const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream);
+
 /* Eq. 5 over caller-owned partial maps: image = sum_r C_{o_r} prod_{m<r} T_{o_m} +
  * bg * prod_m T_m.  order_dev [K] int32 (device) lists the subsets front to back.
  * partial_C [K,3,H,W], partial_T [K,H,W], image [3,H,W], T_out [H,W] (nullable). */
@@ -385,7 +413,8 @@ int rgs_serve_destroy(rgs_server* srv);
  * (projection, compaction, depth sort, offsets, emission, instance sort, ranges, blend
  * forward, blend backward, projection backward, Adam, merge, merge backward, KD build)
  * records a pair of CUDA events on the stream it is launched on (two event records per
- * pass).  Bit 1 turns on pair counting: the blend kernels run in a counting variant that
+ * pass; a batch of views' whole forward is one pass, "batch_fwd").  Bit 1 turns on pair
+ * counting: the blend kernels run in a counting variant that
  * tallies the (pixel, splat) pairs they evaluate, the ones that contribute and why the
  * others fail (slower; keep it off where time is measured).  Process-wide.
  * rgs_profile_read synchronises with the recorded events and writes, per stage index

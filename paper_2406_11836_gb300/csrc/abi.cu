@@ -34,7 +34,8 @@ void set_required_workspace(size_t bytes) { g_required = bytes; }
 // ------------------------------------------------------------------ profiler
 namespace {
 const char* kStageNames[ST_COUNT] = {"project", "compact", "depth_sort", "offsets", "emit", "instance_sort", "ranges",
-                                     "blend_fwd", "blend_bwd", "project_bwd", "adam", "merge", "merge_bwd", "kd"};
+                                     "blend_fwd", "blend_bwd", "project_bwd", "adam", "merge", "merge_bwd", "kd",
+                                     "batch_fwd"};
 struct Profiler {
     std::mutex mu;
     bool on = false;      // stage timing
@@ -332,6 +333,8 @@ std::mutex g_stamp_mu;
 std::unordered_map<const void*, ListStamp> g_stamps;
 std::atomic<unsigned long long> g_nonce_counter{0};
 
+}  // namespace
+
 unsigned long long next_nonce() {
     // splitmix64 of a per-process base and a counter: distinct per forward, never 0
     static const unsigned long long base = (unsigned long long)(uintptr_t)&g_nonce_counter ^
@@ -343,6 +346,8 @@ unsigned long long next_nonce() {
     z ^= z >> 31;
     return z ? z : 1;
 }
+
+namespace {
 
 bool same_gaussians(const rgs_gaussians& a, const rgs_gaussians& b) {
     return a.means == b.means && a.log_scales == b.log_scales && a.quats == b.quats &&

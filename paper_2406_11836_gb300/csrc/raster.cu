@@ -721,8 +721,8 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __
 // consecutive tiles stay in one request.
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
-                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival, const float4* __restrict__ rec,
-                   unsigned long long* __restrict__ counters) {
+                   uint2* __restrict__ ranges, const uint32_t* __restrict__ ival, const float4* __restrict__ rec,
+                   unsigned long long* __restrict__ counters, bool record_ends) {
     __shared__ ViewParams svp;
     __shared__ uint32_t s_tile;
     __shared__ int s_slot;
@@ -749,8 +749,9 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
             cur = slot;
             __syncthreads();
         }
-        blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), ranges + (size_t)t * svp.K, ival, rec,
-                              nullptr, nullptr, slots[slot].image, nullptr, nullptr, nullptr, nullptr);
+        uint2* tr = ranges + (size_t)t * svp.K;
+        blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), tr, ival, rec, nullptr, nullptr,
+                              slots[slot].image, nullptr, nullptr, record_ends ? tr : nullptr, nullptr);
         __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
@@ -1153,12 +1154,17 @@ __device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
 // transmittance in front of each subset (P) rebuilt from the replayed subset ends, and
 // dL/dsigma_i = T_i <g, c_i> - <g, C - A_i> / (1 - sigma_i) where C is the image and A_i the
 // colour blended up to and including pair i (both global).
+//
+// One tile of the view (the whole block calls it): `ranges` points at the tile's K runs
+// (view rank order); payloads are record indices into rec and g2d (>= n_splats: skipped).
 template <bool kCount, bool kFlat>
-__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
-blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
-                 const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
-                 const float* __restrict__ img, const float* __restrict__ gI, float4* __restrict__ g2d,
-                 uint32_t n_inst, uint32_t n_splats, unsigned long long* __restrict__ pairs) {
+__device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
+                                               const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                                               const float4* __restrict__ rec, const float* __restrict__ pC,
+                                               const float* __restrict__ pT, const float* __restrict__ img,
+                                               const float* __restrict__ gI, float4* __restrict__ g2d,
+                                               uint32_t n_inst, uint32_t n_splats,
+                                               unsigned long long* __restrict__ pairs) {
     // <g, S_r> of this pixel for every rank: private to the thread, in local memory (cached),
     // so that shared memory does not grow with K (the flat form needs none)
     float behind_r[kFlat ? 1 : 1 << kMaxRenderDepth];
@@ -1173,7 +1179,6 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     __shared__ float sh_h[kBlendThreads / 32][32 * kBwdSubPad];   // sigma dL/dsigma
     __shared__ float sh_w[kBlendThreads / 32][32 * kBwdSubPad];   // sigma T
     __shared__ float4 s_gc[kBlendThreads];                          // dL/dC_k of each pixel (w unused)
-    const int tile = blockIdx.x;
     const int tyi = tile / vp.tiles_x, txi = tile - tyi * vp.tiles_x;
     int lx, ly;
     thread_pixel(threadIdx.x, lx, ly);
@@ -1189,6 +1194,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     uint8_t* wl = wlist[warp];
     const int wx0 = (warp & 1) << 3, wy0 = (warp >> 1) << 2;   // the warp's 8x4 block in the tile
 
+    __syncthreads();   // a previous tile's readers of the shared arrays are done
     for (int i = threadIdx.x; i < kBlendThreads * 9; i += kBlendThreads) (&sacc[0][0])[i] = 0.f;
 
     // adjoint of Eq. 5: <g, S_r> for every rank, back to front
@@ -1242,7 +1248,7 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
         const bool front_open = Pm >= vp.eps_T;
         if (!kFlat) Pm *= Tk;
         if (threadIdx.x == 0) leaf_path(tp, k, lp);   // read only after the next barrier
-        uint2 rg = ranges[(size_t)tile * vp.K + r];
+        uint2 rg = ranges[r];
         rg.y = min(rg.y, n_inst);   // lists handed over from a forward: never read past them
         rg.x = min(rg.x, rg.y);
         const bool active = inside && front_open && (g0 != 0.f || g1 != 0.f || g2 != 0.f);
@@ -1405,6 +1411,58 @@ blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges,
     if (kCount) {
         count_pairs(pairs + 2, n_eval, n_contrib);
         count_add(pairs + 12, n_iter);
+    }
+}
+
+template <bool kCount, bool kFlat>
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
+blend_bwd_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                 const float4* __restrict__ rec, const float* __restrict__ pC, const float* __restrict__ pT,
+                 const float* __restrict__ img, const float* __restrict__ gI, float4* __restrict__ g2d,
+                 uint32_t n_inst, uint32_t n_splats, unsigned long long* __restrict__ pairs) {
+    blend_bwd_tile<kCount, kFlat>(vp, tp, blockIdx.x, ranges + (size_t)blockIdx.x * vp.K, ival, rec, pC, pT, img,
+                                  gI, g2d, n_inst, n_splats, pairs);
+}
+
+// Flat backward of a batch of views (a training step over several views), persistent over
+// the batch's global tiles like blend_batch_kernel: each block takes the next tile from a
+// device counter (counters[7]); the slot's image and dL/dimage come from its BatchSlot and
+// the payloads index the batch's per-(slot, splat) records and 2D-gradient records.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
+blend_bwd_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
+                       const uint2* __restrict__ ranges, const uint32_t* __restrict__ ival,
+                       const float4* __restrict__ rec, float4* __restrict__ g2d, uint32_t n_inst, uint32_t n_splats,
+                       unsigned long long* __restrict__ counters, unsigned long long* __restrict__ pairs) {
+    __shared__ ViewParams svp;
+    __shared__ uint32_t s_tile;
+    __shared__ int s_slot;
+    const int S = hdr->S;
+    const uint32_t total = hdr->total_tiles;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = (uint32_t)atomicAdd(&counters[7], 1ull);
+            int sl = 0;
+            while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
+            s_tile = t;
+            s_slot = sl;
+        }
+        __syncthreads();
+        const uint32_t t = s_tile;
+        const int slot = s_slot;
+        if (t >= total) break;
+        if (slot != cur) {
+            constexpr int kWords = (int)(sizeof(ViewParams) / 4);
+            for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+                reinterpret_cast<uint32_t*>(&svp)[w] = reinterpret_cast<const uint32_t*>(&slots[slot].vp)[w];
+            cur = slot;
+            __syncthreads();
+        }
+        blend_bwd_tile<kCount, true>(svp, tp, (int)(t - hdr->tile_base[slot]), ranges + (size_t)t * svp.K, ival, rec,
+                                     nullptr, nullptr, slots[slot].image, slots[slot].grad, g2d, n_inst, n_splats,
+                                     pairs);
+        __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
 
@@ -1573,13 +1631,44 @@ int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int
     return RGS_OK;
 }
 
-int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
-                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s) {
+int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, uint2* ranges,
+                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s,
+                       bool record_ends) {
     int dev = 0, sms = 0;
     RGS_CUDA_TRY(cudaGetDevice(&dev));
     RGS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival,
-                                                                                      rec, counters);
+                                                                                      rec, counters, record_ends);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_blend_bwd_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
+                           const uint32_t* ival, const float4* rec, float4* g2d, int64_t n_inst, int64_t n_splats,
+                           unsigned long long* counters, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    RGS_CUDA_TRY(cudaGetDevice(&dev));
+    RGS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    static bool attr_set = false;
+    if (!attr_set) {
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_batch_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        RGS_CUDA_TRY(cudaFuncSetAttribute(blend_bwd_batch_kernel<false>,
+                                          cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        attr_set = true;
+    }
+    RGS_CUDA_TRY(cudaMemsetAsync(counters + 7, 0, 8, s));   // the work-queue head
+    const unsigned grid = (unsigned)(sms * RGS_BLEND_MIN_BLOCKS);
+    unsigned long long* pairs = prof_pair_counters();
+    if (pairs)
+        blend_bwd_batch_kernel<true><<<grid, kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival, rec, g2d,
+                                                                   (uint32_t)n_inst, (uint32_t)n_splats, counters,
+                                                                   pairs);
+    else
+        blend_bwd_batch_kernel<false><<<grid, kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival, rec, g2d,
+                                                                    (uint32_t)n_inst, (uint32_t)n_splats, counters,
+                                                                    nullptr);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

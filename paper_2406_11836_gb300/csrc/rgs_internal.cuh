@@ -85,6 +85,7 @@ constexpr int kMaxSlots = 16;
 struct BatchSlot {
     ViewParams vp;
     float* image;              // [3, H, W] output of the request
+    const float* grad;         // [3, H, W] dL/dimage (the batched backward; null in serving)
     uint32_t tile_base;        // first global tile of the request
     uint32_t pad;
 };
@@ -96,19 +97,26 @@ struct BatchHeader {
     uint32_t tile_base[kMaxSlots + 1];   // prefix of the requests' tile counts
 };
 
+// One lane of batch buffers (serve.cu): the slot table and header the batch's kernels read,
+// its device counters, each slot's plane templates, and the per-(slot, splat) and
+// per-instance arrays.
+struct LaneBufs;
 // Device counters of a batch (uint64): [0] instances, [1] visible (slot, splat) pairs,
 // [2] overflow flag, [3] blend work-queue head, [4] instances to sort (0 on overflow),
-// [5], [6] emission work-queue heads, then (instances, visible) per slot from
-// kBatchSlotCounters.
+// [5], [6] emission work-queue heads, [7] the batched backward's work-queue head, then
+// (instances, visible) per slot from kBatchSlotCounters.
 constexpr int kBatchSlotCounters = 8;
 constexpr int kBatchCounters = kBatchSlotCounters + 2 * kMaxSlots;
+
+struct RasterBuffers;
+int ceil_log2(int64_t x);
 
 // ------------------------------------------------------------------ tracing
 // Passes timed by the profiler (rgs_profile_*): a pair of CUDA events is recorded on the
 // launching stream around each pass while profiling is on.
 enum Stage {
     ST_PROJECT = 0, ST_COMPACT, ST_DEPTH_SORT, ST_OFFSETS, ST_EMIT, ST_INST_SORT, ST_RANGES, ST_BLEND_FWD,
-    ST_BLEND_BWD, ST_PROJECT_BWD, ST_ADAM, ST_MERGE, ST_MERGE_BWD, ST_KD, ST_COUNT
+    ST_BLEND_BWD, ST_PROJECT_BWD, ST_ADAM, ST_MERGE, ST_MERGE_BWD, ST_KD, ST_BATCH_FWD, ST_COUNT
 };
 struct ProfScope {
     int token;
@@ -127,6 +135,9 @@ void prof_suppress(bool on);   // this thread's passes record no events while on
 // ------------------------------------------------------------------ errors
 void set_error(const char* fmt, ...);
 void set_required_workspace(size_t bytes);
+// A value never seen before in this process (never 0): the stamp a forward writes into its
+// workspace so that a backward can tell whether the lists there are still its own.
+unsigned long long next_nonce();
 
 #define RGS_CUDA_TRY(expr)                                                                 \
     do {                                                                                   \
@@ -211,6 +222,25 @@ struct RasterBuffers {
     size_t temp_bytes;
 };
 
+struct LaneBufs {
+    unsigned long long* header;   // train layouts: [32] words, [0] the nonce of the forward whose lists it holds
+    BatchSlot* slots;
+    BatchHeader* hdr;
+    unsigned long long* counters;
+    float4* clip_plane;    // [kMaxSlots * kClipTable]: each request's plane templates
+    float* clip_margin;    // [kMaxSlots * kClipTable]
+    RasterBuffers b;
+};
+// serve.cu: the lane layout (train: with 2D-gradient records) and the batch pipeline
+// (projection of every (slot, splat) pair through the persistent blend, device-counted).
+size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out,
+                   bool train = false);
+// ival_out (nullable): the buffer that holds the sorted instance payloads.
+int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
+                  const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
+                  unsigned long long* status_host, cudaStream_t s, bool record_ends = false,
+                  const uint32_t** ival_out = nullptr);
+
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s);
 // Fills vp.clip_plane / vp.clip_margin (device) for one view, or for every slot of a batch
@@ -229,9 +259,16 @@ int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tree
 int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
                       cudaStream_t s);
 // Persistent forward blend over the batch's global tiles (fused merge into each slot's
-// image; no partial maps).
-int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
-                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s);
+// image; no partial maps).  record_ends: cut each saturated run back to what was staged
+// (the batched backward replays the runs).
+int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, uint2* ranges,
+                       const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s,
+                       bool record_ends = false);
+// Persistent flat backward over the batch's global tiles (counters[7]: its work queue);
+// 2D gradients into g2d indexed like rec (slot * N + splat).
+int launch_blend_bwd_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,
+                           const uint32_t* ival, const float4* rec, float4* g2d, int64_t n_inst, int64_t n_splats,
+                           unsigned long long* counters, cudaStream_t s);
 int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
                 int64_t n_vis, cudaStream_t s);
 int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);

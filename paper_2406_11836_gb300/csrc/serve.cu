@@ -67,18 +67,13 @@ __global__ void check_capacity_kernel(unsigned long long* counters, int64_t inst
     counters[4] = over ? 0ull : I;
 }
 
-// ------------------------------------------------------------------ lanes
-struct LaneBufs {
-    BatchSlot* slots;
-    BatchHeader* hdr;
-    unsigned long long* counters;
-    float4* clip_plane;    // [kMaxSlots * kClipTable]: each request's plane templates
-    float* clip_margin;    // [kMaxSlots * kClipTable]
-    RasterBuffers b;
-};
+}  // namespace
 
-// Carves one lane's buffers from `base` (NULL: measure); returns the bytes used.
-size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out) {
+// ------------------------------------------------------------------ lanes
+// Carves one lane's buffers from `base` (NULL: measure); returns the bytes used.  train:
+// also the per-(slot, splat) 2D-gradient records of a batched backward.
+size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out,
+                   bool train) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -88,6 +83,7 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     LaneBufs l;
     memset(&l, 0, sizeof l);
     const int64_t P = N * slots;   // (request, splat) pairs
+    if (train) l.header = (unsigned long long*)take(256);
     l.slots = (BatchSlot*)take(sizeof(BatchSlot) * kMaxSlots);
     l.hdr = (BatchHeader*)take(sizeof(BatchHeader));
     l.counters = (unsigned long long*)take(8 * kBatchCounters);
@@ -106,6 +102,7 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     b.skey_alt = (uint32_t*)take(4 * P);
     b.sid_alt = (uint32_t*)take(4 * P);
     b.ioff = (uint32_t*)take(4 * P);
+    if (train) b.g2d = (float4*)take(sizeof(float4) * 3 * P);
     b.ranges = (uint2*)take(sizeof(uint2) * tiles_cap * K);
     b.ikey = (uint32_t*)take(4 * inst_cap);
     b.ival = (uint32_t*)take(4 * inst_cap);
@@ -126,9 +123,10 @@ int ceil_log2(int64_t x) {
 }
 
 // Enqueues the whole batch pipeline of one lane on `s` (captured into the lane's graph).
+// record_ends: the blend cuts saturated runs back for a batched backward's replay.
 int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
                   const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
-                  unsigned long long* status_host, cudaStream_t s) {
+                  unsigned long long* status_host, cudaStream_t s, bool record_ends, const uint32_t** ival_out) {
     const int64_t N = g.n, P = N * slots;
     const RasterBuffers& b = l.b;
     unsigned long long* c = l.counters;
@@ -177,11 +175,14 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
         return rc;
     const uint32_t* keys = alt ? b.ikey_alt : b.ikey;
     const uint32_t* ival = alt ? b.ival_alt : b.ival;
+    if (ival_out) *ival_out = ival;
     if ((rc = launch_ranges_dev(keys, &c[4], b.inst_cap, b.ranges, s))) return rc;
-    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s))) return rc;
+    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s, record_ends))) return rc;
     RGS_CUDA_TRY(cudaMemcpyAsync(status_host, c, 8 * kBatchCounters, cudaMemcpyDeviceToHost, s));
     return RGS_OK;
 }
+
+namespace {
 
 // ------------------------------------------------------------------ server state
 using Clock = std::chrono::steady_clock;

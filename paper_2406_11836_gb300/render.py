@@ -67,7 +67,8 @@ class Trainer:
     LR = {"quats": 1e-3, "log_scales": 5e-3, "opacity_logits": 5e-2, "sh_dc": 2.5e-3, "sh_rest": 2.5e-3 / 20}
 
     def __init__(self, scene, depth_L: int, opts: rgs.RenderOpts | None = None, max_steps: int = 60000,
-                 device="cuda", repartition_every: int = 0, cull_occluded: bool = True, backward: str = "flat"):
+                 device="cuda", repartition_every: int = 0, cull_occluded: bool = True, backward: str = "flat",
+                 batched_views: bool = True):
         n = scene.n
         self.n = n
         self.sh_degree = scene.sh_degree
@@ -109,6 +110,9 @@ class Trainer:
         if backward not in ("subsets", "flat"):
             raise ValueError(f"backward must be 'subsets' or 'flat', not {backward!r}")
         self.backward = backward
+        # step_batch renders its views through one launch sequence (rgs_render_batch_fwd/bwd;
+        # flat backward only) rather than one after another
+        self.batched_views = bool(batched_views)
         self.ws = rgs.Workspace(device)
         self.kd = rgs.kd_partition(self.gaussians(), depth_L, float(self.opts.trunc_mult))
 
@@ -189,9 +193,21 @@ class Trainer:
 
     def step_batch(self, cams, targets, return_loss: bool = True):
         """One training step on several views: the mean of their L1 losses, its gradient
-        summed over the views' backwards, then one Adam step.  Returns the mean loss."""
+        summed over the views' backwards, then one Adam step.  Returns the mean loss.
+        With the flat backward (and batched_views) the views go through one batched forward
+        and one batched backward; otherwise one view after another."""
         g = self.gaussians()
         w = 1.0 / len(cams)
+        if self.backward == "flat" and self.batched_views and 1 < len(cams) <= 16:
+            imgs = rgs.render_batch_fwd(self.kd, g, cams, self.opts, self.ws)
+            losses, dls = [], []
+            for img, t in zip(imgs, targets):
+                diff = img - t
+                if return_loss:
+                    losses.append(diff.abs().mean() * w)
+                dls.append(torch.sign(diff).div_(float(diff.numel()) / w))
+            rgs.render_batch_bwd(self.kd, g, cams, self.opts, imgs, dls, self.grads(), self.ws)
+            return self._update(torch.stack(losses).sum() if return_loss else None)
         losses = [self._accumulate(g, c, t, w, return_loss) for c, t in zip(cams, targets)]
         return self._update(torch.stack(losses).mean() if return_loss else None)
 

@@ -90,6 +90,10 @@ def lib():
                                  c_void_p, c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_render_bwd_flat.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                       c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
+    L.rgs_render_batch_fwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), c_int, POINTER(RenderOpts),
+                                       c_void_p, c_void_p, c_size_t, c_void_p]
+    L.rgs_render_batch_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), c_int, POINTER(RenderOpts),
+                                       c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_merge_partials.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_void_p]
     L.rgs_merge_partials_bwd.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -382,6 +386,46 @@ def render_bwd_flat(kd: KD, g: Gaussians, cam, opts: RenderOpts, image, dL_dimag
                                              ws.nbytes, s), ws)
 
 
+def _cams_c(cams):
+    arr = (CameraC * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_c(c)
+    return arr
+
+
+def _ptrs(tensors):
+    arr = (c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def render_batch_fwd(kd: KD, g: Gaussians, cams, opts: RenderOpts, ws: Workspace, stream=None, images=None):
+    """Images [3,H,W] of several views of one scene through one launch sequence (the
+    batched training forward); the lists stay in `ws` for render_batch_bwd."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if images is None:
+        images = [torch.empty(3, int(c.height), int(c.width), device=dev) for c in cams]
+    cc, ip = _cams_c(cams), _ptrs(images)
+    s = _stream(stream)
+    _retry(lambda: lib().rgs_render_batch_fwd(kd.handle, ctypes.byref(g), cc, len(cams), ctypes.byref(opts),
+                                              ctypes.cast(ip, c_void_p), ws.ptr(), ws.nbytes, s), ws)
+    return images
+
+
+def render_batch_bwd(kd: KD, g: Gaussians, cams, opts: RenderOpts, images, dL_dimages, grads, ws: Workspace,
+                     stream=None):
+    """Flat backward of every view of render_batch_fwd in one launch sequence; accumulates
+    into grads = (means, log_scales, quats, opacity_logits, sh)."""
+    gg = GaussianGrads(*(_ptr(t) for t in grads))
+    dls = [d.contiguous() for d in dL_dimages]
+    cc, ip, dp = _cams_c(cams), _ptrs(images), _ptrs(dls)
+    s = _stream(stream)
+    _retry(lambda: lib().rgs_render_batch_bwd(kd.handle, ctypes.byref(g), cc, len(cams), ctypes.byref(opts),
+                                              ctypes.cast(ip, c_void_p), ctypes.cast(dp, c_void_p), ctypes.byref(gg),
+                                              ws.ptr(), ws.nbytes, s), ws)
+
+
 # --------------------------------------------------------------------------- tracing
 def profile_enable(timing: bool = True, counters: bool = False):
     """Per-pass CUDA-event timing (cheap) and/or pair counters (counting kernel variants)."""
@@ -501,7 +545,7 @@ class Server:
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_render_fwd_foot", "rgs_merge_partials", "rgs_merge_partials_bwd",
-               "rgs_render_bwd", "rgs_render_bwd_flat", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
+               "rgs_render_bwd", "rgs_render_bwd_flat", "rgs_render_batch_fwd", "rgs_render_batch_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
                "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",
