@@ -199,13 +199,16 @@ def stage_roofline(name, ms, launches, cnt, peaks, peak_src, geom):
     if name == "blend_fwd":
         P = per("fwd_pairs")
         flops, mufu = FLOPS_PER_PAIR[name] * P, P
-        byts = 36 * per("fwd_instances_staged") + 16 * K * HW + 16 * HW
+        # staged records; per pixel the image (and the partial maps when the forward writes them)
+        byts = 36 * per("fwd_instances_staged") + (0 if geom.get("flat_backward") else 16 * K * HW) + 16 * HW
         own = FLOPS_EVAL * P + FLOPS_CONTRIB[name] * per("fwd_contrib")
     elif name == "blend_bwd":
         P = per("bwd_pairs")
         flops, mufu = FLOPS_PER_PAIR[name] * P, P
-        # the backward replays the lists the forward staged
-        byts = 12 * HW + 32 * K * HW + 36 * per("fwd_instances_staged") + 36 * per("visible")
+        # the backward replays the lists the forward staged; per pixel dL/dC and the image
+        # (flat form) or dL/dC and the partial maps (per-subset form)
+        per_pixel = 24 if geom.get("flat_backward") else 12 + 16 * K
+        byts = per_pixel * HW + 36 * per("fwd_instances_staged") + 36 * per("visible")
         own = FLOPS_EVAL * P + FLOPS_CONTRIB[name] * per("bwd_contrib")
     else:
         I, Nv = per("instances"), per("visible")
@@ -254,7 +257,7 @@ def roofline(prof, peaks, peak_src, source, traffic_table, geom, workload=None):
 
 def _source_hashes():
     out = {}
-    for f in ("raster.cu", "sort.cu", "project.cu"):
+    for f in ("raster.cu", "sort.cu", "project.cu", "adam.cu"):
         p = os.path.join(ROOT, "paper_2406_11836_gb300", "csrc", f)
         out[f] = hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
     return out
@@ -694,7 +697,7 @@ def run_ours(args, rank, world, local_rank):
     value = whole_job_mpix_s(world, args.steps, pix_per_step, ms_max)
     e2e = whole_job_mpix_s(world, args.steps, pix_per_step, e2e_ms_max)
     geom = {"sms": sm_count(), "pixels": H * Wd, "K": trainer.kd.K, "N": trainer.n, "params": int(trainer.flat.numel()),
-            "sort_passes": sort_passes(trainer.kd.L, H, Wd)}
+            "sort_passes": sort_passes(trainer.kd.L, H, Wd), "flat_backward": trainer.backward == "flat"}
     rl = roofline(prof, peaks, peak_src, _source_hashes(), _traffic_table(), geom, WORKLOAD_NAMES[args.workload])
     line = {
         "metric": METRIC if args.workload == "city" else f"fwd+bwd+Adam Mpix/s ({args.workload})",

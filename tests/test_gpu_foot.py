@@ -159,22 +159,25 @@ def test_foot_rejects_missing_outputs(R):
     assert rc == R.RGS_EINVAL
 
 
-@pytest.mark.parametrize("name,view,n_pix,max_flagged,max_over", [("object_1m", 0, 4096, MAX_FLAGGED, 0.0),
-                                                                  ("city_10m", 3, 1024, 0.015, 0.1)])
-def test_foot_fullsize_sampled(R, name, view, n_pix, max_flagged, max_over):
+@pytest.mark.parametrize("name,view,n_pix,max_flagged,max_over,cull", [("object_1m", 0, 4096, MAX_FLAGGED, 0.0, 0),
+                                                                       ("city_10m", 3, 1024, 0.015, 0.1, 0),
+                                                                       ("city_10m", 3, 1024, 0.015, 0.0, 1)])
+def test_foot_fullsize_sampled(R, name, view, n_pix, max_flagged, max_over, cull):
     """Full workload sizes in the benchmark's configuration (1M splats at 1600x1060 with
     8 subsets; 10M at 3840x2160 with 16): the whole frame on the GPU, a seeded sample of
     pixels in the oracle.  In the city view the foot's ball test, which accepts more rays
     than the depth plane's, leaves ~1.1% of the sampled pixels with a pair at a truncation
     threshold: up to 1.5% may be left out there.  The city's clusters put more than 64
-    contributors within one bound window on some pixels: the order buffer blends some
-    contributors early there (counted; at most 0.1 per pixel allowed), and the sampled
-    pixels must still agree with the exact order to 1e-4."""
+    contributors within one bound window on some pixels: with every subset blended on every
+    ray (cull = 0) the order buffer blends some contributors early there (counted; at most
+    0.1 per pixel allowed), and the sampled pixels must still agree with the exact order to
+    1e-4; with the training step's culling behind a saturated front (cull = 1) no
+    contributor is blended early: the per-pixel order is exact at full size."""
     wl = getattr(W, name)(device="cuda")
     cam = wl.cameras[view]
     kd = R.kd_partition(wl.scene, wl.depth_L)
     g = R.scene_c(wl.scene)
-    out = R.render_fwd_foot(kd, g, cam, R.default_opts(), R.Workspace())
+    out = R.render_fwd_foot(kd, g, cam, R.default_opts(cull_occluded=cull), R.Workspace())
     torch.cuda.synchronize()
     pix = W.sample_pixels(cam.width, cam.height, n_pix, seed=23)
     ref = O.render(wl.scene.to("cpu"), cam, foot_opts(), pix=pix)
