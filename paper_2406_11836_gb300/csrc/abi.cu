@@ -274,7 +274,12 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.skey_alt = (uint32_t*)take(4 * N);
     t.sid_alt = (uint32_t*)take(4 * N);
     t.ioff = (uint32_t*)take(4 * N);
-    t.counters = (unsigned long long*)take(64);
+    t.counters = (unsigned long long*)take(128);
+    // deferred emission: per launch a list of (id, base) for up to one splat in four (at
+    // least 8192, at most 2^20)
+    const int64_t ucap = N / 4 < 8192 ? 8192 : (N / 4 > (1 << 20) ? (1 << 20) : N / 4);
+    t.units = (uint4*)take(sizeof(uint2) * 2 * (size_t)ucap);
+    t.unit_cap = (uint32_t)ucap;
     t.ranges = (uint2*)take(sizeof(uint2) * tiles * K);
     t.cull_chunk = (float2*)take(sizeof(float2) * (size_t)tiles * K / 16 + sizeof(float2) * 2048 * K);
     t.clip_plane = (float4*)take(sizeof(float4) * kClipTable);
@@ -403,7 +408,7 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
         if (rc) return rc;
     }
 
-    RGS_CUDA_TRY(cudaMemsetAsync(b->counters, 0, 64, s));
+    RGS_CUDA_TRY(cudaMemsetAsync(b->counters, 0, 128, s));
     {
         ProfScope ps(ST_PROJECT, s);
         rc = launch_project_fwd(*g, *vp, *tp, *b, s);

@@ -57,12 +57,94 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // One warp per depth-sorted splat; lanes take the splat's (subset, tile row) items, find
 // the row's tile columns from the footprint (the same arithmetic as the count), and
 // write the row's instances at the positions a warp prefix sum gives them.
+// The (subset, row) items of one splat, as the emission walks them.
+struct SplatItems {
+    Footprint f;
+    unsigned long long m;
+    float z;
+    int nsub, ty0, rows, items;
+};
+
+template <int kMulti>
+__device__ __forceinline__ SplatItems load_items(const ViewParams& vp, uint32_t id, const ushort4* __restrict__ rect,
+                                                 const unsigned long long* __restrict__ mask,
+                                                 const float4* __restrict__ rec, const float4* __restrict__ foot_side) {
+    SplatItems s;
+    const ushort4 r = rect[id];
+    s.m = mask[id];
+    const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
+    s.f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
+    if (kMulti == 1 && foot_side) s.f.zr = foot_depth_radius(r2.w, foot_side[id].x);
+    s.z = r2.w;
+    s.ty0 = r.y;
+    s.rows = (int)r.w - (int)r.y + 1;
+    s.nsub = __popcll(s.m);
+    s.items = s.nsub * s.rows;
+    return s;
+}
+
+// One round of a splat's items, [it0, it0 + 32) (lane l takes item it0 + l): each lane
+// finds its item's tile columns, a warp prefix sum places the items' runs from `base`,
+// and (kWrite) the instances are written; returns the round's instance count (the same
+// on every lane).  Without depth culling the warp writes the round's contiguous range
+// together (lane l writes positions l, l + 32, ...: coalesced stores), finding each
+// position's item by a forward scan of the run starts.  Global tile indices start at
+// tile_base.  Every lane of the warp calls it.
+template <int kMulti, bool kWrite>
+__device__ __forceinline__ uint32_t emit_round(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of,
+                                               uint32_t id, const SplatItems& s, int it0, uint32_t base,
+                                               uint32_t tile_base, const float* __restrict__ cull,
+                                               const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
+                                               uint32_t* __restrict__ ival, int lane, uint32_t* s_start,
+                                               uint32_t* s_key0) {
+    const int it = it0 + lane;
+    int c0 = 1, c1 = 0, ty = 0;
+    uint32_t rank = 0;
+    if (it < s.items) {
+        int k;
+        item_span<kMulti>(s.f, vp, tp, s.m, s.nsub, s.z, s.ty0, s.rows, it, ty, k, c0, c1);
+        rank = (uint32_t)rank_of[k];
+    }
+    const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, s.z);
+    uint32_t incl = w;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (!kWrite) return total;
+    const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
+    if (!cull) {
+        s_start[lane] = incl - w;
+        s_key0[lane] = ((first + (uint32_t)c0) << vp.L) | rank;
+        __syncwarp();
+        int cur = 0;
+        for (uint32_t o = (uint32_t)lane; o < total; o += 32) {
+            while (cur < 31 && s_start[cur + 1] <= o) ++cur;   // runs of empty items share a start
+            ikey[base + o] = s_key0[cur] + ((o - s_start[cur]) << vp.L);
+            ival[base + o] = id;
+        }
+        __syncwarp();
+    } else if (w) {
+        uint32_t pos = base + incl - w;
+        for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+            const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+            const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
+            if (s.z > mm.y) continue;
+            const bool all = s.z <= mm.x;
+            for (int c = lo; c <= hi; ++c) {
+                if (!all && !keep_tile(cull, vp, ty, c, (int)rank, s.z)) continue;
+                ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                ival[pos] = id;
+                ++pos;
+            }
+        }
+    }
+    return total;
+}
+
 // Instances of one splat (record id, first instance slot `base`), written by the calling
-// warp; global tile indices start at tile_base.  32 (subset, row) items at a time: each
-// lane finds its item's tile columns, a warp prefix sum places the items' runs, and
-// without depth culling the warp then writes the round's contiguous range together
-// (lane l writes positions l, l + 32, ...: coalesced stores), finding each position's
-// item by a forward scan of the run starts.
+// warp round after round.
 template <int kMulti>
 __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of, uint32_t id,
                                          uint32_t base, uint32_t tile_base, const ushort4* __restrict__ rect,
@@ -70,60 +152,24 @@ __device__ __forceinline__ void emit_one(const ViewParams& vp, const TreeParams&
                                          const float* __restrict__ cull, const float2* __restrict__ chunk,
                                          uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane,
                                          uint32_t* s_start, uint32_t* s_key0, const float4* __restrict__ foot_side) {
-    const ushort4 r = rect[id];
-    const unsigned long long m = mask[id];
-    const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
-    Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
-    if (kMulti == 1 && foot_side) f.zr = foot_depth_radius(r2.w, foot_side[id].x);
-    const int ty0 = r.y, rows = (int)r.w - (int)r.y + 1;
-    const int nsub = __popcll(m);
-    const int items = nsub * rows;
-    for (int it0 = 0; it0 < items; it0 += 32) {
-        const int it = it0 + lane;
-        int c0 = 1, c1 = 0, ty = 0;
-        uint32_t rank = 0;
-        if (it < items) {
-            int k;
-            item_span<kMulti>(f, vp, tp, m, nsub, r2.w, ty0, rows, it, ty, k, c0, c1);
-            rank = (uint32_t)rank_of[k];
-        }
-        const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, r2.w);
-        uint32_t incl = w;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
-        if (!cull) {
-            s_start[lane] = incl - w;
-            s_key0[lane] = ((first + (uint32_t)c0) << vp.L) | rank;
-            __syncwarp();
-            int cur = 0;
-            for (uint32_t o = (uint32_t)lane; o < total; o += 32) {
-                while (cur < 31 && s_start[cur + 1] <= o) ++cur;   // runs of empty items share a start
-                ikey[base + o] = s_key0[cur] + ((o - s_start[cur]) << vp.L);
-                ival[base + o] = id;
-            }
-            __syncwarp();
-        } else if (w) {
-            uint32_t pos = base + incl - w;
-            for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
-                const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-                const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
-                if (r2.w > mm.y) continue;
-                const bool all = r2.w <= mm.x;
-                for (int c = lo; c <= hi; ++c) {
-                    if (!all && !keep_tile(cull, vp, ty, c, (int)rank, r2.w)) continue;
-                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                    ival[pos] = id;
-                    ++pos;
-                }
-            }
-        }
-        base += total;
-    }
+    const SplatItems s = load_items<kMulti>(vp, id, rect, mask, rec, foot_side);
+    for (int it0 = 0; it0 < s.items; it0 += 32)
+        base += emit_round<kMulti, true>(vp, tp, rank_of, id, s, it0, base, tile_base, cull, chunk, ikey, ival, lane,
+                                         s_start, s_key0);
 }
+
+// Deferred emission.  The near splats come first in depth order and are the largest, so a
+// warp that took a group of 32 of them would emit them one after another long after the
+// other warps finished.  The first launch therefore emits only the splats a lane handles
+// alone and lists the others with their instance base; the second launch hands the list
+// out with a stride of the number of warps, so that the heavy head of the list spreads
+// over all of them.  A splat that finds the list full is emitted on the spot by its warp.
+// Either way every instance lands at the position its count gives it.
+struct EmitQueues {
+    uint2* list;                   // [cap] (id, instance base) of the deferred splats
+    unsigned long long* count;     // splats listed (may exceed cap: those were emitted on the spot)
+    uint32_t cap;
+};
 
 // Instances of one small splat (at most kEmitThreadItems items), written by one thread.
 constexpr int kEmitThreadItems = 4;
@@ -160,7 +206,7 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
             const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
             const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-            unsigned long long* __restrict__ queue, const float4* __restrict__ foot_side) {
+            unsigned long long* __restrict__ queue, const float4* __restrict__ foot_side, EmitQueues q) {
     __shared__ uint32_t s_start[8][32], s_key0[8][32];
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
@@ -191,7 +237,23 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
                                     ikey, ival);
             }
         }
-        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
+        bool listed = false;
+        if (q.list) {
+            // one atomic per warp: lanes take consecutive slots in lane order
+            const bool mine = items > kEmitThreadItems;
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (bal) {
+                unsigned long long first = 0;
+                if (lane == 0) first = atomicAdd(q.count, (unsigned long long)__popc(bal));
+                first = __shfl_sync(0xffffffffu, first, 0);
+                const unsigned long long slot = first + (unsigned long long)__popc(bal & ((1u << lane) - 1u));
+                if (mine && slot < q.cap) {
+                    q.list[slot] = make_uint2(id, base);
+                    listed = true;
+                }
+            }
+        }
+        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems && !listed);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
@@ -199,6 +261,27 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             emit_one<kMulti>(vp, stp, srank, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
                              s_start[wib], s_key0[wib], foot_side);
         }
+    }
+}
+
+// The listed splats, one per warp: warp w of the grid's W takes entries w, w + W, ...
+template <int kMulti>
+__global__ void __launch_bounds__(256, 2)
+emit_listed_kernel(ViewParams vp, TreeParams tp, EmitQueues q, const ushort4* __restrict__ rect,
+                   const unsigned long long* __restrict__ mask, const float4* __restrict__ rec,
+                   const float* __restrict__ cull, const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
+                   uint32_t* __restrict__ ival, const float4* __restrict__ foot_side) {
+    __shared__ uint32_t s_start[8][32], s_key0[8][32];
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    stage_tree(tp, vp.rank_of, stp, srank);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long n = *q.count < q.cap ? *q.count : q.cap;
+    const unsigned long long W = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib; e < n; e += W) {
+        const uint2 it = q.list[e];
+        emit_one<kMulti>(vp, stp, srank, it.x, it.y, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
+                         s_start[wib], s_key0[wib], foot_side);
     }
 }
 
@@ -475,6 +558,11 @@ __device__ __forceinline__ void stage_for_subset(const float4* __restrict__ rec,
         else msk |= (uint32_t)nc << 8;
     }
     if (msk && ball_holds_ellipse(sr, vp)) sr.b.w = copysignf(kInfF, sr.b.w);
+    // rho2 = +inf marks the records whose pairs need only the Mahalanobis test: the ball
+    // holds the ellipse, one subset holds every pixel, and alpha < alpha_max (so that
+    // sigma = alpha G needs no clamp); a record whose ball holds the ellipse but whose
+    // alpha reaches alpha_max keeps a ball bound that never fails instead
+    if (sr.b.w == kInfF && !(sr.b.y < vp.alpha_max)) sr.b.w = __int_as_float(0x7f7fffff);
 }
 
 // Compacts, per warp, the staged records whose mask has the warp's bit: wl[0..n) in
@@ -634,9 +722,16 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                     const float dx = pcx - A.x, dy = pcy - A.y;
                     const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
                     const float d2 = fmaf(u1, u1, u2 * u2);
-                    const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, x0 + pcx, y0 + pcy);
                     const float G = ex2_approx(d2 * kNegHalfLog2e);
-                    const float sig = ok ? fminf(B.y * G, vp.alpha_max) : 0.f;
+                    bool ok;
+                    float sig;
+                    if (B.w == kInfF) {   // warp-uniform: the Mahalanobis test alone, no clamp
+                        ok = d2 <= B.z;
+                        sig = ok ? B.y * G : 0.f;
+                    } else {
+                        ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, x0 + pcx, y0 + pcy);
+                        sig = ok ? fminf(B.y * G, vp.alpha_max) : 0.f;
+                    }
                     if (kCount && !frozen) {
                         ++n_eval;
                         n_behind += behind_front;
@@ -1307,10 +1402,19 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                         const float dx = pcx - A.x, dy = pcy - A.y;
                         const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
                         const float d2 = fmaf(u1, u1, u2 * u2);
-                        const bool ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
                         const float G = ex2_approx(d2 * kNegHalfLog2e);
                         const float raw = B.y * G;
-                        const float sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
+                        bool ok, grad;
+                        float sig;
+                        if (B.w == kInfF) {   // warp-uniform: the Mahalanobis test alone, no clamp
+                            ok = d2 <= B.z;
+                            grad = ok;
+                            sig = ok ? raw : 0.f;
+                        } else {
+                            ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
+                            grad = ok && raw < vp.alpha_max;
+                            sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
+                        }
                         if (kCount && !frozen) {
                             ++n_eval;
                             n_contrib += ok;
@@ -1319,7 +1423,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                         const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
                         acc = fmaf(w, grgb, acc);
                         const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
-                        const float h = (ok && raw < vp.alpha_max) ? sig * dsig : 0.f;   // sigma dL/dsigma
+                        const float h = grad ? sig * dsig : 0.f;   // sigma dL/dsigma
                         sh_h[warp][lane * kBwdSubPad + (t - s0)] = h;
                         sh_w[warp][lane * kBwdSubPad + (t - s0)] = w;
                         any |= ok;   // a pair that fails has h = w = 0
@@ -1526,16 +1630,37 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     const int64_t want = (n_vis + 255) / 256;      // one warp per 32 splats
     const int64_t cap = 152 * 16;                  // grid-stride beyond: amortises the tree copy
     unsigned grid = (unsigned)(want < cap ? want : cap);
-    // work counters: counters[4] and [5] (zeroed with the others at the start of the list build)
+    // work counters (zeroed with the others at the start of the list build): [4], [5] the
+    // emission queues, [8], [9] the splats each launch deferred
+    auto queues_of = [&](int multi) {
+        EmitQueues q;
+        q.list = b.units ? reinterpret_cast<uint2*>(b.units) + (size_t)multi * b.unit_cap : nullptr;
+        q.count = b.counters + 8 + multi;
+        q.cap = b.units ? b.unit_cap : 0u;
+        return q;
+    };
+    const unsigned lgrid = 152 * 8;
+    const EmitQueues q0 = queues_of(0);
     emit_kernel<0><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
-                                        b.ikey, b.ival, b.counters + 4, nullptr);
+                                        b.ikey, b.ival, b.counters + 4, nullptr, q0);
     RGS_CUDA_LAUNCH_CHECK();
+    if (q0.list) {
+        emit_listed_kernel<0><<<lgrid, 256, 0, s>>>(vp, tp, q0, b.rect, b.mask, b.rec, b.cull, b.cull_chunk, b.ikey,
+                                                    b.ival, nullptr);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
     if (vp.K > 1) {
         // foot reading: straddlers are clipped over the foot's depth interval (side array)
+        const float4* side = vp.foot ? b.foot_side : nullptr;
+        const EmitQueues q1 = queues_of(1);
         emit_kernel<1><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull,
-                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5,
-                                            vp.foot ? b.foot_side : nullptr);
+                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5, side, q1);
         RGS_CUDA_LAUNCH_CHECK();
+        if (q1.list) {
+            emit_listed_kernel<1><<<lgrid, 256, 0, s>>>(vp, tp, q1, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
+                                                        b.ikey, b.ival, side);
+            RGS_CUDA_LAUNCH_CHECK();
+        }
     }
     return RGS_OK;
 }

@@ -197,7 +197,11 @@ struct RasterBuffers {
     uint32_t* skey_alt;   // [N]                         (sort buffer b)
     uint32_t* sid_alt;    // [N]
     uint32_t* ioff;       // [N] instance offsets in depth order
-    unsigned long long* counters;  // [8]: total instances, visible splats, -, -, emission work queues (2)
+    unsigned long long* counters;  // [16]: total instances, visible splats, -, -, emission work queues (2),
+                                   // -, -, the splats each emission launch deferred (2), -
+    uint4* units;         // per emission launch a list of unit_cap (id, instance base) pairs: the
+                          // splats its first kernel defers to the second (nullptr: none deferred)
+    uint32_t unit_cap;
     float4* g2d;          // [N * 3] (backward only)
     // per (tile, subset)
     uint2* ranges;        // [tiles * K]
