@@ -446,10 +446,11 @@ def foot_reading_report(trainer, cams) -> dict:
 
 
 def sort_passes(L, H, W):
-    """Radix passes of the (tile, subset) instance sort: 8-bit digits over the key's bits."""
+    """Radix passes of the (tile, subset) instance sort: two wide passes for keys of 17 to 20
+    bits, 8-bit digits otherwise."""
     tiles = ((H + 15) // 16) * ((W + 15) // 16)
     bits = max(0, (tiles - 1).bit_length()) + L
-    return -(-bits // 8)
+    return 2 if 16 < bits <= 20 else -(-bits // 8)
 
 
 def variant_report(trainer, cams, targets, args) -> dict:

@@ -260,6 +260,22 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
                            int W, const float bg[3], const float* dL_dimage, const float* dL_dT_out,
                            float* dL_dpartial_C, float* dL_dpartial_T, void* stream);
 
+/* Stable LSD radix sort of (uint32 key, uint32 value) pairs by the low end_bit bits of the
+ * keys (1..32): the primitive that orders the tile instances by (tile, subset), leaving each
+ * subset's instances of a tile in the depth order of Eq. 3 (Sec. 3.1-3.2), and the splats
+ * by depth.  keys, vals, keys_alt, vals_alt: device arrays of n pairs (0 <= n < 2^32), owned
+ * by the caller.  The sorted pairs end up in (keys, vals), or in (keys_alt, vals_alt) when
+ * *in_alt is 1 on return; the other two arrays are overwritten as scratch.  Every key must
+ * be below 2^end_bit (higher bits may or may not take part in the order); pairs with equal
+ * keys keep their input order.  temp:
+ * device scratch of at least rgs_sort_temp_bytes(n) bytes.  Asynchronous on `stream`.
+ * n = 0 returns at once (*in_alt = 0; the arrays may then be NULL).  RGS_EINVAL on a NULL
+ * in_alt, a NULL array when n > 0, n < 0 or end_bit outside 1..32; RGS_EOVERFLOW when temp
+ * is too small or n >= 2^32. */
+size_t rgs_sort_temp_bytes(int64_t n);
+int rgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int end_bit,
+                   void* temp, size_t temp_bytes, void* stream, int* in_alt);
+
 /* Backward of rgs_render_fwd with the merge (the "backward process" of Sec. 3.4): routes
  * dL/dimage [3,H,W] through Eq. 5 to each subset's (C_k, T_k), replays each subset's blend
  * from the stored partials, and pulls the per-splat 2D gradients back through the

@@ -279,6 +279,12 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     // least 8192, at most 2^20)
     const int64_t ucap = N / 4 < 8192 ? 8192 : (N / 4 > (1 << 20) ? (1 << 20) : N / 4);
     t.units = (uint4*)take(sizeof(uint2) * 2 * (size_t)ucap);
+    // items kept by the count: up to 8 per splat (at least 2^16, at most 2^27 records of 16 B)
+    const int64_t icap = N * 8 < (1 << 16) ? (1 << 16) : (N * 8 > (1ll << 27) ? (1ll << 27) : N * 8);
+    t.item_at = (uint32_t*)take(4 * (size_t)N);
+    t.ibase = (uint32_t*)take(4 * (size_t)N);
+    t.items = (uint4*)take(sizeof(uint4) * (size_t)icap);
+    t.item_cap = (uint32_t)icap;
     t.unit_cap = (uint32_t)ucap;
     t.ranges = (uint2*)take(sizeof(uint2) * tiles * K);
     t.cull_chunk = (float2*)take(sizeof(float2) * (size_t)tiles * K / 16 + sizeof(float2) * 2048 * K);
@@ -849,6 +855,27 @@ int rgs_merge_partials_bwd(const float* partial_C, const float* partial_T, const
     ProfScope ps(ST_MERGE_BWD, (cudaStream_t)stream);
     return launch_merge_bwd(partial_C, partial_T, order_dev, K, H, W, bg, dL_dimage, dL_dT_out, dL_dpartial_C,
                             dL_dpartial_T, (cudaStream_t)stream);
+}
+
+size_t rgs_sort_temp_bytes(int64_t n) { return radix_temp_bytes(n > 0 ? n : 1); }
+
+int rgs_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, int64_t n, int end_bit,
+                   void* temp, size_t temp_bytes, void* stream, int* in_alt) {
+    if (!in_alt || n < 0 || end_bit < 1 || end_bit > 32) {
+        set_error("sort_pairs: invalid argument");
+        return RGS_EINVAL;
+    }
+    *in_alt = 0;
+    if (n == 0) return RGS_OK;
+    if (!keys || !vals || !keys_alt || !vals_alt || !temp) {
+        set_error("sort_pairs: NULL array");
+        return RGS_EINVAL;
+    }
+    bool alt = false;
+    const int rc = radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, end_bit, temp, temp_bytes, (cudaStream_t)stream,
+                                    &alt);
+    *in_alt = alt ? 1 : 0;
+    return rc;
 }
 
 int rgs_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const int64_t* seg_offsets_host,

@@ -326,6 +326,29 @@ __device__ __forceinline__ void item_span(const Footprint& f, const ViewParams& 
     item_cols<kMulti>(f, vp, tp, k, nsub, z, ty, c0, c1);
 }
 
+// A splat with at most this many (subset, row) items is counted and emitted by one
+// thread; the others by a warp.
+constexpr int kSplatThreadItems = 4;
+
+// Items kept by the count for the emission.  A warp-counted splat j whose items fit in
+// the list gets item_at[j] = its first entry there (kNoItems: not kept, the emission
+// derives its items again); entry item_at[j] + it describes item it of the splat:
+//   x = j, y = the item's first instance relative to the splat's first instance,
+//   z = tile columns c0 | c1 << 16 (int16 each; (1, 0) when empty),
+//   w = tile row | subset << 16;  x = kNoItems marks an entry that holds no item.
+// The emission then writes every kept item without the footprint arithmetic, and count
+// and emission agree by construction.
+constexpr uint32_t kNoItems = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint4 pack_item(uint32_t j, uint32_t first, int c0, int c1, int ty, int k) {
+    if (c0 > c1) {
+        c0 = 1;
+        c1 = 0;
+    }
+    return make_uint4(j, first, (uint32_t)(uint16_t)(int16_t)c0 | ((uint32_t)(uint16_t)(int16_t)c1 << 16),
+                      (uint32_t)ty | ((uint32_t)k << 16));
+}
+
 // Depth culling of the backward's instances: `cull` ([tiles, K] by view rank, nullptr:
 // keep all) holds, per (tile, subset), the depth of the last splat the forward staged
 // before every pixel of the tile was done in that subset (+inf if that never happened).

@@ -269,7 +269,7 @@ __device__ __forceinline__ uint32_t depth_fraction(float zh, float zl) {
 }
 
 // ------------------------------------------------------------------ forward kernel
-constexpr int kWarpCountItems = 4;   // splats with more (subset, row) items are counted by the whole warp
+constexpr int kWarpCountItems = kSplatThreadItems;   // splats with more items are counted by the whole warp
 
 // Projection of splat i (valid: i < n) into one view.  Outputs go to index j of the
 // per-splat arrays of b; the instance and visible-splat totals are added to counters[0..1]
@@ -372,6 +372,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
             count += item_tiles(f, vp, tp, rank_of, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
     }
     unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
+    uint32_t span_at = kNoItems;
     while (big) {
         const int src = __ffs(big) - 1;
         big &= big - 1;
@@ -385,13 +386,45 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         Footprint f = make_footprint(fx_, fy_, a_, b_, c_, al_, r_, vp);
         f.zr = __shfl_sync(0xffffffffu, zr, src);
         const int ns = __popcll(m_);
-        uint32_t acc = 0;
-        for (int it = lane; it < items_; it += 32)
-            acc += item_tiles(f, vp, tp, rank_of, m_, ns, z_, t0_, rows_, it, b.cull, b.cull_chunk);
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == src) count = acc;
+        const uint32_t j_ = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)j, src);
+        // keep the items for the emission when the list has room (counters[12] counts the
+        // entries taken; the one reservation that crosses the end voids its part inside)
+        uint32_t sb = kNoItems;
+        if (b.items) {
+            unsigned long long s0 = 0;
+            if (lane == 0) s0 = atomicAdd(&counters[12], (unsigned long long)items_);
+            s0 = __shfl_sync(0xffffffffu, s0, 0);
+            if (s0 + (unsigned long long)items_ <= b.item_cap) {
+                sb = (uint32_t)s0;
+            } else {
+                for (unsigned long long q = s0 + (unsigned long long)lane; q < b.item_cap; q += 32)
+                    b.items[q] = make_uint4(kNoItems, 0u, 0u, 0u);
+            }
+        }
+        uint32_t acc = 0;   // instances of the rounds before
+        for (int it0 = 0; it0 < items_; it0 += 32) {
+            const int it = it0 + lane;
+            int ty = 0, k = 0, c0 = 1, c1 = 0;
+            uint32_t w = 0;
+            if (it < items_) {
+                item_span(f, vp, tp, m_, ns, z_, t0_, rows_, it, ty, k, c0, c1);
+                w = kept_tiles(b.cull, b.cull_chunk, vp, ty, c0, c1, rank_of[k], z_);
+            }
+            uint32_t incl = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (sb != kNoItems && it < items_) b.items[sb + it] = pack_item(j_, acc + incl - w, c0, c1, ty, k);
+            acc += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == src) {
+            count = acc;
+            span_at = sb;
+        }
     }
     if (valid) b.cnt[j] = count;
+    if (valid && b.item_at && items > kWarpCountItems) b.item_at[j] = span_at;
     // totals: instances and visible splats
     unsigned long long c64 = count;
     unsigned vis_n = count > 0;

@@ -93,10 +93,10 @@ __device__ __forceinline__ SplatItems load_items(const ViewParams& vp, uint32_t 
 template <int kMulti, bool kWrite>
 __device__ __forceinline__ uint32_t emit_round(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of,
                                                uint32_t id, const SplatItems& s, int it0, uint32_t base,
-                                               uint32_t tile_base, const float* __restrict__ cull,
-                                               const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
-                                               uint32_t* __restrict__ ival, int lane, uint32_t* s_start,
-                                               uint32_t* s_key0) {
+                                               uint32_t tile_base,
+                                               const float* __restrict__ cull, const float2* __restrict__ chunk,
+                                               uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival, int lane,
+                                               uint32_t* s_start, uint32_t* s_key0) {
     const int it = it0 + lane;
     int c0 = 1, c1 = 0, ty = 0;
     uint32_t rank = 0;
@@ -172,7 +172,7 @@ struct EmitQueues {
 };
 
 // Instances of one small splat (at most kEmitThreadItems items), written by one thread.
-constexpr int kEmitThreadItems = 4;
+constexpr int kEmitThreadItems = kSplatThreadItems;
 
 template <int kMulti>
 __device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreeParams& tp, const int8_t* rank_of,
@@ -206,7 +206,8 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const uint32_t* __restrict__ ioff, const ushort4* __restrict__ rect,
             const unsigned long long* __restrict__ mask, const float4* __restrict__ rec, const float* __restrict__ cull,
             const float2* __restrict__ chunk, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-            unsigned long long* __restrict__ queue, const float4* __restrict__ foot_side, EmitQueues q) {
+            unsigned long long* __restrict__ queue, const float4* __restrict__ foot_side, EmitQueues q,
+            const uint32_t* __restrict__ item_at, uint32_t* __restrict__ ibase) {
     __shared__ uint32_t s_start[8][32], s_key0[8][32];
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
@@ -238,9 +239,13 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             }
         }
         bool listed = false;
+        if (item_at && items > kEmitThreadItems && item_at[id] != kNoItems) {
+            ibase[id] = base;   // the count kept its items: emit_items_kernel writes them
+            listed = true;
+        }
         if (q.list) {
             // one atomic per warp: lanes take consecutive slots in lane order
-            const bool mine = items > kEmitThreadItems;
+            const bool mine = items > kEmitThreadItems && !listed;
             const unsigned bal = __ballot_sync(0xffffffffu, mine);
             if (bal) {
                 unsigned long long first = 0;
@@ -282,6 +287,84 @@ emit_listed_kernel(ViewParams vp, TreeParams tp, EmitQueues q, const ushort4* __
         const uint2 it = q.list[e];
         emit_one<kMulti>(vp, stp, srank, it.x, it.y, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
                          s_start[wib], s_key0[wib], foot_side);
+    }
+}
+
+// The items the count kept, 32 per warp round (lane l takes entry q0 + l): each lane
+// reads its item's record, the warp places the items' instance runs in one virtual range
+// by a prefix sum and writes it together (lane l writes positions l, l + 32, ...), each
+// position going to its item's run at that splat's first instance plus the item's offset.
+// Items of one splat are consecutive entries with consecutive runs, so the stores stay
+// contiguous within a splat.
+__global__ void __launch_bounds__(256)
+emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const unsigned long long* __restrict__ n_items,
+                  uint32_t cap, const uint32_t* __restrict__ ibase, const float4* __restrict__ rec,
+                  const float* __restrict__ cull, const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
+                  uint32_t* __restrict__ ival) {
+    __shared__ uint32_t s_start[8][32], s_key0[8][32], s_dst[8][32], s_id[8][32];
+    __shared__ int8_t srank[64];
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) srank[k] = vp.rank_of[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long taken = *n_items;
+    const unsigned long long n = taken < cap ? taken : cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32;
+    for (unsigned long long q0 = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib) * 32; q0 < n;
+         q0 += stride) {
+        const unsigned long long q = q0 + lane;
+        uint32_t id = kNoItems, w = 0, dst = 0, key0 = 0, rank = 0;
+        int ty = 0, c0 = 1, c1 = 0;
+        float z = 0.f;
+        if (q < n) {
+            const uint4 r = items[q];
+            id = r.x;
+            if (id != kNoItems) {
+                c0 = (int)(int16_t)(r.z & 0xFFFFu);
+                c1 = (int)(int16_t)(r.z >> 16);
+                ty = (int)(r.w & 0xFFFFu);
+                rank = (uint32_t)srank[r.w >> 16];
+                if (cull) z = rec[3 * (size_t)id + 2].w;
+                w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, z);
+                dst = ibase[id] + r.y;
+                key0 = (((uint32_t)(ty * vp.tiles_x) + (uint32_t)c0) << vp.L) | rank;
+            }
+        }
+        uint32_t incl = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (!cull) {
+            s_start[wib][lane] = incl - w;
+            s_key0[wib][lane] = key0;
+            s_dst[wib][lane] = dst;
+            s_id[wib][lane] = id;
+            __syncwarp();
+            int cur = 0;
+            for (uint32_t o = (uint32_t)lane; o < total; o += 32) {
+                while (cur < 31 && s_start[wib][cur + 1] <= o) ++cur;   // runs of empty items share a start
+                const uint32_t off = o - s_start[wib][cur];
+                ikey[s_dst[wib][cur] + off] = s_key0[wib][cur] + (off << vp.L);
+                ival[s_dst[wib][cur] + off] = s_id[wib][cur];
+            }
+            __syncwarp();
+        } else if (w) {
+            uint32_t pos = dst;
+            const uint32_t first = (uint32_t)(ty * vp.tiles_x);
+            for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+                const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+                const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
+                if (z > mm.y) continue;
+                const bool all = z <= mm.x;
+                for (int c = lo; c <= hi; ++c) {
+                    if (!all && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
+                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+                    ival[pos] = id;
+                    ++pos;
+                }
+            }
+        }
     }
 }
 
@@ -1631,7 +1714,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     const int64_t cap = 152 * 16;                  // grid-stride beyond: amortises the tree copy
     unsigned grid = (unsigned)(want < cap ? want : cap);
     // work counters (zeroed with the others at the start of the list build): [4], [5] the
-    // emission queues, [8], [9] the splats each launch deferred
+    // emission queues, [8], [9] the splats each launch deferred, [12] the items the count kept
     auto queues_of = [&](int multi) {
         EmitQueues q;
         q.list = b.units ? reinterpret_cast<uint2*>(b.units) + (size_t)multi * b.unit_cap : nullptr;
@@ -1640,23 +1723,32 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
         return q;
     };
     const unsigned lgrid = 152 * 8;
-    const EmitQueues q0 = queues_of(0);
+    const uint32_t* item_at = b.items ? b.item_at : nullptr;
+    const EmitQueues q0 = queues_of(0), q1 = queues_of(1);
+    // foot reading: straddlers are clipped over the foot's depth interval (side array)
+    const float4* side = vp.foot ? b.foot_side : nullptr;
+    // 1. splats of few items, the first instance of each splat whose items the count kept,
+    //    and the list of the others
     emit_kernel<0><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
-                                        b.ikey, b.ival, b.counters + 4, nullptr, q0);
+                                        b.ikey, b.ival, b.counters + 4, nullptr, q0, item_at, b.ibase);
     RGS_CUDA_LAUNCH_CHECK();
+    if (vp.K > 1) {
+        emit_kernel<1><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull,
+                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5, side, q1, item_at, b.ibase);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
+    // 2. the kept items
+    if (item_at) {
+        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.counters + 12, b.item_cap, b.ibase, b.rec, b.cull,
+                                                  b.cull_chunk, b.ikey, b.ival);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
+    // 3. the listed splats
     if (q0.list) {
         emit_listed_kernel<0><<<lgrid, 256, 0, s>>>(vp, tp, q0, b.rect, b.mask, b.rec, b.cull, b.cull_chunk, b.ikey,
                                                     b.ival, nullptr);
         RGS_CUDA_LAUNCH_CHECK();
-    }
-    if (vp.K > 1) {
-        // foot reading: straddlers are clipped over the foot's depth interval (side array)
-        const float4* side = vp.foot ? b.foot_side : nullptr;
-        const EmitQueues q1 = queues_of(1);
-        emit_kernel<1><<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.ioff, b.rect, b.mask, b.rec, b.cull,
-                                            b.cull_chunk, b.ikey, b.ival, b.counters + 5, side, q1);
-        RGS_CUDA_LAUNCH_CHECK();
-        if (q1.list) {
+        if (vp.K > 1) {
             emit_listed_kernel<1><<<lgrid, 256, 0, s>>>(vp, tp, q1, b.rect, b.mask, b.rec, b.cull, b.cull_chunk,
                                                         b.ikey, b.ival, side);
             RGS_CUDA_LAUNCH_CHECK();

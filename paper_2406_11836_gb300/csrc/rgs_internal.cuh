@@ -198,7 +198,12 @@ struct RasterBuffers {
     uint32_t* sid_alt;    // [N]
     uint32_t* ioff;       // [N] instance offsets in depth order
     unsigned long long* counters;  // [16]: total instances, visible splats, -, -, emission work queues (2),
-                                   // -, -, the splats each emission launch deferred (2), -
+                                   // -, -, the splats each emission launch deferred (2), -, -,
+                                   // items kept by the count (may exceed item_cap), -
+    uint32_t* item_at;    // [N] items kept by the count (footprint.cuh; nullptr: none kept)
+    uint4* items;         // [item_cap] their records
+    uint32_t* ibase;      // [N] first instance of each splat whose items were kept (set by the emission)
+    uint32_t item_cap;
     uint4* units;         // per emission launch a list of unit_cap (id, instance base) pairs: the
                           // splats its first kernel defers to the second (nullptr: none deferred)
     uint32_t unit_cap;

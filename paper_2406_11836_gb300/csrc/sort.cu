@@ -119,9 +119,10 @@ constexpr int kBlockItems = kSortTile * kBlockTiles;   // 16384
 // keys per round (two 16-byte loads when `vec` and lo is a multiple of 8) and adds each
 // run of equal digits with one shared atomic (the later passes see keys already ordered
 // by their low digits, whose high digits repeat).  The whole block calls it.
+template <int kThreads = kSortThreads, uint32_t kMask = kRadix - 1>
 __device__ __forceinline__ void hist_runs(const uint32_t* __restrict__ keys, int64_t lo, int64_t hi, int shift, bool vec,
                                           uint32_t* hist) {
-    for (int64_t b = lo; b < hi; b += kSortThreads * 8) {   // uniform trip count across the block
+    for (int64_t b = lo; b < hi; b += kThreads * 8) {   // uniform trip count across the block
         const int64_t i0 = b + (int64_t)threadIdx.x * 8;
         uint32_t k[8];
         if (vec && i0 + 8 <= hi) {
@@ -134,11 +135,11 @@ __device__ __forceinline__ void hist_runs(const uint32_t* __restrict__ keys, int
         }
         const int m = hi - i0 < 8 ? (int)(hi - i0) : 8;   // may be <= 0 past the end
         if (m > 0) {
-            uint32_t cur = (k[0] >> shift) & (kRadix - 1), run = 1;
+            uint32_t cur = (k[0] >> shift) & kMask, run = 1;
 #pragma unroll
             for (int j = 1; j < 8; ++j) {
                 if (j >= m) break;
-                const uint32_t d = (k[j] >> shift) & (kRadix - 1);
+                const uint32_t d = (k[j] >> shift) & kMask;
                 if (d != cur) {
                     atomicAdd(&hist[cur], run);
                     cur = d;
@@ -285,6 +286,179 @@ radix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restr
     }
 }
 
+// ------------------------------------------------------------------ wide-digit passes
+// Keys of 17 to 20 bits (the (tile, subset) keys of a 4K view) are sorted in two passes of
+// up to 10 bits instead of three of 8: a third less traffic.  With 1024 digits a tile must
+// be large for its runs of equal digits to fill whole sectors when they are written out,
+// so a block of 512 threads ranks 8192 keys at a time (16 per thread), with 16-bit
+// per-warp digit counters; the tile and the counters take 108 KB of shared memory, two
+// blocks per SM.  Same structure as the 8-bit passes otherwise: per-block digit histograms
+// written digit-major, one scan, a stable downsweep.
+constexpr int kWideThreads = 512;
+constexpr int kWideWarps = kWideThreads / 32;
+constexpr int kWideItems = 16;
+constexpr int kWideTile = kWideThreads * kWideItems;           // 8192
+constexpr int kWideBlockTiles = 8;
+constexpr int kWideBlockItems = kWideTile * kWideBlockTiles;   // 65536
+constexpr int kWideMaxBits = 10;
+
+template <int kBits>
+struct WideSmem {
+    static constexpr int kBins = 1 << kBits;
+    uint16_t whist[kWideWarps][kBins];
+    uint32_t skeys[kWideTile];
+    uint32_t svals[kWideTile];
+    uint32_t dstart[kBins];
+    uint32_t dtot[kBins];
+    uint32_t goff[kBins];
+    uint32_t wsum[kWideWarps];
+};
+
+template <int kBits>
+__global__ void __launch_bounds__(kWideThreads, 2)
+wide_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
+                    uint32_t nblocks, bool vec) {
+    constexpr int kBins = 1 << kBits;
+    __shared__ uint32_t hist[kBins];
+    for (int d = threadIdx.x; d < kBins; d += kWideThreads) hist[d] = 0;
+    __syncthreads();
+    const int64_t lo = (int64_t)blockIdx.x * kWideBlockItems;
+    hist_runs<kWideThreads, (uint32_t)(kBins - 1)>(keys, lo, min(n, lo + kWideBlockItems), shift, vec, hist);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kBins; d += kWideThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
+}
+
+template <int kBits>
+__global__ void __launch_bounds__(kWideThreads, 2)
+wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                      uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
+                      uint32_t nblocks) {
+    constexpr int kBins = 1 << kBits;
+    constexpr uint32_t kMask = (uint32_t)kBins - 1u;
+    constexpr int kPer = kBins / kWideThreads > 0 ? kBins / kWideThreads : 1;   // digits per thread in the scan
+    extern __shared__ __align__(16) unsigned char wide_smem_raw[];
+    WideSmem<kBits>& sm = *reinterpret_cast<WideSmem<kBits>*>(wide_smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kBins; d += kWideThreads) sm.goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    const int64_t lo = (int64_t)blockIdx.x * kWideBlockItems;
+    const int64_t hi = min(n, lo + kWideBlockItems);
+    for (int64_t base = lo; base < hi; base += kWideTile) {   // tiles in order: stable
+        const int count = hi - base < kWideTile ? (int)(hi - base) : kWideTile;
+        uint32_t* wh = reinterpret_cast<uint32_t*>(&sm.whist[0][0]);
+        for (int i = threadIdx.x; i < kWideWarps * kBins / 2; i += kWideThreads) wh[i] = 0u;
+        // warp w holds tile items [w*512, (w+1)*512) in 16 rounds of 32 lanes: (round, lane)
+        // order is input order
+        // (the values are read only when the keys are placed, to keep registers for the ranks)
+        uint32_t key[kWideItems];
+#pragma unroll
+        for (int r = 0; r < kWideItems; ++r) {
+            const int li = warp * (kWideItems * 32) + r * 32 + lane;
+            key[r] = li < count ? kin[base + li] : 0u;
+        }
+        __syncthreads();
+        uint32_t rank2[kWideItems / 2];   // ranks within the warp, two 16-bit halves per word
+#pragma unroll
+        for (int r = 0; r < kWideItems; ++r) {
+            const int li = warp * (kWideItems * 32) + r * 32 + lane;
+            const uint32_t dig = li < count ? (key[r] >> shift) & kMask : (uint32_t)kBins;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig);
+            const unsigned lower = peers & ((1u << lane) - 1u);
+            const uint32_t prior = dig < (uint32_t)kBins ? (uint32_t)sm.whist[warp][dig] : 0u;
+            const uint32_t rk = prior + (uint32_t)__popc(lower);
+            if (r & 1) rank2[r >> 1] |= rk << 16;
+            else rank2[r >> 1] = rk;
+            __syncwarp();
+            if (dig < (uint32_t)kBins && lower == 0u)
+                sm.whist[warp][dig] = (uint16_t)(prior + (uint32_t)__popc(peers));
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps, then the digit totals
+        for (int d = threadIdx.x; d < kBins; d += kWideThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kWideWarps; ++w) {
+                const uint32_t c = sm.whist[w][d];
+                sm.whist[w][d] = (uint16_t)run;
+                run += c;
+            }
+            sm.dtot[d] = run;
+        }
+        __syncthreads();
+        // exclusive block scan of the digit totals: thread t owns digits [t kPer, t kPer + kPer)
+        {
+            const int d0 = threadIdx.x * kPer;
+            uint32_t loc = 0;
+            if (d0 < kBins) {
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) loc += sm.dtot[d0 + j];
+            }
+            uint32_t incl = loc;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) sm.wsum[warp] = incl;
+            __syncthreads();
+            uint32_t b = 0;
+            for (int w = 0; w < warp; ++w) b += sm.wsum[w];
+            uint32_t run = b + incl - loc;
+            if (d0 < kBins) {
+#pragma unroll
+                for (int j = 0; j < kPer; ++j) {
+                    sm.dstart[d0 + j] = run;
+                    run += sm.dtot[d0 + j];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kWideItems; ++r) {
+            const int li = warp * (kWideItems * 32) + r * 32 + lane;
+            if (li < count) {
+                const uint32_t dig = (key[r] >> shift) & kMask;
+                const uint32_t rk = (r & 1) ? rank2[r >> 1] >> 16 : rank2[r >> 1] & 0xFFFFu;
+                const uint32_t pos = sm.dstart[dig] + (uint32_t)sm.whist[warp][dig] + rk;
+                sm.skeys[pos] = key[r];
+                sm.svals[pos] = vin[base + li];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < count; i += kWideThreads) {
+            const uint32_t k = sm.skeys[i];
+            const uint32_t d = (k >> shift) & kMask;
+            const uint32_t o = sm.goff[d] + (uint32_t)i - sm.dstart[d];
+            kout[o] = k;
+            vout[o] = sm.svals[i];
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < kBins; d += kWideThreads) sm.goff[d] += sm.dtot[d];
+        __syncthreads();
+    }
+}
+
+template <int kBits>
+int wide_pass(const uint32_t* ka, const uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n, int shift,
+              uint32_t* counts, void* stemp, size_t sbytes, cudaStream_t s) {
+    constexpr int kBins = 1 << kBits;
+    const int64_t nb = (n + kWideBlockItems - 1) / kWideBlockItems;
+    const int64_t nc = nb * kBins;
+    const size_t smem = sizeof(WideSmem<kBits>);
+    // the attribute belongs to the function on the current device; setting it on every
+    // call costs a driver call per pass and is always right
+    RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    wide_upsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb,
+                                                                      ((uintptr_t)ka & 15) == 0);
+    RGS_CUDA_LAUNCH_CHECK();
+    int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
+    if (rc != RGS_OK) return rc;
+    wide_downsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, smem, s>>>(ka, va, kb, vb, n, shift, counts,
+                                                                           (uint32_t)nb);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
 // ------------------------------------------------------------------ device-counted passes
 // Variants whose element count is read from device memory (a counter written by an
 // earlier kernel on the stream), so that the launches need no host round trip and can
@@ -401,8 +575,9 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, int load, c
 }
 
 size_t radix_temp_bytes(int64_t n) {
-    int64_t nb = cdiv(n > 0 ? n : 1, kBlockItems);
-    int64_t nc = nb * kRadix;
+    const int64_t nc8 = cdiv(n > 0 ? n : 1, kBlockItems) * kRadix;
+    const int64_t ncw = cdiv(n > 0 ? n : 1, kWideBlockItems) * ((int64_t)1 << kWideMaxBits);
+    const int64_t nc = nc8 > ncw ? nc8 : ncw;
     return align256((size_t)nc * 4) + scan_temp_bytes(nc);
 }
 
@@ -416,8 +591,9 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_
     }
     int64_t nb = cdiv(n, kBlockItems);
     int64_t nc = nb * kRadix;
-    size_t cbytes = align256((size_t)nc * 4);
-    if (temp_bytes < cbytes + scan_temp_bytes(nc)) {
+    const int64_t ncw = cdiv(n, kWideBlockItems) * ((int64_t)1 << kWideMaxBits);
+    size_t cbytes = align256((size_t)(nc > ncw ? nc : ncw) * 4);
+    if (temp_bytes < cbytes + scan_temp_bytes(nc > ncw ? nc : ncw)) {
         set_error("radix sort: temporary buffer too small");
         return RGS_EOVERFLOW;
     }
@@ -425,6 +601,24 @@ int radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_
     void* stemp = (char*)temp + cbytes;
     size_t sbytes = temp_bytes - cbytes;
     uint32_t *ka = keys, *va = vals, *kb = keys_alt, *vb = vals_alt;
+    if (end_bit > 2 * kRadixBits && end_bit <= 2 * kWideMaxBits) {
+        // two wide passes: the low ceil(end_bit / 2) bits, then the rest
+        const int b0 = (end_bit + 1) / 2;
+        int shift = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int bits = pass == 0 ? b0 : end_bit - b0;
+            int rc = bits == 10   ? wide_pass<10>(ka, va, kb, vb, n, shift, counts, stemp, sbytes, s)
+                     : bits == 9  ? wide_pass<9>(ka, va, kb, vb, n, shift, counts, stemp, sbytes, s)
+                                  : wide_pass<8>(ka, va, kb, vb, n, shift, counts, stemp, sbytes, s);
+            if (rc != RGS_OK) return rc;
+            shift += bits;
+            uint32_t* t;
+            t = ka; ka = kb; kb = t;
+            t = va; va = vb; vb = t;
+            *in_alt = !*in_alt;
+        }
+        return RGS_OK;
+    }
     for (int shift = 0; shift < end_bit; shift += kRadixBits) {
         radix_upsweep_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb,
                                                                    ((uintptr_t)ka & 15) == 0);

@@ -118,6 +118,10 @@ def lib():
     L.rgs_serve_lane_bytes.argtypes = [c_void_p, POINTER(Gaussians), POINTER(ServeConfig), c_int64, POINTER(c_size_t)]
     L.rgs_serve_destroy.argtypes = [c_void_p]
     L.rgs_serve_hold.argtypes = [c_void_p, c_int]
+    L.rgs_sort_temp_bytes.restype = c_size_t
+    L.rgs_sort_temp_bytes.argtypes = [c_int64]
+    L.rgs_sort_pairs.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int, c_void_p, c_size_t, c_void_p,
+                                 POINTER(c_int)]
     _lib = L
     return L
 
@@ -354,6 +358,22 @@ def merge_partials_bwd(partial_C, partial_T, order, dL_dimage, dL_dT=None, bg=(0
     return dC, dT
 
 
+def sort_pairs(keys, vals, end_bit, stream=None):
+    """Stable radix sort of int32 device tensors (uint32 bit patterns) whose keys are all
+    below 2**end_bit; returns the sorted (keys, vals) (new tensors)."""
+    n = int(keys.numel())
+    if int(vals.numel()) != n:
+        raise ValueError("sort_pairs: keys and values differ in length")
+    ka, va = keys.contiguous().clone(), vals.contiguous().clone()
+    kb, vb = torch.empty_like(ka), torch.empty_like(va)
+    temp = torch.empty(int(lib().rgs_sort_temp_bytes(n)), dtype=torch.uint8, device=keys.device)
+    alt = ctypes.c_int(0)
+    _check(lib().rgs_sort_pairs(_ptr(ka), _ptr(va), _ptr(kb), _ptr(vb), n, int(end_bit), _ptr(temp), temp.numel(),
+                                _stream(stream), ctypes.byref(alt)))
+    torch.cuda.current_stream().synchronize()
+    return (kb, vb) if alt.value else (ka, va)
+
+
 def adam_step(param, grad, m, v, seg_offsets, seg_lr, step, beta1=0.9, beta2=0.999, eps=1e-15, zero_grad=True,
               stream=None, periodic=None):
     """One Adam step over flat buffers split into segments with their own rates.
@@ -549,4 +569,4 @@ ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
                "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",
-               "rgs_serve_hold")
+               "rgs_serve_hold", "rgs_sort_temp_bytes", "rgs_sort_pairs")

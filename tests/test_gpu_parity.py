@@ -160,6 +160,21 @@ def test_forward_edge_cases(R):
                    part_cap=1.0)
 
 
+def test_forward_large_splats_overflow_emission_lists(R):
+    """20,000 large splats over a 128x128 view and 16 subsets: nearly every splat has more
+    (subset, row) items than one thread emits, so the emission defers them to its second
+    launch and the count keeps their item spans, and both lists overflow (the deferred
+    list holds 8,192 splats, the span cache 2^16 items): the splats beyond them are emitted
+    on the spot from recomputed spans.  Image and final transmittance on every sampled
+    pixel; the partial maps where no contributor lies within rounding of a split plane
+    (with this many large splats about a fifth of the rays hold one, which either subset
+    may keep)."""
+    scene = W.uniform_cube_scene(20_000, seed=17, log_scale_mean=-1.0, log_scale_std=0.3)
+    cam = W.look_at((0.2, -2.6, 1.1), (0.0, 0.0, 0.0), 128, 128)
+    pix = W.sample_pixels(128, 128, count=1024, seed=3)
+    _check_forward(R, scene, cam, 4, pix=pix, part_cap=1.0)
+
+
 def test_forward_deterministic(R):
     wl = W.tiny()
     _, a = _render(R, wl.scene, wl.cameras[0], 2)
