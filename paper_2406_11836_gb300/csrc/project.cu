@@ -452,6 +452,62 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
     project_fwd_body<DEG, kVecSH, kFoot>(g, i, i < g.n, vp, stp, srank, b, i, b.counters, nullptr);
 }
 
+// Screen cull before the projection: a splat stays a candidate unless it is certainly
+// culled by the projection's own tests (behind the near plane, alpha below alpha_min, or
+// its ball-test ellipse off the image), judged in plain fp32 with margins that cover the
+// difference to the compensated centre: 1e-4 of the near depth, 1% of the ellipse's
+// semi-axes plus 2 pixels.  Alpha is computed exactly as the projection computes it.
+// Candidates are appended to `cand` (counters[13]); every other splat gets cnt = 0.
+// The projection then runs on full warps of candidates.
+__global__ void __launch_bounds__(256)
+screen_cull_kernel(rgs_gaussians g, ViewParams vp, uint32_t* __restrict__ cnt, uint32_t* __restrict__ cand,
+                   unsigned long long* __restrict__ counters) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    if (i < g.n) {
+        const float mx = g.means[3 * i], my = g.means[3 * i + 1], mz = g.means[3 * i + 2];
+        const float ls = fmaxf(g.log_scales[3 * i], fmaxf(g.log_scales[3 * i + 1], g.log_scales[3 * i + 2]));
+        const float alpha = 1.f / (1.f + __expf(-g.opacity_logits[i]));
+        const float x = fmaf(vp.R[0], mx, fmaf(vp.R[1], my, fmaf(vp.R[2], mz, vp.t[0])));
+        const float y = fmaf(vp.R[3], mx, fmaf(vp.R[4], my, fmaf(vp.R[5], mz, vp.t[1])));
+        const float z = fmaf(vp.R[6], mx, fmaf(vp.R[7], my, fmaf(vp.R[8], mz, vp.t[2])));
+        keep = alpha >= vp.alpha_min && !(z < vp.near_z * (1.f - 1e-4f));
+        if (keep && z > 0.f) {
+            const float rball = vp.trunc_mult * __expf(ls) / z;
+            const float cxp = fmaf(vp.fx, x / z, vp.cx), cyp = fmaf(vp.fy, y / z, vp.cy);
+            const float bx = (vp.fx * rball * 1.001f + 1.f) * 1.01f + 2.f, by = (vp.fy * rball * 1.001f + 1.f) * 1.01f + 2.f;
+            // off screen only when every comparison is certain (NaN and inf stay candidates)
+            if (cxp + bx < 0.f || cxp - bx > (float)vp.W || cyp + by < 0.f || cyp - by > (float)vp.H) keep = false;
+        }
+        if (!keep) cnt[i] = 0u;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(&counters[13], (unsigned long long)__popc(bal));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (keep) cand[first + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
+// The projection over the candidates of screen_cull_kernel, one per thread; the grid
+// covers every splat and the blocks past the candidate count (read from the device) end
+// at once.
+template <int DEG, bool kVecSH>
+__global__ void __launch_bounds__(256, 3)
+project_cand_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers b, const uint32_t* __restrict__ cand) {
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    const unsigned long long nc = b.counters[13];
+    const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((unsigned long long)blockIdx.x * blockDim.x >= nc) return;   // uniform across the block
+    stage_tree(tp, vp.rank_of, stp, srank);
+    const bool valid = c < nc;
+    const int64_t i = valid ? (int64_t)cand[c] : 0;
+    project_fwd_body<DEG, kVecSH, false>(g, i, valid, vp, stp, srank, b, i, b.counters, nullptr);
+}
+
 // Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
 // x % kMaxSlots, so the blocks of one splat range run back to back and read its
 // parameters from L2 after the first slot.  Outputs go to index slot * N + i.
@@ -710,10 +766,16 @@ int launch_clip_table_batch(const BatchSlot* slots, const BatchHeader* hdr, cons
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s) {
     unsigned grid = (unsigned)((g.n + 255) / 256);
-    if (vp.foot)
+    if (vp.foot) {
         RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V, true><<<grid, 256, 0, s>>>(g, vp, tp, b)));
-    else
-        RGS_DISPATCH_SH(g.sh_degree, vec_sh(g), (project_fwd_kernel<D, V, false><<<grid, 256, 0, s>>>(g, vp, tp, b)));
+    } else {
+        // the candidate list lives in vis_pos, which the compaction after the projection
+        // overwrites; counters[13] counts the candidates (zeroed with the others)
+        screen_cull_kernel<<<grid, 256, 0, s>>>(g, vp, b.cnt, b.vis_pos, b.counters);
+        RGS_CUDA_LAUNCH_CHECK();
+        RGS_DISPATCH_SH(g.sh_degree, vec_sh(g),
+                        (project_cand_kernel<D, V><<<grid, 256, 0, s>>>(g, vp, tp, b, b.vis_pos)));
+    }
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -199,7 +199,8 @@ struct RasterBuffers {
     uint32_t* ioff;       // [N] instance offsets in depth order
     unsigned long long* counters;  // [16]: total instances, visible splats, -, -, emission work queues (2),
                                    // -, -, the splats each emission launch deferred (2), -, -,
-                                   // items kept by the count (may exceed item_cap), -
+                                   // items kept by the count (may exceed item_cap), projection
+                                   // candidates (the list is in vis_pos until the compaction)
     uint32_t* item_at;    // [N] items kept by the count (footprint.cuh; nullptr: none kept)
     uint4* items;         // [item_cap] their records
     uint32_t* ibase;      // [N] first instance of each splat whose items were kept (set by the emission)

@@ -305,12 +305,12 @@ constexpr int kWideMaxBits = 10;
 template <int kBits>
 struct WideSmem {
     static constexpr int kBins = 1 << kBits;
-    uint16_t whist[kWideWarps][kBins];
+    uint16_t whist[kWideWarps][kBins];   // per-warp digit counts, then each (warp, digit)'s first tile slot
     uint32_t skeys[kWideTile];
     uint32_t svals[kWideTile];
-    uint32_t dstart[kBins];
-    uint32_t dtot[kBins];
-    uint32_t goff[kBins];
+    uint32_t dtot[kBins];                // the tile's digit totals
+    uint32_t goff[kBins];                // where the block's next key of each digit goes
+    uint32_t gbase[kBins];               // goff - (first tile slot of the digit), for the write-out
     uint32_t wsum[kWideWarps];
 };
 
@@ -339,23 +339,26 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
     extern __shared__ __align__(16) unsigned char wide_smem_raw[];
     WideSmem<kBits>& sm = *reinterpret_cast<WideSmem<kBits>*>(wide_smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* wh = reinterpret_cast<uint32_t*>(&sm.whist[0][0]);
+    for (int i = threadIdx.x; i < kWideWarps * kBins / 2; i += kWideThreads) wh[i] = 0u;
     for (int d = threadIdx.x; d < kBins; d += kWideThreads) sm.goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
     const int64_t lo = (int64_t)blockIdx.x * kWideBlockItems;
     const int64_t hi = min(n, lo + kWideBlockItems);
-    for (int64_t base = lo; base < hi; base += kWideTile) {   // tiles in order: stable
-        const int count = hi - base < kWideTile ? (int)(hi - base) : kWideTile;
-        uint32_t* wh = reinterpret_cast<uint32_t*>(&sm.whist[0][0]);
-        for (int i = threadIdx.x; i < kWideWarps * kBins / 2; i += kWideThreads) wh[i] = 0u;
-        // warp w holds tile items [w*512, (w+1)*512) in 16 rounds of 32 lanes: (round, lane)
-        // order is input order
-        // (the values are read only when the keys are placed, to keep registers for the ranks)
-        uint32_t key[kWideItems];
+    // warp w holds tile items [w*512, (w+1)*512) in 16 rounds of 32 lanes: (round, lane)
+    // order is input order.  The values are read only when the keys are placed (registers),
+    // and the next tile's keys are read while this tile is written out.
+    uint32_t key[kWideItems];
+    auto load_keys = [&](int64_t base, int count) {
 #pragma unroll
         for (int r = 0; r < kWideItems; ++r) {
             const int li = warp * (kWideItems * 32) + r * 32 + lane;
             key[r] = li < count ? kin[base + li] : 0u;
         }
-        __syncthreads();
+    };
+    if (lo < hi) load_keys(lo, hi - lo < kWideTile ? (int)(hi - lo) : kWideTile);
+    __syncthreads();
+    for (int64_t base = lo; base < hi; base += kWideTile) {   // tiles in order: stable
+        const int count = hi - base < kWideTile ? (int)(hi - base) : kWideTile;
         uint32_t rank2[kWideItems / 2];   // ranks within the warp, two 16-bit halves per word
 #pragma unroll
         for (int r = 0; r < kWideItems; ++r) {
@@ -373,25 +376,22 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
             __syncwarp();
         }
         __syncthreads();
-        // per digit: exclusive prefix over warps, then the digit totals
+        // the tile's digit totals, their exclusive scan (thread t owns digits
+        // [t kPer, t kPer + kPer)), then each (warp, digit)'s first slot in the tile
         for (int d = threadIdx.x; d < kBins; d += kWideThreads) {
-            uint32_t run = 0;
+            uint32_t t = 0;
 #pragma unroll
-            for (int w = 0; w < kWideWarps; ++w) {
-                const uint32_t c = sm.whist[w][d];
-                sm.whist[w][d] = (uint16_t)run;
-                run += c;
-            }
-            sm.dtot[d] = run;
+            for (int w = 0; w < kWideWarps; ++w) t += sm.whist[w][d];
+            sm.dtot[d] = t;
         }
         __syncthreads();
-        // exclusive block scan of the digit totals: thread t owns digits [t kPer, t kPer + kPer)
         {
             const int d0 = threadIdx.x * kPer;
-            uint32_t loc = 0;
-            if (d0 < kBins) {
+            uint32_t loc = 0, v[kPer];
 #pragma unroll
-                for (int j = 0; j < kPer; ++j) loc += sm.dtot[d0 + j];
+            for (int j = 0; j < kPer; ++j) {
+                v[j] = d0 < kBins ? sm.dtot[d0 + j] : 0u;
+                loc += v[j];
             }
             uint32_t incl = loc;
             for (int o = 1; o < 32; o <<= 1) {
@@ -400,14 +400,22 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
             }
             if (lane == 31) sm.wsum[warp] = incl;
             __syncthreads();
-            uint32_t b = 0;
-            for (int w = 0; w < warp; ++w) b += sm.wsum[w];
-            uint32_t run = b + incl - loc;
+            uint32_t run = incl - loc;
+            for (int w = 0; w < warp; ++w) run += sm.wsum[w];
             if (d0 < kBins) {
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) {
-                    sm.dstart[d0 + j] = run;
-                    run += sm.dtot[d0 + j];
+                    const int d = d0 + j;
+                    uint32_t slot = run;
+#pragma unroll
+                    for (int w = 0; w < kWideWarps; ++w) {
+                        const uint32_t c = sm.whist[w][d];
+                        sm.whist[w][d] = (uint16_t)slot;
+                        slot += c;
+                    }
+                    sm.gbase[d] = sm.goff[d] - run;
+                    sm.goff[d] += v[j];
+                    run += v[j];
                 }
             }
         }
@@ -418,22 +426,22 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
             if (li < count) {
                 const uint32_t dig = (key[r] >> shift) & kMask;
                 const uint32_t rk = (r & 1) ? rank2[r >> 1] >> 16 : rank2[r >> 1] & 0xFFFFu;
-                const uint32_t pos = sm.dstart[dig] + (uint32_t)sm.whist[warp][dig] + rk;
+                const uint32_t pos = (uint32_t)sm.whist[warp][dig] + rk;
                 sm.skeys[pos] = key[r];
                 sm.svals[pos] = vin[base + li];
             }
         }
         __syncthreads();
+        const int64_t next = base + kWideTile;
+        if (next < hi) load_keys(next, hi - next < kWideTile ? (int)(hi - next) : kWideTile);
         for (int i = threadIdx.x; i < count; i += kWideThreads) {
             const uint32_t k = sm.skeys[i];
-            const uint32_t d = (k >> shift) & kMask;
-            const uint32_t o = sm.goff[d] + (uint32_t)i - sm.dstart[d];
+            const uint32_t o = sm.gbase[(k >> shift) & kMask] + (uint32_t)i;
             kout[o] = k;
             vout[o] = sm.svals[i];
         }
-        __syncthreads();
-        for (int d = threadIdx.x; d < kBins; d += kWideThreads) sm.goff[d] += sm.dtot[d];
-        __syncthreads();
+        for (int i = threadIdx.x; i < kWideWarps * kBins / 2; i += kWideThreads) wh[i] = 0u;
+        __syncthreads();   // the next tile ranks into whist and rewrites gbase, skeys and svals
     }
 }
 
