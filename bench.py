@@ -461,6 +461,8 @@ def variant_report(trainer, cams, targets, args) -> dict:
       backward_flat / backward_subsets: the step with the other backward form than the
                       headline's (flat: image-only forward and one replay of each pixel's
                       concatenated list; subsets: partial maps and the merge adjoint);
+      one_group:      the headline step with the image-only forward binned in one group of
+                      view ranks (group_binning = 0) instead of two;
       bwd_recompute:  the backward with a workspace that does not hold the forward's lists,
                       so it re-derives them (projection, binning, sorting) with the forward's
                       per-(tile, subset) depth table culling splats behind saturated tiles."""
@@ -497,6 +499,12 @@ def variant_report(trainer, cams, targets, args) -> dict:
     ms, st = timed(step)
     res[f"backward_{trainer.backward}"] = {"ms_per_step": round(ms, 3), "stages_ms": st}
     trainer.backward = saved_bwd
+    # the image-only forward binned in one group
+    one = rgs.default_opts(cull_occluded=saved.cull_occluded, group_binning=0)
+    trainer.opts = one
+    ms, st = timed(step)
+    res["one_group"] = {"ms_per_step": round(ms, 3), "stages_ms": st}
+    trainer.opts = saved
 
     g = trainer.gaussians()
     ws2 = rgs.Workspace(trainer.flat.device)

@@ -90,6 +90,16 @@ typedef struct {
                                      merge's prod_{m<r} T_{o_m}, Eq. 5) is below eps_T; its
                                      partials there are C = 0, T = 1.  The merged image moves
                                      by less than eps_T times the largest colour. */
+    int group_binning;            /* 1 (default): a forward without partial maps bins and
+                                     blends the subsets in two groups of view ranks, the first
+                                     max(1, K/8) ranks and then the others, the second group
+                                     only in tiles where some pixel's transmittance in front is
+                                     still at least eps_T; this when K >= 4 and the render's
+                                     tile instances average at least 12 per visible splat
+                                     (otherwise one group).  The image, T_final, tile_depth and
+                                     the lists a backward replays are those of one group; fewer
+                                     instances are emitted and sorted.  Synchronises once more
+                                     with the stream.  0: one group. */
 } rgs_render_opts;
 
 typedef struct rgs_kd rgs_kd;          /* KD partition: splits, leaf boxes, subset lists */

@@ -369,9 +369,60 @@ __device__ __forceinline__ size_t cull_chunk_index(const ViewParams& vp, int ty,
     return ((size_t)ty * cull_nchunk(vp) + ch) * vp.K + rank;
 }
 
-// Number of tiles of [c0, c1] in row ty kept for a splat at depth z in subset `rank`.
+// Whether the current binning group takes subsets of this view rank.
+__device__ __forceinline__ bool rank_binned(const ViewParams& vp, int rank) {
+    return rank >= vp.bin_lo && rank < vp.bin_hi;
+}
+
+// Whether tile (ty, c) is open in the group's open-tile table (which must be set).
+__device__ __forceinline__ bool tile_open(const ViewParams& vp, int ty, int c) {
+    const uint32_t* row = vp.open_prefix() + (size_t)ty * (vp.tiles_x + 1);
+    return row[c + 1] != row[c];
+}
+
+// Tile columns [c0, c1] that bound every item span of the footprint (its ellipse and ball
+// extents, widened by a pixel and a half against rounding).
+__device__ __forceinline__ void footprint_tile_cols(const Footprint& f, const ViewParams& vp, int& c0, int& c1) {
+    const float w = fminf(f.ex, f.bx) + 1.5f;
+    c0 = (int)fmaxf(floorf((f.cx - w) * (1.f / kTile)), 0.f);
+    c1 = (int)fminf(floorf((f.cx + w) * (1.f / kTile)), (float)(vp.tiles_x - 1));
+}
+
+// Whether the splat's tile box (rect: columns x..z, rows y..w) holds an open tile of the
+// binning group (always, without an open-tile table).
+__device__ __forceinline__ bool box_open(const ViewParams& vp, ushort4 r) {
+    const uint32_t* sat = vp.open_sat();
+    if (!sat) return true;
+    if (r.x > r.z || r.y > r.w) return false;
+    const size_t W1 = (size_t)vp.tiles_x + 1;
+    const uint32_t n = sat[(r.w + 1) * W1 + r.z + 1] - sat[(size_t)r.y * W1 + r.z + 1] - sat[(r.w + 1) * W1 + r.x] +
+                       sat[(size_t)r.y * W1 + r.x];
+    return n != 0u;
+}
+
+// Number of tiles of [c0, c1] in row ty, ignoring the binning group, kept for a splat at
+// depth z in subset `rank`.
+__device__ __forceinline__ uint32_t kept_tiles_any_group(const float* __restrict__ cull,
+                                                         const float2* __restrict__ chunk, const ViewParams& vp,
+                                                         int ty, int c0, int c1, int rank, float z);
+
+// Number of tiles of [c0, c1] in row ty kept for a splat at depth z in subset `rank`: in
+// the binning group (rank range, open tiles), and not behind the depth table `cull`.  A
+// group with an open-tile table is binned without a depth table.
 __device__ __forceinline__ uint32_t kept_tiles(const float* __restrict__ cull, const float2* __restrict__ chunk,
                                                const ViewParams& vp, int ty, int c0, int c1, int rank, float z) {
+    if (c0 > c1 || !rank_binned(vp, rank)) return 0u;
+    const uint32_t* open = vp.open_prefix();
+    if (open) {
+        const uint32_t* row = open + (size_t)ty * (vp.tiles_x + 1);
+        return row[c1 + 1] - row[c0];
+    }
+    return kept_tiles_any_group(cull, chunk, vp, ty, c0, c1, rank, z);
+}
+
+__device__ __forceinline__ uint32_t kept_tiles_any_group(const float* __restrict__ cull,
+                                                         const float2* __restrict__ chunk, const ViewParams& vp,
+                                                         int ty, int c0, int c1, int rank, float z) {
     if (c0 > c1) return 0u;
     if (!cull) return (uint32_t)(c1 - c0 + 1);
     uint32_t n = 0;

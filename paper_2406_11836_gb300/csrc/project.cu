@@ -286,7 +286,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     bool cand = false;
     float mxh = 0.f, myh = 0.f, l11 = 0.f, l12 = 0.f, l22 = 0.f, alpha = 0.f, rho2 = 0.f, z = 0.f, zr = 0.f;
     unsigned long long mask = 0;
-    int ty0 = 0, ty1 = -1, nsub = 0;
+    int ty0 = 0, ty1 = -1, tx0 = 0, tx1 = 0, nsub = 0;
     if (valid) {
         SplatIn si;
         load_splat(g, i, si);
@@ -337,6 +337,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
             if (isfinite(P.det) && P.det > 0.f && isfinite(l11) && isfinite(l22)) {
                 const Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
                 footprint_tile_rows(f, vp, ty0, ty1);
+                footprint_tile_cols(f, vp, tx0, tx1);
                 cand = ty0 <= ty1;
             }
             if (cand) {
@@ -354,7 +355,8 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
                 b.rec[3 * j + 1] = make_float4(l11, l12, l22, rho2);
                 b.rec[3 * j + 2] = make_float4(rgb[0], rgb[1], rgb[2], z);
                 if (kFoot) b.foot_side[j] = make_float4(rb * rb, zl, mxl, myl);
-                b.rect[j] = make_ushort4(0, (unsigned short)ty0, 0, (unsigned short)ty1);
+                b.rect[j] = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1,
+                                         (unsigned short)ty1);
                 b.mask[j] = mask;
                 b.dkey[j] = __float_as_uint(z);   // z > 0: the bit pattern sorts like the value
                 b.dkey_lo[j] = depth_fraction(z, zl);
@@ -364,12 +366,19 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     // ---- count the tile instances: small splats per thread, large ones per warp
     const int rows = ty1 - ty0 + 1;
     const int items = cand ? nsub * rows : 0;
-    uint32_t count = 0;
+    // count: every instance (visibility and capacity); count_bin: those of the first
+    // binning group (its ranks; no open-tile table is set before the first blend)
+    uint32_t count = 0, count_bin = 0;
     if (cand && items <= kWarpCountItems) {
         Footprint f = make_footprint(mxh, myh, l11, l12, l22, alpha, rho2, vp);
         f.zr = zr;
-        for (int it = 0; it < items; ++it)
-            count += item_tiles(f, vp, tp, rank_of, mask, nsub, z, ty0, rows, it, b.cull, b.cull_chunk);
+        for (int it = 0; it < items; ++it) {
+            int ty, k, c0, c1;
+            item_span(f, vp, tp, mask, nsub, z, ty0, rows, it, ty, k, c0, c1);
+            const uint32_t w = kept_tiles_any_group(b.cull, b.cull_chunk, vp, ty, c0, c1, rank_of[k], z);
+            count += w;
+            count_bin += rank_binned(vp, rank_of[k]) ? w : 0u;
+        }
     }
     unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
     uint32_t span_at = kNoItems;
@@ -401,29 +410,41 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
                     b.items[q] = make_uint4(kNoItems, 0u, 0u, 0u);
             }
         }
-        uint32_t acc = 0;   // instances of the rounds before
+        // the records hold each item's first instance among the first group's instances
+        uint32_t acc = 0, acc_bin = 0;   // instances of the rounds before
         for (int it0 = 0; it0 < items_; it0 += 32) {
             const int it = it0 + lane;
             int ty = 0, k = 0, c0 = 1, c1 = 0;
-            uint32_t w = 0;
+            uint32_t w = 0, wb = 0;
             if (it < items_) {
                 item_span(f, vp, tp, m_, ns, z_, t0_, rows_, it, ty, k, c0, c1);
-                w = kept_tiles(b.cull, b.cull_chunk, vp, ty, c0, c1, rank_of[k], z_);
+                w = kept_tiles_any_group(b.cull, b.cull_chunk, vp, ty, c0, c1, rank_of[k], z_);
+                wb = rank_binned(vp, rank_of[k]) ? w : 0u;
             }
-            uint32_t incl = w;
+            uint32_t incl = wb, incl_all = w;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                const uint32_t ya = __shfl_up_sync(0xffffffffu, incl_all, o);
+                if (lane >= o) {
+                    incl += y;
+                    incl_all += ya;
+                }
             }
-            if (sb != kNoItems && it < items_) b.items[sb + it] = pack_item(j_, acc + incl - w, c0, c1, ty, k);
-            acc += __shfl_sync(0xffffffffu, incl, 31);
+            if (sb != kNoItems && it < items_) {
+                b.items[sb + it] = pack_item(j_, acc_bin + incl - wb, c0, c1, ty, k);
+                b.item_first_all[sb + it] = acc + incl_all - w;
+            }
+            acc_bin += __shfl_sync(0xffffffffu, incl, 31);
+            acc += __shfl_sync(0xffffffffu, incl_all, 31);
         }
         if (lane == src) {
             count = acc;
+            count_bin = acc_bin;
             span_at = sb;
         }
     }
     if (valid) b.cnt[j] = count;
+    if (valid && b.cnt_bin) b.cnt_bin[j] = count_bin;
     if (valid && b.item_at && items > kWarpCountItems) b.item_at[j] = span_at;
     // totals: instances and visible splats
     unsigned long long c64 = count;
@@ -431,6 +452,11 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     for (int o = 16; o > 0; o >>= 1) {
         c64 += __shfl_xor_sync(0xffffffffu, c64, o);
         vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
+    }
+    if (b.cnt_bin) {
+        unsigned long long cb = count_bin;
+        for (int o = 16; o > 0; o >>= 1) cb += __shfl_xor_sync(0xffffffffu, cb, o);
+        if (lane == 0 && cb) atomicAdd(&counters[14], cb);   // the first group's instances
     }
     if (lane == 0 && (c64 | vis_n)) {
         atomicAdd(&counters[0], c64);

@@ -57,6 +57,36 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // One warp per depth-sorted splat; lanes take the splat's (subset, tile row) items, find
 // the row's tile columns from the footprint (the same arithmetic as the count), and
 // write the row's instances at the positions a warp prefix sum gives them.
+// Writes from slot `pos` on the instances of an item's tiles [c0, c1] in row ty (subset
+// `rank`, splat `id` at depth z) that the depth table or the binning group's open-tile
+// table keeps; `first` is the global index of the row's first tile.
+__device__ __forceinline__ void write_kept(const ViewParams& vp, const float* __restrict__ cull,
+                                           const float2* __restrict__ chunk, uint32_t first, int ty, int c0, int c1,
+                                           uint32_t rank, float z, uint32_t id, uint32_t pos,
+                                           uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+    if (vp.open_prefix()) {
+        for (int c = c0; c <= c1; ++c) {
+            if (!tile_open(vp, ty, c)) continue;
+            ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+            ival[pos] = id;
+            ++pos;
+        }
+        return;
+    }
+    for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
+        const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
+        const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
+        if (z > mm.y) continue;
+        const bool all = z <= mm.x;
+        for (int c = lo; c <= hi; ++c) {
+            if (!all && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
+            ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
+            ival[pos] = id;
+            ++pos;
+        }
+    }
+}
+
 // The (subset, row) items of one splat, as the emission walks them.
 struct SplatItems {
     Footprint f;
@@ -114,7 +144,7 @@ __device__ __forceinline__ uint32_t emit_round(const ViewParams& vp, const TreeP
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     if (!kWrite) return total;
     const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
-    if (!cull) {
+    if (!cull && !vp.open_prefix()) {
         s_start[lane] = incl - w;
         s_key0[lane] = ((first + (uint32_t)c0) << vp.L) | rank;
         __syncwarp();
@@ -126,19 +156,7 @@ __device__ __forceinline__ uint32_t emit_round(const ViewParams& vp, const TreeP
         }
         __syncwarp();
     } else if (w) {
-        uint32_t pos = base + incl - w;
-        for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
-            const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-            const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
-            if (s.z > mm.y) continue;
-            const bool all = s.z <= mm.x;
-            for (int c = lo; c <= hi; ++c) {
-                if (!all && !keep_tile(cull, vp, ty, c, (int)rank, s.z)) continue;
-                ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                ival[pos] = id;
-                ++pos;
-            }
-        }
+        write_kept(vp, cull, chunk, first, ty, c0, c1, rank, s.z, id, base + incl - w, ikey, ival);
     }
     return total;
 }
@@ -185,9 +203,15 @@ __device__ __forceinline__ void emit_thread(const ViewParams& vp, const TreePara
         int ty, k, c0, c1;
         item_span<kMulti>(f, vp, tp, m, nsub, z, ty0, rows, it, ty, k, c0, c1);
         const uint32_t rank = (uint32_t)rank_of[k];
+        if (!rank_binned(vp, (int)rank) || c0 > c1) continue;
         const uint32_t first = tile_base + (uint32_t)(ty * vp.tiles_x);
+        if (cull || vp.open_prefix()) {
+            const uint32_t w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, z);
+            write_kept(vp, cull, chunk, first, ty, c0, c1, rank, z, id, pos, ikey, ival);
+            pos += w;
+            continue;
+        }
         for (int c = c0; c <= c1; ++c) {
-            if (cull && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
             ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
             ival[pos] = id;
             ++pos;
@@ -229,7 +253,7 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             const ushort4 r = rect[id];
             const unsigned long long m = mask[id];
             const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
-            items = ((nsub > 1) == (kMulti == 1)) ? nsub * rows : 0;
+            items = ((nsub > 1) == (kMulti == 1)) && box_open(vp, r) ? nsub * rows : 0;
             if (items > 0 && items <= kEmitThreadItems) {
                 const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
                 Footprint f = make_footprint(r0.x, r0.y, r1.x, r1.y, r1.z, r0.w, r1.w, vp);
@@ -297,10 +321,10 @@ emit_listed_kernel(ViewParams vp, TreeParams tp, EmitQueues q, const ushort4* __
 // Items of one splat are consecutive entries with consecutive runs, so the stores stay
 // contiguous within a splat.
 __global__ void __launch_bounds__(256)
-emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const unsigned long long* __restrict__ n_items,
-                  uint32_t cap, const uint32_t* __restrict__ ibase, const float4* __restrict__ rec,
-                  const float* __restrict__ cull, const float2* __restrict__ chunk, uint32_t* __restrict__ ikey,
-                  uint32_t* __restrict__ ival) {
+emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const uint32_t* __restrict__ first,
+                  const unsigned long long* __restrict__ n_items, uint32_t cap, const uint32_t* __restrict__ ibase,
+                  const float4* __restrict__ rec, const float* __restrict__ cull, const float2* __restrict__ chunk,
+                  uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
     __shared__ uint32_t s_start[8][32], s_key0[8][32], s_dst[8][32], s_id[8][32];
     __shared__ int8_t srank[64];
     for (int k = threadIdx.x; k < 64; k += blockDim.x) srank[k] = vp.rank_of[k];
@@ -325,7 +349,7 @@ emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const unsigned
                 rank = (uint32_t)srank[r.w >> 16];
                 if (cull) z = rec[3 * (size_t)id + 2].w;
                 w = kept_tiles(cull, chunk, vp, ty, c0, c1, (int)rank, z);
-                dst = ibase[id] + r.y;
+                if (w) dst = ibase[id] + (first ? first[q] : r.y);
                 key0 = (((uint32_t)(ty * vp.tiles_x) + (uint32_t)c0) << vp.L) | rank;
             }
         }
@@ -335,7 +359,7 @@ emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const unsigned
             if (lane >= o) incl += y;
         }
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        if (!cull) {
+        if (!cull && !vp.open_prefix()) {
             s_start[wib][lane] = incl - w;
             s_key0[wib][lane] = key0;
             s_dst[wib][lane] = dst;
@@ -350,21 +374,123 @@ emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const unsigned
             }
             __syncwarp();
         } else if (w) {
-            uint32_t pos = dst;
-            const uint32_t first = (uint32_t)(ty * vp.tiles_x);
-            for (int ch = c0 / kCullChunk; ch <= c1 / kCullChunk; ++ch) {
-                const int lo = max(c0, ch * kCullChunk), hi = min(c1, ch * kCullChunk + kCullChunk - 1);
-                const float2 mm = chunk[cull_chunk_index(vp, ty, ch, (int)rank)];
-                if (z > mm.y) continue;
-                const bool all = z <= mm.x;
-                for (int c = lo; c <= hi; ++c) {
-                    if (!all && !keep_tile(cull, vp, ty, c, (int)rank, z)) continue;
-                    ikey[pos] = ((first + (uint32_t)c) << vp.L) | rank;
-                    ival[pos] = id;
-                    ++pos;
+            write_kept(vp, cull, chunk, (uint32_t)(ty * vp.tiles_x), ty, c0, c1, rank, z, id, dst, ikey, ival);
+        }
+    }
+}
+
+// Open-tile table of a binning group: per tile row, the number of open tiles before each
+// column (tiles_x + 1 entries); one warp per row.
+__global__ void __launch_bounds__(256)
+open_prefix_kernel(const uint8_t* __restrict__ open, int tiles_x, int tiles_y, uint32_t* __restrict__ prefix) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= tiles_y) return;
+    uint32_t* out = prefix + (size_t)row * (tiles_x + 1);
+    uint32_t run = 0;
+    for (int c0 = 0; c0 < tiles_x; c0 += 32) {
+        const int c = c0 + lane;
+        const bool o = c < tiles_x && open[(size_t)row * tiles_x + c] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, o);
+        if (c < tiles_x) out[c] = run + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+        run += (uint32_t)__popc(bal);
+    }
+    if (lane == 0) out[tiles_x] = run;
+}
+
+// Summed-area table of the open tiles from the per-row prefixes: one thread per column
+// boundary x, down the rows.
+__global__ void __launch_bounds__(256)
+open_sat_kernel(const uint32_t* __restrict__ prefix, int tiles_x, int tiles_y, uint32_t* __restrict__ sat) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x > tiles_x) return;
+    const size_t W1 = (size_t)tiles_x + 1;
+    uint32_t acc = 0;
+    sat[x] = 0u;
+    for (int y = 0; y < tiles_y; ++y) {
+        acc += prefix[(size_t)y * W1 + x];
+        sat[(size_t)(y + 1) * W1 + x] = acc;
+    }
+}
+
+// Count of a later binning group (vp's rank range and open-tile table) for every visible
+// splat, in depth order: cnt_out[p] for the splat at depth position p; the group's total
+// is added to *total.  A splat of few items is counted by its lane from its footprint; a
+// splat whose items the count kept is counted by the warp from its item records, whose
+// first-instance offsets are rewritten for this group; other splats by the warp from
+// their footprint.  Groups of 32 splats are claimed from *queue (zeroed beforehand).
+__global__ void __launch_bounds__(256)
+recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
+               const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
+               const float4* __restrict__ rec, const uint32_t* __restrict__ item_at, uint4* __restrict__ items,
+               uint32_t item_cap, uint32_t* __restrict__ cnt_out, unsigned long long* __restrict__ queue,
+               unsigned long long* __restrict__ total) {
+    __shared__ TreeParams stp;
+    __shared__ int8_t srank[64];
+    stage_tree(tp, vp.rank_of, stp, srank);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long gq = 0;
+        if (lane == 0) gq = atomicAdd(queue, 1ull);
+        const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 32;
+        if (p0 >= n_vis) break;
+        const int64_t p = p0 + lane;
+        uint32_t id = 0, count = 0;
+        int nitems = 0;
+        if (p < n_vis) {
+            id = sorted_ids[p];
+            const ushort4 r = rect[id];
+            const int rows = (int)r.w - (int)r.y + 1;
+            nitems = box_open(vp, r) ? __popcll(mask[id]) * rows : 0;   // no open tile: nothing
+            if (nitems <= kSplatThreadItems) {
+                const SplatItems si = load_items<-1>(vp, id, rect, mask, rec, nullptr);
+                for (int it = 0; it < nitems; ++it) {
+                    int ty, k, c0, c1;
+                    item_span<-1>(si.f, vp, stp, si.m, si.nsub, si.z, si.ty0, si.rows, it, ty, k, c0, c1);
+                    count += kept_tiles(nullptr, nullptr, vp, ty, c0, c1, srank[k], si.z);
                 }
             }
         }
+        unsigned big = __ballot_sync(0xffffffffu, nitems > kSplatThreadItems);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t sid = __shfl_sync(0xffffffffu, id, src);
+            const int sitems = __shfl_sync(0xffffffffu, nitems, src);
+            const uint32_t at = item_at ? item_at[sid] : kNoItems;
+            SplatItems si;
+            if (at == kNoItems) si = load_items<-1>(vp, sid, rect, mask, rec, nullptr);
+            uint32_t acc = 0;
+            for (int it0 = 0; it0 < sitems; it0 += 32) {
+                const int it = it0 + lane;
+                uint32_t w = 0;
+                uint4 rc = make_uint4(0u, 0u, 0u, 0u);
+                if (it < sitems) {
+                    int ty, k, c0, c1;
+                    if (at != kNoItems) {
+                        rc = items[at + it];
+                        c0 = (int)(int16_t)(rc.z & 0xFFFFu);
+                        c1 = (int)(int16_t)(rc.z >> 16);
+                        ty = (int)(rc.w & 0xFFFFu);
+                        k = (int)(rc.w >> 16);
+                    } else {
+                        item_span<-1>(si.f, vp, stp, si.m, si.nsub, si.z, si.ty0, si.rows, it, ty, k, c0, c1);
+                    }
+                    w = kept_tiles(nullptr, nullptr, vp, ty, c0, c1, srank[k], 0.f);
+                }
+                uint32_t incl = w;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (at != kNoItems && it < sitems) items[at + it].y = acc + incl - w;
+                acc += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == src) count = acc;
+        }
+        if (p < n_vis) cnt_out[p] = count;
+        unsigned long long c64 = count;
+        for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+        if (lane == 0 && c64) atomicAdd(total, c64);
     }
 }
 
@@ -459,7 +585,7 @@ __global__ void cull_chunk_kernel(ViewParams vp, const float* __restrict__ cull,
 // Run boundaries of the sorted keys: a thread takes 4 consecutive keys per round (one
 // 16-byte load when `vec`) and their right neighbour; grid-stride over a resident grid.
 __global__ void __launch_bounds__(256)
-ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, bool vec, uint2* __restrict__ ranges) {
+ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, bool vec, uint2* __restrict__ ranges, uint32_t first) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
     for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; j0 < n; j0 += stride) {
         uint32_t k[5];
@@ -475,8 +601,8 @@ ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, bool vec, uint2* __r
         for (int q = 0; q < 4; ++q) {
             const int64_t j = j0 + q;
             if (j >= n) break;
-            if (j == 0 || (q == 0 ? prev : k[q - 1]) != k[q]) ranges[k[q]].x = (uint32_t)j;
-            if (j == n - 1 || k[q + 1] != k[q]) ranges[k[q]].y = (uint32_t)(j + 1);
+            if (j == 0 || (q == 0 ? prev : k[q - 1]) != k[q]) ranges[k[q]].x = first + (uint32_t)j;
+            if (j == n - 1 || k[q + 1] != k[q]) ranges[k[q]].y = first + (uint32_t)(j + 1);
         }
     }
 }
@@ -707,13 +833,23 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 // ends (nullable, the tile's K ranges again): where a subset saturated the tile, the
 // range's end is moved back to the end of the last batch staged, so that a backward
 // replaying these lists stops where the forward did.
+//
+// Groups of ranks (the image-only forward binned group by group): the call blends view
+// ranks [r_begin, r_end) only.  With r_begin > 0 each pixel's merged colour and
+// transmittance in front come from `state` (a float4 per pixel); with r_end < K a tile
+// that still has a pixel whose front transmittance is at least eps_T stores them there and
+// sets its flag in `open`, and a tile with none writes its image (nothing behind can
+// change it), clears its flag and marks the later ranks' depths -inf.
 template <bool kCount>
 __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
                                                const uint2* ranges, const uint32_t* __restrict__ ival,
                                                const float4* __restrict__ rec, float* __restrict__ pC,
                                                float* __restrict__ pT, float* __restrict__ image,
                                                float* __restrict__ Tfin, float* __restrict__ tile_depth,
-                                               uint2* ends, unsigned long long* __restrict__ pairs) {
+                                               uint2* ends, unsigned long long* __restrict__ pairs,
+                                               int r_begin = 0, int r_end = -1, float4* __restrict__ state = nullptr,
+                                               uint8_t* __restrict__ open = nullptr) {
+    if (r_end < 0) r_end = vp.K;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -738,10 +874,18 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     const size_t pix = (size_t)py * vp.W + px;
     uint8_t* wl = wlist[warp];
     const int tid = threadIdx.x;
-    s_img[0][tid] = 0.f;
-    s_img[1][tid] = 0.f;
-    s_img[2][tid] = 0.f;
-    s_img[3][tid] = 1.f;
+    if (r_begin > 0 && inside) {
+        const float4 st = state[pix];
+        s_img[0][tid] = st.x;
+        s_img[1][tid] = st.y;
+        s_img[2][tid] = st.z;
+        s_img[3][tid] = st.w;
+    } else {
+        s_img[0][tid] = 0.f;
+        s_img[1][tid] = 0.f;
+        s_img[2][tid] = 0.f;
+        s_img[3][tid] = 1.f;
+    }
 
     // Culling (always without partial maps, where only the image is wanted; with them when
     // the options ask for it): a pixel whose transmittance in front of subset k (the merge's
@@ -749,7 +893,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     // eps_T max(rgb); its partials there stay C = 0, T = 1), and a tile with no pixel left
     // skips the subset.
     const bool cull = pC == nullptr || vp.cull_occluded != 0;
-    for (int r = 0; r < vp.K; ++r) {
+    for (int r = r_begin; r < r_end; ++r) {
         const int k = vp.order[r];
         const uint2 rg = ranges[r];
         const bool live = inside && !(cull && s_img[3][tid] < vp.eps_T);
@@ -861,6 +1005,18 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
             s_img[3][tid] = Pm * T;
         }
     }
+    if (r_end < vp.K) {
+        // end of a group: keep the state of a tile that later ranks can still change
+        const bool open_px = inside && !(s_img[3][tid] < vp.eps_T);
+        if (__syncthreads_count(open_px) > 0) {
+            if (inside) state[pix] = make_float4(s_img[0][tid], s_img[1][tid], s_img[2][tid], s_img[3][tid]);
+            if (tid == 0) open[tile] = 1;
+            image = nullptr;   // the last group writes it
+        } else {
+            if (tid == 0) open[tile] = 0;
+            if (tile_depth && tid < vp.K && tid >= r_end) tile_depth[tid] = -kInfF;   // nothing needed behind
+        }
+    }
     if (inside && image) {
         const float Pm = s_img[3][tid];
         image[0 * HW + pix] = fmaf(vp.bg[0], Pm, s_img[0][tid]);
@@ -886,11 +1042,14 @@ __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __restrict__ ival,
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
                  float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth, bool record_ends,
-                 unsigned long long* __restrict__ pairs) {
+                 unsigned long long* __restrict__ pairs, int r_begin, int r_end, float4* __restrict__ state,
+                 uint8_t* __restrict__ open) {
     const int tile = blockIdx.x;
+    if (r_begin > 0 && !open[tile]) return;   // closed by an earlier group (uniform across the block)
     uint2* tr = ranges + (size_t)tile * vp.K;
     blend_fwd_tile<kCount>(vp, tp, tile, tr, ival, rec, pC, pT, image, Tfin,
-                           tile_depth ? tile_depth + (size_t)tile * vp.K : nullptr, record_ends ? tr : nullptr, pairs);
+                           tile_depth ? tile_depth + (size_t)tile * vp.K : nullptr, record_ends ? tr : nullptr, pairs,
+                           r_begin, r_end, state, open);
 }
 
 // Persistent forward blend over the global tiles of a batch: each block takes the next
@@ -1739,8 +1898,8 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     }
     // 2. the kept items
     if (item_at) {
-        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.counters + 12, b.item_cap, b.ibase, b.rec, b.cull,
-                                                  b.cull_chunk, b.ikey, b.ival);
+        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.item_first, b.counters + 12, b.item_cap, b.ibase,
+                                                  b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
         RGS_CUDA_LAUNCH_CHECK();
     }
     // 3. the listed splats
@@ -1764,27 +1923,55 @@ int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, c
     return RGS_OK;
 }
 
-int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s) {
-    RGS_CUDA_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s));
+int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s, uint32_t first,
+                  bool clear) {
+    if (clear) RGS_CUDA_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s));
     if (n <= 0) return RGS_OK;
     const int64_t want = (n + 1023) / 1024;
     ranges_kernel<<<(unsigned)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(keys, n, ((uintptr_t)keys & 15) == 0,
-                                                                            ranges);
+                                                                            ranges, first);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_open_prefix(const ViewParams& vp, const uint8_t* open, uint32_t* prefix, uint32_t* sat, cudaStream_t s) {
+    const unsigned grid = (unsigned)((vp.tiles_y + 7) / 8);
+    open_prefix_kernel<<<grid, 256, 0, s>>>(open, vp.tiles_x, vp.tiles_y, prefix);
+    RGS_CUDA_LAUNCH_CHECK();
+    open_sat_kernel<<<(unsigned)((vp.tiles_x + 1 + 255) / 256), 256, 0, s>>>(prefix, vp.tiles_x, vp.tiles_y, sat);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_recount(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
+                   int64_t n_vis, uint32_t* cnt_out, cudaStream_t s) {
+    if (n_vis <= 0) return RGS_OK;
+    const int64_t want = (n_vis + 255) / 256;
+    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    recount_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.rect, b.mask, b.rec, b.item_at, b.items,
+                                        b.items ? b.item_cap : 0u, cnt_out, b.counters + 4, b.counters + 15);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
 
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                     cudaStream_t s, bool record_ends) {
+                     cudaStream_t s, bool record_ends, int r_begin, int r_end) {
+    if (r_end < 0) r_end = vp.K;
+    if ((r_begin > 0 || r_end < vp.K) && (partial_C || !b.state || !b.open)) {
+        set_error("blend: ranks blended in groups need an image-only render and the group state buffers");
+        return RGS_EINVAL;
+    }
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
     unsigned long long* pairs = prof_pair_counters();
     if (pairs)
         blend_fwd_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
-                                                              T_final, tile_depth, record_ends, pairs);
+                                                              T_final, tile_depth, record_ends, pairs, r_begin, r_end,
+                                                              b.state, b.open);
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
-                                                               image, T_final, tile_depth, record_ends, nullptr);
+                                                               image, T_final, tile_depth, record_ends, nullptr,
+                                                               r_begin, r_end, b.state, b.open);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

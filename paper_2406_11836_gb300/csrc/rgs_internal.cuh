@@ -73,6 +73,27 @@ struct ViewParams {
     // 1: a subset is not blended on a ray whose merged transmittance in front of it is
     // below eps_T (rgs_render_opts::cull_occluded)
     int cull_occluded;
+    // Binning by groups of view ranks (the image-only forward): count and emission take
+    // only the subsets of rank in [bin_lo, bin_hi), and, when the open-tile table is set,
+    // only the tiles it marks open: entry ty * (tiles_x + 1) + c holds the number of open
+    // tiles among columns [0, c) of tile row ty.  fill_view sets every rank, no table.
+    // With the open-tile table comes its summed-area table: entry y * (tiles_x + 1) + x
+    // holds the open tiles in rows [0, y) and columns [0, x), so that a splat whose tile
+    // box holds no open tile is passed over at once.
+    int bin_lo, bin_hi;
+    uint32_t open_addr[4];
+    __host__ __device__ const uint32_t* open_prefix() const {
+        return reinterpret_cast<const uint32_t*>(((uint64_t)open_addr[1] << 32) | open_addr[0]);
+    }
+    __host__ __device__ const uint32_t* open_sat() const {
+        return reinterpret_cast<const uint32_t*>(((uint64_t)open_addr[3] << 32) | open_addr[2]);
+    }
+    __host__ void set_open(const uint32_t* table, const uint32_t* sat) {
+        open_addr[0] = (uint32_t)(uintptr_t)table;
+        open_addr[1] = (uint32_t)((uint64_t)(uintptr_t)table >> 32);
+        open_addr[2] = (uint32_t)(uintptr_t)sat;
+        open_addr[3] = (uint32_t)((uint64_t)(uintptr_t)sat >> 32);
+    }
 };
 constexpr int kClipTable = 64 * kMaxRenderDepth;   // entries of one view's plane-template table
 
@@ -187,6 +208,12 @@ struct RasterBuffers {
     // per splat
     float4* rec;          // [N * 3]
     uint32_t* cnt;        // [N] instances of the splat (0: culled)
+    uint32_t* cnt_bin;    // [N] instances in the first binning group (nullptr: one group, cnt)
+    // binning in groups of ranks (image-only forward)
+    float4* state;        // [tiles * 256] each pixel's merged colour and front transmittance between groups
+    uint8_t* open;        // [tiles] 1: a later group can still change the tile
+    uint32_t* open_prefix;   // [tiles_y * (tiles_x + 1)] open tiles before each column, per tile row
+    uint32_t* open_sat;      // [(tiles_y + 1) * (tiles_x + 1)] its summed-area table
     ushort4* rect;        // [N] tile rectangle (x0, y0, x1, y1), inclusive
     unsigned long long* mask;  // [N] subsets containing the splat
     uint32_t* dkey;       // [N] depth key (float bits of z)
@@ -200,9 +227,13 @@ struct RasterBuffers {
     unsigned long long* counters;  // [16]: total instances, visible splats, -, -, emission work queues (2),
                                    // -, -, the splats each emission launch deferred (2), -, -,
                                    // items kept by the count (may exceed item_cap), projection
-                                   // candidates (the list is in vis_pos until the compaction)
+                                   // candidates (the list is in vis_pos until the compaction),
+                                   // instances of the first binning group, of a later group
     uint32_t* item_at;    // [N] items kept by the count (footprint.cuh; nullptr: none kept)
-    uint4* items;         // [item_cap] their records
+    uint4* items;         // [item_cap] their records (first instance among the first binning group's)
+    uint32_t* item_first_all;   // [item_cap] each kept item's first instance among all the splat's
+    const uint32_t* item_first; // what the emission takes the items' first instances from
+                                // (nullptr: the records; else item_first_all, one group)
     uint32_t* ibase;      // [N] first instance of each splat whose items were kept (set by the emission)
     uint32_t item_cap;
     uint4* units;         // per emission launch a list of unit_cap (id, instance base) pairs: the
@@ -281,13 +312,24 @@ int launch_blend_bwd_batch(const BatchSlot* slots, const BatchHeader* hdr, const
                            unsigned long long* counters, cudaStream_t s);
 int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
                 int64_t n_vis, cudaStream_t s);
-int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s);
+// first: the index of keys[0] in the whole instance array; clear: zero the table first.
+int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_ranges, cudaStream_t s,
+                  uint32_t first = 0, bool clear = true);
+// Binning in groups of ranks: the open-tile tables from the per-tile flags, and the count of
+// a later group (vp's rank range and open-tile table) per visible splat in depth order
+// (rewrites the kept items' offsets for that group; counters[4] is its work queue and
+// counters[15] its total, both zeroed by the caller).
+int launch_open_prefix(const ViewParams& vp, const uint8_t* open, uint32_t* prefix, uint32_t* sat, cudaStream_t s);
+int launch_recount(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* sorted_ids,
+                   int64_t n_vis, uint32_t* cnt_out, cudaStream_t s);
 int launch_cull_chunks(const ViewParams& vp, const float* cull, float2* chunk, cudaStream_t s);
 // record_ends: where a subset saturates a tile, b.ranges' end is moved back to the end of
 // the last batch the blend staged (the prefix a backward has to replay).
+// r_begin, r_end: the view ranks blended (r_end < 0: to K); a group other than the whole
+// range needs an image-only render and b.state / b.open (blend_fwd_tile).
 int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                      float* partial_C, float* partial_T, float* image, float* T_final, float* tile_depth,
-                     cudaStream_t s, bool record_ends = false);
+                     cudaStream_t s, bool record_ends = false, int r_begin = 0, int r_end = -1);
 // Foot reading (forward only): orders the emitted instances by (tile, subset, bound of
 // the foot's ray parameter over the tile) and returns the sorted keys and payloads.
 int launch_foot_order(const ViewParams& vp, const RasterBuffers& b, int64_t I, cudaStream_t s,

@@ -42,7 +42,8 @@ class CameraC(ctypes.Structure):
 
 class RenderOpts(ctypes.Structure):
     _fields_ = [("tile", c_int), ("trunc_mult", c_float), ("eps_T", c_float), ("alpha_min", c_float),
-                ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3), ("cull_occluded", c_int)]
+                ("alpha_max", c_float), ("dilation", c_float), ("bg", c_float * 3), ("cull_occluded", c_int),
+                ("group_binning", c_int)]
 
 
 class ServeConfig(ctypes.Structure):

@@ -583,6 +583,41 @@ def test_flat_backward_replays_the_image_only_forward_lists(R):
         assert rel_l2(a, b) <= 1e-5
 
 
+@pytest.mark.parametrize("L", [2, 3, 4, 6])
+def test_group_binning_matches_one_group(R, L):
+    """An image-only forward binned in two groups of view ranks (the second group only in
+    the tiles the first left open) gives the image, T_final and tile depths of one group
+    bit for bit, and the flat backward replaying its lists the same gradients; it bins
+    fewer instances.  (Large splats: a render bins in groups only when its instances
+    average many per visible splat.)"""
+    scene = W.uniform_cube_scene(20_000, seed=61 + L, log_scale_mean=-1.6, sh_degree=1)
+    dev = _dev_scene(scene)
+    kd = R.kd_partition(dev, L)
+    cam = W.look_at((0.25, -2.5, 0.6), (0, 0, 0), 157, 93)
+    g = R.scene_c(dev)
+    dL = torch.from_numpy(np.random.default_rng(L).normal(size=(3, 93, 157)).astype(np.float32) * 1e-3).cuda()
+    res = {}
+    for gb in (0, 1):
+        opts = R.default_opts(group_binning=gb)
+        ws = R.Workspace()
+        R.profile_enable(timing=False, counters=True)
+        R.profile_read(reset=True)
+        out = R.render_fwd(kd, g, cam, opts, ws, partials=False)
+        gr = tuple(torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh))
+        R.render_bwd_flat(kd, g, cam, opts, out["image"], dL, gr, ws, tile_depth=out["tile_depth"])
+        torch.cuda.synchronize()
+        c = R.profile_read(reset=True)["counters"]
+        R.profile_enable(False, False)
+        res[gb] = (out, [t.double().cpu().numpy() for t in gr], c)
+    one, two = res[0], res[1]
+    for key in ("image", "T_final", "tile_depth"):
+        assert torch.equal(one[0][key], two[0][key]), key
+    for a, b in zip(one[1], two[1]):
+        assert rel_l2(b, a) <= 1e-6
+    assert 0 < two[2]["instances"] < one[2]["instances"]
+    assert two[2]["bwd_contrib"] == one[2]["bwd_contrib"] > 0
+
+
 def test_backward_replays_the_forward_lists(R):
     """Given the forward's workspace and arguments, the backward replays the forward's lists
     (cut back to what the forward staged) instead of re-deriving them: no instances are

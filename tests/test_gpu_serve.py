@@ -105,12 +105,13 @@ def test_plain_mode_matches(R, scene):
 
 
 def _instances(R, kd, g, cam):
-    """Tile instances of one render of cam (the library's tracing counters)."""
+    """Tile instances of one render of cam (the library's tracing counters), binned in one
+    group as the batch path bins them."""
     ws = R.Workspace()
     R.profile_enable(timing=False, counters=True)
     try:
         R.profile_read(reset=True)
-        R.render_fwd(kd, g, cam, R.default_opts(), ws, partials=False)
+        R.render_fwd(kd, g, cam, R.default_opts(group_binning=0), ws, partials=False)
         torch.cuda.synchronize()
         return R.profile_read(reset=True)["counters"]["instances"]
     finally:

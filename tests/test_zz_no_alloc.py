@@ -87,7 +87,7 @@ def test_noalloc_rejects_a_render_beyond_its_scratch(R):
 def test_noalloc_rejects_too_many_instances_then_renders_correctly(R):
     """After binning: the splats fit, their tile instances do not.  The refused call has
     already projected into the shared array; the next call must not see its leftovers."""
-    big = W.uniform_cube_scene(200_000, seed=63, log_scale_mean=-1.2)
+    big = W.uniform_cube_scene(100_000, seed=63, log_scale_mean=-1.0)
     bdev = big.to("cuda")
     bkd = R.kd_partition(bdev, 1)
     rc, _ = _noalloc(R, bkd, R.scene_c(bdev), W.axis_camera((0.0, 0.0, -3.0), 1024, 1024), R.default_opts())
