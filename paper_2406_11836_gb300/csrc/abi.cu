@@ -556,9 +556,9 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
 // ranks [vp->bin_hi, K) in the tiles that blend left open.  Counts them per visible splat
 // (in depth order), emits them after the first group's instances, sorts them (into the
 // buffer that holds the first group's), adds their (tile, subset) ranges; returns their
-// number in *I1.
+// number in *I1 and in *any_open whether the first group left any tile open.
 int bin_second_group(ViewParams* vp, const TreeParams& tp, const RasterBuffers& b, const GroupBins& grp,
-                     int64_t* I1, cudaStream_t s) {
+                     int64_t* I1, bool* any_open, cudaStream_t s) {
     int rc;
     const int64_t tiles = (int64_t)vp->tiles_x * vp->tiles_y;
     vp->bin_lo = vp->bin_hi;
@@ -568,6 +568,16 @@ int bin_second_group(ViewParams* vp, const TreeParams& tp, const RasterBuffers& 
     {
         ProfScope ps(ST_OFFSETS, s);
         if ((rc = launch_open_prefix(*vp, b.open, b.open_prefix, b.open_sat, s))) return rc;
+        // no tile left open (the first group saturated every one): nothing more to bin
+        uint32_t open_tiles = 0;
+        const size_t last = (size_t)vp->tiles_y * ((size_t)vp->tiles_x + 1) + (size_t)vp->tiles_x;
+        RGS_CUDA_TRY(cudaMemcpyAsync(&open_tiles, b.open_sat + last, 4, cudaMemcpyDeviceToHost, s));
+        RGS_CUDA_TRY(cudaStreamSynchronize(s));
+        *any_open = open_tiles != 0;
+        if (open_tiles == 0) {
+            *I1 = 0;
+            return RGS_OK;
+        }
         // work queues [4, 12) and the group's total [15]; [12] (the kept items) stays
         RGS_CUDA_TRY(cudaMemsetAsync(b.counters + 4, 0, 8 * 8, s));
         RGS_CUDA_TRY(cudaMemsetAsync(b.counters + 15, 0, 8, s));
@@ -646,10 +656,13 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
     }
     if (two) {
         int64_t I1 = 0;
-        if ((rc = bin_second_group(&vp, tp, b, grp, &I1, s))) return rc;
-        ProfScope ps(ST_BLEND_FWD, s);
-        rc = launch_blend_fwd(vp, tp, b, ival, nullptr, nullptr, image, T_final, tile_depth, s, keep, r1, K);
-        if (rc) return rc;
+        bool any_open = false;
+        if ((rc = bin_second_group(&vp, tp, b, grp, &I1, &any_open, s))) return rc;
+        if (any_open) {   // (every closed tile has its image already)
+            ProfScope ps(ST_BLEND_FWD, s);
+            rc = launch_blend_fwd(vp, tp, b, ival, nullptr, nullptr, image, T_final, tile_depth, s, keep, r1, K);
+            if (rc) return rc;
+        }
         I += I1;
     }
     if (keep) {
