@@ -294,9 +294,11 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400,
     # batched: `lanes` concurrent lanes of up to `max_slots` requests per batch; lanes_only: the
     # same lanes with one request per batch (concurrency without batching); plain: one request
     # at a time through the render entry point
-    modes = {"batched": dict(max_slots=max_slots, lanes=lanes, plain=False),
-             "lanes_only": dict(max_slots=1, lanes=lanes, plain=False),
-             "plain": dict(max_slots=max_slots, lanes=lanes, plain=True)}
+    # every server is sized for the stream's largest request (3840x2160)
+    big = dict(max_width=max(w for w, _ in W.RESOLUTIONS), max_height=max(h for _, h in W.RESOLUTIONS))
+    modes = {"batched": dict(max_slots=max_slots, lanes=lanes, plain=False, **big),
+             "lanes_only": dict(max_slots=1, lanes=lanes, plain=False, **big),
+             "plain": dict(max_slots=max_slots, lanes=lanes, plain=True, **big)}
     for mode, kw in modes.items():
         srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, keepalive=wl.scene, **kw)
         for (w, h), bufs in outs.items():     # warm every resolution once

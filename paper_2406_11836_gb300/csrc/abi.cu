@@ -281,6 +281,7 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.sid_alt = (uint32_t*)take(4 * N);
     t.ioff = (uint32_t*)take(4 * N);
     t.counters = (unsigned long long*)take(128);
+    t.item_ctr = t.counters ? t.counters + 12 : nullptr;
     // deferred emission: per launch a list of (id, base) for up to one splat in four (at
     // least 8192, at most 2^20)
     const int64_t ucap = N / 4 < 8192 ? 8192 : (N / 4 > (1 << 20) ? (1 << 20) : N / 4);

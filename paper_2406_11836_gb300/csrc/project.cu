@@ -396,12 +396,12 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         f.zr = __shfl_sync(0xffffffffu, zr, src);
         const int ns = __popcll(m_);
         const uint32_t j_ = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)j, src);
-        // keep the items for the emission when the list has room (counters[12] counts the
+        // keep the items for the emission when the list has room (item_ctr counts the
         // entries taken; the one reservation that crosses the end voids its part inside)
         uint32_t sb = kNoItems;
         if (b.items) {
             unsigned long long s0 = 0;
-            if (lane == 0) s0 = atomicAdd(&counters[12], (unsigned long long)items_);
+            if (lane == 0) s0 = atomicAdd(b.item_ctr, (unsigned long long)items_);
             s0 = __shfl_sync(0xffffffffu, s0, 0);
             if (s0 + (unsigned long long)items_ <= b.item_cap) {
                 sb = (uint32_t)s0;
@@ -432,7 +432,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
             }
             if (sb != kNoItems && it < items_) {
                 b.items[sb + it] = pack_item(j_, acc_bin + incl - wb, c0, c1, ty, k);
-                b.item_first_all[sb + it] = acc + incl_all - w;
+                if (b.item_first_all) b.item_first_all[sb + it] = acc + incl_all - w;
             }
             acc_bin += __shfl_sync(0xffffffffu, incl, 31);
             acc += __shfl_sync(0xffffffffu, incl_all, 31);
@@ -485,36 +485,66 @@ project_fwd_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers 
 // semi-axes plus 2 pixels.  Alpha is computed exactly as the projection computes it.
 // Candidates are appended to `cand` (counters[13]); every other splat gets cnt = 0.
 // The projection then runs on full warps of candidates.
+__device__ __forceinline__ bool screen_keep(const rgs_gaussians& g, const ViewParams& vp, int64_t i) {
+    const float mx = g.means[3 * i], my = g.means[3 * i + 1], mz = g.means[3 * i + 2];
+    const float ls = fmaxf(g.log_scales[3 * i], fmaxf(g.log_scales[3 * i + 1], g.log_scales[3 * i + 2]));
+    const float alpha = 1.f / (1.f + __expf(-g.opacity_logits[i]));
+    const float x = fmaf(vp.R[0], mx, fmaf(vp.R[1], my, fmaf(vp.R[2], mz, vp.t[0])));
+    const float y = fmaf(vp.R[3], mx, fmaf(vp.R[4], my, fmaf(vp.R[5], mz, vp.t[1])));
+    const float z = fmaf(vp.R[6], mx, fmaf(vp.R[7], my, fmaf(vp.R[8], mz, vp.t[2])));
+    bool keep = alpha >= vp.alpha_min && !(z < vp.near_z * (1.f - 1e-4f));
+    if (keep && z > 0.f) {
+        const float rball = vp.trunc_mult * __expf(ls) / z;
+        const float cxp = fmaf(vp.fx, x / z, vp.cx), cyp = fmaf(vp.fy, y / z, vp.cy);
+        const float bx = (vp.fx * rball * 1.001f + 1.f) * 1.01f + 2.f, by = (vp.fy * rball * 1.001f + 1.f) * 1.01f + 2.f;
+        // off screen only when every comparison is certain (NaN and inf stay candidates)
+        if (cxp + bx < 0.f || cxp - bx > (float)vp.W || cyp + by < 0.f || cyp - by > (float)vp.H) keep = false;
+    }
+    return keep;
+}
+
+// Appends the lanes that keep their splat to list[*count ...] (one atomic per warp).
+__device__ __forceinline__ void append_kept(bool keep, uint32_t value, uint32_t* __restrict__ list,
+                                            unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(count, (unsigned long long)__popc(bal));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (keep) list[first + __popc(bal & ((1u << lane) - 1u))] = value;
+    }
+}
+
 __global__ void __launch_bounds__(256)
 screen_cull_kernel(rgs_gaussians g, ViewParams vp, uint32_t* __restrict__ cnt, uint32_t* __restrict__ cand,
                    unsigned long long* __restrict__ counters) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    bool keep = false;
-    if (i < g.n) {
-        const float mx = g.means[3 * i], my = g.means[3 * i + 1], mz = g.means[3 * i + 2];
-        const float ls = fmaxf(g.log_scales[3 * i], fmaxf(g.log_scales[3 * i + 1], g.log_scales[3 * i + 2]));
-        const float alpha = 1.f / (1.f + __expf(-g.opacity_logits[i]));
-        const float x = fmaf(vp.R[0], mx, fmaf(vp.R[1], my, fmaf(vp.R[2], mz, vp.t[0])));
-        const float y = fmaf(vp.R[3], mx, fmaf(vp.R[4], my, fmaf(vp.R[5], mz, vp.t[1])));
-        const float z = fmaf(vp.R[6], mx, fmaf(vp.R[7], my, fmaf(vp.R[8], mz, vp.t[2])));
-        keep = alpha >= vp.alpha_min && !(z < vp.near_z * (1.f - 1e-4f));
-        if (keep && z > 0.f) {
-            const float rball = vp.trunc_mult * __expf(ls) / z;
-            const float cxp = fmaf(vp.fx, x / z, vp.cx), cyp = fmaf(vp.fy, y / z, vp.cy);
-            const float bx = (vp.fx * rball * 1.001f + 1.f) * 1.01f + 2.f, by = (vp.fy * rball * 1.001f + 1.f) * 1.01f + 2.f;
-            // off screen only when every comparison is certain (NaN and inf stay candidates)
-            if (cxp + bx < 0.f || cxp - bx > (float)vp.W || cyp + by < 0.f || cyp - by > (float)vp.H) keep = false;
-        }
-        if (!keep) cnt[i] = 0u;
+    const bool keep = i < g.n && screen_keep(g, vp, i);
+    if (i < g.n && !keep) cnt[i] = 0u;
+    append_kept(keep, (uint32_t)i, cand, &counters[13]);
+}
+
+// The screen cull of a batch: block x tests splats [256 (x / kMaxSlots), +256) against the
+// view of slot x % kMaxSlots and appends the candidates to the slot's list (vis_pos from
+// slot * N on, counted in counters[kBatchCandCounters + slot]).
+__global__ void __launch_bounds__(256)
+screen_cull_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                         uint32_t* __restrict__ cnt, uint32_t* __restrict__ cand,
+                         unsigned long long* __restrict__ counters) {
+    const int slot = blockIdx.x % kMaxSlots;
+    if (slot >= hdr->S) return;   // uniform across the block
+    __shared__ ViewParams svp;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&slots[slot].vp);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&svp);
+        for (int w = threadIdx.x; w < (int)(sizeof(ViewParams) / 4); w += blockDim.x) dst[w] = src[w];
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (bal) {
-        unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(&counters[13], (unsigned long long)__popc(bal));
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (keep) cand[first + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
-    }
+    __syncthreads();
+    const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
+    const bool keep = i < g.n && screen_keep(g, svp, i);
+    if (i < g.n && !keep) cnt[(int64_t)slot * g.n + i] = 0u;
+    append_kept(keep, (uint32_t)i, cand + (int64_t)slot * g.n, &counters[kBatchCandCounters + slot]);
 }
 
 // The projection over the candidates of screen_cull_kernel, one per thread; the grid
@@ -534,15 +564,17 @@ project_cand_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers
     project_fwd_body<DEG, kVecSH, false>(g, i, valid, vp, stp, srank, b, i, b.counters, nullptr);
 }
 
-// Batched projection: block x handles splats [256 (x / kMaxSlots), +256) for request slot
-// x % kMaxSlots, so the blocks of one splat range run back to back and read its
-// parameters from L2 after the first slot.  Outputs go to index slot * N + i.
+// The batch projection over each slot's screen-cull candidates: block x takes candidates
+// [256 (x / kMaxSlots), +256) of slot x % kMaxSlots; blocks past the slot's count end at once.
 template <int DEG, bool kVecSH>
 __global__ void __launch_bounds__(256, 3)
-project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
-                     TreeParams tp, RasterBuffers b, unsigned long long* __restrict__ counters) {
+project_cand_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                          TreeParams tp, RasterBuffers b, unsigned long long* __restrict__ counters) {
     const int slot = blockIdx.x % kMaxSlots;
     if (slot >= hdr->S) return;   // uniform across the block
+    const unsigned long long nc = counters[kBatchCandCounters + slot];
+    const unsigned long long c0 = (unsigned long long)(blockIdx.x / kMaxSlots) * blockDim.x;
+    if (c0 >= nc) return;
     __shared__ ViewParams svp;
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(&slots[slot].vp);
@@ -552,9 +584,11 @@ project_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const
     __shared__ TreeParams stp;
     __shared__ int8_t srank[64];
     stage_tree(tp, slots[slot].vp.rank_of, stp, srank);   // its barrier also publishes svp
-    const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
-    project_fwd_body<DEG, kVecSH>(g, i, i < g.n, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
-                          counters + kBatchSlotCounters + 2 * slot);
+    const unsigned long long c = c0 + threadIdx.x;
+    const bool valid = c < nc;
+    const int64_t i = valid ? (int64_t)b.vis_pos[(int64_t)slot * g.n + (int64_t)c] : 0;
+    project_fwd_body<DEG, kVecSH>(g, i, valid, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
+                                  counters + kBatchSlotCounters + 2 * slot);
 }
 
 // ------------------------------------------------------------------ backward kernel
@@ -809,8 +843,12 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
 int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp,
                          const RasterBuffers& b, unsigned long long* counters, cudaStream_t s) {
     const unsigned grid = (unsigned)((g.n + 255) / 256) * (unsigned)kMaxSlots;
+    // screen cull first: each slot's candidates to its part of vis_pos (the compaction
+    // after the projection overwrites it); the projection then runs on full warps
+    screen_cull_batch_kernel<<<grid, 256, 0, s>>>(g, slots, hdr, b.cnt, b.vis_pos, counters);
+    RGS_CUDA_LAUNCH_CHECK();
     RGS_DISPATCH_SH(g.sh_degree, vec_sh(g),
-                    (project_batch_kernel<D, V><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters)));
+                    (project_cand_batch_kernel<D, V><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters)));
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

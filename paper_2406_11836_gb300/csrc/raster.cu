@@ -512,7 +512,8 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
                   const uint32_t* __restrict__ sorted_ids, int64_t n_cap, int64_t N,
                   unsigned long long* __restrict__ counters, const uint32_t* __restrict__ ioff,
                   const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
-                  const float4* __restrict__ rec, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival) {
+                  const float4* __restrict__ rec, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
+                  const uint32_t* __restrict__ item_at, uint32_t* __restrict__ ibase) {
     if (counters[2]) return;   // overflow: the batch is discarded
     __shared__ ViewParams svp[kMaxSlots];
     __shared__ uint32_t sbase[kMaxSlots];
@@ -551,7 +552,10 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
                                     nullptr, nullptr, ikey, ival);
             }
         }
-        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems);
+        // a splat whose items the projection kept: emit_items_batch_kernel writes them
+        const bool kept = item_at && items > kEmitThreadItems && item_at[id] != kNoItems;
+        if (kept) ibase[id] = base;
+        unsigned big = __ballot_sync(0xffffffffu, items > kEmitThreadItems && !kept);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
@@ -560,6 +564,67 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             emit_one<kMulti>(svp[ss], stp, svp[ss].rank_of, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr,
                              ikey, ival, lane, s_start[wib], s_key0[wib], nullptr);
         }
+    }
+}
+
+// The batch's kept items, as emit_items_kernel: record ids are slot * N + i, so each lane
+// takes its item's view (tile columns, subset ranks) and tile base from the block's shared
+// copy of the slot table.
+__global__ void __launch_bounds__(256)
+emit_items_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                        const uint4* __restrict__ items, const unsigned long long* __restrict__ n_items,
+                        uint32_t cap, const uint32_t* __restrict__ ibase, int64_t N,
+                        const unsigned long long* __restrict__ counters, uint32_t* __restrict__ ikey,
+                        uint32_t* __restrict__ ival) {
+    if (counters[2]) return;   // overflow: the batch is discarded
+    __shared__ ViewParams svp[kMaxSlots];
+    __shared__ uint32_t sbase[kMaxSlots];
+    __shared__ uint32_t s_start[8][32], s_key0[8][32], s_dst[8][32], s_id[8][32];
+    const int S = hdr->S;
+    if ((int)threadIdx.x < S) sbase[threadIdx.x] = hdr->tile_base[threadIdx.x];
+    load_batch_views(slots, S, svp);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned long long taken = *n_items;
+    const unsigned long long n = taken < cap ? taken : cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32;
+    const int L = svp[0].L;
+    for (unsigned long long q0 = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib) * 32; q0 < n;
+         q0 += stride) {
+        const unsigned long long q = q0 + lane;
+        uint32_t id = kNoItems, w = 0, dst = 0, key0 = 0;
+        if (q < n) {
+            const uint4 r = items[q];
+            id = r.x;
+            if (id != kNoItems) {
+                const int c0 = (int)(int16_t)(r.z & 0xFFFFu), c1 = (int)(int16_t)(r.z >> 16);
+                const int ty = (int)(r.w & 0xFFFFu), k = (int)(r.w >> 16);
+                const int slot = (int)(id / (uint64_t)N);
+                const ViewParams& vp = svp[slot];
+                const uint32_t rank = (uint32_t)vp.rank_of[k];
+                w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+                if (w) dst = ibase[id] + r.y;
+                key0 = ((sbase[slot] + (uint32_t)(ty * vp.tiles_x) + (uint32_t)c0) << L) | rank;
+            }
+        }
+        uint32_t incl = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        s_start[wib][lane] = incl - w;
+        s_key0[wib][lane] = key0;
+        s_dst[wib][lane] = dst;
+        s_id[wib][lane] = id;
+        __syncwarp();
+        int cur = 0;
+        for (uint32_t o = (uint32_t)lane; o < total; o += 32) {
+            while (cur < 31 && s_start[wib][cur + 1] <= o) ++cur;   // runs of empty items share a start
+            const uint32_t off = o - s_start[wib][cur];
+            ikey[s_dst[wib][cur] + off] = s_key0[wib][cur] + (off << L);
+            ival[s_dst[wib][cur] + off] = s_id[wib][cur];
+        }
+        __syncwarp();
     }
 }
 
@@ -1898,7 +1963,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     }
     // 2. the kept items
     if (item_at) {
-        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.item_first, b.counters + 12, b.item_cap, b.ibase,
+        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.item_first, b.item_ctr, b.item_cap, b.ibase,
                                                   b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
         RGS_CUDA_LAUNCH_CHECK();
     }
@@ -2017,12 +2082,18 @@ int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBu
 int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
                       const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
                       cudaStream_t s) {
+    const uint32_t* item_at = b.items ? b.item_at : nullptr;
     emit_batch_kernel<0><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
-                                                 b.mask, b.rec, b.ikey, b.ival);
+                                                 b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase);
     RGS_CUDA_LAUNCH_CHECK();
     if (tp.L > 0) {
         emit_batch_kernel<1><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
-                                                     b.mask, b.rec, b.ikey, b.ival);
+                                                     b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase);
+        RGS_CUDA_LAUNCH_CHECK();
+    }
+    if (item_at) {
+        emit_items_batch_kernel<<<152 * 8, 256, 0, s>>>(slots, hdr, b.items, b.item_ctr, b.item_cap, b.ibase, N,
+                                                        counters, b.ikey, b.ival);
         RGS_CUDA_LAUNCH_CHECK();
     }
     return RGS_OK;

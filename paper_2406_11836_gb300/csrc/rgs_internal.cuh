@@ -125,9 +125,13 @@ struct LaneBufs;
 // Device counters of a batch (uint64): [0] instances, [1] visible (slot, splat) pairs,
 // [2] overflow flag, [3] blend work-queue head, [4] instances to sort (0 on overflow),
 // [5], [6] emission work-queue heads, [7] the batched backward's work-queue head, then
-// (instances, visible) per slot from kBatchSlotCounters.
+// (instances, visible) per slot from kBatchSlotCounters, then the kept items.
 constexpr int kBatchSlotCounters = 8;
-constexpr int kBatchCounters = kBatchSlotCounters + 2 * kMaxSlots;
+// ... then the items the projection kept for the emission (one counter), then the
+// projection candidates of each slot (their lists lie in vis_pos, slot s at s * N)
+constexpr int kBatchItemCounter = kBatchSlotCounters + 2 * kMaxSlots;
+constexpr int kBatchCandCounters = kBatchItemCounter + 1;
+constexpr int kBatchCounters = kBatchCandCounters + kMaxSlots;
 
 struct RasterBuffers;
 int ceil_log2(int64_t x);
@@ -199,6 +203,9 @@ size_t scan_dev_temp_bytes();
 int exclusive_scan_dev(const uint32_t* in, uint32_t* out, const unsigned long long* n_dev, int64_t cap, int load,
                        const uint32_t* gather, void* temp, size_t temp_bytes, cudaStream_t s);
 size_t radix_dev_temp_bytes();
+// Sets the wide sort passes' shared-memory attribute on the current device; call it before
+// capturing a stream that sorts (the passes set it themselves outside a capture).
+int sort_prepare();
 int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                          const unsigned long long* n_dev, int64_t cap, int end_bit, void* temp, size_t temp_bytes,
                          cudaStream_t s, bool* in_alt);
@@ -231,6 +238,7 @@ struct RasterBuffers {
                                    // instances of the first binning group, of a later group
     uint32_t* item_at;    // [N] items kept by the count (footprint.cuh; nullptr: none kept)
     uint4* items;         // [item_cap] their records (first instance among the first binning group's)
+    unsigned long long* item_ctr;   // records taken (may exceed item_cap)
     uint32_t* item_first_all;   // [item_cap] each kept item's first instance among all the splat's
     const uint32_t* item_first; // what the emission takes the items' first instances from
                                 // (nullptr: the records; else item_first_all, one group)

@@ -102,6 +102,14 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     b.skey_alt = (uint32_t*)take(4 * P);
     b.sid_alt = (uint32_t*)take(4 * P);
     b.ioff = (uint32_t*)take(4 * P);
+    // items the projection keeps for the emission: up to 4 per (request, splat) pair, at
+    // most 2^26 records
+    const int64_t icap = P * 4 < (1 << 16) ? (1 << 16) : (P * 4 > (1ll << 26) ? (1ll << 26) : P * 4);
+    b.item_at = (uint32_t*)take(4 * P);
+    b.ibase = (uint32_t*)take(4 * P);
+    b.items = (uint4*)take(sizeof(uint4) * (size_t)icap);
+    b.item_cap = (uint32_t)icap;
+    b.item_ctr = l.counters ? l.counters + kBatchItemCounter : nullptr;
     if (train) b.g2d = (float4*)take(sizeof(float4) * 3 * P);
     b.ranges = (uint2*)take(sizeof(uint2) * tiles_cap * K);
     b.ikey = (uint32_t*)take(4 * inst_cap);
@@ -650,6 +658,7 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
             memset(ln.slots_host, 0, sizeof(BatchSlot) * kMaxSlots);
             memset(ln.hdr_host, 0, sizeof(BatchHeader));
             // capture the lane's batch pipeline once
+            if ((rc = sort_prepare())) return fail(rc);
             cudaGraph_t graph = nullptr;
             RGS_CUDA_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
             prof_suppress(true);

@@ -302,6 +302,26 @@ constexpr int kWideBlockTiles = 8;
 constexpr int kWideBlockItems = kWideTile * kWideBlockTiles;   // 65536
 constexpr int kWideMaxBits = 10;
 
+// Blocks of the device-counted wide passes (two per SM).
+constexpr int kWideChunks = 304;
+
+// The keys block b owns: with n_dev, the b-th of nblocks contiguous chunks of whole
+// tiles of the first min(*n_dev, n) keys; without, [b * kWideBlockItems, +kWideBlockItems).
+__device__ __forceinline__ void wide_range(int64_t n, const unsigned long long* n_dev, uint32_t nblocks, int64_t& lo,
+                                           int64_t& hi) {
+    if (n_dev) {
+        const unsigned long long v = *n_dev;
+        const int64_t m = v < (unsigned long long)n ? (int64_t)v : n;
+        const int64_t tiles = (m + kWideTile - 1) / kWideTile;
+        const int64_t per = (tiles + nblocks - 1) / nblocks;
+        lo = min(m, (int64_t)blockIdx.x * per * kWideTile);
+        hi = min(m, lo + per * kWideTile);
+    } else {
+        lo = (int64_t)blockIdx.x * kWideBlockItems;
+        hi = min(n, lo + kWideBlockItems);
+    }
+}
+
 template <int kBits>
 struct WideSmem {
     static constexpr int kBins = 1 << kBits;
@@ -317,13 +337,14 @@ struct WideSmem {
 template <int kBits>
 __global__ void __launch_bounds__(kWideThreads, 2)
 wide_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
-                    uint32_t nblocks, bool vec) {
+                    uint32_t nblocks, bool vec, const unsigned long long* __restrict__ n_dev) {
     constexpr int kBins = 1 << kBits;
     __shared__ uint32_t hist[kBins];
     for (int d = threadIdx.x; d < kBins; d += kWideThreads) hist[d] = 0;
     __syncthreads();
-    const int64_t lo = (int64_t)blockIdx.x * kWideBlockItems;
-    hist_runs<kWideThreads, (uint32_t)(kBins - 1)>(keys, lo, min(n, lo + kWideBlockItems), shift, vec, hist);
+    int64_t lo, hi;
+    wide_range(n, n_dev, nblocks, lo, hi);
+    hist_runs<kWideThreads, (uint32_t)(kBins - 1)>(keys, lo, hi, shift, vec, hist);
     __syncthreads();
     for (int d = threadIdx.x; d < kBins; d += kWideThreads) counts[(int64_t)d * nblocks + blockIdx.x] = hist[d];
 }
@@ -332,7 +353,7 @@ template <int kBits>
 __global__ void __launch_bounds__(kWideThreads, 2)
 wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                       uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
-                      uint32_t nblocks) {
+                      uint32_t nblocks, const unsigned long long* __restrict__ n_dev) {
     constexpr int kBins = 1 << kBits;
     constexpr uint32_t kMask = (uint32_t)kBins - 1u;
     constexpr int kPer = kBins / kWideThreads > 0 ? kBins / kWideThreads : 1;   // digits per thread in the scan
@@ -342,8 +363,8 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
     uint32_t* wh = reinterpret_cast<uint32_t*>(&sm.whist[0][0]);
     for (int i = threadIdx.x; i < kWideWarps * kBins / 2; i += kWideThreads) wh[i] = 0u;
     for (int d = threadIdx.x; d < kBins; d += kWideThreads) sm.goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
-    const int64_t lo = (int64_t)blockIdx.x * kWideBlockItems;
-    const int64_t hi = min(n, lo + kWideBlockItems);
+    int64_t lo, hi;
+    wide_range(n, n_dev, nblocks, lo, hi);
     // warp w holds tile items [w*512, (w+1)*512) in 16 rounds of 32 lanes: (round, lane)
     // order is input order.  The values are read only when the keys are placed (registers),
     // and the next tile's keys are read while this tile is written out.
@@ -445,24 +466,30 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
     }
 }
 
+// n_dev (nullable): the key count lives in device memory and n is the capacity; the grid
+// is then kWideChunks blocks (stream-capturable).
 template <int kBits>
 int wide_pass(const uint32_t* ka, const uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n, int shift,
-              uint32_t* counts, void* stemp, size_t sbytes, cudaStream_t s) {
+              uint32_t* counts, void* stemp, size_t sbytes, cudaStream_t s,
+              const unsigned long long* n_dev = nullptr) {
     constexpr int kBins = 1 << kBits;
-    const int64_t nb = (n + kWideBlockItems - 1) / kWideBlockItems;
+    const int64_t nb = n_dev ? kWideChunks : (n + kWideBlockItems - 1) / kWideBlockItems;
     const int64_t nc = nb * kBins;
     const size_t smem = sizeof(WideSmem<kBits>);
-    // the attribute belongs to the function on the current device; setting it on every
-    // call costs a driver call per pass and is always right
-    RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    // the attribute belongs to the function on the current device; it is set on every call
+    // outside a stream capture (a driver call per pass), and by sort_prepare before one
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    RGS_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone)
+        RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
     wide_upsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb,
-                                                                      ((uintptr_t)ka & 15) == 0);
+                                                                      ((uintptr_t)ka & 15) == 0, n_dev);
     RGS_CUDA_LAUNCH_CHECK();
     int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
     if (rc != RGS_OK) return rc;
     wide_downsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, smem, s>>>(ka, va, kb, vb, n, shift, counts,
-                                                                           (uint32_t)nb);
+                                                                           (uint32_t)nb, n_dev);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -663,8 +690,19 @@ int exclusive_scan_dev(const uint32_t* in, uint32_t* out, const unsigned long lo
     return RGS_OK;
 }
 
+int sort_prepare() {
+    RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(WideSmem<8>)));
+    RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(WideSmem<9>)));
+    RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(WideSmem<10>)));
+    return RGS_OK;
+}
+
 size_t radix_dev_temp_bytes() {
-    const int64_t nc = (int64_t)kRadix * kChunks;
+    const int64_t nc8 = (int64_t)kRadix * kChunks, ncw = ((int64_t)1 << kWideMaxBits) * kWideChunks;
+    const int64_t nc = nc8 > ncw ? nc8 : ncw;
     return align256((size_t)nc * 4) + scan_temp_bytes(nc);
 }
 
@@ -678,8 +716,8 @@ int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
         set_error("radix sort: capacity %lld exceeds the 32-bit index range", (long long)cap);
         return RGS_EOVERFLOW;
     }
-    const int64_t nc = (int64_t)kRadix * kChunks;
-    const size_t cbytes = align256((size_t)nc * 4);
+    const int64_t nc = (int64_t)kRadix * kChunks, ncw = ((int64_t)1 << kWideMaxBits) * kWideChunks;
+    const size_t cbytes = align256((size_t)(nc > ncw ? nc : ncw) * 4);
     if (temp_bytes < radix_dev_temp_bytes()) {
         set_error("radix sort: temporary buffer too small");
         return RGS_EOVERFLOW;
@@ -688,6 +726,24 @@ int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
     void* stemp = (char*)temp + cbytes;
     const size_t sbytes = temp_bytes - cbytes;
     uint32_t *ka = keys, *va = vals, *kb = keys_alt, *vb = vals_alt;
+    if (end_bit > 2 * kRadixBits && end_bit <= 2 * kWideMaxBits) {
+        // two wide passes, as radix_sort_pairs
+        const int b0 = (end_bit + 1) / 2;
+        int shift = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int bits = pass == 0 ? b0 : end_bit - b0;
+            int rc = bits == 10   ? wide_pass<10>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev)
+                     : bits == 9  ? wide_pass<9>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev)
+                                  : wide_pass<8>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev);
+            if (rc != RGS_OK) return rc;
+            shift += bits;
+            uint32_t* t;
+            t = ka; ka = kb; kb = t;
+            t = va; va = vb; vb = t;
+            *in_alt = !*in_alt;
+        }
+        return RGS_OK;
+    }
     for (int shift = 0; shift < end_bit; shift += kRadixBits) {
         dradix_upsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, n_dev, cap, shift, counts);
         RGS_CUDA_LAUNCH_CHECK();
