@@ -95,11 +95,13 @@ typedef struct {
                                      max(1, K/8) ranks and then the others, the second group
                                      only in tiles where some pixel's transmittance in front is
                                      still at least eps_T; this when K >= 4 and the render's
-                                     tile instances average at least 12 per visible splat
-                                     (otherwise one group).  The image, T_final, tile_depth and
-                                     the lists a backward replays are those of one group; fewer
-                                     instances are emitted and sorted.  Synchronises once more
-                                     with the stream.  0: one group. */
+                                     tile instances average at least 12 per visible splat and
+                                     number at least 2^24 (otherwise one group).  The image,
+                                     T_final, tile_depth and the lists a backward replays are
+                                     those of one group; fewer instances are emitted and
+                                     sorted.  Synchronises once more with the stream.  2: as 1
+                                     whatever the instance counts (when K >= 4).  0: one
+                                     group. */
 } rgs_render_opts;
 
 typedef struct rgs_kd rgs_kd;          /* KD partition: splits, leaf boxes, subset lists */
@@ -379,6 +381,13 @@ typedef struct {
     int max_queue;              /* queued requests beyond which submit returns RGS_EAGAIN */
     float inst_per_pixel;       /* first admission estimate of tile instances per pixel (later:
                                    measured); a low value only costs a re-run of the batch */
+    float group_per_splat;      /* batched mode, opts.group_binning set and at least 4 subsets:
+                                   a request bins its subsets in two groups of view ranks (as
+                                   rgs_render_fwd's image-only forward) once the batches before
+                                   measured at its resolution at least this many tile
+                                   instances per visible splat ... */
+    float group_min_instances;  /* ... and at least this many tile instances; with both 0, or
+                                   with group_binning 2, every request is grouped */
 } rgs_serve_config;
 
 typedef struct {
@@ -390,12 +399,14 @@ typedef struct {
 } rgs_serve_stats;
 
 /* Defaults: 8 GiB, 8 slots, 2 lanes, batched, 4096x4096, 65536 queued, 16 instances
- * per pixel. */
+ * per pixel, groups from 12 instances per visible splat and 2^24 instances. */
 void rgs_serve_default_config(rgs_serve_config* cfg);
 
 /* Device bytes one lane of a batched server with this configuration takes for a capacity
  * of `instance_capacity` tile instances (pure host arithmetic; mem_budget_bytes and
- * lanes are ignored).  A lane needs at least 65536 instances. */
+ * lanes are ignored), with the buffers of binning in groups of view ranks when the KD
+ * tree has at least 4 subsets (a server whose options set group_binning).  A lane needs
+ * at least 65536 instances. */
 int rgs_serve_lane_bytes(const rgs_kd* kd, const rgs_gaussians* g, const rgs_serve_config* cfg,
                          int64_t instance_capacity, size_t* bytes);
 

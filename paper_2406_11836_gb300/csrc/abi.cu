@@ -173,8 +173,8 @@ int check_opts(const rgs_render_opts* o) {
         set_error("opts: cull_occluded must be 0 or 1");
         return RGS_EINVAL;
     }
-    if (o->group_binning != 0 && o->group_binning != 1) {
-        set_error("opts: group_binning must be 0 or 1");
+    if (o->group_binning < 0 || o->group_binning > 2) {
+        set_error("opts: group_binning must be 0, 1 or 2");
         return RGS_EINVAL;
     }
     return RGS_OK;
@@ -282,6 +282,7 @@ size_t layout(char* base, int64_t N, int64_t tiles, int K, int64_t inst_cap, Ras
     t.ioff = (uint32_t*)take(4 * N);
     t.counters = (unsigned long long*)take(128);
     t.item_ctr = t.counters ? t.counters + 12 : nullptr;
+    t.bin_ctr = t.counters ? t.counters + 14 : nullptr;
     // deferred emission: per launch a list of (id, base) for up to one splat in four (at
     // least 8192, at most 2^20)
     const int64_t ucap = N / 4 < 8192 ? 8192 : (N / 4 > (1 << 20) ? (1 << 20) : N / 4);
@@ -397,12 +398,6 @@ thread_local PinnedCounters g_pinned;
 // payloads in blend order.
 // Binning in groups of ranks: build_lists bins the first group (view ranks [0, bin_hi))
 // and leaves here what a later group needs.
-// A render bins in groups only when its tile instances average at least this many per
-// visible splat: the later group's count and emission go over every visible splat (about
-// 0.3 ns each on a GB300) while each instance it spares the sort and the emission saves
-// about 25 ps, and in the views measured about a third of the instances past the first
-// group were left to bin.
-constexpr int64_t kGroupInstancesPerSplat = 12;
 
 struct GroupBins {
     bool grouped = false;                   // the render binned its first group only
@@ -415,7 +410,8 @@ struct GroupBins {
 int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                 void* workspace, size_t ws_bytes, cudaStream_t s, ViewParams* vp, TreeParams* tp, RasterBuffers* b,
                 const uint32_t** sorted_ival, const float* cull, unsigned long long* host_counters = nullptr,
-                int64_t* n_inst = nullptr, bool foot = false, int bin_hi = -1, GroupBins* grp = nullptr) {
+                int64_t* n_inst = nullptr, bool foot = false, int bin_hi = -1, GroupBins* grp = nullptr,
+                bool force_groups = false) {
     int rc;
     if ((rc = check_gaussians(g)) || (rc = check_camera(cam)) || (rc = check_opts(opts))) return rc;
     if (!kd) { set_error("render: NULL kd"); return RGS_EINVAL; }
@@ -466,7 +462,8 @@ int build_lists(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
     RGS_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t I_all = (int64_t)hc[0];
     const int64_t n_vis = (int64_t)hc[1];
-    const bool grouped = two_counts && I_all >= kGroupInstancesPerSplat * n_vis;
+    const bool grouped = two_counts && (force_groups || (I_all >= kGroupInstancesPerSplat * n_vis &&
+                                                         I_all >= kGroupMinInstances));
     if (two_counts && !grouped) {   // one group after all: every rank, the items' full offsets
         vp->bin_hi = vp->K;
         b->item_first = b->item_first_all;
@@ -641,11 +638,11 @@ int render_fwd_into(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* 
     if (keep_lists) stamp_erase(workspace);   // its lists are about to be replaced
     // an image-only forward bins its subsets in two groups of view ranks (group_binning)
     const int K = kd ? 1 << kd->b.L : 1;
-    const bool grouped = opts && opts->group_binning == 1 && !partial_C && image && K >= 4;
+    const bool grouped = opts && opts->group_binning >= 1 && !partial_C && image && K >= 4;
     const int r1 = grouped ? (K / 8 > 1 ? K / 8 : 1) : K;
     GroupBins grp;
     int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, host_counters, &I,
-                         false, r1, grouped ? &grp : nullptr);
+                         false, r1, grouped ? &grp : nullptr, opts && opts->group_binning == 2);
     if (rc) return rc;
     const bool keep = keep_lists && (partial_C != nullptr || image != nullptr);   // a backward may follow
     const bool two = grouped && grp.grouped;

@@ -456,7 +456,7 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     if (b.cnt_bin) {
         unsigned long long cb = count_bin;
         for (int o = 16; o > 0; o >>= 1) cb += __shfl_xor_sync(0xffffffffu, cb, o);
-        if (lane == 0 && cb) atomicAdd(&counters[14], cb);   // the first group's instances
+        if (lane == 0 && cb) atomicAdd(b.bin_ctr, cb);   // the first group's instances
     }
     if (lane == 0 && (c64 | vis_n)) {
         atomicAdd(&counters[0], c64);

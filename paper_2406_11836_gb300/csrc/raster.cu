@@ -381,15 +381,12 @@ emit_items_kernel(ViewParams vp, const uint4* __restrict__ items, const uint32_t
 
 // Open-tile table of a binning group: per tile row, the number of open tiles before each
 // column (tiles_x + 1 entries); one warp per row.
-__global__ void __launch_bounds__(256)
-open_prefix_kernel(const uint8_t* __restrict__ open, int tiles_x, int tiles_y, uint32_t* __restrict__ prefix) {
-    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (row >= tiles_y) return;
-    uint32_t* out = prefix + (size_t)row * (tiles_x + 1);
+__device__ __forceinline__ void open_prefix_row(const uint8_t* __restrict__ open_row, int tiles_x,
+                                                uint32_t* __restrict__ out, int lane) {
     uint32_t run = 0;
     for (int c0 = 0; c0 < tiles_x; c0 += 32) {
         const int c = c0 + lane;
-        const bool o = c < tiles_x && open[(size_t)row * tiles_x + c] != 0;
+        const bool o = c < tiles_x && open_row[c] != 0;
         const unsigned bal = __ballot_sync(0xffffffffu, o);
         if (c < tiles_x) out[c] = run + (uint32_t)__popc(bal & ((1u << lane) - 1u));
         run += (uint32_t)__popc(bal);
@@ -397,12 +394,17 @@ open_prefix_kernel(const uint8_t* __restrict__ open, int tiles_x, int tiles_y, u
     if (lane == 0) out[tiles_x] = run;
 }
 
+__global__ void __launch_bounds__(256)
+open_prefix_kernel(const uint8_t* __restrict__ open, int tiles_x, int tiles_y, uint32_t* __restrict__ prefix) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= tiles_y) return;
+    open_prefix_row(open + (size_t)row * tiles_x, tiles_x, prefix + (size_t)row * (tiles_x + 1), lane);
+}
+
 // Summed-area table of the open tiles from the per-row prefixes: one thread per column
 // boundary x, down the rows.
-__global__ void __launch_bounds__(256)
-open_sat_kernel(const uint32_t* __restrict__ prefix, int tiles_x, int tiles_y, uint32_t* __restrict__ sat) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x > tiles_x) return;
+__device__ __forceinline__ void open_sat_col(const uint32_t* __restrict__ prefix, int tiles_x, int tiles_y,
+                                             uint32_t* __restrict__ sat, int x) {
     const size_t W1 = (size_t)tiles_x + 1;
     uint32_t acc = 0;
     sat[x] = 0u;
@@ -412,21 +414,114 @@ open_sat_kernel(const uint32_t* __restrict__ prefix, int tiles_x, int tiles_y, u
     }
 }
 
-// Count of a later binning group (vp's rank range and open-tile table) for every visible
-// splat, in depth order: cnt_out[p] for the splat at depth position p; the group's total
-// is added to *total.  A splat of few items is counted by its lane from its footprint; a
-// splat whose items the count kept is counted by the warp from its item records, whose
-// first-instance offsets are rewritten for this group; other splats by the warp from
-// their footprint.  Groups of 32 splats are claimed from *queue (zeroed beforehand).
 __global__ void __launch_bounds__(256)
-recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
+open_sat_kernel(const uint32_t* __restrict__ prefix, int tiles_x, int tiles_y, uint32_t* __restrict__ sat) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x > tiles_x) return;
+    open_sat_col(prefix, tiles_x, tiles_y, sat, x);
+}
+
+// The same tables for every request of a batch (slot blockIdx.y; the open flags of its
+// tiles from its tile_base; its tables where its view points), grid-stride over the rows
+// and the column boundaries.
+__global__ void __launch_bounds__(256)
+open_prefix_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                         const uint8_t* __restrict__ open) {
+    const int sl = blockIdx.y;
+    if (sl >= hdr->S) return;
+    const ViewParams& vp = slots[sl].vp;
+    const int tiles_x = vp.tiles_x, tiles_y = vp.tiles_y;
+    const uint8_t* o = open + hdr->tile_base[sl];
+    uint32_t* prefix = const_cast<uint32_t*>(vp.open_prefix());
+    const int lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * 8 + (threadIdx.x >> 5); row < tiles_y; row += gridDim.x * 8)
+        open_prefix_row(o + (size_t)row * tiles_x, tiles_x, prefix + (size_t)row * (tiles_x + 1), lane);
+}
+
+__global__ void __launch_bounds__(256)
+open_sat_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr) {
+    const int sl = blockIdx.y;
+    if (sl >= hdr->S) return;
+    const ViewParams& vp = slots[sl].vp;
+    uint32_t* sat = const_cast<uint32_t*>(vp.open_sat());
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x <= vp.tiles_x; x += gridDim.x * blockDim.x)
+        open_sat_col(vp.open_prefix(), vp.tiles_x, vp.tiles_y, sat, x);
+}
+
+// The batch's open tiles as a list of global tiles, request by request in row-major order
+// (each tile's place from its request's tables), and their number in *n_list.
+__global__ void __launch_bounds__(256)
+open_list_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
+                 const uint8_t* __restrict__ open, uint32_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
+    __shared__ uint32_t soff[kMaxSlots + 1];
+    const int S = hdr->S;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int sl = 0; sl < S; ++sl) {
+            soff[sl] = acc;
+            const ViewParams& vp = slots[sl].vp;
+            acc += vp.open_sat()[(size_t)vp.tiles_y * (vp.tiles_x + 1) + vp.tiles_x];
+        }
+        soff[S] = acc;
+        if (blockIdx.x == 0) *n_list = acc;
+    }
+    __syncthreads();
+    const uint32_t total = hdr->total_tiles;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        if (!open[t]) continue;
+        int sl = 0;
+        while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
+        const ViewParams& vp = slots[sl].vp;
+        const int tiles_x = vp.tiles_x;
+        const uint32_t lt = t - hdr->tile_base[sl];
+        const uint32_t y = lt / (uint32_t)tiles_x, x = lt - y * (uint32_t)tiles_x;
+        const size_t W1 = (size_t)tiles_x + 1;
+        list[soff[sl] + vp.open_sat()[(size_t)y * W1 + tiles_x] + vp.open_prefix()[(size_t)y * W1 + x]] = t;
+    }
+}
+
+// Copies the batch's view parameters into shared memory (the whole block).
+__device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ slots, int S, ViewParams* svp) {
+    constexpr int kWords = (int)(sizeof(ViewParams) / 4);
+    for (int w = threadIdx.x; w < S * kWords; w += blockDim.x) {
+        const int sl = w / kWords, o = w - sl * kWords;
+        reinterpret_cast<uint32_t*>(&svp[sl])[o] = reinterpret_cast<const uint32_t*>(&slots[sl].vp)[o];
+    }
+    __syncthreads();
+}
+
+// Count of a later binning group (the view's rank range and open-tile table) for every
+// visible splat, in depth order: cnt_out[p] for the splat at depth position p; the group's
+// total is added to *total.  A splat of few items is counted by its lane from its
+// footprint; a splat whose items the count kept is counted by the warp from its item
+// records, whose first-instance offsets are rewritten for this group; other splats by the
+// warp from their footprint.  Groups of 32 splats are claimed from *queue (zeroed
+// beforehand).  kBatch: the splats are a batch's (slot * N + i), each counted in its slot's
+// view (slots[s].vp), *n_dev of them (at most n_vis), nothing when the overflow flag is set;
+// else one view, vp1, and n_vis splats.
+template <bool kBatch>
+__global__ void __launch_bounds__(256)
+recount_kernel(ViewParams vp1, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, int64_t N,
+               TreeParams tp, const uint32_t* __restrict__ sorted_ids, int64_t n_vis,
+               const unsigned long long* __restrict__ n_dev, const unsigned long long* __restrict__ overflow,
                const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
                const float4* __restrict__ rec, const uint32_t* __restrict__ item_at, uint4* __restrict__ items,
                uint32_t item_cap, uint32_t* __restrict__ cnt_out, unsigned long long* __restrict__ queue,
                unsigned long long* __restrict__ total) {
+    __shared__ ViewParams svp[kBatch ? kMaxSlots : 1];
     __shared__ TreeParams stp;
-    __shared__ int8_t srank[64];
-    stage_tree(tp, vp.rank_of, stp, srank);
+    __shared__ int8_t srank_unused[64];
+    if (kBatch) {
+        if (*overflow) return;   // the batch is discarded
+        load_batch_views(slots, hdr->S, svp);
+        const unsigned long long nv = *n_dev;
+        if (nv < (unsigned long long)n_vis) n_vis = (int64_t)nv;
+    } else {
+        constexpr int kWords = (int)(sizeof(ViewParams) / 4);
+        for (int w = threadIdx.x; w < kWords; w += blockDim.x)
+            reinterpret_cast<uint32_t*>(&svp[0])[w] = reinterpret_cast<const uint32_t*>(&vp1)[w];
+    }
+    stage_tree(tp, vp1.rank_of, stp, srank_unused);   // the views' ranks: svp[slot].rank_of
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long gq = 0;
@@ -435,9 +530,11 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
         if (p0 >= n_vis) break;
         const int64_t p = p0 + lane;
         uint32_t id = 0, count = 0;
-        int nitems = 0;
+        int nitems = 0, slot = 0;
         if (p < n_vis) {
             id = sorted_ids[p];
+            if (kBatch) slot = (int)(id / (uint64_t)N);
+            const ViewParams& vp = svp[slot];
             const ushort4 r = rect[id];
             const int rows = (int)r.w - (int)r.y + 1;
             nitems = box_open(vp, r) ? __popcll(mask[id]) * rows : 0;   // no open tile: nothing
@@ -446,7 +543,7 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
                 for (int it = 0; it < nitems; ++it) {
                     int ty, k, c0, c1;
                     item_span<-1>(si.f, vp, stp, si.m, si.nsub, si.z, si.ty0, si.rows, it, ty, k, c0, c1);
-                    count += kept_tiles(nullptr, nullptr, vp, ty, c0, c1, srank[k], si.z);
+                    count += kept_tiles(nullptr, nullptr, vp, ty, c0, c1, vp.rank_of[k], si.z);
                 }
             }
         }
@@ -456,6 +553,7 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
             big &= big - 1;
             const uint32_t sid = __shfl_sync(0xffffffffu, id, src);
             const int sitems = __shfl_sync(0xffffffffu, nitems, src);
+            const ViewParams& vp = svp[__shfl_sync(0xffffffffu, slot, src)];
             const uint32_t at = item_at ? item_at[sid] : kNoItems;
             SplatItems si;
             if (at == kNoItems) si = load_items<-1>(vp, sid, rect, mask, rec, nullptr);
@@ -463,11 +561,10 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
             for (int it0 = 0; it0 < sitems; it0 += 32) {
                 const int it = it0 + lane;
                 uint32_t w = 0;
-                uint4 rc = make_uint4(0u, 0u, 0u, 0u);
                 if (it < sitems) {
                     int ty, k, c0, c1;
                     if (at != kNoItems) {
-                        rc = items[at + it];
+                        const uint4 rc = items[at + it];
                         c0 = (int)(int16_t)(rc.z & 0xFFFFu);
                         c1 = (int)(int16_t)(rc.z >> 16);
                         ty = (int)(rc.w & 0xFFFFu);
@@ -475,7 +572,7 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
                     } else {
                         item_span<-1>(si.f, vp, stp, si.m, si.nsub, si.z, si.ty0, si.rows, it, ty, k, c0, c1);
                     }
-                    w = kept_tiles(nullptr, nullptr, vp, ty, c0, c1, srank[k], 0.f);
+                    w = kept_tiles(nullptr, nullptr, vp, ty, c0, c1, vp.rank_of[k], 0.f);
                 }
                 uint32_t incl = w;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -494,18 +591,10 @@ recount_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted
     }
 }
 
-// Copies the batch's view parameters into shared memory (the whole block).
-__device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ slots, int S, ViewParams* svp) {
-    constexpr int kWords = (int)(sizeof(ViewParams) / 4);
-    for (int w = threadIdx.x; w < S * kWords; w += blockDim.x) {
-        const int sl = w / kWords, o = w - sl * kWords;
-        reinterpret_cast<uint32_t*>(&svp[sl])[o] = reinterpret_cast<const uint32_t*>(&slots[sl].vp)[o];
-    }
-    __syncthreads();
-}
-
 // Batch emission: sorted ids are slot * N + i, so each lane takes its splat's view from
 // the block's shared copy of the slot table; the same thread / warp split as emit_kernel.
+// Each view's binning group (rank range, open-tile tables) selects what is written;
+// inst_base (nullable): the group's instances start at that index (a device value).
 template <int kMulti>
 __global__ void __launch_bounds__(256)
 emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
@@ -513,8 +602,14 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
                   unsigned long long* __restrict__ counters, const uint32_t* __restrict__ ioff,
                   const ushort4* __restrict__ rect, const unsigned long long* __restrict__ mask,
                   const float4* __restrict__ rec, uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-                  const uint32_t* __restrict__ item_at, uint32_t* __restrict__ ibase) {
+                  const uint32_t* __restrict__ item_at, uint32_t* __restrict__ ibase,
+                  const unsigned long long* __restrict__ inst_base) {
     if (counters[2]) return;   // overflow: the batch is discarded
+    if (inst_base) {
+        const unsigned long long b0 = *inst_base;
+        ikey += b0;
+        ival += b0;
+    }
     __shared__ ViewParams svp[kMaxSlots];
     __shared__ uint32_t sbase[kMaxSlots];
     const int S = hdr->S;
@@ -543,7 +638,7 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             const ushort4 r = rect[id];
             const unsigned long long m = mask[id];
             const int rows = (int)r.w - (int)r.y + 1, nsub = __popcll(m);
-            items = ((nsub > 1) == (kMulti == 1)) ? nsub * rows : 0;
+            items = ((nsub > 1) == (kMulti == 1)) && box_open(svp[slot], r) ? nsub * rows : 0;
             if (items > 0 && items <= kEmitThreadItems) {
                 const ViewParams& vp = svp[slot];
                 const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1], r2 = rec[3 * (size_t)id + 2];
@@ -568,15 +663,24 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
 }
 
 // The batch's kept items, as emit_items_kernel: record ids are slot * N + i, so each lane
-// takes its item's view (tile columns, subset ranks) and tile base from the block's shared
-// copy of the slot table.
+// takes its item's view (tile columns, subset ranks, binning group) and tile base from the
+// block's shared copy of the slot table.  open_tables: the views carry open-tile tables
+// (a later binning group: each lane writes its item's open tiles, below the group's count
+// *n_group_dev); inst_base as emit_batch_kernel.
 __global__ void __launch_bounds__(256)
 emit_items_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
                         const uint4* __restrict__ items, const unsigned long long* __restrict__ n_items,
                         uint32_t cap, const uint32_t* __restrict__ ibase, int64_t N,
                         const unsigned long long* __restrict__ counters, uint32_t* __restrict__ ikey,
-                        uint32_t* __restrict__ ival) {
+                        uint32_t* __restrict__ ival, const unsigned long long* __restrict__ inst_base,
+                        bool open_tables, const unsigned long long* __restrict__ n_group_dev) {
     if (counters[2]) return;   // overflow: the batch is discarded
+    if (inst_base) {
+        const unsigned long long b0 = *inst_base;
+        ikey += b0;
+        ival += b0;
+    }
+    const unsigned long long n_group = n_group_dev ? *n_group_dev : ~0ull;
     __shared__ ViewParams svp[kMaxSlots];
     __shared__ uint32_t sbase[kMaxSlots];
     __shared__ uint32_t s_start[8][32], s_key0[8][32], s_dst[8][32], s_id[8][32];
@@ -591,20 +695,34 @@ emit_items_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* 
     for (unsigned long long q0 = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib) * 32; q0 < n;
          q0 += stride) {
         const unsigned long long q = q0 + lane;
-        uint32_t id = kNoItems, w = 0, dst = 0, key0 = 0;
+        uint32_t id = kNoItems, w = 0, dst = 0, key0 = 0, rank = 0;
+        int ty = 0, c0 = 1, c1 = 0, slot = 0;
         if (q < n) {
             const uint4 r = items[q];
             id = r.x;
             if (id != kNoItems) {
-                const int c0 = (int)(int16_t)(r.z & 0xFFFFu), c1 = (int)(int16_t)(r.z >> 16);
-                const int ty = (int)(r.w & 0xFFFFu), k = (int)(r.w >> 16);
-                const int slot = (int)(id / (uint64_t)N);
+                c0 = (int)(int16_t)(r.z & 0xFFFFu);
+                c1 = (int)(int16_t)(r.z >> 16);
+                ty = (int)(r.w & 0xFFFFu);
+                const int k = (int)(r.w >> 16);
+                slot = (int)(id / (uint64_t)N);
                 const ViewParams& vp = svp[slot];
-                const uint32_t rank = (uint32_t)vp.rank_of[k];
-                w = c0 <= c1 ? (uint32_t)(c1 - c0 + 1) : 0u;
+                rank = (uint32_t)vp.rank_of[k];
+                w = kept_tiles(nullptr, nullptr, vp, ty, c0, c1, (int)rank, 0.f);
                 if (w) dst = ibase[id] + r.y;
                 key0 = ((sbase[slot] + (uint32_t)(ty * vp.tiles_x) + (uint32_t)c0) << L) | rank;
             }
+        }
+        if (open_tables) {   // uniform: the kept tiles of each item are not contiguous
+            // (a record of a splat this group passes over has no open tile in its span, so
+            // its stale base is never used; the group's count bounds the writes regardless)
+            if (w && (unsigned long long)dst + w > n_group) w = 0;
+            if (w) {
+                const ViewParams& vp = svp[slot];
+                write_kept(vp, nullptr, nullptr, sbase[slot] + (uint32_t)(ty * vp.tiles_x), ty, c0, c1, rank, 0.f, id,
+                           dst, ikey, ival);
+            }
+            continue;
         }
         uint32_t incl = w;
         for (int o = 1; o < 32; o <<= 1) {
@@ -672,14 +790,18 @@ ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, bool vec, uint2* __r
     }
 }
 
+// base_dev (nullable): the keys start at that index of the instance array (device value).
 __global__ void ranges_dev_kernel(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev,
-                                  int64_t cap, uint2* __restrict__ ranges) {
+                                  int64_t cap, uint2* __restrict__ ranges,
+                                  const unsigned long long* __restrict__ base_dev) {
     const unsigned long long nv = *n_dev;
     const int64_t n = nv < (unsigned long long)cap ? (int64_t)nv : cap;
+    const uint32_t base = base_dev ? (uint32_t)*base_dev : 0u;
+    keys += base;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = keys[j];
-        if (j == 0 || keys[j - 1] != k) ranges[k].x = (uint32_t)j;
-        if (j == n - 1 || keys[j + 1] != k) ranges[k].y = (uint32_t)(j + 1);
+        if (j == 0 || keys[j - 1] != k) ranges[k].x = base + (uint32_t)j;
+        if (j == n - 1 || keys[j + 1] != k) ranges[k].y = base + (uint32_t)(j + 1);
     }
 }
 
@@ -901,10 +1023,12 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 //
 // Groups of ranks (the image-only forward binned group by group): the call blends view
 // ranks [r_begin, r_end) only.  With r_begin > 0 each pixel's merged colour and
-// transmittance in front come from `state` (a float4 per pixel); with r_end < K a tile
-// that still has a pixel whose front transmittance is at least eps_T stores them there and
-// sets its flag in `open`, and a tile with none writes its image (nothing behind can
-// change it), clears its flag and marks the later ranks' depths -inf.
+// transmittance in front come from `state` (a float4 per pixel, 256 per tile, tiles
+// numbered by state_tile: the view's tile, or a batch request's tile past its state base);
+// with r_end < K a tile that still has a pixel whose front transmittance is at least eps_T
+// stores them there and sets its flag in `open` (entry open_tile: the view's tile, or the
+// batch's global tile), and a tile with none writes its image (nothing behind can change
+// it), clears its flag and marks the later ranks' depths -inf.
 template <bool kCount>
 __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
                                                const uint2* ranges, const uint32_t* __restrict__ ival,
@@ -913,8 +1037,12 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                                                float* __restrict__ Tfin, float* __restrict__ tile_depth,
                                                uint2* ends, unsigned long long* __restrict__ pairs,
                                                int r_begin = 0, int r_end = -1, float4* __restrict__ state = nullptr,
-                                               uint8_t* __restrict__ open = nullptr) {
+                                               uint8_t* __restrict__ open = nullptr, int state_tile = -1,
+                                               int open_tile = -1) {
     if (r_end < 0) r_end = vp.K;
+    // state and open flags are kept per tile (global over a batch): 256 entries a tile
+    const size_t st_tile = state_tile >= 0 ? (size_t)state_tile : (size_t)tile;
+    const size_t op_tile = open_tile >= 0 ? (size_t)open_tile : (size_t)tile;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -940,7 +1068,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     uint8_t* wl = wlist[warp];
     const int tid = threadIdx.x;
     if (r_begin > 0 && inside) {
-        const float4 st = state[pix];
+        const float4 st = state[st_tile * kBlendThreads + threadIdx.x];
         s_img[0][tid] = st.x;
         s_img[1][tid] = st.y;
         s_img[2][tid] = st.z;
@@ -1074,11 +1202,13 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         // end of a group: keep the state of a tile that later ranks can still change
         const bool open_px = inside && !(s_img[3][tid] < vp.eps_T);
         if (__syncthreads_count(open_px) > 0) {
-            if (inside) state[pix] = make_float4(s_img[0][tid], s_img[1][tid], s_img[2][tid], s_img[3][tid]);
-            if (tid == 0) open[tile] = 1;
+            if (inside)
+                state[st_tile * kBlendThreads + tid] = make_float4(s_img[0][tid], s_img[1][tid], s_img[2][tid],
+                                                                   s_img[3][tid]);
+            if (tid == 0) open[op_tile] = 1;
             image = nullptr;   // the last group writes it
         } else {
-            if (tid == 0) open[tile] = 0;
+            if (tid == 0) open[op_tile] = 0;
             if (tile_depth && tid < vp.K && tid >= r_end) tile_depth[tid] = -kInfF;   // nothing needed behind
         }
     }
@@ -1118,23 +1248,30 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __
 }
 
 // Persistent forward blend over the global tiles of a batch: each block takes the next
-// tile from a device counter until all are done; a tile belongs to the last request
-// whose tile_base it reaches.  The request's view is kept in shared memory while
-// consecutive tiles stay in one request.
+// tile from a device counter (*queue) until all are done; a tile belongs to the last
+// request whose tile_base it reaches.  The request's view is kept in shared memory while
+// consecutive tiles stay in one request.  Each request blends its binning group's view
+// ranks [bin_lo, bin_hi) (state: the group state of blend_fwd_tile, a grouped request's
+// tiles from its state_base; open: its flags, by global tile);
+// list (nullable): the tiles are the *n_list entries of list (a later group's open tiles).
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
                    uint2* __restrict__ ranges, const uint32_t* __restrict__ ival, const float4* __restrict__ rec,
-                   unsigned long long* __restrict__ counters, bool record_ends) {
+                   unsigned long long* __restrict__ counters, bool record_ends, unsigned long long* __restrict__ queue,
+                   float4* __restrict__ state, uint8_t* __restrict__ open, const uint32_t* __restrict__ list,
+                   const unsigned long long* __restrict__ n_list) {
     __shared__ ViewParams svp;
     __shared__ uint32_t s_tile;
     __shared__ int s_slot;
     if (counters[2]) return;   // overflow: the batch is discarded
     const int S = hdr->S;
     const uint32_t total = hdr->total_tiles;
+    const unsigned long long n_claims = list ? *n_list : (unsigned long long)total;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            const uint32_t t = (uint32_t)atomicAdd(&counters[3], 1ull);
+            const unsigned long long q = atomicAdd(queue, 1ull);
+            const uint32_t t = q >= n_claims ? total : list ? list[q] : (uint32_t)q;
             int sl = 0;
             while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
             s_tile = t;
@@ -1153,7 +1290,9 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
         }
         uint2* tr = ranges + (size_t)t * svp.K;
         blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), tr, ival, rec, nullptr, nullptr,
-                              slots[slot].image, nullptr, nullptr, record_ends ? tr : nullptr, nullptr);
+                              slots[slot].image, nullptr, nullptr, record_ends ? tr : nullptr, nullptr, svp.bin_lo,
+                              svp.bin_hi, state, open, (int)(slots[slot].state_base + (t - hdr->tile_base[slot])),
+                              (int)t);
         __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
@@ -2013,8 +2152,9 @@ int launch_recount(const ViewParams& vp, const TreeParams& tp, const RasterBuffe
     if (n_vis <= 0) return RGS_OK;
     const int64_t want = (n_vis + 255) / 256;
     const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    recount_kernel<<<grid, 256, 0, s>>>(vp, tp, sorted_ids, n_vis, b.rect, b.mask, b.rec, b.item_at, b.items,
-                                        b.items ? b.item_cap : 0u, cnt_out, b.counters + 4, b.counters + 15);
+    recount_kernel<false><<<grid, 256, 0, s>>>(vp, nullptr, nullptr, 0, tp, sorted_ids, n_vis, nullptr, nullptr,
+                                               b.rect, b.mask, b.rec, b.item_at, b.items, b.items ? b.item_cap : 0u,
+                                               cnt_out, b.counters + 4, b.counters + 15);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -2081,39 +2221,66 @@ int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBu
 
 int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
                       const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
-                      cudaStream_t s) {
+                      cudaStream_t s, const unsigned long long* inst_base, bool open_tables) {
     const uint32_t* item_at = b.items ? b.item_at : nullptr;
     emit_batch_kernel<0><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
-                                                 b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase);
+                                                 b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase, inst_base);
     RGS_CUDA_LAUNCH_CHECK();
     if (tp.L > 0) {
         emit_batch_kernel<1><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
-                                                     b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase);
+                                                     b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase, inst_base);
         RGS_CUDA_LAUNCH_CHECK();
     }
     if (item_at) {
         emit_items_batch_kernel<<<152 * 8, 256, 0, s>>>(slots, hdr, b.items, b.item_ctr, b.item_cap, b.ibase, N,
-                                                        counters, b.ikey, b.ival);
+                                                        counters, b.ikey, b.ival, inst_base, open_tables,
+                                                        open_tables ? counters + kBatchBinCounter + 1 : nullptr);
         RGS_CUDA_LAUNCH_CHECK();
     }
     return RGS_OK;
 }
 
 int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
-                      cudaStream_t s) {
-    ranges_dev_kernel<<<152 * 8, 256, 0, s>>>(keys, n_dev, cap, ranges);
+                      cudaStream_t s, const unsigned long long* base_dev) {
+    ranges_dev_kernel<<<152 * 8, 256, 0, s>>>(keys, n_dev, cap, ranges, base_dev);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
 
 int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, uint2* ranges,
                        const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s,
-                       bool record_ends) {
+                       bool record_ends, const BatchGroup* grp) {
     int dev = 0, sms = 0;
     RGS_CUDA_TRY(cudaGetDevice(&dev));
     RGS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival,
-                                                                                      rec, counters, record_ends);
+    const BatchGroup none{};
+    const BatchGroup& g = grp ? *grp : none;
+    blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(
+        slots, hdr, tp, ranges, ival, rec, counters, record_ends, g.queue ? g.queue : counters + 3, g.state, g.open,
+        g.list, g.n_list);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_open_tables_batch(const BatchSlot* slots, const BatchHeader* hdr, const uint8_t* open, uint32_t* list,
+                             unsigned long long* n_list, cudaStream_t s) {
+    open_prefix_batch_kernel<<<dim3(16, kMaxSlots), 256, 0, s>>>(slots, hdr, open);
+    RGS_CUDA_LAUNCH_CHECK();
+    open_sat_batch_kernel<<<dim3(4, kMaxSlots), 256, 0, s>>>(slots, hdr);
+    RGS_CUDA_LAUNCH_CHECK();
+    open_list_kernel<<<152 * 2, 256, 0, s>>>(slots, hdr, open, list, n_list);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_recount_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
+                         const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
+                         uint32_t* cnt_out, unsigned long long* queue, unsigned long long* total, cudaStream_t s) {
+    ViewParams vp_unused;
+    memset(&vp_unused, 0, sizeof vp_unused);
+    recount_kernel<true><<<152 * 8, 256, 0, s>>>(vp_unused, slots, hdr, N, tp, sorted_ids, n_cap, counters + 1,
+                                                 counters + 2, b.rect, b.mask, b.rec, b.item_at, b.items,
+                                                 b.items ? b.item_cap : 0u, cnt_out, queue, total);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -20,6 +20,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "rgs_internal.cuh"
@@ -59,12 +60,26 @@ __global__ void batch_key_kernel(const uint32_t* __restrict__ src, const uint32_
         key[p] = src ? src[id[p]] : (uint32_t)(id[p] / (uint64_t)N);
 }
 
-// Overflow check: instances beyond the lane's capacity discard the batch.
-__global__ void check_capacity_kernel(unsigned long long* counters, int64_t inst_cap) {
+// Overflow check: instances beyond the lane's capacity discard the batch.  grouped: the
+// first binning group's instances are the ones sorted now (the total bounds every group's).
+__global__ void check_capacity_kernel(unsigned long long* counters, int64_t inst_cap, bool grouped) {
     const unsigned long long I = counters[0];
     const bool over = I > (unsigned long long)inst_cap;
     counters[2] = over ? 1ull : 0ull;
-    counters[4] = over ? 0ull : I;
+    counters[4] = over ? 0ull : grouped ? counters[kBatchBinCounter] : I;
+}
+
+// The second binning group's instances go after the first group's.  The two groups' counts
+// add up to at most the total by construction; a batch where they do not is failed
+// (overflow flag 2) before anything is written past the first group.
+__global__ void check_group2_kernel(unsigned long long* counters, int64_t inst_cap) {
+    unsigned long long& n1 = counters[kBatchBinCounter + 1];
+    if (counters[2]) {
+        n1 = 0ull;
+    } else if (counters[4] + n1 > (unsigned long long)inst_cap) {
+        counters[2] = 2ull;
+        n1 = 0ull;
+    }
 }
 
 }  // namespace
@@ -73,7 +88,7 @@ __global__ void check_capacity_kernel(unsigned long long* counters, int64_t inst
 // Carves one lane's buffers from `base` (NULL: measure); returns the bytes used.  train:
 // also the per-(slot, splat) 2D-gradient records of a batched backward.
 size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out,
-                   bool train) {
+                   bool train, int64_t group_tiles) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -111,6 +126,22 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     b.item_cap = (uint32_t)icap;
     b.item_ctr = l.counters ? l.counters + kBatchItemCounter : nullptr;
     if (train) b.g2d = (float4*)take(sizeof(float4) * 3 * P);
+    if (group_tiles > 0) {
+        // the group state of up to group_tiles tiles of the batch's grouped requests; per
+        // slot, its tables take tiles_y (tiles_x + 1) <= 2 tiles prefix entries and
+        // (tiles_y + 1)(tiles_x + 1) <= 3 tiles + 1 summed-area entries
+        b.cnt_bin = (uint32_t*)take(4 * P);
+        b.bin_ctr = l.counters ? l.counters + kBatchBinCounter : nullptr;
+        l.group_tiles = group_tiles;
+        b.state = (float4*)take(sizeof(float4) * (size_t)kTilePixels * (size_t)group_tiles);
+        b.open = (uint8_t*)take((size_t)tiles_cap);
+        l.prefix_cap = 2 * tiles_cap + slots;
+        l.sat_cap = 3 * tiles_cap + 2 * slots;
+        b.open_prefix = (uint32_t*)take(4 * (size_t)l.prefix_cap);
+        b.open_sat = (uint32_t*)take(4 * (size_t)l.sat_cap);
+        l.slots2 = (BatchSlot*)take(sizeof(BatchSlot) * kMaxSlots);
+        l.open_list = (uint32_t*)take(4 * (size_t)tiles_cap);
+    }
     b.ranges = (uint2*)take(sizeof(uint2) * tiles_cap * K);
     b.ikey = (uint32_t*)take(4 * inst_cap);
     b.ival = (uint32_t*)take(4 * inst_cap);
@@ -134,15 +165,26 @@ int ceil_log2(int64_t x) {
 // record_ends: the blend cuts saturated runs back for a batched backward's replay.
 int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
                   const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
-                  unsigned long long* status_host, cudaStream_t s, bool record_ends, const uint32_t** ival_out) {
+                  unsigned long long* status_host, cudaStream_t s, bool record_ends, const uint32_t** ival_out,
+                  const BatchSlot* slots2_host) {
     const int64_t N = g.n, P = N * slots;
-    const RasterBuffers& b = l.b;
+    const bool grouped = slots2_host != nullptr;
+    if (grouped && (!l.slots2 || !l.b.cnt_bin || record_ends)) {
+        set_error("serve: binning in groups needs a lane laid out for it (and no recorded run ends)");
+        return RGS_EINVAL;
+    }
+    RasterBuffers b = l.b;
+    if (!grouped) b.cnt_bin = nullptr;   // one group: the projection counts every rank only
     unsigned long long* c = l.counters;
+    unsigned long long* cb = c + kBatchBinCounter;
     int rc;
     RGS_CUDA_TRY(cudaMemcpyAsync(l.hdr, hdr_host, sizeof(BatchHeader), cudaMemcpyHostToDevice, s));
     RGS_CUDA_TRY(cudaMemcpyAsync(l.slots, slots_host, sizeof(BatchSlot) * slots, cudaMemcpyHostToDevice, s));
+    if (grouped)
+        RGS_CUDA_TRY(cudaMemcpyAsync(l.slots2, slots2_host, sizeof(BatchSlot) * slots, cudaMemcpyHostToDevice, s));
     RGS_CUDA_TRY(cudaMemsetAsync(c, 0, 8 * kBatchCounters, s));
     RGS_CUDA_TRY(cudaMemsetAsync(b.ranges, 0, sizeof(uint2) * tiles_cap * K, s));
+    if (grouped) RGS_CUDA_TRY(cudaMemsetAsync(b.open, 0, (size_t)tiles_cap, s));
     if ((rc = launch_clip_table_batch(l.slots, l.hdr, tp, s))) return rc;
     if ((rc = launch_project_batch(g, l.slots, l.hdr, tp, b, c, s))) return rc;
     // compaction in (request, splat) order
@@ -172,8 +214,10 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
         if ((rc = sort(ceil_log2(slots)))) return rc;
     }
     const uint32_t* sorted_ids = va;
-    if ((rc = exclusive_scan_dev(b.cnt, b.ioff, &c[1], P, 2, sorted_ids, b.temp, b.temp_bytes, s))) return rc;
-    check_capacity_kernel<<<1, 1, 0, s>>>(c, b.inst_cap);
+    if ((rc = exclusive_scan_dev(grouped ? b.cnt_bin : b.cnt, b.ioff, &c[1], P, 2, sorted_ids, b.temp, b.temp_bytes,
+                                 s)))
+        return rc;
+    check_capacity_kernel<<<1, 1, 0, s>>>(c, b.inst_cap, grouped);
     RGS_CUDA_LAUNCH_CHECK();
     if ((rc = launch_emit_batch(l.slots, l.hdr, tp, b, sorted_ids, P, N, c, s))) return rc;
     bool alt = false;
@@ -185,7 +229,42 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
     const uint32_t* ival = alt ? b.ival_alt : b.ival;
     if (ival_out) *ival_out = ival;
     if ((rc = launch_ranges_dev(keys, &c[4], b.inst_cap, b.ranges, s))) return rc;
-    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s, record_ends))) return rc;
+    BatchGroup g1;
+    g1.state = b.state;
+    g1.open = b.open;
+    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s, record_ends,
+                                 grouped ? &g1 : nullptr)))
+        return rc;
+    if (grouped) {
+        // the second group: ranks [bin_lo, K) of the slots2 views in the tiles left open,
+        // counted per visible pair in depth order (into vis_pos), emitted after the first
+        // group's instances, sorted there (same key bits: the same buffer parity), blended
+        // over the list of open tiles
+        if ((rc = launch_open_tables_batch(l.slots2, l.hdr, b.open, l.open_list, cb + 3, s))) return rc;
+        if ((rc = launch_recount_batch(l.slots2, l.hdr, tp, b, sorted_ids, P, N, c, b.vis_pos, cb + 2, cb + 1, s)))
+            return rc;
+        check_group2_kernel<<<1, 1, 0, s>>>(c, b.inst_cap);
+        RGS_CUDA_LAUNCH_CHECK();
+        if ((rc = exclusive_scan_dev(b.vis_pos, b.ioff, &c[1], P, 0, nullptr, b.temp, b.temp_bytes, s))) return rc;
+        RGS_CUDA_TRY(cudaMemsetAsync(c + 5, 0, 16, s));   // the emission's work queues
+        if ((rc = launch_emit_batch(l.slots2, l.hdr, tp, b, sorted_ids, P, N, c, s, &c[4], true))) return rc;
+        bool alt2 = false;
+        if ((rc = radix_sort_pairs_dev(b.ikey, b.ival, b.ikey_alt, b.ival_alt, cb + 1, b.inst_cap, key_bits, b.temp,
+                                       b.temp_bytes, s, &alt2, &c[4])))
+            return rc;
+        if (alt2 != alt) {
+            set_error("serve: the binning groups' sorts end in different buffers");
+            return RGS_EINVAL;
+        }
+        if ((rc = launch_ranges_dev(keys, cb + 1, b.inst_cap, b.ranges, s, &c[4]))) return rc;
+        BatchGroup g2;
+        g2.state = b.state;
+        g2.open = b.open;
+        g2.list = l.open_list;
+        g2.n_list = cb + 3;
+        g2.queue = cb + 4;
+        if ((rc = launch_blend_batch(l.slots2, l.hdr, tp, b.ranges, ival, b.rec, c, s, false, &g2))) return rc;
+    }
     RGS_CUDA_TRY(cudaMemcpyAsync(status_host, c, 8 * kBatchCounters, cudaMemcpyDeviceToHost, s));
     return RGS_OK;
 }
@@ -217,6 +296,8 @@ struct Request {
 struct Lane {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec2 = nullptr;     // the batch with binning in two groups of ranks
+    BatchSlot* slots2_host = nullptr;    // pinned: the second group's slot table
     cudaEvent_t done_ev = nullptr;
     char* mem = nullptr;
     LaneBufs bufs;
@@ -256,6 +337,9 @@ struct rgs_server {
     bool broken = false;
     bool hold = false;
     double inst_per_pixel = 16.0;   // running estimate for admission
+    bool group_lanes = false;       // lanes laid out (and captured) for binning in two groups
+    // measured tile instances (per visible splat, and in all), by resolution (width << 32 | height)
+    std::unordered_map<uint64_t, std::pair<double, double>> inst_history;
     rgs_serve_stats stats;
     int64_t batched_requests = 0;
     std::thread worker;
@@ -294,24 +378,64 @@ void form_batch(rgs_server* S, std::vector<Request*>& batch) {
     }
 }
 
+uint64_t resolution_key(const Request* r) {
+    return ((uint64_t)(uint32_t)r->cam.width << 32) | (uint32_t)r->cam.height;
+}
+
+// Whether a request bins its subsets in two groups of view ranks: the lanes allow it and
+// the batches before measured enough instances (per visible splat, and in all) at its
+// resolution (the rule of rgs_render_fwd's image-only forward, from the resolution's
+// history), or the options or thresholds ask for it always.
+bool wants_groups(const rgs_server* S, const Request* r) {
+    if (!S->group_lanes) return false;
+    if (S->opts.group_binning == 2 || (!(S->cfg.group_per_splat > 0.f) && !(S->cfg.group_min_instances > 0.f)))
+        return true;
+    const auto it = S->inst_history.find(resolution_key(r));
+    return it != S->inst_history.end() && it->second.first >= (double)S->cfg.group_per_splat &&
+           it->second.second >= (double)S->cfg.group_min_instances;
+}
+
 int launch_lane(rgs_server* S, Lane& ln, std::vector<Request*>& batch) {
     BatchHeader& h = *ln.hdr_host;
     memset(&h, 0, sizeof h);
     h.S = (int)batch.size();
     h.n_total = (unsigned long long)S->g.n * (unsigned long long)h.S;
+    const int r1 = S->K / 8 > 1 ? S->K / 8 : 1;   // the first group's ranks, as rgs_render_fwd
+    bool any_grouped = false;
+    int64_t poff = 0, soff = 0, sbase = 0;
     uint32_t base = 0;
     for (int s = 0; s < h.S; ++s) {
         h.tile_base[s] = base;
-        ln.slots_host[s].vp = batch[s]->vp;
-        ln.slots_host[s].vp.set_clip(ln.bufs.clip_plane + (size_t)s * kClipTable,
-                                     ln.bufs.clip_margin + (size_t)s * kClipTable);
-        ln.slots_host[s].image = batch[s]->out;
-        ln.slots_host[s].tile_base = base;
+        BatchSlot& a = ln.slots_host[s];
+        a.vp = batch[s]->vp;
+        a.vp.set_clip(ln.bufs.clip_plane + (size_t)s * kClipTable, ln.bufs.clip_margin + (size_t)s * kClipTable);
+        a.image = batch[s]->out;
+        a.tile_base = base;
+        // grouped while the lane's group state has room for the request's tiles
+        const bool grp = wants_groups(S, batch[s]) && sbase + batch[s]->tiles <= ln.bufs.group_tiles;
+        a.state_base = (uint32_t)sbase;
+        if (grp) sbase += batch[s]->tiles;
+        a.vp.bin_lo = 0;
+        a.vp.bin_hi = grp ? r1 : S->K;
+        if (S->group_lanes) {
+            BatchSlot& a2 = ln.slots2_host[s];
+            a2 = a;
+            a2.vp.bin_lo = grp ? r1 : S->K;   // none: every rank went with the first group
+            a2.vp.bin_hi = S->K;
+            a2.vp.set_open(ln.bufs.b.open_prefix + poff, ln.bufs.b.open_sat + soff);
+            poff += (int64_t)a.vp.tiles_y * (a.vp.tiles_x + 1);
+            soff += (int64_t)(a.vp.tiles_y + 1) * (a.vp.tiles_x + 1);
+        }
+        any_grouped |= grp;
         base += (uint32_t)batch[s]->tiles;
+    }
+    if (poff > ln.bufs.prefix_cap || soff > ln.bufs.sat_cap) {
+        set_error("serve: open-tile tables exceed the lane's");
+        return RGS_EOVERFLOW;
     }
     for (int s = h.S; s <= kMaxSlots; ++s) h.tile_base[s] = base;
     h.total_tiles = base;
-    RGS_CUDA_TRY(cudaGraphLaunch(ln.exec, ln.stream));
+    RGS_CUDA_TRY(cudaGraphLaunch(any_grouped ? ln.exec2 : ln.exec, ln.stream));
     RGS_CUDA_TRY(cudaEventRecord(ln.done_ev, ln.stream));
     ln.inflight = batch;
     ln.busy = true;
@@ -325,12 +449,26 @@ void complete_lane(rgs_server* S, Lane& ln) {
     const unsigned long long* st = ln.status_host;
     const bool overflow = st[2] != 0;
     const int n = (int)ln.inflight.size();
-    if (!overflow) {
+    if (st[2] == 2) {   // inconsistent group counts (not expected): nothing was written
+        for (Request* r : ln.inflight)
+            finish(S, r, RGS_EINVAL, "serve: the binning groups' instance counts disagree; batch not rendered");
+    } else if (!overflow) {
         int64_t inst = 0, pix = 0;
         for (int s = 0; s < n; ++s) {
             finish(S, ln.inflight[s], RGS_OK, nullptr);
-            inst += (int64_t)st[kBatchSlotCounters + 2 * s];
+            const unsigned long long I = st[kBatchSlotCounters + 2 * s], V = st[kBatchSlotCounters + 2 * s + 1];
+            inst += (int64_t)I;
             pix += ln.inflight[s]->pixels;
+            if (V > 0) {
+                const double r = (double)I / (double)V;
+                auto it = S->inst_history.find(resolution_key(ln.inflight[s]));
+                if (it == S->inst_history.end()) {
+                    S->inst_history[resolution_key(ln.inflight[s])] = std::make_pair(r, (double)I);
+                } else {
+                    it->second.first = 0.7 * it->second.first + 0.3 * r;
+                    it->second.second = 0.7 * it->second.second + 0.3 * (double)I;
+                }
+            }
         }
         if (pix > 0) S->inst_per_pixel = 0.8 * S->inst_per_pixel + 0.2 * ((double)inst / (double)pix);
     } else {
@@ -486,6 +624,8 @@ void worker_main(rgs_server* S) {
 
 void free_lane(Lane& ln) {
     if (ln.exec) cudaGraphExecDestroy(ln.exec);
+    if (ln.exec2) cudaGraphExecDestroy(ln.exec2);
+    if (ln.slots2_host) cudaFreeHost(ln.slots2_host);
     if (ln.done_ev) cudaEventDestroy(ln.done_ev);
     if (ln.stream) cudaStreamDestroy(ln.stream);
     if (ln.mem) cudaFree(ln.mem);
@@ -523,7 +663,22 @@ void rgs_serve_default_config(rgs_serve_config* cfg) {
     cfg->max_height = 4096;
     cfg->max_queue = 65536;
     cfg->inst_per_pixel = 16.f;
+    cfg->group_per_splat = (float)kGroupInstancesPerSplat;
+    cfg->group_min_instances = (float)kGroupMinInstances;
 }
+
+}  // extern "C"
+
+namespace rgs {
+// Tiles of group state a lane keeps: two requests of the largest size (or fewer slots).
+int64_t group_state_tiles(const rgs_serve_config* cfg) {
+    const int64_t max_tiles =
+        (int64_t)((cfg->max_width + kTile - 1) / kTile) * ((cfg->max_height + kTile - 1) / kTile);
+    return max_tiles * (cfg->max_slots < 2 ? cfg->max_slots : 2);
+}
+}  // namespace rgs
+
+extern "C" {
 
 int rgs_serve_lane_bytes(const rgs_kd* kd, const rgs_gaussians* g, const rgs_serve_config* cfg,
                          int64_t instance_capacity, size_t* bytes) {
@@ -538,7 +693,7 @@ int rgs_serve_lane_bytes(const rgs_kd* kd, const rgs_gaussians* g, const rgs_ser
     const int64_t max_tiles =
         (int64_t)((cfg->max_width + kTile - 1) / kTile) * ((cfg->max_height + kTile - 1) / kTile);
     *bytes = lane_layout(nullptr, g->n, cfg->max_slots, max_tiles * cfg->max_slots, 1 << kd->b.L, instance_capacity,
-                         nullptr);
+                         nullptr, false, (1 << kd->b.L) >= 4 ? group_state_tiles(cfg) : 0);
     return RGS_OK;
 }
 
@@ -564,9 +719,10 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
     }
     if (cfg->max_slots < 1 || cfg->max_slots > kMaxSlots || cfg->lanes < 1 || cfg->lanes > 4 ||
         cfg->max_width < 1 || cfg->max_width > 16384 || cfg->max_height < 1 || cfg->max_height > 16384 ||
-        cfg->max_queue < 1 || !(cfg->inst_per_pixel > 0.f)) {
+        cfg->max_queue < 1 || !(cfg->inst_per_pixel > 0.f) || !(cfg->group_per_splat >= 0.f) ||
+        !(cfg->group_min_instances >= 0.f)) {
         set_error("serve_create: need max_slots in [1,%d], lanes in [1,4], max size in [1,16384], max_queue >= 1, "
-                  "inst_per_pixel > 0", kMaxSlots);
+                  "inst_per_pixel > 0, group thresholds >= 0", kMaxSlots);
         return RGS_EINVAL;
     }
     rgs_server* S = new (std::nothrow) rgs_server();
@@ -625,7 +781,9 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
         const size_t lane_budget = cfg->mem_budget_bytes / (size_t)cfg->lanes;
         S->tiles_cap = max_tiles * cfg->max_slots;
         if (ceil_log2(S->tiles_cap) + S->L > 32) { set_error("serve_create: tile keys exceed 32 bits"); return fail(RGS_EINVAL); }
-        const size_t fixed = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, 0, nullptr);
+        S->group_lanes = opts->group_binning >= 1 && S->K >= 4;
+        const int64_t gl = S->group_lanes ? group_state_tiles(cfg) : 0;
+        const size_t fixed = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, 0, nullptr, false, gl);
         const int64_t min_inst = (int64_t)1 << 16;
         if (lane_budget < fixed + (size_t)min_inst * 16) {
             set_error("serve_create: a lane needs at least %zu bytes (%zu given per lane)", fixed + (size_t)min_inst * 16,
@@ -633,20 +791,22 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
             return fail(RGS_EINVAL);
         }
         int64_t cap = (int64_t)((lane_budget - fixed) / 16);
-        while (cap > min_inst && lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr) > lane_budget)
+        while (cap > min_inst &&
+               lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr, false, gl) > lane_budget)
             cap -= 64;
         if (cap > 0xFFFFFFFEll) cap = 0xFFFFFFFEll;
         S->inst_cap = cap;
         S->lanes.resize(cfg->lanes);
         for (auto& ln : S->lanes) {
-            const size_t bytes = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr);
+            const size_t bytes = lane_layout(nullptr, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, nullptr, false, gl);
             if (cudaMalloc(&ln.mem, bytes) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("serve_create: cannot allocate %zu device bytes for a lane", bytes);
                 return fail(RGS_ENOMEM);
             }
-            lane_layout(ln.mem, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, &ln.bufs);
+            lane_layout(ln.mem, g->n, cfg->max_slots, S->tiles_cap, S->K, cap, &ln.bufs, false, gl);
             if (cudaMallocHost(&ln.slots_host, sizeof(BatchSlot) * kMaxSlots) != cudaSuccess ||
+                cudaMallocHost(&ln.slots2_host, sizeof(BatchSlot) * kMaxSlots) != cudaSuccess ||
                 cudaMallocHost(&ln.hdr_host, sizeof(BatchHeader)) != cudaSuccess ||
                 cudaMallocHost(&ln.status_host, 8 * kBatchCounters) != cudaSuccess ||
                 cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -656,26 +816,30 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
                 return fail(RGS_ECUDA);
             }
             memset(ln.slots_host, 0, sizeof(BatchSlot) * kMaxSlots);
+            memset(ln.slots2_host, 0, sizeof(BatchSlot) * kMaxSlots);
             memset(ln.hdr_host, 0, sizeof(BatchHeader));
-            // capture the lane's batch pipeline once
+            // capture the lane's batch pipeline once (and once binning in two groups)
             if ((rc = sort_prepare())) return fail(rc);
-            cudaGraph_t graph = nullptr;
-            RGS_CUDA_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
-            prof_suppress(true);
-            rc = enqueue_batch(S->g, S->tp, S->K, S->L, cfg->max_slots, S->tiles_cap, ln.bufs, ln.slots_host,
-                               ln.hdr_host, ln.status_host, ln.stream);
-            prof_suppress(false);
-            const cudaError_t ec = cudaStreamEndCapture(ln.stream, &graph);
-            if (rc || ec != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                if (!rc) set_error("serve_create: stream capture failed: %s", cudaGetErrorString(ec));
-                return fail(rc ? rc : RGS_ECUDA);
-            }
-            const cudaError_t ei = cudaGraphInstantiate(&ln.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) {
-                set_error("serve_create: graph instantiation failed: %s", cudaGetErrorString(ei));
-                return fail(RGS_ECUDA);
+            for (int v = 0; v < (gl ? 2 : 1); ++v) {
+                cudaGraph_t graph = nullptr;
+                RGS_CUDA_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
+                prof_suppress(true);
+                rc = enqueue_batch(S->g, S->tp, S->K, S->L, cfg->max_slots, S->tiles_cap, ln.bufs, ln.slots_host,
+                                   ln.hdr_host, ln.status_host, ln.stream, false, nullptr,
+                                   v ? ln.slots2_host : nullptr);
+                prof_suppress(false);
+                const cudaError_t ec = cudaStreamEndCapture(ln.stream, &graph);
+                if (rc || ec != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    if (!rc) set_error("serve_create: stream capture failed: %s", cudaGetErrorString(ec));
+                    return fail(rc ? rc : RGS_ECUDA);
+                }
+                const cudaError_t ei = cudaGraphInstantiate(v ? &ln.exec2 : &ln.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ei != cudaSuccess) {
+                    set_error("serve_create: graph instantiation failed: %s", cudaGetErrorString(ei));
+                    return fail(RGS_ECUDA);
+                }
             }
         }
     }

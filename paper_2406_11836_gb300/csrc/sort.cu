@@ -337,9 +337,14 @@ struct WideSmem {
 template <int kBits>
 __global__ void __launch_bounds__(kWideThreads, 2)
 wide_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ counts,
-                    uint32_t nblocks, bool vec, const unsigned long long* __restrict__ n_dev) {
+                    uint32_t nblocks, bool vec, const unsigned long long* __restrict__ n_dev,
+                    const unsigned long long* __restrict__ base_dev) {
     constexpr int kBins = 1 << kBits;
     __shared__ uint32_t hist[kBins];
+    if (base_dev) {
+        keys += *base_dev;
+        vec = vec && ((uintptr_t)keys & 15) == 0;
+    }
     for (int d = threadIdx.x; d < kBins; d += kWideThreads) hist[d] = 0;
     __syncthreads();
     int64_t lo, hi;
@@ -353,9 +358,14 @@ template <int kBits>
 __global__ void __launch_bounds__(kWideThreads, 2)
 wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                       uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offsets,
-                      uint32_t nblocks, const unsigned long long* __restrict__ n_dev) {
+                      uint32_t nblocks, const unsigned long long* __restrict__ n_dev,
+                      const unsigned long long* __restrict__ base_dev) {
     constexpr int kBins = 1 << kBits;
     constexpr uint32_t kMask = (uint32_t)kBins - 1u;
+    if (base_dev) {
+        const unsigned long long b = *base_dev;
+        kin += b; vin += b; kout += b; vout += b;
+    }
     constexpr int kPer = kBins / kWideThreads > 0 ? kBins / kWideThreads : 1;   // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char wide_smem_raw[];
     WideSmem<kBits>& sm = *reinterpret_cast<WideSmem<kBits>*>(wide_smem_raw);
@@ -467,11 +477,12 @@ wide_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restri
 }
 
 // n_dev (nullable): the key count lives in device memory and n is the capacity; the grid
-// is then kWideChunks blocks (stream-capturable).
+// is then kWideChunks blocks (stream-capturable).  base_dev (nullable, with n_dev): the
+// keys start at that element of the arrays (a device value).
 template <int kBits>
 int wide_pass(const uint32_t* ka, const uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n, int shift,
               uint32_t* counts, void* stemp, size_t sbytes, cudaStream_t s,
-              const unsigned long long* n_dev = nullptr) {
+              const unsigned long long* n_dev = nullptr, const unsigned long long* base_dev = nullptr) {
     constexpr int kBins = 1 << kBits;
     const int64_t nb = n_dev ? kWideChunks : (n + kWideBlockItems - 1) / kWideBlockItems;
     const int64_t nc = nb * kBins;
@@ -484,12 +495,12 @@ int wide_pass(const uint32_t* ka, const uint32_t* va, uint32_t* kb, uint32_t* vb
         RGS_CUDA_TRY(cudaFuncSetAttribute(wide_downsweep_kernel<kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     wide_upsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, 0, s>>>(ka, n, shift, counts, (uint32_t)nb,
-                                                                      ((uintptr_t)ka & 15) == 0, n_dev);
+                                                                      ((uintptr_t)ka & 15) == 0, n_dev, base_dev);
     RGS_CUDA_LAUNCH_CHECK();
     int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
     if (rc != RGS_OK) return rc;
     wide_downsweep_kernel<kBits><<<(unsigned)nb, kWideThreads, smem, s>>>(ka, va, kb, vb, n, shift, counts,
-                                                                           (uint32_t)nb, n_dev);
+                                                                           (uint32_t)nb, n_dev, base_dev);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -544,8 +555,9 @@ dscan_tile_kernel(const uint32_t* in, uint32_t* out, const unsigned long long* _
 
 __global__ void __launch_bounds__(kSortThreads, 4)
 dradix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev, int64_t cap,
-                      int shift, uint32_t* __restrict__ counts) {
+                      int shift, uint32_t* __restrict__ counts, const unsigned long long* __restrict__ base_dev) {
     __shared__ uint32_t hist[kRadix];
+    if (base_dev) keys += *base_dev;
     hist[threadIdx.x] = 0;
     __syncthreads();
     int64_t lo, hi;
@@ -558,8 +570,13 @@ dradix_upsweep_kernel(const uint32_t* __restrict__ keys, const unsigned long lon
 __global__ void __launch_bounds__(kSortThreads, 4)
 dradix_downsweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
                         uint32_t* __restrict__ vout, const unsigned long long* __restrict__ n_dev, int64_t cap,
-                        int shift, const uint32_t* __restrict__ offsets) {
+                        int shift, const uint32_t* __restrict__ offsets,
+                        const unsigned long long* __restrict__ base_dev) {
     __shared__ uint32_t goff[kRadix];
+    if (base_dev) {
+        const unsigned long long b = *base_dev;
+        kin += b; vin += b; kout += b; vout += b;
+    }
     goff[threadIdx.x] = offsets[(int64_t)threadIdx.x * kChunks + blockIdx.x];
     int64_t lo, hi;
     chunk_range(device_count(n_dev, cap), kSortTile, lo, hi);
@@ -708,7 +725,7 @@ size_t radix_dev_temp_bytes() {
 
 int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                          const unsigned long long* n_dev, int64_t cap, int end_bit, void* temp, size_t temp_bytes,
-                         cudaStream_t s, bool* in_alt) {
+                         cudaStream_t s, bool* in_alt, const unsigned long long* base_dev) {
     static_assert(kRadix == kSortThreads, "one digit per thread");
     *in_alt = false;
     if (cap <= 1 || end_bit <= 0) return RGS_OK;
@@ -732,9 +749,9 @@ int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
         int shift = 0;
         for (int pass = 0; pass < 2; ++pass) {
             const int bits = pass == 0 ? b0 : end_bit - b0;
-            int rc = bits == 10   ? wide_pass<10>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev)
-                     : bits == 9  ? wide_pass<9>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev)
-                                  : wide_pass<8>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev);
+            int rc = bits == 10   ? wide_pass<10>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev, base_dev)
+                     : bits == 9  ? wide_pass<9>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev, base_dev)
+                                  : wide_pass<8>(ka, va, kb, vb, cap, shift, counts, stemp, sbytes, s, n_dev, base_dev);
             if (rc != RGS_OK) return rc;
             shift += bits;
             uint32_t* t;
@@ -745,11 +762,11 @@ int radix_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uin
         return RGS_OK;
     }
     for (int shift = 0; shift < end_bit; shift += kRadixBits) {
-        dradix_upsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, n_dev, cap, shift, counts);
+        dradix_upsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, n_dev, cap, shift, counts, base_dev);
         RGS_CUDA_LAUNCH_CHECK();
         int rc = exclusive_scan_u32(counts, counts, nc, 0, nullptr, stemp, sbytes, s);
         if (rc != RGS_OK) return rc;
-        dradix_downsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, va, kb, vb, n_dev, cap, shift, counts);
+        dradix_downsweep_kernel<<<kChunks, kSortThreads, 0, s>>>(ka, va, kb, vb, n_dev, cap, shift, counts, base_dev);
         RGS_CUDA_LAUNCH_CHECK();
         uint32_t* t;
         t = ka; ka = kb; kb = t;

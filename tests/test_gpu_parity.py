@@ -597,7 +597,7 @@ def test_group_binning_matches_one_group(R, L):
     g = R.scene_c(dev)
     dL = torch.from_numpy(np.random.default_rng(L).normal(size=(3, 93, 157)).astype(np.float32) * 1e-3).cuda()
     res = {}
-    for gb in (0, 1):
+    for gb in (0, 2):     # 2: grouped whatever the instance counts (this view has few)
         opts = R.default_opts(group_binning=gb)
         ws = R.Workspace()
         R.profile_enable(timing=False, counters=True)
@@ -609,7 +609,7 @@ def test_group_binning_matches_one_group(R, L):
         c = R.profile_read(reset=True)["counters"]
         R.profile_enable(False, False)
         res[gb] = (out, [t.double().cpu().numpy() for t in gr], c)
-    one, two = res[0], res[1]
+    one, two = res[0], res[2]
     for key in ("image", "T_final", "tile_depth"):
         assert torch.equal(one[0][key], two[0][key]), key
     for a, b in zip(one[1], two[1]):

@@ -104,6 +104,63 @@ def test_plain_mode_matches(R, scene):
         assert torch.equal(a, b)
 
 
+def _render_counts(R, kd, g, cam):
+    """(tile instances, visible splats) of one render of cam binned in one group."""
+    ws = R.Workspace()
+    R.profile_enable(timing=False, counters=True)
+    try:
+        R.profile_read(reset=True)
+        R.render_fwd(kd, g, cam, R.default_opts(group_binning=0), ws, partials=False)
+        torch.cuda.synchronize()
+        c = R.profile_read(reset=True)["counters"]
+        return c["instances"], c["visible"]
+    finally:
+        R.profile_enable(timing=False, counters=False)
+
+
+def test_grouped_batches_match_render_fwd(R, scene):
+    """Requests that bin their subsets in two groups of view ranks (the nearest first, the
+    rest only in the tiles the first left open) give rgs_render_fwd's image bit for bit,
+    in batches of grouped requests only and in batches that mix grouped and one-group
+    requests (the server groups a resolution once its measured instances per visible
+    splat reach group_per_splat)."""
+    wl, g, kd, cams = scene
+    assert kd.K >= 4
+    ws = R.Workspace()
+    refs = []
+    for c in cams:
+        refs.append(R.render_fwd(kd, g, c, R.default_opts(), ws, partials=False)["image"].clone())
+    torch.cuda.synchronize()
+    outs, _, st = _serve(R, scene, cams, mem_budget_bytes=4 << 30, max_slots=8, lanes=1, group_per_splat=0.0,
+                         group_min_instances=0.0)
+    assert st["completed"] == len(cams) and st["failed"] == 0 and st["mean_batch"] > 1.0
+    for c, r, o in zip(cams, refs, outs):
+        assert torch.equal(r, o), (c.width, c.height, (r - o).abs().max().item())
+    # a threshold between the views' ratios: the second batch mixes both kinds of request
+    ratios = []
+    for c in cams:
+        inst, vis = _render_counts(R, kd, g, c)
+        ratios.append(inst / vis)
+    thr = sorted(ratios)[len(ratios) // 2]
+    n_grouped = sum(r >= thr for r in ratios)
+    assert 0 < n_grouped < len(cams)
+    srv = R.Server(kd, g, R.default_opts(), 4 << 30, max_slots=8, lanes=1, group_per_splat=float(thr),
+                   group_min_instances=0.0, keepalive=wl.scene)
+    try:
+        for rnd in range(2):     # the first batch measures, the second groups by the measure
+            outs = [torch.full((3, c.height, c.width), -1.0, device="cuda") for c in cams]
+            srv.hold(True)
+            ts = [srv.submit(c, o) for c, o in zip(cams, outs)]
+            srv.hold(False)
+            for t in ts:
+                srv.wait(t, timeout_s=120)
+            torch.cuda.synchronize()
+            for c, r, o in zip(cams, refs, outs):
+                assert torch.equal(r, o), (rnd, c.width, c.height)
+    finally:
+        srv.close()
+
+
 def _instances(R, kd, g, cam):
     """Tile instances of one render of cam (the library's tracing counters), binned in one
     group as the batch path bins them."""
