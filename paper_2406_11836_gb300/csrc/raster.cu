@@ -448,38 +448,6 @@ open_sat_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __
         open_sat_col(vp.open_prefix(), vp.tiles_x, vp.tiles_y, sat, x);
 }
 
-// The batch's open tiles as a list of global tiles, request by request in row-major order
-// (each tile's place from its request's tables), and their number in *n_list.
-__global__ void __launch_bounds__(256)
-open_list_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
-                 const uint8_t* __restrict__ open, uint32_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
-    __shared__ uint32_t soff[kMaxSlots + 1];
-    const int S = hdr->S;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int sl = 0; sl < S; ++sl) {
-            soff[sl] = acc;
-            const ViewParams& vp = slots[sl].vp;
-            acc += vp.open_sat()[(size_t)vp.tiles_y * (vp.tiles_x + 1) + vp.tiles_x];
-        }
-        soff[S] = acc;
-        if (blockIdx.x == 0) *n_list = acc;
-    }
-    __syncthreads();
-    const uint32_t total = hdr->total_tiles;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        if (!open[t]) continue;
-        int sl = 0;
-        while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
-        const ViewParams& vp = slots[sl].vp;
-        const int tiles_x = vp.tiles_x;
-        const uint32_t lt = t - hdr->tile_base[sl];
-        const uint32_t y = lt / (uint32_t)tiles_x, x = lt - y * (uint32_t)tiles_x;
-        const size_t W1 = (size_t)tiles_x + 1;
-        list[soff[sl] + vp.open_sat()[(size_t)y * W1 + tiles_x] + vp.open_prefix()[(size_t)y * W1 + x]] = t;
-    }
-}
-
 // Copies the batch's view parameters into shared memory (the whole block).
 __device__ __forceinline__ void load_batch_views(const BatchSlot* __restrict__ slots, int S, ViewParams* svp) {
     constexpr int kWords = (int)(sizeof(ViewParams) / 4);
@@ -1023,12 +991,10 @@ __device__ __forceinline__ void count_pairs(unsigned long long* pairs, uint32_t 
 //
 // Groups of ranks (the image-only forward binned group by group): the call blends view
 // ranks [r_begin, r_end) only.  With r_begin > 0 each pixel's merged colour and
-// transmittance in front come from `state` (a float4 per pixel, 256 per tile, tiles
-// numbered by state_tile: the view's tile, or a batch request's tile past its state base);
-// with r_end < K a tile that still has a pixel whose front transmittance is at least eps_T
-// stores them there and sets its flag in `open` (entry open_tile: the view's tile, or the
-// batch's global tile), and a tile with none writes its image (nothing behind can change
-// it), clears its flag and marks the later ranks' depths -inf.
+// transmittance in front come from `state` (a float4 per pixel, 256 per tile); with
+// r_end < K a tile that still has a pixel whose front transmittance is at least eps_T
+// stores them there and sets its flag in `open`, and a tile with none writes its image
+// (nothing behind can change it), clears its flag and marks the later ranks' depths -inf.
 template <bool kCount>
 __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeParams& tp, int tile,
                                                const uint2* ranges, const uint32_t* __restrict__ ival,
@@ -1037,12 +1003,8 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                                                float* __restrict__ Tfin, float* __restrict__ tile_depth,
                                                uint2* ends, unsigned long long* __restrict__ pairs,
                                                int r_begin = 0, int r_end = -1, float4* __restrict__ state = nullptr,
-                                               uint8_t* __restrict__ open = nullptr, int state_tile = -1,
-                                               int open_tile = -1) {
+                                               uint8_t* __restrict__ open = nullptr) {
     if (r_end < 0) r_end = vp.K;
-    // state and open flags are kept per tile (global over a batch): 256 entries a tile
-    const size_t st_tile = state_tile >= 0 ? (size_t)state_tile : (size_t)tile;
-    const size_t op_tile = open_tile >= 0 ? (size_t)open_tile : (size_t)tile;
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float4 splane[kBlendThreads][kMaxCutPlanes];
@@ -1068,7 +1030,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
     uint8_t* wl = wlist[warp];
     const int tid = threadIdx.x;
     if (r_begin > 0 && inside) {
-        const float4 st = state[st_tile * kBlendThreads + threadIdx.x];
+        const float4 st = state[(size_t)tile * kBlendThreads + threadIdx.x];
         s_img[0][tid] = st.x;
         s_img[1][tid] = st.y;
         s_img[2][tid] = st.z;
@@ -1203,12 +1165,12 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
         const bool open_px = inside && !(s_img[3][tid] < vp.eps_T);
         if (__syncthreads_count(open_px) > 0) {
             if (inside)
-                state[st_tile * kBlendThreads + tid] = make_float4(s_img[0][tid], s_img[1][tid], s_img[2][tid],
+                state[(size_t)tile * kBlendThreads + tid] = make_float4(s_img[0][tid], s_img[1][tid], s_img[2][tid],
                                                                    s_img[3][tid]);
-            if (tid == 0) open[op_tile] = 1;
+            if (tid == 0) open[tile] = 1;
             image = nullptr;   // the last group writes it
         } else {
-            if (tid == 0) open[op_tile] = 0;
+            if (tid == 0) open[tile] = 0;
             if (tile_depth && tid < vp.K && tid >= r_end) tile_depth[tid] = -kInfF;   // nothing needed behind
         }
     }
@@ -1238,7 +1200,8 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __
                  const float4* __restrict__ rec, float* __restrict__ pC, float* __restrict__ pT,
                  float* __restrict__ image, float* __restrict__ Tfin, float* __restrict__ tile_depth, bool record_ends,
                  unsigned long long* __restrict__ pairs, int r_begin, int r_end, float4* __restrict__ state,
-                 uint8_t* __restrict__ open) {
+                 uint8_t* __restrict__ open, const unsigned long long* __restrict__ skip) {
+    if (skip && *skip) return;   // a batch's overflow flag, or an unused request slot
     const int tile = blockIdx.x;
     if (r_begin > 0 && !open[tile]) return;   // closed by an earlier group (uniform across the block)
     uint2* tr = ranges + (size_t)tile * vp.K;
@@ -1248,30 +1211,23 @@ blend_fwd_kernel(ViewParams vp, TreeParams tp, uint2* ranges, const uint32_t* __
 }
 
 // Persistent forward blend over the global tiles of a batch: each block takes the next
-// tile from a device counter (*queue) until all are done; a tile belongs to the last
-// request whose tile_base it reaches.  The request's view is kept in shared memory while
-// consecutive tiles stay in one request.  Each request blends its binning group's view
-// ranks [bin_lo, bin_hi) (state: the group state of blend_fwd_tile, a grouped request's
-// tiles from its state_base; open: its flags, by global tile);
-// list (nullable): the tiles are the *n_list entries of list (a later group's open tiles).
+// tile from a device counter until all are done; a tile belongs to the last request
+// whose tile_base it reaches.  The request's view is kept in shared memory while
+// consecutive tiles stay in one request.
 __global__ void __launch_bounds__(kBlendThreads, RGS_BLEND_MIN_BLOCKS)
 blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr, TreeParams tp,
                    uint2* __restrict__ ranges, const uint32_t* __restrict__ ival, const float4* __restrict__ rec,
-                   unsigned long long* __restrict__ counters, bool record_ends, unsigned long long* __restrict__ queue,
-                   float4* __restrict__ state, uint8_t* __restrict__ open, const uint32_t* __restrict__ list,
-                   const unsigned long long* __restrict__ n_list) {
+                   unsigned long long* __restrict__ counters, bool record_ends) {
     __shared__ ViewParams svp;
     __shared__ uint32_t s_tile;
     __shared__ int s_slot;
     if (counters[2]) return;   // overflow: the batch is discarded
     const int S = hdr->S;
     const uint32_t total = hdr->total_tiles;
-    const unsigned long long n_claims = list ? *n_list : (unsigned long long)total;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned long long q = atomicAdd(queue, 1ull);
-            const uint32_t t = q >= n_claims ? total : list ? list[q] : (uint32_t)q;
+            const uint32_t t = (uint32_t)atomicAdd(&counters[3], 1ull);
             int sl = 0;
             while (sl + 1 < S && hdr->tile_base[sl + 1] <= t) ++sl;
             s_tile = t;
@@ -1290,9 +1246,7 @@ blend_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __res
         }
         uint2* tr = ranges + (size_t)t * svp.K;
         blend_fwd_tile<false>(svp, tp, (int)(t - hdr->tile_base[slot]), tr, ival, rec, nullptr, nullptr,
-                              slots[slot].image, nullptr, nullptr, record_ends ? tr : nullptr, nullptr, svp.bin_lo,
-                              svp.bin_hi, state, open, (int)(slots[slot].state_base + (t - hdr->tile_base[slot])),
-                              (int)t);
+                              slots[slot].image, nullptr, nullptr, record_ends ? tr : nullptr, nullptr);
         __syncthreads();   // s_tile is rewritten by the next claim
     }
 }
@@ -2172,12 +2126,55 @@ int launch_blend_fwd(const ViewParams& vp, const TreeParams& tp, const RasterBuf
     if (pairs)
         blend_fwd_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T, image,
                                                               T_final, tile_depth, record_ends, pairs, r_begin, r_end,
-                                                              b.state, b.open);
+                                                              b.state, b.open, nullptr);
     else
         blend_fwd_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, partial_C, partial_T,
                                                                image, T_final, tile_depth, record_ends, nullptr,
-                                                               r_begin, r_end, b.state, b.open);
+                                                               r_begin, r_end, b.state, b.open, nullptr);
     RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+// One request of a batch blended as its own launch of blend_fwd_kernel (its view a kernel
+// parameter): the argument list of that launch, and its launch during a stream capture or
+// the update of its graph node for the next batch.
+namespace {
+struct BlendNodeParams {
+    void* args[17];
+    bool record_ends = false;
+    unsigned long long* pairs = nullptr;
+    float *pC = nullptr, *pT = nullptr, *Tfin = nullptr, *tile_depth = nullptr;
+    BlendNodeArgs a;
+    explicit BlendNodeParams(const BlendNodeArgs& x) : a(x) {
+        void* p[17] = {&a.vp,    &a.tp,         &a.ranges,      &a.ival,  &a.rec,     &pC,     &pT,      &a.image, &Tfin,
+                       &tile_depth, &record_ends, &pairs, &a.r_begin, &a.r_end, &a.state, &a.open, &a.skip};
+        for (int i = 0; i < 17; ++i) args[i] = p[i];
+    }
+    cudaKernelNodeParams node(unsigned grid) {
+        cudaKernelNodeParams k;
+        memset(&k, 0, sizeof k);
+        k.func = (void*)blend_fwd_kernel<false>;
+        k.gridDim = dim3(grid > 0 ? grid : 1u);
+        k.blockDim = dim3(kBlendThreads);
+        k.sharedMemBytes = 0;
+        k.kernelParams = args;
+        return k;
+    }
+};
+}  // namespace
+
+int launch_blend_node(const BlendNodeArgs& a, unsigned grid, cudaStream_t s) {
+    blend_fwd_kernel<false><<<grid > 0 ? grid : 1u, kBlendThreads, 0, s>>>(
+        a.vp, a.tp, a.ranges, a.ival, a.rec, nullptr, nullptr, a.image, nullptr, nullptr, false, nullptr, a.r_begin,
+        a.r_end, a.state, a.open, a.skip);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int set_blend_node(cudaGraphExec_t exec, cudaGraphNode_t node, const BlendNodeArgs& a, unsigned grid) {
+    BlendNodeParams p(a);
+    const cudaKernelNodeParams k = p.node(grid);
+    RGS_CUDA_TRY(cudaGraphExecKernelNodeSetParams(exec, node, &k));
     return RGS_OK;
 }
 
@@ -2249,26 +2246,20 @@ int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int
 
 int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, uint2* ranges,
                        const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s,
-                       bool record_ends, const BatchGroup* grp) {
+                       bool record_ends) {
     int dev = 0, sms = 0;
     RGS_CUDA_TRY(cudaGetDevice(&dev));
     RGS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const BatchGroup none{};
-    const BatchGroup& g = grp ? *grp : none;
-    blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(
-        slots, hdr, tp, ranges, ival, rec, counters, record_ends, g.queue ? g.queue : counters + 3, g.state, g.open,
-        g.list, g.n_list);
+    blend_batch_kernel<<<(unsigned)(sms * RGS_BLEND_MIN_BLOCKS), kBlendThreads, 0, s>>>(slots, hdr, tp, ranges, ival,
+                                                                                      rec, counters, record_ends);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
 
-int launch_open_tables_batch(const BatchSlot* slots, const BatchHeader* hdr, const uint8_t* open, uint32_t* list,
-                             unsigned long long* n_list, cudaStream_t s) {
+int launch_open_tables_batch(const BatchSlot* slots, const BatchHeader* hdr, const uint8_t* open, cudaStream_t s) {
     open_prefix_batch_kernel<<<dim3(16, kMaxSlots), 256, 0, s>>>(slots, hdr, open);
     RGS_CUDA_LAUNCH_CHECK();
     open_sat_batch_kernel<<<dim3(4, kMaxSlots), 256, 0, s>>>(slots, hdr);
-    RGS_CUDA_LAUNCH_CHECK();
-    open_list_kernel<<<152 * 2, 256, 0, s>>>(slots, hdr, open, list, n_list);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -132,20 +132,9 @@ constexpr int kBatchSlotCounters = 8;
 constexpr int kBatchItemCounter = kBatchSlotCounters + 2 * kMaxSlots;
 constexpr int kBatchCandCounters = kBatchItemCounter + 1;
 // ... then, binning in two groups of ranks: [0] the first group's instances, [1] the
-// second's, [2] the second group's count work-queue head, [3] the tiles the first group
-// left open, [4] the second group's blend work-queue head
+// second's, [2] the second group's count work-queue head
 constexpr int kBatchBinCounter = kBatchCandCounters + kMaxSlots;
-constexpr int kBatchCounters = kBatchBinCounter + 5;
-
-// A later binning group's blend over a batch: group state and open flags by global tile,
-// the open tiles as a list of *n_list global tiles, claimed from *queue.
-struct BatchGroup {
-    float4* state = nullptr;
-    uint8_t* open = nullptr;
-    const uint32_t* list = nullptr;
-    const unsigned long long* n_list = nullptr;
-    unsigned long long* queue = nullptr;
-};
+constexpr int kBatchCounters = kBatchBinCounter + 3;
 
 struct RasterBuffers;
 int ceil_log2(int64_t x);
@@ -303,10 +292,10 @@ struct LaneBufs {
     unsigned long long* counters;
     float4* clip_plane;    // [kMaxSlots * kClipTable]: each request's plane templates
     float* clip_margin;    // [kMaxSlots * kClipTable]
+    unsigned long long* one;   // a device word that is never 0 (the skip flag of unused slots)
     // binning in two groups of view ranks (serving lanes): the second group's slot table
-    // (each request's view with its rank range and open-tile tables) and the open tiles
+    // (each request's view with its rank range and open-tile tables)
     BatchSlot* slots2;
-    uint32_t* open_list;       // [tiles_cap]
     int64_t prefix_cap, sat_cap;   // entries of b.open_prefix / b.open_sat
     int64_t group_tiles;           // tiles of group state (b.state: 256 pixels each)
     RasterBuffers b;
@@ -316,13 +305,23 @@ struct LaneBufs {
 size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, int64_t inst_cap, LaneBufs* out,
                    bool train = false, int64_t group_tiles = 0);
 // ival_out (nullable): the buffer that holds the sorted instance payloads.
-// grouped (a lane laid out with group state): the slots bin view ranks [0, bin_hi) first, and
-// those of slots2 ranks [bin_lo, K) in the tiles the first group left open; slots2_host is
-// then the second table.
+// The per-request blend launches of a captured serving batch (graph nodes whose arguments
+// each batch sets): first group (or every rank), second group; and the buffer that holds
+// the sorted instance payloads.
+struct BlendNodes {
+    cudaGraphNode_t g1[kMaxSlots];
+    cudaGraphNode_t g2[kMaxSlots];
+    const uint32_t* ival;
+};
+// nodes (nullable): blend each request by its own launch (recorded in *nodes) instead of
+// the persistent batch blend.  grouped (slots2_host set; needs nodes and a lane laid out
+// with group state): the slots bin view ranks [0, bin_hi) first, and those of slots2 ranks
+// [bin_lo, K) in the tiles the first group left open.
 int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
                   const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
                   unsigned long long* status_host, cudaStream_t s, bool record_ends = false,
-                  const uint32_t** ival_out = nullptr, const BatchSlot* slots2_host = nullptr);
+                  const uint32_t** ival_out = nullptr, const BatchSlot* slots2_host = nullptr,
+                  BlendNodes* nodes = nullptr);
 
 int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeParams& tp, RasterBuffers& b,
                        cudaStream_t s);
@@ -342,9 +341,8 @@ int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tree
                       const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
                       cudaStream_t s, const unsigned long long* inst_base = nullptr, bool open_tables = false);
 // A later binning group of a batch: each slot's open-tile tables from the open flags (at
-// the addresses its view carries), and the list of open global tiles.
-int launch_open_tables_batch(const BatchSlot* slots, const BatchHeader* hdr, const uint8_t* open, uint32_t* list,
-                             unsigned long long* n_list, cudaStream_t s);
+// the addresses its view carries).
+int launch_open_tables_batch(const BatchSlot* slots, const BatchHeader* hdr, const uint8_t* open, cudaStream_t s);
 // ... and its count for every visible (slot, splat) pair in depth order (into cnt_out;
 // total into *total), as launch_recount.
 int launch_recount_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const RasterBuffers& b,
@@ -355,11 +353,27 @@ int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int
 // Persistent forward blend over the batch's global tiles (fused merge into each slot's
 // image; no partial maps).  record_ends: cut each saturated run back to what was staged
 // (the batched backward replays the runs).
-// Each slot blends its group's view ranks [bin_lo, bin_hi); grp (nullable): the group state
-// (required when a slot's range is not every rank) and, for a later group, its open tiles.
+// One request of a serving batch blended by its own launch of the forward blend kernel
+// (view ranks [r_begin, r_end), its tiles' ranges, group state and open flags, its image;
+// nothing when *skip is set): launched while a lane's graph is captured, its graph node
+// then given each batch's arguments and grid (the request's tiles).
+struct BlendNodeArgs {
+    ViewParams vp;
+    TreeParams tp;
+    uint2* ranges;
+    const uint32_t* ival;
+    const float4* rec;
+    float* image;
+    int r_begin, r_end;
+    float4* state;
+    uint8_t* open;
+    const unsigned long long* skip;
+};
+int launch_blend_node(const BlendNodeArgs& a, unsigned grid, cudaStream_t s);
+int set_blend_node(cudaGraphExec_t exec, cudaGraphNode_t node, const BlendNodeArgs& a, unsigned grid);
 int launch_blend_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, uint2* ranges,
                        const uint32_t* ival, const float4* rec, unsigned long long* counters, cudaStream_t s,
-                       bool record_ends = false, const BatchGroup* grp = nullptr);
+                       bool record_ends = false);
 // Persistent flat backward over the batch's global tiles (counters[7]: its work queue);
 // 2D gradients into g2d indexed like rec (slot * N + splat).
 int launch_blend_bwd_batch(const BatchSlot* slots, const BatchHeader* hdr, const TreeParams& tp, const uint2* ranges,

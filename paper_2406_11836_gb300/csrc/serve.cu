@@ -140,8 +140,8 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
         b.open_prefix = (uint32_t*)take(4 * (size_t)l.prefix_cap);
         b.open_sat = (uint32_t*)take(4 * (size_t)l.sat_cap);
         l.slots2 = (BatchSlot*)take(sizeof(BatchSlot) * kMaxSlots);
-        l.open_list = (uint32_t*)take(4 * (size_t)tiles_cap);
     }
+    l.one = (unsigned long long*)take(8);
     b.ranges = (uint2*)take(sizeof(uint2) * tiles_cap * K);
     b.ikey = (uint32_t*)take(4 * inst_cap);
     b.ival = (uint32_t*)take(4 * inst_cap);
@@ -155,6 +155,27 @@ size_t lane_layout(char* base, int64_t N, int slots, int64_t tiles_cap, int K, i
     return off;
 }
 
+// A per-request blend launch during the capture of a lane's graph, with arguments that do
+// nothing (each batch sets its own before the graph runs), and its graph node.
+int capture_blend_node(const LaneBufs& l, const TreeParams& tp, cudaStream_t s, cudaGraphNode_t* node) {
+    BlendNodeArgs a;
+    memset(&a, 0, sizeof a);
+    a.tp = tp;
+    a.skip = l.one;
+    int rc = launch_blend_node(a, 1, s);
+    if (rc) return rc;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    RGS_CUDA_TRY(cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive || nd != 1 || !deps) {
+        set_error("serve: the per-request blend is not the capture's last node");
+        return RGS_ECUDA;
+    }
+    *node = deps[0];
+    return RGS_OK;
+}
+
 int ceil_log2(int64_t x) {
     int b = 0;
     while (((int64_t)1 << b) < x) ++b;
@@ -166,11 +187,15 @@ int ceil_log2(int64_t x) {
 int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, int slots, int64_t tiles_cap,
                   const LaneBufs& l, const BatchSlot* slots_host, const BatchHeader* hdr_host,
                   unsigned long long* status_host, cudaStream_t s, bool record_ends, const uint32_t** ival_out,
-                  const BatchSlot* slots2_host) {
+                  const BatchSlot* slots2_host, BlendNodes* nodes) {
     const int64_t N = g.n, P = N * slots;
     const bool grouped = slots2_host != nullptr;
-    if (grouped && (!l.slots2 || !l.b.cnt_bin || record_ends)) {
-        set_error("serve: binning in groups needs a lane laid out for it (and no recorded run ends)");
+    if (grouped && (!l.slots2 || !l.b.cnt_bin || record_ends || !nodes)) {
+        set_error("serve: binning in groups needs a lane laid out for it, per-request blends, no recorded run ends");
+        return RGS_EINVAL;
+    }
+    if (nodes && (record_ends || slots > kMaxSlots)) {
+        set_error("serve: per-request blends record no run ends");
         return RGS_EINVAL;
     }
     RasterBuffers b = l.b;
@@ -229,18 +254,19 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
     const uint32_t* ival = alt ? b.ival_alt : b.ival;
     if (ival_out) *ival_out = ival;
     if ((rc = launch_ranges_dev(keys, &c[4], b.inst_cap, b.ranges, s))) return rc;
-    BatchGroup g1;
-    g1.state = b.state;
-    g1.open = b.open;
-    if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s, record_ends,
-                                 grouped ? &g1 : nullptr)))
+    if (nodes) {
+        nodes->ival = ival;
+        for (int q = 0; q < slots; ++q)
+            if ((rc = capture_blend_node(l, tp, s, &nodes->g1[q]))) return rc;
+    } else if ((rc = launch_blend_batch(l.slots, l.hdr, tp, b.ranges, ival, b.rec, c, s, record_ends))) {
         return rc;
+    }
     if (grouped) {
         // the second group: ranks [bin_lo, K) of the slots2 views in the tiles left open,
         // counted per visible pair in depth order (into vis_pos), emitted after the first
         // group's instances, sorted there (same key bits: the same buffer parity), blended
-        // over the list of open tiles
-        if ((rc = launch_open_tables_batch(l.slots2, l.hdr, b.open, l.open_list, cb + 3, s))) return rc;
+        // request by request in the open tiles
+        if ((rc = launch_open_tables_batch(l.slots2, l.hdr, b.open, s))) return rc;
         if ((rc = launch_recount_batch(l.slots2, l.hdr, tp, b, sorted_ids, P, N, c, b.vis_pos, cb + 2, cb + 1, s)))
             return rc;
         check_group2_kernel<<<1, 1, 0, s>>>(c, b.inst_cap);
@@ -257,13 +283,8 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
             return RGS_EINVAL;
         }
         if ((rc = launch_ranges_dev(keys, cb + 1, b.inst_cap, b.ranges, s, &c[4]))) return rc;
-        BatchGroup g2;
-        g2.state = b.state;
-        g2.open = b.open;
-        g2.list = l.open_list;
-        g2.n_list = cb + 3;
-        g2.queue = cb + 4;
-        if ((rc = launch_blend_batch(l.slots2, l.hdr, tp, b.ranges, ival, b.rec, c, s, false, &g2))) return rc;
+        for (int q = 0; q < slots; ++q)
+            if ((rc = capture_blend_node(l, tp, s, &nodes->g2[q]))) return rc;
     }
     RGS_CUDA_TRY(cudaMemcpyAsync(status_host, c, 8 * kBatchCounters, cudaMemcpyDeviceToHost, s));
     return RGS_OK;
@@ -297,6 +318,8 @@ struct Lane {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphExec_t exec2 = nullptr;     // the batch with binning in two groups of ranks
+    cudaGraph_t graph[2] = {nullptr, nullptr};   // kept: their per-request blend nodes
+    BlendNodes nodes[2];
     BatchSlot* slots2_host = nullptr;    // pinned: the second group's slot table
     cudaEvent_t done_ev = nullptr;
     char* mem = nullptr;
@@ -435,7 +458,38 @@ int launch_lane(rgs_server* S, Lane& ln, std::vector<Request*>& batch) {
     }
     for (int s = h.S; s <= kMaxSlots; ++s) h.tile_base[s] = base;
     h.total_tiles = base;
-    RGS_CUDA_TRY(cudaGraphLaunch(any_grouped ? ln.exec2 : ln.exec, ln.stream));
+    // each request's blend launches: its view, tiles and group; the unused slots' do nothing
+    const BlendNodes& nd = ln.nodes[any_grouped ? 1 : 0];
+    cudaGraphExec_t ex = any_grouped ? ln.exec2 : ln.exec;
+    const LaneBufs& l = ln.bufs;
+    for (int s = 0; s < S->cfg.max_slots; ++s) {
+        for (int grp2 = 0; grp2 < (any_grouped ? 2 : 1); ++grp2) {
+            const BatchSlot& sl = grp2 ? ln.slots2_host[s] : ln.slots_host[s];
+            BlendNodeArgs a;
+            memset(&a, 0, sizeof a);
+            a.tp = S->tp;
+            a.skip = l.one;
+            unsigned grid = 1;
+            if (s < h.S && (grp2 == 0 || sl.vp.bin_lo < S->K)) {
+                a.vp = sl.vp;
+                a.ival = nd.ival;
+                a.rec = l.b.rec;
+                a.ranges = l.b.ranges + (size_t)sl.tile_base * S->K;
+                a.image = sl.image;
+                a.r_begin = sl.vp.bin_lo;
+                a.r_end = sl.vp.bin_hi;
+                if (sl.vp.bin_lo > 0 || sl.vp.bin_hi < S->K) {   // a grouped request: its state
+                    a.state = l.b.state + (size_t)sl.state_base * kTilePixels;
+                    a.open = l.b.open + sl.tile_base;
+                }
+                a.skip = l.counters + 2;   // the overflow flag
+                grid = (unsigned)((int64_t)sl.vp.tiles_x * sl.vp.tiles_y);
+            }
+            int rc = set_blend_node(ex, grp2 ? nd.g2[s] : nd.g1[s], a, grid);
+            if (rc) return rc;
+        }
+    }
+    RGS_CUDA_TRY(cudaGraphLaunch(ex, ln.stream));
     RGS_CUDA_TRY(cudaEventRecord(ln.done_ev, ln.stream));
     ln.inflight = batch;
     ln.busy = true;
@@ -625,6 +679,8 @@ void worker_main(rgs_server* S) {
 void free_lane(Lane& ln) {
     if (ln.exec) cudaGraphExecDestroy(ln.exec);
     if (ln.exec2) cudaGraphExecDestroy(ln.exec2);
+    for (cudaGraph_t gr : ln.graph)
+        if (gr) cudaGraphDestroy(gr);
     if (ln.slots2_host) cudaFreeHost(ln.slots2_host);
     if (ln.done_ev) cudaEventDestroy(ln.done_ev);
     if (ln.stream) cudaStreamDestroy(ln.stream);
@@ -820,13 +876,18 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
             memset(ln.hdr_host, 0, sizeof(BatchHeader));
             // capture the lane's batch pipeline once (and once binning in two groups)
             if ((rc = sort_prepare())) return fail(rc);
+            if (cudaMemset(ln.bufs.one, 0xFF, 8) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("serve_create: cannot initialise a lane");
+                return fail(RGS_ECUDA);
+            }
             for (int v = 0; v < (gl ? 2 : 1); ++v) {
                 cudaGraph_t graph = nullptr;
                 RGS_CUDA_TRY(cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
                 prof_suppress(true);
                 rc = enqueue_batch(S->g, S->tp, S->K, S->L, cfg->max_slots, S->tiles_cap, ln.bufs, ln.slots_host,
                                    ln.hdr_host, ln.status_host, ln.stream, false, nullptr,
-                                   v ? ln.slots2_host : nullptr);
+                                   v ? ln.slots2_host : nullptr, &ln.nodes[v]);
                 prof_suppress(false);
                 const cudaError_t ec = cudaStreamEndCapture(ln.stream, &graph);
                 if (rc || ec != cudaSuccess) {
@@ -834,8 +895,8 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
                     if (!rc) set_error("serve_create: stream capture failed: %s", cudaGetErrorString(ec));
                     return fail(rc ? rc : RGS_ECUDA);
                 }
+                ln.graph[v] = graph;   // its blend nodes take each batch's arguments
                 const cudaError_t ei = cudaGraphInstantiate(v ? &ln.exec2 : &ln.exec, graph, 0);
-                cudaGraphDestroy(graph);
                 if (ei != cudaSuccess) {
                     set_error("serve_create: graph instantiation failed: %s", cudaGetErrorString(ei));
                     return fail(RGS_ECUDA);
