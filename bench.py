@@ -273,36 +273,36 @@ def _traffic_table():
 
 
 # --------------------------------------------------------------------------- serving
-def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400, device=None, lanes=4, max_slots=4):
-    warm = min(warm, requests // 4)
-    burst = min(burst, requests)
+def run_serving(requests=3000, warm=200, rates=(200.0, 300.0), budget_gb=32, burst=400, device=None, lanes=4,
+                max_slots=4):
     """Serving on the 5M-splat city scene (K=8): a seeded Poisson stream of mixed-resolution
-    requests against the batched server and the plain one-request-per-launch server.
-    Latency = host time from submit to completion; Mpix/s = pixels of all requests over the
-    wall time from the first arrival to the last completion.  The saturation figure submits
-    `burst` requests at once."""
+    requests against the batched server and the plain one-request-per-launch server, at each
+    offered rate of `rates` (the same requests, arrival gaps scaled; the first rate is the
+    headline).  Latency = host time from submit to completion; Mpix/s = pixels of all
+    requests over the wall time from the first arrival to the last completion.  The
+    saturation figure submits `burst` requests at once."""
     import torch
     from paper_2406_11836_gb300 import rgs
     from paper_2406_11836_gb300 import workloads as W
+    warm = min(warm, requests // 4)
+    burst = min(burst, requests)
     wl = W.serving_5m(device=device)
     g = rgs.scene_c(wl.scene)
     kd = rgs.kd_partition(wl.scene, wl.depth_L)
-    stream = W.request_stream(requests, rate_hz=rate_hz, seed=7)
+    streams = {rate: W.request_stream(requests, rate_hz=rate, seed=7) for rate in rates}
     ring = 32   # output buffers per resolution, reused round robin
     outs = {(w, h): [torch.empty(3, h, w, device=device) for _ in range(ring)] for (w, h) in W.RESOLUTIONS}
     res = {}
     # batched: `lanes` concurrent lanes of up to `max_slots` requests per batch; lanes_only: the
-    # same lanes with one request per batch (concurrency without batching); plain: one request
-    # at a time through the render entry point
+    # same lanes with one request per batch (concurrency without batching; headline rate only);
+    # plain: one request at a time through the render entry point
     # every server is sized for the stream's largest request (3840x2160)
     big = dict(max_width=max(w for w, _ in W.RESOLUTIONS), max_height=max(h for _, h in W.RESOLUTIONS))
     modes = {"batched": dict(max_slots=max_slots, lanes=lanes, plain=False, **big),
              "lanes_only": dict(max_slots=1, lanes=lanes, plain=False, **big),
              "plain": dict(max_slots=max_slots, lanes=lanes, plain=True, **big)}
-    for mode, kw in modes.items():
-        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, keepalive=wl.scene, **kw)
-        for (w, h), bufs in outs.items():     # warm every resolution once
-            srv.wait(srv.submit(W.look_at((6.0, 6.0, 5.0), (0, 0, 0), w, h), bufs[0]))
+
+    def measure(srv, stream):
         tickets = []
         t0 = time.perf_counter()
         for k, (ta, cam) in enumerate(stream):
@@ -311,11 +311,35 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400,
             tickets.append((srv.submit(cam, outs[(cam.width, cam.height)][k % ring]), cam.width * cam.height))
         lats = [srv.wait(t, timeout_s=600) for t, _ in tickets]
         span = time.perf_counter() - t0
-        st = srv.stats()
         L = np.array(lats[warm:])
-        pix = sum(px for _, px in tickets)
+        by_res = {}
+        for (w, h) in W.RESOLUTIONS:
+            Lr = np.array([lt for lt, (_, c) in zip(lats[warm:], stream[warm:]) if (c.width, c.height) == (w, h)])
+            if len(Lr):
+                by_res[f"{w}x{h}"] = {"p50_ms": float(np.percentile(Lr, 50)), "p99_ms": float(np.percentile(Lr, 99)),
+                                      "n": int(len(Lr))}
+        return {"p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+                "mean_ms": float(L.mean()), "mpix_s": sum(px for _, px in tickets) / span / 1e6,
+                "requests_measured": int(len(L)), "by_resolution": by_res}
+
+    for mode, kw in modes.items():
+        srv = rgs.Server(kd, g, rgs.default_opts(), int(budget_gb) << 30, keepalive=wl.scene, **kw)
+        for (w, h), bufs in outs.items():     # warm every resolution once
+            srv.wait(srv.submit(W.look_at((6.0, 6.0, 5.0), (0, 0, 0), w, h), bufs[0]))
+        for ri, rate in enumerate(rates):
+            if ri > 0 and mode == "lanes_only":
+                continue
+            st0 = srv.stats()
+            entry = measure(srv, streams[rate])
+            st = srv.stats()
+            entry["mean_batch"] = (st["completed"] - st0["completed"]) / max(st["batches"] - st0["batches"], 1)
+            if ri == 0:
+                res[mode] = entry
+            else:
+                res.setdefault("rates", {}).setdefault(f"{rate:g}", {})[mode] = entry
         # saturation: everything queued at once
-        sub = stream[:burst]
+        st = srv.stats()
+        sub = streams[rates[0]][:burst]
         t1 = time.perf_counter()
         bt = [srv.submit(cam, outs[(cam.width, cam.height)][k % ring]) for k, (_, cam) in enumerate(sub)]
         for t in bt:
@@ -324,17 +348,17 @@ def run_serving(requests=2200, warm=200, rate_hz=200.0, budget_gb=32, burst=400,
         st2 = srv.stats()
         srv.close()
         sat_batches = max(st2["batches"] - st["batches"], 1)
-        res[mode] = {"p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
-                     "mean_ms": float(L.mean()), "mpix_s": pix / span / 1e6, "saturation_mpix_s": sat,
-                     "requests_measured": int(len(L)), "mean_batch": st["mean_batch"],
-                     "saturation_mean_batch": (st2["completed"] - st["completed"]) / sat_batches,
-                     "requeued": st2["requeued"], "max_slots": kw["max_slots"], "lanes": 1 if kw["plain"] else lanes}
+        res[mode].update({"saturation_mpix_s": sat,
+                          "saturation_mean_batch": (st2["completed"] - st["completed"]) / sat_batches,
+                          "requeued": st2["requeued"], "max_slots": kw["max_slots"],
+                          "lanes": 1 if kw["plain"] else lanes})
     torch.cuda.synchronize()
     res["config"] = {"workload": "serve-5M-K8", "splats": int(g.n), "subsets": kd.K,
-                     "arrivals": f"Poisson {rate_hz:g} req/s, {requests} requests ({warm} warm-up)",
-                     "resolutions": [f"{w}x{h}" for w, h in W.RESOLUTIONS], "budget_gb": budget_gb,
-                     "max_slots": max_slots, "lanes": lanes,
-                     "offered_mpix_s": rate_hz * float(np.mean([w * h for w, h in W.RESOLUTIONS])) / 1e6}
+                     "arrivals": f"Poisson, {requests} requests ({warm} warm-up) at each rate",
+                     "rates_hz": list(rates), "resolutions": [f"{w}x{h}" for w, h in W.RESOLUTIONS],
+                     "budget_gb": budget_gb, "max_slots": max_slots, "lanes": lanes,
+                     "offered_mpix_s": {f"{r:g}": r * float(np.mean([w * h for w, h in W.RESOLUTIONS])) / 1e6
+                                        for r in rates}}
     return res
 
 
@@ -792,7 +816,7 @@ def main():
                     help="skip the batched multi-view training comparison (object 1M workload)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the exact-partials step and the recomputing backward comparisons")
-    ap.add_argument("--serve-requests", type=int, default=2200, help="requests of the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=3000, help="requests of the serving stream at each rate")
     ap.add_argument("--profile-only", action="store_true",
                     help="warm-up and timed steps only (no counter replay, end-to-end loop, CPU baseline or "
                          "serving): for launch lists under a profiler; its numbers are not bench values")

@@ -388,6 +388,9 @@ typedef struct {
                                    instances per visible splat ... */
     float group_min_instances;  /* ... and at least this many tile instances; with both 0, or
                                    with group_binning 2, every request is grouped */
+    int64_t batch_max_pixels;   /* batched mode: a batch takes more requests only while their
+                                   pixels stay within this (the first is always taken), so that
+                                   small requests do not wait behind a large one; 0: no limit */
 } rgs_serve_config;
 
 typedef struct {
@@ -399,7 +402,8 @@ typedef struct {
 } rgs_serve_stats;
 
 /* Defaults: 8 GiB, 8 slots, 2 lanes, batched, 4096x4096, 65536 queued, 16 instances
- * per pixel, groups from 12 instances per visible splat and 2^24 instances. */
+ * per pixel, groups from 12 instances per visible splat and 2^24 instances, batches of at
+ * most 2^21 pixels. */
 void rgs_serve_default_config(rgs_serve_config* cfg);
 
 /* Device bytes one lane of a batched server with this configuration takes for a capacity

@@ -389,14 +389,18 @@ int64_t est_instances(const rgs_server* S, const Request* r) {
 
 // Pops the next batch for a lane (caller holds S->mu).
 void form_batch(rgs_server* S, std::vector<Request*>& batch) {
-    int64_t tiles = 0, inst = 0;
+    int64_t tiles = 0, inst = 0, pix = 0;
+    const int64_t max_pix = S->cfg.batch_max_pixels;
     while (!S->queue.empty() && (int)batch.size() < S->cfg.max_slots) {
         Request* r = S->queue.front();
         const int64_t e = est_instances(S, r);
-        if (!batch.empty() && (tiles + r->tiles > S->tiles_cap || inst + e > S->inst_cap)) break;
+        if (!batch.empty() && (tiles + r->tiles > S->tiles_cap || inst + e > S->inst_cap ||
+                               (max_pix > 0 && pix + r->pixels > max_pix)))
+            break;
         S->queue.pop_front();
         tiles += r->tiles;
         inst += e;
+        pix += r->pixels;
         batch.push_back(r);
     }
 }
@@ -721,6 +725,7 @@ void rgs_serve_default_config(rgs_serve_config* cfg) {
     cfg->inst_per_pixel = 16.f;
     cfg->group_per_splat = (float)kGroupInstancesPerSplat;
     cfg->group_min_instances = (float)kGroupMinInstances;
+    cfg->batch_max_pixels = (int64_t)1 << 21;
 }
 
 }  // extern "C"
@@ -776,9 +781,9 @@ int rgs_serve_create_ex(const rgs_kd* kd, const rgs_gaussians* g, const rgs_rend
     if (cfg->max_slots < 1 || cfg->max_slots > kMaxSlots || cfg->lanes < 1 || cfg->lanes > 4 ||
         cfg->max_width < 1 || cfg->max_width > 16384 || cfg->max_height < 1 || cfg->max_height > 16384 ||
         cfg->max_queue < 1 || !(cfg->inst_per_pixel > 0.f) || !(cfg->group_per_splat >= 0.f) ||
-        !(cfg->group_min_instances >= 0.f)) {
+        !(cfg->group_min_instances >= 0.f) || cfg->batch_max_pixels < 0) {
         set_error("serve_create: need max_slots in [1,%d], lanes in [1,4], max size in [1,16384], max_queue >= 1, "
-                  "inst_per_pixel > 0, group thresholds >= 0", kMaxSlots);
+                  "inst_per_pixel > 0, group thresholds and batch_max_pixels >= 0", kMaxSlots);
         return RGS_EINVAL;
     }
     rgs_server* S = new (std::nothrow) rgs_server();

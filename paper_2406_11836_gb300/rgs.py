@@ -49,7 +49,7 @@ class RenderOpts(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", c_size_t), ("max_slots", c_int), ("lanes", c_int), ("plain", c_int),
                 ("max_width", c_int), ("max_height", c_int), ("max_queue", c_int), ("inst_per_pixel", c_float),
-                ("group_per_splat", c_float), ("group_min_instances", c_float)]
+                ("group_per_splat", c_float), ("group_min_instances", c_float), ("batch_max_pixels", c_int64)]
 
 
 class ServeStats(ctypes.Structure):
@@ -476,7 +476,7 @@ def profile_read(reset: bool = True) -> dict:
 # --------------------------------------------------------------------------- serving
 def serve_config(mem_budget_bytes=8 << 30, max_slots=8, lanes=2, plain=False, max_width=4096, max_height=4096,
                  max_queue=65536, inst_per_pixel=16.0, group_per_splat=12.0,
-                 group_min_instances=float(1 << 24)) -> ServeConfig:
+                 group_min_instances=float(1 << 24), batch_max_pixels=1 << 21) -> ServeConfig:
     cfg = ServeConfig()
     lib().rgs_serve_default_config(ctypes.byref(cfg))
     cfg.mem_budget_bytes = int(mem_budget_bytes)
@@ -485,6 +485,7 @@ def serve_config(mem_budget_bytes=8 << 30, max_slots=8, lanes=2, plain=False, ma
     cfg.inst_per_pixel = float(inst_per_pixel)
     cfg.group_per_splat = float(group_per_splat)
     cfg.group_min_instances = float(group_min_instances)
+    cfg.batch_max_pixels = int(batch_max_pixels)
     return cfg
 
 
@@ -504,10 +505,10 @@ class Server:
     def __init__(self, kd: KD, g: Gaussians, opts: RenderOpts, mem_budget_bytes: int, max_slots: int = 8,
                  lanes: int = 2, plain: bool = False, max_width: int = 4096, max_height: int = 4096,
                  max_queue: int = 65536, inst_per_pixel: float = 16.0, group_per_splat: float = 12.0,
-                 group_min_instances: float = float(1 << 24), keepalive=None):
+                 group_min_instances: float = float(1 << 24), batch_max_pixels: int = 1 << 21, keepalive=None):
         L = lib()
         cfg = serve_config(mem_budget_bytes, max_slots, lanes, plain, max_width, max_height, max_queue, inst_per_pixel,
-                           group_per_splat, group_min_instances)
+                           group_per_splat, group_min_instances, batch_max_pixels)
         self._keep = (kd, g, opts, keepalive)
         self._g, self._opts = g, opts
         h = c_void_p()
