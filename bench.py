@@ -61,10 +61,13 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t_end = time.perf_counter() + 3.0      # sampling is running before the timed region starts
+            while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
@@ -81,7 +84,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         sm, mx, reasons = [], None, set()
-        for ln in self.lines:
+        for ln in self.lines[1:] if len(self.lines) > 1 else self.lines:   # the first predates the region
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue

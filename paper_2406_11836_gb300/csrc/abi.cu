@@ -31,6 +31,21 @@ void set_error(const char* fmt, ...) {
 }
 void set_required_workspace(size_t bytes) { g_required = bytes; }
 
+namespace {
+constexpr int kMaxSmCache = 64;
+std::atomic<int> g_sms[kMaxSmCache];   // 0: not queried yet
+}  // namespace
+
+int sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int n = dev >= 0 && dev < kMaxSmCache ? g_sms[dev].load(std::memory_order_relaxed) : 0;
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev >= 0 && dev < kMaxSmCache) g_sms[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 // ------------------------------------------------------------------ profiler
 namespace {
 const char* kStageNames[ST_COUNT] = {"project", "compact", "depth_sort", "offsets", "emit", "instance_sort", "ranges",

@@ -114,9 +114,7 @@ int launch_adam(float* p, float* g, float* m, float* v, int64_t n, const int64_t
     segs.head_lr = head_lr;
     for (int q = 0; q <= nseg; ++q) segs.off[q] = seg_off[q];
     for (int q = 0; q < nseg; ++q) segs.lr[q] = seg_lr_h[q];
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     int64_t want = (n / 4 + 255) / 256;
     int64_t cap = (int64_t)sms * 8;
     unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));

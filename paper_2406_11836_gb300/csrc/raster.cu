@@ -1793,7 +1793,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                     // the pair with the same predicate (a pair that fails gets sigma = 0 and
                     // zero gradients); two scalars per (pixel, entry) go to shared memory
                     bool any = false;
-                    for (int t = s0; t < s1; ++t) {
+                    auto pair = [&](int t, int e) {
                         if (kCount && lane == 0) ++n_iter;
                         const int j = wl[t];
                         const float4 A = srec[j].a;
@@ -1804,30 +1804,42 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                         const float d2 = fmaf(u1, u1, u2 * u2);
                         const float G = ex2_approx(d2 * kNegHalfLog2e);
                         const float raw = B.y * G;
-                        bool ok, grad;
+                        bool ok;
                         float sig;
+                        const float w_T = T;
+                        const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
+                        float h;
                         if (B.w == kInfF) {   // warp-uniform: the Mahalanobis test alone, no clamp
                             ok = d2 <= B.z;
-                            grad = ok;
                             sig = ok ? raw : 0.f;
+                            const float w = sig * w_T;
+                            acc = fmaf(w, grgb, acc);
+                            // a failing pair has sigma = 0, so h = 0 with no select
+                            h = sig * (w_T * grgb - __fdividef(q - acc, 1.f - sig));
+                            sh_w[warp][lane * kBwdSubPad + e] = w;
                         } else {
                             ok = pair_passes(B, Cc, dx, dy, d2, splane[j], smask[j], vp, lp, Xc, Yc);
-                            grad = ok && raw < vp.alpha_max;
+                            const bool grad = ok && raw < vp.alpha_max;
                             sig = ok ? fminf(raw, vp.alpha_max) : 0.f;
+                            const float w = sig * w_T;
+                            acc = fmaf(w, grgb, acc);
+                            const float dsig = w_T * grgb - __fdividef(q - acc, 1.f - sig);
+                            h = grad ? sig * dsig : 0.f;   // sigma dL/dsigma
+                            sh_w[warp][lane * kBwdSubPad + e] = w;
                         }
                         if (kCount && !frozen) {
                             ++n_eval;
                             n_contrib += ok;
                         }
-                        const float w = sig * T;
-                        const float grgb = gC0 * Cc.x + gC1 * Cc.y + gC2 * Cc.z;
-                        acc = fmaf(w, grgb, acc);
-                        const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
-                        const float h = grad ? sig * dsig : 0.f;   // sigma dL/dsigma
-                        sh_h[warp][lane * kBwdSubPad + (t - s0)] = h;
-                        sh_w[warp][lane * kBwdSubPad + (t - s0)] = w;
+                        sh_h[warp][lane * kBwdSubPad + e] = h;
                         any |= ok;   // a pair that fails has h = w = 0
                         T = fmaf(-sig, T, T);
+                    };
+                    if (s1 - s0 == kBwdSub) {   // a full stretch: fixed shared-memory offsets
+#pragma unroll 4
+                        for (int e = 0; e < kBwdSub; ++e) pair(s0 + e, e);
+                    } else {
+                        for (int t = s0; t < s1; ++t) pair(t, t - s0);
                     }
                     if (!__any_sync(0xffffffffu, any)) continue;   // a frozen or empty stretch
                     __syncwarp();
@@ -2028,7 +2040,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
                 int64_t n_vis, cudaStream_t s) {
     if (n_vis <= 0) return RGS_OK;
     const int64_t want = (n_vis + 255) / 256;      // one warp per 32 splats
-    const int64_t cap = 152 * 16;                  // grid-stride beyond: amortises the tree copy
+    const int64_t cap = (int64_t)sm_count() * 16;                  // grid-stride beyond: amortises the tree copy
     unsigned grid = (unsigned)(want < cap ? want : cap);
     // work counters (zeroed with the others at the start of the list build): [4], [5] the
     // emission queues, [8], [9] the splats each launch deferred, [12] the items the count kept
@@ -2039,7 +2051,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
         q.cap = b.units ? b.unit_cap : 0u;
         return q;
     };
-    const unsigned lgrid = 152 * 8;
+    const unsigned lgrid = (unsigned)sm_count() * 8;
     const uint32_t* item_at = b.items ? b.item_at : nullptr;
     const EmitQueues q0 = queues_of(0), q1 = queues_of(1);
     // foot reading: straddlers are clipped over the foot's depth interval (side array)
@@ -2056,7 +2068,7 @@ int launch_emit(const ViewParams& vp, const TreeParams& tp, const RasterBuffers&
     }
     // 2. the kept items
     if (item_at) {
-        emit_items_kernel<<<152 * 8, 256, 0, s>>>(vp, b.items, b.item_first, b.item_ctr, b.item_cap, b.ibase,
+        emit_items_kernel<<<(unsigned)sm_count() * 8, 256, 0, s>>>(vp, b.items, b.item_first, b.item_ctr, b.item_cap, b.ibase,
                                                   b.rec, b.cull, b.cull_chunk, b.ikey, b.ival);
         RGS_CUDA_LAUNCH_CHECK();
     }
@@ -2085,8 +2097,8 @@ int launch_ranges(const uint32_t* keys, int64_t n, uint2* ranges, int64_t n_rang
                   bool clear) {
     if (clear) RGS_CUDA_TRY(cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s));
     if (n <= 0) return RGS_OK;
-    const int64_t want = (n + 1023) / 1024;
-    ranges_kernel<<<(unsigned)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(keys, n, ((uintptr_t)keys & 15) == 0,
+    const int64_t want = (n + 1023) / 1024, cap = (int64_t)sm_count() * 8;
+    ranges_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(keys, n, ((uintptr_t)keys & 15) == 0,
                                                                             ranges, first);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
@@ -2105,7 +2117,8 @@ int launch_recount(const ViewParams& vp, const TreeParams& tp, const RasterBuffe
                    int64_t n_vis, uint32_t* cnt_out, cudaStream_t s) {
     if (n_vis <= 0) return RGS_OK;
     const int64_t want = (n_vis + 255) / 256;
-    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    const int64_t cap = (int64_t)sm_count() * 16;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
     recount_kernel<false><<<grid, 256, 0, s>>>(vp, nullptr, nullptr, 0, tp, sorted_ids, n_vis, nullptr, nullptr,
                                                b.rect, b.mask, b.rec, b.item_at, b.items, b.items ? b.item_cap : 0u,
                                                cnt_out, b.counters + 4, b.counters + 15);
@@ -2186,7 +2199,8 @@ int launch_foot_order(const ViewParams& vp, const RasterBuffers& b, int64_t I, c
         return RGS_OK;
     }
     const int64_t want = (I + 255) / 256;
-    const unsigned grid = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    const int64_t cap = (int64_t)sm_count() * 16;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
     foot_keys_kernel<<<grid, 256, 0, s>>>(vp, b.ikey, b.ival, I, b.rec, b.fkey, b.fidx);
     RGS_CUDA_LAUNCH_CHECK();
     // LSD: the bound first, then stably the (tile, subset) key
@@ -2220,16 +2234,16 @@ int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tree
                       const uint32_t* sorted_ids, int64_t n_cap, int64_t N, unsigned long long* counters,
                       cudaStream_t s, const unsigned long long* inst_base, bool open_tables) {
     const uint32_t* item_at = b.items ? b.item_at : nullptr;
-    emit_batch_kernel<0><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
+    emit_batch_kernel<0><<<(unsigned)sm_count() * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
                                                  b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase, inst_base);
     RGS_CUDA_LAUNCH_CHECK();
     if (tp.L > 0) {
-        emit_batch_kernel<1><<<152 * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
+        emit_batch_kernel<1><<<(unsigned)sm_count() * 8, 256, 0, s>>>(slots, hdr, tp, sorted_ids, n_cap, N, counters, b.ioff, b.rect,
                                                      b.mask, b.rec, b.ikey, b.ival, item_at, b.ibase, inst_base);
         RGS_CUDA_LAUNCH_CHECK();
     }
     if (item_at) {
-        emit_items_batch_kernel<<<152 * 8, 256, 0, s>>>(slots, hdr, b.items, b.item_ctr, b.item_cap, b.ibase, N,
+        emit_items_batch_kernel<<<(unsigned)sm_count() * 8, 256, 0, s>>>(slots, hdr, b.items, b.item_ctr, b.item_cap, b.ibase, N,
                                                         counters, b.ikey, b.ival, inst_base, open_tables,
                                                         open_tables ? counters + kBatchBinCounter + 1 : nullptr);
         RGS_CUDA_LAUNCH_CHECK();
@@ -2239,7 +2253,7 @@ int launch_emit_batch(const BatchSlot* slots, const BatchHeader* hdr, const Tree
 
 int launch_ranges_dev(const uint32_t* keys, const unsigned long long* n_dev, int64_t cap, uint2* ranges,
                       cudaStream_t s, const unsigned long long* base_dev) {
-    ranges_dev_kernel<<<152 * 8, 256, 0, s>>>(keys, n_dev, cap, ranges, base_dev);
+    ranges_dev_kernel<<<(unsigned)sm_count() * 8, 256, 0, s>>>(keys, n_dev, cap, ranges, base_dev);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }
@@ -2269,7 +2283,7 @@ int launch_recount_batch(const BatchSlot* slots, const BatchHeader* hdr, const T
                          uint32_t* cnt_out, unsigned long long* queue, unsigned long long* total, cudaStream_t s) {
     ViewParams vp_unused;
     memset(&vp_unused, 0, sizeof vp_unused);
-    recount_kernel<true><<<152 * 8, 256, 0, s>>>(vp_unused, slots, hdr, N, tp, sorted_ids, n_cap, counters + 1,
+    recount_kernel<true><<<(unsigned)sm_count() * 8, 256, 0, s>>>(vp_unused, slots, hdr, N, tp, sorted_ids, n_cap, counters + 1,
                                                  counters + 2, b.rect, b.mask, b.rec, b.item_at, b.items,
                                                  b.items ? b.item_cap : 0u, cnt_out, queue, total);
     RGS_CUDA_LAUNCH_CHECK();

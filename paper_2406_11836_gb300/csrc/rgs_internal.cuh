@@ -175,6 +175,9 @@ void set_required_workspace(size_t bytes);
 // A value never seen before in this process (never 0): the stamp a forward writes into its
 // workspace so that a backward can tell whether the lists there are still its own.
 unsigned long long next_nonce();
+// Streaming multiprocessors of the current device (queried once per device, cached); grid
+// sizes of the grid-stride and persistent kernels are multiples of it.
+int sm_count();
 
 #define RGS_CUDA_TRY(expr)                                                                 \
     do {                                                                                   \

@@ -32,7 +32,7 @@ namespace {
 static_assert(sizeof(ViewParams) % 4 == 0, "view parameters are copied as 32-bit words");
 
 // ------------------------------------------------------------------ batch kernels
-constexpr int kGridStride = 152 * 8;   // blocks of the grid-stride passes
+inline unsigned grid_stride_blocks() { return (unsigned)sm_count() * 8; }   // the grid-stride passes
 
 __device__ __forceinline__ int64_t dev_count(const unsigned long long* n, int64_t cap) {
     const unsigned long long v = *n;
@@ -215,7 +215,7 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
     // compaction in (request, splat) order
     if ((rc = exclusive_scan_dev(b.cnt, b.vis_pos, &l.hdr->n_total, P, 1, nullptr, b.temp, b.temp_bytes, s)))
         return rc;
-    compact_batch_kernel<<<kGridStride, 256, 0, s>>>(b.cnt, b.vis_pos, b.dkey_lo, &l.hdr->n_total, P, b.skey, b.sid);
+    compact_batch_kernel<<<grid_stride_blocks(), 256, 0, s>>>(b.cnt, b.vis_pos, b.dkey_lo, &l.hdr->n_total, P, b.skey, b.sid);
     RGS_CUDA_LAUNCH_CHECK();
     // (request, depth, index) order: LSD passes on the low depth bits, the float bits of
     // z, then the request
@@ -230,11 +230,11 @@ int enqueue_batch(const rgs_gaussians& g, const TreeParams& tp, int K, int L, in
         return r;
     };
     if ((rc = sort(16))) return rc;
-    batch_key_kernel<<<kGridStride, 256, 0, s>>>(b.dkey, va, N, &c[1], P, ka);
+    batch_key_kernel<<<grid_stride_blocks(), 256, 0, s>>>(b.dkey, va, N, &c[1], P, ka);
     RGS_CUDA_LAUNCH_CHECK();
     if ((rc = sort(31))) return rc;
     if (slots > 1) {
-        batch_key_kernel<<<kGridStride, 256, 0, s>>>(nullptr, va, N, &c[1], P, ka);
+        batch_key_kernel<<<grid_stride_blocks(), 256, 0, s>>>(nullptr, va, N, &c[1], P, ka);
         RGS_CUDA_LAUNCH_CHECK();
         if ((rc = sort(ceil_log2(slots)))) return rc;
     }

@@ -511,7 +511,10 @@ int wide_pass(const uint32_t* ka, const uint32_t* va, uint32_t* kb, uint32_t* vb
 // be captured in a CUDA graph.  The grid is fixed: block c owns the c-th of kChunks
 // contiguous chunks (whole tiles) of [0, n) and walks its tiles in order, so scans and
 // sorts stay stable.
-constexpr int kChunks = 608;   // 152 SMs x 4 resident blocks
+// A fixed chunk count (it sizes the count tables and the graph's launches): four resident
+// blocks on each SM of a GB300 (152 SMs); on a device with other SM counts only the
+// balance of the chunks changes, not the result.
+constexpr int kChunks = 608;
 
 __device__ __forceinline__ void chunk_range(int64_t n, int64_t tile, int64_t& lo, int64_t& hi) {
     const int64_t tiles = (n + tile - 1) / tile;
