@@ -931,14 +931,30 @@ __device__ __forceinline__ void stage_for_subset(const float4* __restrict__ rec,
 
 // Compacts, per warp, the staged records whose mask has the warp's bit: wl[0..n) in
 // record order.  Returns n (uniform across the warp).
+// kHoist: all eight mask loads issued before the first ballot (faster in the forward; the
+// backward, with more live registers, keeps the loop).
+template <bool kHoist>
 __device__ __forceinline__ int warp_list(const uint32_t* smask, int nb, int warp, int lane, uint8_t* wl) {
     int n = 0;
     const unsigned lower = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < nb; c0 += 32) {
-        const bool hit = c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u);
-        const unsigned bits = __ballot_sync(0xffffffffu, hit);
-        if (hit) wl[n + __popc(bits & lower)] = (uint8_t)(c0 + lane);
-        n += __popc(bits);
+    if (kHoist) {
+        uint32_t m[kBlendThreads / 32];
+#pragma unroll
+        for (int c = 0; c < kBlendThreads / 32; ++c) m[c] = smask[c * 32 + lane];
+#pragma unroll
+        for (int c = 0; c < kBlendThreads / 32; ++c) {
+            const bool hit = c * 32 + lane < nb && ((m[c] >> warp) & 1u);
+            const unsigned bits = __ballot_sync(0xffffffffu, hit);
+            if (hit) wl[n + __popc(bits & lower)] = (uint8_t)(c * 32 + lane);
+            n += __popc(bits);
+        }
+    } else {
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const bool hit = c0 + lane < nb && ((smask[c0 + lane] >> warp) & 1u);
+            const unsigned bits = __ballot_sync(0xffffffffu, hit);
+            if (hit) wl[n + __popc(bits & lower)] = (uint8_t)(c0 + lane);
+            n += __popc(bits);
+        }
     }
     __syncwarp();
     return n;
@@ -1085,7 +1101,7 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 }
             }
             __syncthreads();
-            const int n = warp_list(smask, nb, warp, lane, wl);
+            const int n = warp_list<true>(smask, nb, warp, lane, wl);
             for (int t0 = 0; t0 < n; t0 += 32) {
                 if (!frozen && T < vp.eps_T) {
                     frozen = true;
@@ -1094,6 +1110,33 @@ __device__ __forceinline__ void blend_fwd_tile(const ViewParams& vp, const TreeP
                 }
                 if (__all_sync(0xffffffffu, frozen)) break;
                 const int t1 = min(n, t0 + 32);
+                // a group of simple records only (the Mahalanobis test alone, no clamp) takes
+                // the same arithmetic with no per-pair branch
+                bool all_simple = false;
+                if (!kCount) {
+                    const bool simple_l = t0 + lane >= t1 || srec[wl[t0 + lane]].b.w == kInfF;
+                    all_simple = __all_sync(0xffffffffu, simple_l);
+                }
+                if (all_simple) {
+                    #pragma unroll 2
+                    for (int t = t0; t < t1; ++t) {
+                        const int j = wl[t];
+                        const float4 A = srec[j].a;
+                        const float4 B = srec[j].b;
+                        const float4 Cc = srec[j].c;
+                        const float dx = pcx - A.x, dy = pcy - A.y;
+                        const float u1 = fmaf(A.z, dx, A.w * dy), u2 = B.x * dy;
+                        const float d2 = fmaf(u1, u1, u2 * u2);
+                        const float G = ex2_approx(d2 * kNegHalfLog2e);
+                        const float sig = d2 <= B.z ? B.y * G : 0.f;
+                        const float w = sig * T;
+                        C0 = fmaf(Cc.x, w, C0);
+                        C1 = fmaf(Cc.y, w, C1);
+                        C2 = fmaf(Cc.z, w, C2);
+                        T = fmaf(-sig, T, T);
+                    }
+                    continue;
+                }
                 #pragma unroll 2
                 for (int t = t0; t < t1; ++t) {
                     if (kCount && lane == 0) ++n_iter;
@@ -1532,7 +1575,7 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
                 sid[threadIdx.x] = id;
             }
             __syncthreads();
-            const int n = warp_list(smask, nb, warp, lane, wl);
+            const int n = warp_list<false>(smask, nb, warp, lane, wl);
             {
                 // block bounds of the warp's entries, then their suffix minimum, back to front
                 const float cap = sbound[nb - 1];
@@ -1775,7 +1818,7 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                 smask[threadIdx.x] = msk;
             }
             __syncthreads();
-            const int n = warp_list(smask, nb, warp, lane, wl);
+            const int n = warp_list<false>(smask, nb, warp, lane, wl);
             for (int t0 = 0; t0 < n; t0 += 32) {
                 if (!frozen && T < vp.eps_T) {
                     // frozen as in the forward: later pairs get sigma * T = 0, and q = acc
@@ -1792,7 +1835,6 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                     // phase 1, pixel by pixel: the forward's arithmetic, then the adjoint of
                     // the pair with the same predicate (a pair that fails gets sigma = 0 and
                     // zero gradients); two scalars per (pixel, entry) go to shared memory
-                    bool any = false;
                     auto pair = [&](int t, int e) {
                         if (kCount && lane == 0) ++n_iter;
                         const int j = wl[t];
@@ -1832,16 +1874,14 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                             n_contrib += ok;
                         }
                         sh_h[warp][lane * kBwdSubPad + e] = h;
-                        any |= ok;   // a pair that fails has h = w = 0
                         T = fmaf(-sig, T, T);
                     };
                     if (s1 - s0 == kBwdSub) {   // a full stretch: fixed shared-memory offsets
-#pragma unroll 4
+#pragma unroll 2
                         for (int e = 0; e < kBwdSub; ++e) pair(s0 + e, e);
                     } else {
                         for (int t = s0; t < s1; ++t) pair(t, t - s0);
                     }
-                    if (!__any_sync(0xffffffffu, any)) continue;   // a frozen or empty stretch
                     __syncwarp();
                     // phase 2, record by record: lane (half g of the warp's block, entry e)
                     // sums rows 2g and 2g + 1 (8 pixels each).  With delta = (dx, dy) from the
@@ -1889,13 +1929,9 @@ __device__ __forceinline__ void blend_bwd_tile(const ViewParams& vp, const TreeP
                         o[5] = __fdividef(Sh_all, B.y);
                     }
                     // the two halves of an entry: lanes e and e + 16
-                    bool nz = false;
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
-                        nz |= o[c] != 0.f;
-                    }
-                    if (g == 0 && s0 + e < s1 && nz) {
+                    for (int c = 0; c < 9; ++c) o[c] += __shfl_xor_sync(0xffffffffu, o[c], 16);
+                    if (g == 0 && s0 + e < s1) {
 #pragma unroll
                         for (int c = 0; c < 9; ++c) atomicAdd(&sacc[jr][c], o[c]);
                     }
