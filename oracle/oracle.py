@@ -256,7 +256,9 @@ def adjoint(scene, cam, dLdC, opts: Opts = Opts(), pix=None) -> dict:
     """Reverse mode of the flat form (Eq. 2 and the projection of Sec. 3.1), written by
     hand: given dL/dC [P,3] at the listed pixels, returns dL/d(means, log_scales, quats,
     opacity_logits, sh) in float64, and the per-splat 2D gradients g2d [N,9] =
-    (mean x, mean y, conic a, b, c, alpha, r, g, b)."""
+    (mean x, mean y, conic a, b, c, alpha, r, g, b).  With opts.foot the contributors and
+    their order are the foot reading's (Sec. 3.2, the perpendicular-foot reading of x_i);
+    the per-pair adjoint is the same, since that reading changes only discrete decisions."""
     s = _Scene(scene)
     p = _pix(cam, pix)
     g = np.ascontiguousarray(np.asarray(dLdC, np.float64).reshape(p.shape[0], 3))

@@ -27,7 +27,10 @@
  *                 of the perpendicular from u_i onto the ray, o + (d^T (u_i - o)) d for the
  *                 unit direction d, and the contributors of each ray are ordered by that
  *                 ray parameter (ties by splat index); the ball test is taken at the foot.
- *                 A comparison mode: the adjoint supports the depth-plane reading only.
+ *                 A comparison mode.  Its adjoint is the flat adjoint over that order: the
+ *                 reading moves only discrete decisions (which pairs pass, in what order),
+ *                 whose gradients are zero, and leaves each pair's weight alpha exp(-d^2/2)
+ *                 a function of the 2D Gaussian alone.
  *   o_l           per ray: the subspaces the ray crosses, ordered by the ray parameter at
  *                 which it enters them (slab test).  This is computed per ray here; the
  *                 CUDA path uses one near-child-first KD traversal per view instead.
@@ -902,7 +905,6 @@ int or_adjoint(int64_t n, const double* means, const double* log_scales, const d
                double* g2d_out) {
     cam_t cam; opt_t opt;
     read_cam(camv, &cam); read_opt(optv, &opt);
-    if (opt.foot) return -3;   /* the adjoint is of the depth-plane reading only */
     scene_t sc = make_scene(n, means, log_scales, quats, logits, sh, deg);
     proj_t* P = project_all(&sc, &cam, &opt);
     if (!P) return -2;

@@ -553,14 +553,15 @@ def _loss(sc, cam, w, opts):
     return float(np.sum(O.render(sc, cam, opts)["C"] * w))
 
 
-@pytest.mark.parametrize("deg", [0, 3])
-def test_adjoint_matches_finite_differences(deg):
+@pytest.mark.parametrize("deg,foot", [(0, False), (3, False), (3, True)])
+def test_adjoint_matches_finite_differences(deg, foot):
     """Hand-written reverse mode vs central differences of the FP64 forward for L = <w, C>,
     every parameter of every splat; perturbations that change the set of contributing
-    pairs are skipped."""
+    pairs or their order are skipped.  foot: the same under the perpendicular-foot reading
+    of x_i (its own contributors and per-ray order)."""
     sc0 = rand_scene(16, 30 + deg, extent=0.6, log_scale=(-2.0, 0.3), deg=deg).copy()
     cam = W.look_at((0.4, -2.5, 0.6), (0, 0, 0), 20, 16)
-    opts = O.Opts(bg=(0.1, 0.2, 0.3))
+    opts = O.Opts(bg=(0.1, 0.2, 0.3), foot=foot)
     w = np.random.default_rng(1).uniform(-1, 1, (cam.width * cam.height, 3))
     adj = O.adjoint(sc0, cam, w, opts)
     sig0 = O.pair_signature(sc0, cam, opts)
@@ -591,6 +592,9 @@ def test_adjoint_matches_finite_differences(deg):
             checked += 1
     assert checked > 0.95 * (checked + skipped)
     assert np.abs(adj["means"]).max() > 0 and np.abs(adj["sh"]).max() > 0
+    if foot:   # the reading matters in this scene: its gradients are not the depth plane's
+        other = O.adjoint(sc0, cam, w, O.Opts(bg=(0.1, 0.2, 0.3)))
+        assert np.abs(other["means"] - adj["means"]).max() > 1e-3 * np.abs(adj["means"]).max()
 
 
 # --------------------------------------------------------------------------- Eq. 5 merge
