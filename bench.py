@@ -421,7 +421,8 @@ def foot_reading_report(trainer, cams) -> dict:
     CUDA events (untimed warm-up pass first), then once more with per-stage timing.  The
     foot forward sorts every (tile, subset) run by a per-tile bound of the foot's ray
     parameter and restores each pixel's order in a 64-entry buffer; `overflow` counts the
-    contributors that buffer blended early (0: exact order)."""
+    contributors that buffer blended early (0: exact order).  The foot reading's backward
+    is timed on two views (`backward_ms`)."""
     import torch
     from paper_2406_11836_gb300 import rgs
     g = trainer.gaussians()
@@ -471,6 +472,32 @@ def foot_reading_report(trainer, cams) -> dict:
             res[name]["overflow_per_view"] = over / len(cams)
     res["views"] = len(cams)
     res["foot_over_depth_plane"] = round(res["foot"]["forward_ms"] / res["depth_plane"]["forward_ms"], 3)
+    # the foot reading's backward (lists re-derived, per-pixel order replayed, pair adjoints
+    # added with atomics, projection backward) after its image-only forward, on the first
+    # two views with a seeded dL/dC; compare with variants.bwd_recompute (the depth-plane
+    # backward that re-derives its lists)
+    grads = [torch.zeros_like(t) for t in (trainer.p["means"], trainer.p["log_scales"], trainer.p["quats"],
+                                           trainer.p["opacity_logits"], trainer.p["sh"])]
+    gen = torch.Generator(device=dev).manual_seed(3)
+    dL = (torch.randint(0, 2, (3, H, Wd), generator=gen, device=dev).float() * 2 - 1) / float(H * Wd)
+    img = torch.empty(3, H, Wd, device=dev)
+    bms, bover = [], 0
+    bviews = cams[:2]
+    for timed in (False, True):
+        for c in bviews:
+            rgs.render_fwd_foot(kd, g, c, opts, ws, partials=False, out={"image": img, "T_final": out["T_final"]})
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = rgs.render_bwd_foot(kd, g, c, opts, img, dL, grads, ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if timed:
+                bms.append(e0.elapsed_time(e1))
+                bover += o
+    res["foot"]["backward_ms"] = round(float(np.mean(bms)), 3)
+    res["foot"]["backward_views"] = len(bviews)
+    res["foot"]["backward_overflow_per_view"] = bover / len(bviews)
+    del grads
     return res
 
 

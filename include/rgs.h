@@ -226,10 +226,28 @@ int rgs_render_fwd_noalloc(const rgs_kd* kd, const rgs_gaussians* g, const rgs_c
  * contributors blended early because it was full.  Arguments, outputs, eps_T stopping and
  * errors as rgs_render_fwd, without tile_depth; the workspace needs 8 more bytes per
  * instance and 16 per splat (EOVERFLOW reports the size).  rgs_render_bwd does not accept
- * its partials: they are not the depth-plane reading's. */
+ * its partials (they are not the depth-plane reading's); its backward is
+ * rgs_render_bwd_foot. */
 int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
                         const rgs_render_opts* opts, float* partial_C, float* partial_T, float* image,
                         float* T_final, void* workspace, size_t ws_bytes, uint64_t* overflow_host, void* stream);
+
+/* Backward of rgs_render_fwd_foot (the comparison reading of Sec. 3.2, flat form of Eq. 2):
+ * the reading changes only discrete decisions (which pairs pass the ball test and Eq. 6 at
+ * the foot, and each ray's order), whose gradients are zero, so each pair's adjoint is the
+ * depth-plane one, dL/dsigma_i = T_i <g, c_i> - <g, C - A_i> / (1 - sigma_i), taken in the
+ * foot reading's per-pixel order.  It re-derives the forward's lists and replays its
+ * per-pixel order buffer (same pairs, same order, same freeze points and eps_T stopping)
+ * from the forward's image ([3,H,W], as written by rgs_render_fwd_foot without partial
+ * maps) and dL_dimage [3,H,W]; each blended pair adds its 2D gradients with atomics, then
+ * the projection backward accumulates into `grads` (as rgs_render_bwd).  *overflow_host
+ * (nullable) as in rgs_render_fwd_foot.  The workspace needs what rgs_render_fwd_foot
+ * needs (EOVERFLOW reports the size).  Synchronises once with `stream` (twice when
+ * overflow_host is given).  Errors as rgs_render_fwd. */
+int rgs_render_bwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                        const rgs_render_opts* opts, const float* image, const float* dL_dimage,
+                        const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, uint64_t* overflow_host,
+                        void* stream);
 
 /* Training on several views of one scene per step (Sec. 4 trains with a batch size per
  * step), through one launch sequence instead of one per view.

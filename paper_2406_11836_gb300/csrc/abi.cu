@@ -965,6 +965,51 @@ int rgs_render_fwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_came
     return RGS_OK;
 }
 
+int rgs_render_bwd_foot(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam,
+                        const rgs_render_opts* opts, const float* image, const float* dL_dimage,
+                        const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, uint64_t* overflow_host,
+                        void* stream) {
+    if (!image || !dL_dimage || !grads || !grads->means || !grads->log_scales || !grads->quats ||
+        !grads->opacity_logits || !grads->sh) {
+        set_error("render_bwd_foot: NULL argument");
+        return RGS_EINVAL;
+    }
+    if (!aligned(grads->quats, 16)) {
+        set_error("render_bwd_foot: grads->quats must be 16-byte aligned");
+        return RGS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    stamp_erase(workspace);   // its lists are about to be replaced
+    ViewParams vp;
+    TreeParams tp;
+    RasterBuffers b;
+    const uint32_t* ival = nullptr;
+    int64_t I = 0;
+    int rc = build_lists(kd, g, cam, opts, workspace, ws_bytes, s, &vp, &tp, &b, &ival, nullptr, nullptr, &I, true);
+    if (rc) return rc;
+    unsigned long long* over = b.counters + 6;
+    RGS_CUDA_TRY(cudaMemsetAsync(over, 0, 8, s));
+    {
+        ProfScope ps(ST_BLEND_BWD, s);
+        RGS_CUDA_TRY(cudaMemsetAsync(b.g2d, 0, sizeof(float4) * 3 * (size_t)g->n, s));
+        rc = launch_blend_foot_bwd(vp, tp, b, ival, image, dL_dimage, over, s);
+        if (rc) return rc;
+    }
+    {
+        ProfScope ps(ST_PROJECT_BWD, s);
+        rc = launch_project_bwd(*g, *grads, vp, b, s);
+        if (rc) return rc;
+    }
+    if (overflow_host) {
+        if (!g_pinned.h) RGS_CUDA_TRY(cudaMallocHost(&g_pinned.h, 64));
+        unsigned long long* h = g_pinned.h;
+        RGS_CUDA_TRY(cudaMemcpyAsync(h + 6, over, 8, cudaMemcpyDeviceToHost, s));
+        RGS_CUDA_TRY(cudaStreamSynchronize(s));
+        *overflow_host = (uint64_t)h[6];
+    }
+    return RGS_OK;
+}
+
 int rgs_render_bwd(const rgs_kd* kd, const rgs_gaussians* g, const rgs_camera* cam, const rgs_render_opts* opts,
                    const float* partial_C, const float* partial_T, const float* dL_dimage, const float* tile_depth,
                    const rgs_gaussian_grads* grads, void* workspace, size_t ws_bytes, void* stream) {

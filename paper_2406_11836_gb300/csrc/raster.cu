@@ -1473,18 +1473,60 @@ __device__ __forceinline__ void foot_insert(FootPending& P, const float4* __rest
     if (i == 0) hs = s;
 }
 
-// Forward blend of one tile under the foot reading: the structure of the depth-plane
-// forward (subsets in view order, batches staged in shared memory, per-warp lists,
-// freezing below eps_T, the merge of Eq. 5 in shared memory), with the per-pixel order
-// restored through the pending buffer.  A contributor's key s = z (fx^2 + a b + k c d) is
-// carried as a float pair (b = mx - cx, d = my - cy and z from the projection's float
-// pairs; a and, for square pixels, k c exact), so that the order is exact to about 1e-12
-// of the key.  `over` counts buffer overflows.
+// Adds a float4 into global memory with one vector reduction.
+__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
+// The adjoint of one blended pair (flat form, Eq. 2): with T the transmittance in front of
+// it inside its subset, gC = dL/dC times the transmittance in front of the subset, acc the
+// pixel's <gC, colour> blended so far (this pair included) and q = <dL/dC, image>,
+//   h = sigma dL/dsigma = sigma (T <gC, c> - (q - acc) / (1 - sigma))   (0 when clamped),
+// and the pair's 2D gradients, added to the splat's record with vector reductions:
+//   mean h L^T u (u = L delta, delta = pixel centre - centre), conic -h/2 (dx^2, 2 dx dy,
+//   dy^2), alpha h / alpha, colour gC sigma T.
+// Used by the foot reading's backward, whose pairs are blended in a per-pixel order.
+__device__ __forceinline__ void pair_adjoint_add(const float4* __restrict__ rec, uint32_t id, float sig, float T,
+                                                 float4 c, float gC0, float gC1, float gC2, float q, float& acc,
+                                                 float pcx, float pcy, float x0, float y0, float alpha_max,
+                                                 float4* __restrict__ g2d) {
+    const float w = sig * T;
+    const float grgb = gC0 * c.x + gC1 * c.y + gC2 * c.z;
+    acc = fmaf(w, grgb, acc);
+    const float dsig = T * grgb - __fdividef(q - acc, 1.f - sig);
+    const float h = sig < alpha_max ? sig * dsig : 0.f;
+    const float4 r0 = rec[3 * (size_t)id], r1 = rec[3 * (size_t)id + 1];
+    uint32_t lo_bits = __float_as_uint(r0.z);
+    const float2 lof = __half22float2(*reinterpret_cast<__half2*>(&lo_bits));
+    const float dx = pcx - __fadd_rn(__fsub_rn(r0.x, x0), lof.x), dy = pcy - __fadd_rn(__fsub_rn(r0.y, y0), lof.y);
+    const float u1 = fmaf(r1.x, dx, r1.y * dy), u2 = r1.z * dy;
+    const float hdx = h * dx, hdy = h * dy;
+    float4* dst = g2d + 3 * (size_t)id;
+    red_add_v4(dst, make_float4(h * r1.x * u1, h * fmaf(r1.y, u1, r1.z * u2), -0.5f * hdx * dx, -hdx * dy));
+    red_add_v4(dst + 1, make_float4(-0.5f * hdy * dy, __fdividef(h, r0.w), gC0 * w, gC1 * w));
+    atomicAdd(&dst[2].x, gC2 * w);
+}
+
+// Blend of one tile under the foot reading: the structure of the depth-plane forward
+// (subsets in view order, batches staged in shared memory, per-warp lists, freezing below
+// eps_T, the merge of Eq. 5 in shared memory), with the per-pixel order restored through
+// the pending buffer.  A contributor's key s = z (fx^2 + a b + k c d) is carried as a float
+// pair (b = mx - cx, d = my - cy and z from the projection's float pairs; a and, for square
+// pixels, k c exact), so that the order is exact to about 1e-12 of the key.  `over` counts
+// buffer overflows.
+//
+// kBwd: the backward of that forward (flat form).  The same replay, the same pairs in the
+// same per-pixel order and the same freeze points; `image` is the forward's image (read),
+// gI is dL/dimage, and each blended pair adds its adjoint to g2d (pair_adjoint_add).
+// Pixels with dL/dC = 0 are left out (they add nothing).  pC, pT and Tfin are unused.
+template <bool kBwd>
 __global__ void __launch_bounds__(kBlendThreads, 2)
 blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges_all, const uint32_t* __restrict__ ival,
                   const float4* __restrict__ rec, const float4* __restrict__ side, float* __restrict__ pC,
                   float* __restrict__ pT, float* __restrict__ image, float* __restrict__ Tfin,
-                  unsigned long long* __restrict__ over) {
+                  unsigned long long* __restrict__ over, const float* __restrict__ gI, float4* __restrict__ g2d) {
     __shared__ StagedRec srec[kBlendThreads];
     __shared__ uint32_t smask[kBlendThreads];
     __shared__ float sbound[kBlendThreads];
@@ -1525,6 +1567,15 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
     const float g0 = fmaf(vp.R[0], rx, fmaf(vp.R[3], ry, vp.R[6]));
     const float g1 = fmaf(vp.R[1], rx, fmaf(vp.R[4], ry, vp.R[7]));
     const float g2 = fmaf(vp.R[2], rx, fmaf(vp.R[5], ry, vp.R[8]));
+    // backward: dL/dC of the pixel, <dL/dC, image> and <gC, colour blended so far>
+    float gI0 = 0.f, gI1 = 0.f, gI2 = 0.f, qf = 0.f, acc = 0.f;
+    if (kBwd && inside) {
+        gI0 = gI[pix];
+        gI1 = gI[HW + pix];
+        gI2 = gI[2 * HW + pix];
+        qf = gI0 * image[pix] + gI1 * image[HW + pix] + gI2 * image[2 * HW + pix];
+    }
+    const bool want = !kBwd || gI0 != 0.f || gI1 != 0.f || gI2 != 0.f;
     uint8_t* wl = wlist[warp];
     // the warp's 8x4 pixel block, clipped to the image (an empty block gives no entries)
     const int bx0 = txi * kTile + ((warp & 1) << 3), by0 = tyi * kTile + ((warp >> 1) << 2);
@@ -1538,7 +1589,7 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
     for (int r = 0; r < vp.K; ++r) {
         const int k = vp.order[r];
         const uint2 rg = ranges[r];
-        const bool live = inside && !(cull && s_img[3][tid] < vp.eps_T);
+        const bool live = inside && want && !(cull && s_img[3][tid] < vp.eps_T);
         if (cull && __syncthreads_count(live) == 0) {
             if (inside && pC) {
                 pC[((size_t)k * 3 + 0) * HW + pix] = 0.f;
@@ -1554,6 +1605,17 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
         bool frozen = !live;
         int ph = 0, pn = 0;
         float hs = kInfF;
+        const float Pf = s_img[3][tid];   // transmittance in front of the subset
+        const float gC0 = gI0 * Pf, gC1 = gI1 * Pf, gC2 = gI2 * Pf;
+        // blends the nearest pending contributor (and, backward, adds its adjoint first)
+        auto pop = [&]() {
+            if (kBwd) {
+                const uint32_t id = P.id[ph];
+                pair_adjoint_add(rec, id, P.sig[ph], T, rec[3 * (size_t)id + 2], gC0, gC1, gC2, qf, acc, pcx, pcy,
+                                 x0, y0, vp.alpha_max, g2d);
+            }
+            foot_pop(P, rec, ph, pn, hs, C0, C1, C2, T);
+        };
         for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kBlendThreads) {
             const int nb = (int)min((uint32_t)kBlendThreads, rg.y - b0);
             __syncthreads();
@@ -1612,7 +1674,7 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
                     const int j = wl[t];
                     const float bound = wthr[warp][t];
                     // nothing from here on can come before a pending key below this bound
-                    while (hs < bound) foot_pop(P, rec, ph, pn, hs, C0, C1, C2, T);
+                    while (hs < bound) pop();
                     const float4 A = srec[j].a;
                     const float4 B = srec[j].b;
                     const float4 Cc = srec[j].c;
@@ -1645,13 +1707,17 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
                         fast_two_sum(kh, kl, kh, kl);
                         const float G = ex2_approx(d2 * kNegHalfLog2e);
                         const float sig = fminf(B.y * G, vp.alpha_max);
+                        if (pn == kFootPend) {   // full: the nearest is blended early
+                            pop();
+                            ++n_over;
+                        }
                         foot_insert(P, rec, ph, pn, hs, kh, kl, sig, sid[j], C0, C1, C2, T, n_over);
                     }
                 }
             }
             if (__syncthreads_count(frozen || T < vp.eps_T) == kBlendThreads) break;
         }
-        while (pn > 0) foot_pop(P, rec, ph, pn, hs, C0, C1, C2, T);
+        while (pn > 0) pop();
         if (frozen && inside) T = live ? s_tkeep[tid] : 1.f;
         if (inside) {
             if (pC) {
@@ -1667,7 +1733,7 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
             s_img[3][tid] = Pm * T;
         }
     }
-    if (inside && image) {
+    if (!kBwd && inside && image) {
         const float Pm = s_img[3][tid];
         image[0 * HW + pix] = fmaf(vp.bg[0], Pm, s_img[0][tid]);
         image[1 * HW + pix] = fmaf(vp.bg[1], Pm, s_img[1][tid]);
@@ -1678,12 +1744,6 @@ blend_foot_kernel(ViewParams vp, TreeParams tp, const uint2* __restrict__ ranges
 }
 
 // ------------------------------------------------------------------ blend backward
-// Adds a float4 into global memory with one vector reduction.
-__device__ __forceinline__ void red_add_v4(float4* addr, float4 v) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w)
-                 : "memory");
-}
 
 // kFlat = false: the adjoint of Eq. 5 and each subset's replay from its stored partials
 // (pC, pT; `img` unused).  kFlat = true: the adjoint of the flat form (Eq. 2, which Eq. 5
@@ -2260,8 +2320,18 @@ int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBu
                       float* partial_C, float* partial_T, float* image, float* T_final,
                       unsigned long long* over, cudaStream_t s) {
     unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
-    blend_foot_kernel<<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, b.foot_side, partial_C, partial_T,
-                                                     image, T_final, over);
+    blend_foot_kernel<false><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, b.foot_side, partial_C,
+                                                            partial_T, image, T_final, over, nullptr, nullptr);
+    RGS_CUDA_LAUNCH_CHECK();
+    return RGS_OK;
+}
+
+int launch_blend_foot_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                          const float* image, const float* dL_dimage, unsigned long long* over, cudaStream_t s) {
+    unsigned grid = (unsigned)(vp.tiles_x * vp.tiles_y);
+    blend_foot_kernel<true><<<grid, kBlendThreads, 0, s>>>(vp, tp, b.ranges, ival, b.rec, b.foot_side, nullptr,
+                                                           nullptr, const_cast<float*>(image), nullptr, over,
+                                                           dL_dimage, b.g2d);
     RGS_CUDA_LAUNCH_CHECK();
     return RGS_OK;
 }

@@ -410,6 +410,10 @@ int launch_foot_order(const ViewParams& vp, const RasterBuffers& b, int64_t I, c
 int launch_blend_foot(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
                       float* partial_C, float* partial_T, float* image, float* T_final,
                       unsigned long long* over, cudaStream_t s);
+// Its backward (flat form): adds each blended pair's 2D gradients to b.g2d (zeroed by the
+// caller); image is the forward's, dL_dimage [3,H,W]; `over` as above.
+int launch_blend_foot_bwd(const ViewParams& vp, const TreeParams& tp, const RasterBuffers& b, const uint32_t* ival,
+                          const float* image, const float* dL_dimage, unsigned long long* over, cudaStream_t s);
 // n_inst: instances in ival (ranges are clamped to it); n_splats: records in b.rec (other
 // payloads are skipped).  image != nullptr: the flat form (from the merged image; the
 // partial maps are not read), else the per-subset form from the partial maps.

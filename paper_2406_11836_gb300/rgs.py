@@ -88,6 +88,9 @@ def lib():
     L.rgs_render_fwd_foot.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, POINTER(ctypes.c_uint64),
                                       c_void_p]
+    L.rgs_render_bwd_foot.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
+                                      c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, POINTER(ctypes.c_uint64),
+                                      c_void_p]
     L.rgs_render_bwd.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
                                  c_void_p, c_void_p, c_void_p, POINTER(GaussianGrads), c_void_p, c_size_t, c_void_p]
     L.rgs_render_bwd_flat.argtypes = [c_void_p, POINTER(Gaussians), POINTER(CameraC), POINTER(RenderOpts), c_void_p,
@@ -301,8 +304,9 @@ def render_fwd(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, image
 def render_fwd_foot(kd: KD, g: Gaussians, cam, opts: RenderOpts, ws: Workspace, partials=True, stream=None,
                     out=None):
     """Forward render under the perpendicular-foot reading of x_i (Sec. 3.2; comparison
-    mode, no backward): like render_fwd, plus "overflow", the number of contributors the
-    per-pixel order buffer had to blend early (0: the per-pixel order is exact)."""
+    mode): like render_fwd, plus "overflow", the number of contributors the per-pixel order
+    buffer had to blend early (0: the per-pixel order is exact).  Its backward is
+    render_bwd_foot."""
     H, W = int(cam.height), int(cam.width)
     dev = torch.device("cuda", torch.cuda.current_device())
     if out is None:
@@ -406,6 +410,22 @@ def render_bwd_flat(kd: KD, g: Gaussians, cam, opts: RenderOpts, image, dL_dimag
     _retry(lambda: lib().rgs_render_bwd_flat(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
                                              _ptr(image), _ptr(dL), _ptr(tile_depth), ctypes.byref(gg), ws.ptr(),
                                              ws.nbytes, s), ws)
+
+
+def render_bwd_foot(kd: KD, g: Gaussians, cam, opts: RenderOpts, image, dL_dimage, grads, ws: Workspace,
+                    stream=None):
+    """Backward of render_fwd_foot (flat form, the foot reading's per-pixel order), from the
+    forward's image (rendered without partial maps).  Accumulates into grads like
+    render_bwd; returns the order buffer's overflow count."""
+    gg = GaussianGrads(*(_ptr(t) for t in grads))
+    c = camera_c(cam)
+    s = _stream(stream)
+    dL = dL_dimage.contiguous()
+    over = ctypes.c_uint64(0)
+    _retry(lambda: lib().rgs_render_bwd_foot(kd.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(opts),
+                                             _ptr(image), _ptr(dL), ctypes.byref(gg), ws.ptr(), ws.nbytes,
+                                             ctypes.byref(over), s), ws)
+    return int(over.value)
 
 
 def _cams_c(cams):
@@ -573,7 +593,7 @@ class Server:
 ABI_SYMBOLS = ("rgs_last_error", "rgs_last_required_workspace", "rgs_version", "rgs_default_opts", "rgs_kd_partition",
                "rgs_kd_info", "rgs_kd_from_splits", "rgs_kd_splits", "rgs_kd_subsets", "rgs_kd_destroy", "rgs_view_order",
                "rgs_render_workspace_size", "rgs_render_fwd", "rgs_render_fwd_foot", "rgs_merge_partials", "rgs_merge_partials_bwd",
-               "rgs_render_bwd", "rgs_render_bwd_flat", "rgs_render_batch_fwd", "rgs_render_batch_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
+               "rgs_render_bwd", "rgs_render_bwd_flat", "rgs_render_bwd_foot", "rgs_render_batch_fwd", "rgs_render_batch_bwd", "rgs_adam_step", "rgs_adam_step_periodic", "rgs_position_lr", "rgs_profile_enable",
                "rgs_profile_num_stages", "rgs_profile_stage_name", "rgs_profile_read", "rgs_render_fwd_noalloc",
                "rgs_serve_default_config", "rgs_serve_create", "rgs_serve_create_ex", "rgs_serve_submit",
                "rgs_serve_poll", "rgs_serve_stats_read", "rgs_serve_destroy", "rgs_serve_lane_bytes",

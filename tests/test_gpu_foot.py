@@ -2,7 +2,8 @@
 
 rgs_render_fwd_foot against the FP64 oracle with opts.foot: the image against the flat
 form (contributors of each ray ordered by the foot's ray parameter), the partial maps
-against the literal Eq. 3-4 with the indicator of Eq. 6 at the foot.  The per-pixel order
+against the literal Eq. 3-4 with the indicator of Eq. 6 at the foot.  rgs_render_bwd_foot
+against the oracle's adjoint under the same reading (every sampled pixel in the loss).  The per-pixel order
 buffer must not overflow on these scenes (the order is then exact), and the two readings
 must really differ on each scene.
 
@@ -18,8 +19,8 @@ import numpy as np
 import pytest
 import torch
 
-from _helpers import (FWD_FLAGS, MAX_FLAGGED, PART_FLAGS, PART_MAX_FLAGGED, PIXEL_TOL, image_at, oracle_opts,
-                      partials_at)
+from _helpers import (FWD_FLAGS, GRAD_RTOL, MAX_FLAGGED, PART_FLAGS, PART_MAX_FLAGGED, PIXEL_TOL, image_at,
+                      oracle_opts, partials_at, rel_l2)
 from oracle import oracle as O
 from paper_2406_11836_gb300 import workloads as W
 
@@ -187,3 +188,95 @@ def test_foot_fullsize_sampled(R, name, view, n_pix, max_flagged, max_over, cull
     assert err <= PIXEL_TOL, err
     assert (ref["ncontrib"] > 0).mean() > 0.5
     assert out["overflow"] <= max_over * cam.width * cam.height, out["overflow"]
+
+
+# --------------------------------------------------------------------------- backward
+def _foot_grad_parity(R, scene, cam, L, opts=None, pix_loss=None, seed=1, differ=True):
+    """L1 loss against a random target over the given pixels (none left out as ambiguous);
+    dL/dC is formed from the GPU's foot-reading image and both sides get the same dL/dC.
+    Per parameter tensor, the relative L2 error against the oracle's foot-reading adjoint
+    must be at most GRAD_RTOL; with `differ`, the depth-plane adjoint of the same loss must
+    be farther from it than that."""
+    dev = scene.to("cuda")
+    kd = R.kd_partition(dev, L)
+    opts = opts if opts is not None else R.default_opts()
+    g = R.scene_c(dev)
+    ws = R.Workspace()
+    img = R.render_fwd_foot(kd, g, cam, opts, ws, partials=False)["image"]
+    H, Wd = cam.height, cam.width
+    pix = np.arange(H * Wd) if pix_loss is None else np.asarray(pix_loss)
+    target = W.target_image(Wd, H, seed=seed, device="cuda")
+    mask = torch.zeros(H * Wd, device="cuda")
+    mask[torch.as_tensor(pix, device="cuda")] = 1.0
+    dL = (torch.sign(img - target) * mask.view(1, H, Wd) / float(len(pix))).contiguous()
+    grads = [torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh)]
+    over = R.render_bwd_foot(kd, g, cam, opts, img, dL, grads, ws)
+    torch.cuda.synchronize()
+    assert over == 0
+    dLdC = dL.reshape(3, -1)[:, torch.as_tensor(pix, device="cuda")].T.double().cpu().numpy()
+    host = scene.to("cpu")
+    adj = O.adjoint(host, cam, dLdC, foot_opts(opts), pix=pix)
+    names = ["means", "log_scales", "quats", "opacity_logits", "sh"]
+    errs = {n: rel_l2(t.double().cpu().numpy(), adj[n]) for n, t in zip(names, grads)}
+    for n in names:
+        assert np.abs(adj[n]).max() > 0, n
+        assert errs[n] <= GRAD_RTOL, errs
+    if differ:
+        plane = O.adjoint(host, cam, dLdC, oracle_opts(opts), pix=pix)
+        assert rel_l2(plane["means"], adj["means"]) > 10 * GRAD_RTOL
+    return errs
+
+
+def test_foot_backward_tiny(R):
+    """4,096 splats, 128x128, K = 2, every pixel in the loss."""
+    wl = W.tiny()
+    _foot_grad_parity(R, wl.scene, wl.cameras[0], wl.depth_L)
+
+
+@pytest.mark.parametrize("L", [0, 3])
+def test_foot_backward_inside_camera(R, L):
+    """A camera inside the scene (rays cross many subspaces), 64x40 (ragged tiles), SH
+    degree 3, a background colour."""
+    scene = W.uniform_cube_scene(1500, seed=11 + L, log_scale_mean=-3.0, sh_degree=3)
+    cam = W.look_at((0.1, -0.15, 0.05), (0.2, 1.0, 0.1), 64, 40)
+    _foot_grad_parity(R, scene, cam, L, opts=R.default_opts(bg=(0.2, 0.4, 0.6)))
+
+
+def test_foot_backward_thin_slabs(R):
+    """The thin-slab scene, where the foot order differs from the depth order on most
+    pixels: the gradients follow the foot's per-pixel order."""
+    g = torch.Generator().manual_seed(5)
+    n = 3000
+    means = torch.rand(n, 3, generator=g) * 2 - 1
+    slab = torch.tensor([-0.4, 0.0, 0.4])[torch.randint(0, 3, (n,), generator=g)]
+    means[:, 2] = slab + 0.01 * torch.randn(n, generator=g)
+    log_scales = torch.randn(n, 3, generator=g) * 0.3 - 3.0
+    q = torch.randn(n, 4, generator=g)
+    scene = W.Scene(means, log_scales, q / q.norm(dim=1, keepdim=True), torch.randn(n, generator=g),
+                    torch.rand(n, 1, 3, generator=g), 0)
+    cam = W.axis_camera((0.1, -0.05, -3.0), 160, 120)
+    _foot_grad_parity(R, scene, cam, 2)
+
+
+def test_foot_backward_object_1m_sampled(R):
+    """The object workload at full size (1M splats, 1600x1060, K = 8): the loss on a
+    seeded sample of pixels, the whole frame replayed on the GPU."""
+    wl = W.object_1m(device="cuda")
+    cam = wl.cameras[0]
+    pix = W.sample_pixels(cam.width, cam.height, 1024, seed=29)
+    _foot_grad_parity(R, wl.scene, cam, wl.depth_L, pix_loss=pix, differ=False)
+
+
+def test_foot_backward_rejects_missing_image(R):
+    """A NULL image: EINVAL, nothing launched."""
+    import ctypes
+    wl = W.tiny()
+    dev = wl.scene.to("cuda")
+    kd = R.kd_partition(dev, 1)
+    grads = [torch.zeros_like(t) for t in (dev.means, dev.log_scales, dev.quats, dev.opacity_logits, dev.sh)]
+    gg = R.GaussianGrads(*(ctypes.c_void_p(t.data_ptr()) for t in grads))
+    dL = torch.zeros(3, 128, 128, device="cuda")
+    rc = R.lib().rgs_render_bwd_foot(kd.handle, ctypes.byref(R.scene_c(dev)), ctypes.byref(R.camera_c(wl.cameras[0])),
+                                     ctypes.byref(R.default_opts()), None, ctypes.c_void_p(dL.data_ptr()),
+                                     ctypes.byref(gg), None, 0, None, None)
+    assert rc == R.RGS_EINVAL
