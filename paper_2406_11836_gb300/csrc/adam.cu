@@ -62,12 +62,27 @@ adam_kernel(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
         const int64_t e = 4 * i;
         float l0, l1, l2, l3;
         if (periodic) {
-            const int64_t r1 = r + 1 >= per ? r + 1 - per : r + 1, r2 = r1 + 1 >= per ? r1 + 1 - per : r1 + 1,
-                          r3 = r2 + 1 >= per ? r2 + 1 - per : r2 + 1;
-            l0 = elem_lr(segs, e, r);
-            l1 = elem_lr(segs, e + 1, r1);
-            l2 = elem_lr(segs, e + 2, r2);
-            l3 = elem_lr(segs, e + 3, r3);
+            const int q0 = seg_of(segs, e), q3 = seg_of(segs, e + 3);
+            if (q0 == q3) {   // four elements of one segment
+                const float lq = segs.lr[q0];
+                if (q0 != segs.pseg) {
+                    l0 = l1 = l2 = l3 = lq;
+                } else {
+                    const int64_t r1 = r + 1 >= per ? r + 1 - per : r + 1, r2 = r1 + 1 >= per ? r1 + 1 - per : r1 + 1,
+                                  r3 = r2 + 1 >= per ? r2 + 1 - per : r2 + 1;
+                    l0 = r < segs.head ? segs.head_lr : lq;
+                    l1 = r1 < segs.head ? segs.head_lr : lq;
+                    l2 = r2 < segs.head ? segs.head_lr : lq;
+                    l3 = r3 < segs.head ? segs.head_lr : lq;
+                }
+            } else {
+                const int64_t r1 = r + 1 >= per ? r + 1 - per : r + 1, r2 = r1 + 1 >= per ? r1 + 1 - per : r1 + 1,
+                              r3 = r2 + 1 >= per ? r2 + 1 - per : r2 + 1;
+                l0 = elem_lr(segs, e, r);
+                l1 = elem_lr(segs, e + 1, r1);
+                l2 = elem_lr(segs, e + 2, r2);
+                l3 = elem_lr(segs, e + 3, r3);
+            }
             r += step_mod;
             if (r >= per) r -= per;
         } else {
