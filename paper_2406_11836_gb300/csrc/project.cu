@@ -516,13 +516,46 @@ __device__ __forceinline__ void append_kept(bool keep, uint32_t value, uint32_t*
     }
 }
 
+// Four splats per thread (a block covers kCullPerBlock consecutive splats) and one append
+// per block: one atomic per warp on the single candidate counter serialised the pass.
+constexpr int kCullPerThread = 4;
+constexpr int kCullPerBlock = 256 * kCullPerThread;
 __global__ void __launch_bounds__(256)
 screen_cull_kernel(rgs_gaussians g, ViewParams vp, uint32_t* __restrict__ cnt, uint32_t* __restrict__ cand,
                    unsigned long long* __restrict__ counters) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool keep = i < g.n && screen_keep(g, vp, i);
-    if (i < g.n && !keep) cnt[i] = 0u;
-    append_kept(keep, (uint32_t)i, cand, &counters[13]);
+    __shared__ uint32_t s_off[8];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * kCullPerBlock + threadIdx.x;
+    unsigned bal[kCullPerThread];
+    uint32_t wn = 0;
+#pragma unroll
+    for (int k = 0; k < kCullPerThread; ++k) {
+        const int64_t i = i0 + 256 * k;
+        const bool keep = i < g.n && screen_keep(g, vp, i);
+        if (i < g.n && !keep) cnt[i] = 0u;
+        bal[k] = __ballot_sync(0xffffffffu, keep);
+        wn += __popc(bal[k]);
+    }
+    if (lane == 0) s_off[warp] = wn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_off[w];
+            s_off[w] = run;
+            run += c;
+        }
+        s_base = run ? atomicAdd(&counters[13], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = s_base + s_off[warp];
+    const unsigned lower = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kCullPerThread; ++k) {
+        if ((bal[k] >> lane) & 1u) cand[pos + __popc(bal[k] & lower)] = (uint32_t)(i0 + 256 * k);
+        pos += __popc(bal[k]);
+    }
 }
 
 // The screen cull of a batch: block x tests splats [256 (x / kMaxSlots), +256) against the
@@ -831,7 +864,8 @@ int launch_project_fwd(const rgs_gaussians& g, const ViewParams& vp, const TreeP
     } else {
         // the candidate list lives in vis_pos, which the compaction after the projection
         // overwrites; counters[13] counts the candidates (zeroed with the others)
-        screen_cull_kernel<<<grid, 256, 0, s>>>(g, vp, b.cnt, b.vis_pos, b.counters);
+        screen_cull_kernel<<<(unsigned)((g.n + kCullPerBlock - 1) / kCullPerBlock), 256, 0, s>>>(g, vp, b.cnt,
+                                                                                               b.vis_pos, b.counters);
         RGS_CUDA_LAUNCH_CHECK();
         RGS_DISPATCH_SH(g.sh_degree, vec_sh(g),
                         (project_cand_kernel<D, V><<<grid, 256, 0, s>>>(g, vp, tp, b, b.vis_pos)));
