@@ -279,7 +279,8 @@ template <int DEG, bool kVecSH, bool kFoot = false>
 __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t i, bool valid, const ViewParams& vp,
                                                  const TreeParams& tp, const int8_t* rank_of, const RasterBuffers& b,
                                                  int64_t j, unsigned long long* counters,
-                                                 unsigned long long* slot_counters) {
+                                                 unsigned long long* slot_counters,
+                                                 unsigned long long* blk_tot = nullptr) {
     constexpr int NSH = (DEG + 1) * (DEG + 1);
     const int lane = threadIdx.x & 31;
     // candidate state handed to the counting phase
@@ -382,6 +383,21 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
     }
     unsigned big = __ballot_sync(0xffffffffu, items > kWarpCountItems);
     uint32_t span_at = kNoItems;
+    // one reservation of item-list entries for all the warp's large splats: lane l's
+    // entries start at res + (the large splats' items in lanes below l)
+    unsigned long long res = 0;
+    uint32_t res_pre = 0;
+    if (big && b.items) {
+        uint32_t mine = items > kWarpCountItems ? (uint32_t)items : 0u, incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        res_pre = incl - mine;
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 0) res = atomicAdd(b.item_ctr, (unsigned long long)tot);
+        res = __shfl_sync(0xffffffffu, res, 0);
+    }
     while (big) {
         const int src = __ffs(big) - 1;
         big &= big - 1;
@@ -397,12 +413,11 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         const int ns = __popcll(m_);
         const uint32_t j_ = (uint32_t)__shfl_sync(0xffffffffu, (uint32_t)j, src);
         // keep the items for the emission when the list has room (item_ctr counts the
-        // entries taken; the one reservation that crosses the end voids its part inside)
+        // entries taken, reserved once per warp; the one splat whose entries cross the end
+        // voids its part inside)
         uint32_t sb = kNoItems;
         if (b.items) {
-            unsigned long long s0 = 0;
-            if (lane == 0) s0 = atomicAdd(b.item_ctr, (unsigned long long)items_);
-            s0 = __shfl_sync(0xffffffffu, s0, 0);
+            const unsigned long long s0 = res + (unsigned long long)__shfl_sync(0xffffffffu, res_pre, src);
             if (s0 + (unsigned long long)items_ <= b.item_cap) {
                 sb = (uint32_t)s0;
             } else {
@@ -453,14 +468,16 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         c64 += __shfl_xor_sync(0xffffffffu, c64, o);
         vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
     }
+    // blk_tot (shared, nullable): the block's totals, added to the counters once per block
+    // by the caller
     if (b.cnt_bin) {
         unsigned long long cb = count_bin;
         for (int o = 16; o > 0; o >>= 1) cb += __shfl_xor_sync(0xffffffffu, cb, o);
-        if (lane == 0 && cb) atomicAdd(b.bin_ctr, cb);   // the first group's instances
+        if (lane == 0 && cb) atomicAdd(blk_tot ? &blk_tot[2] : b.bin_ctr, cb);   // the first group's instances
     }
     if (lane == 0 && (c64 | vis_n)) {
-        atomicAdd(&counters[0], c64);
-        atomicAdd(&counters[1], (unsigned long long)vis_n);
+        atomicAdd(blk_tot ? &blk_tot[0] : &counters[0], c64);
+        atomicAdd(blk_tot ? &blk_tot[1] : &counters[1], (unsigned long long)vis_n);
         if (slot_counters) {
             atomicAdd(&slot_counters[0], c64);
             atomicAdd(&slot_counters[1], (unsigned long long)vis_n);
@@ -591,10 +608,20 @@ project_cand_kernel(rgs_gaussians g, ViewParams vp, TreeParams tp, RasterBuffers
     const unsigned long long nc = b.counters[13];
     const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if ((unsigned long long)blockIdx.x * blockDim.x >= nc) return;   // uniform across the block
-    stage_tree(tp, vp.rank_of, stp, srank);
+    __shared__ unsigned long long s_tot[3];   // instances, visible splats, first-group instances
+    if (threadIdx.x < 3) s_tot[threadIdx.x] = 0ull;
+    stage_tree(tp, vp.rank_of, stp, srank);   // (its barrier also orders the zeroing)
     const bool valid = c < nc;
     const int64_t i = valid ? (int64_t)cand[c] : 0;
-    project_fwd_body<DEG, kVecSH, false>(g, i, valid, vp, stp, srank, b, i, b.counters, nullptr);
+    project_fwd_body<DEG, kVecSH, false>(g, i, valid, vp, stp, srank, b, i, b.counters, nullptr, s_tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // one atomic per counter and block: per warp they serialised
+        if (s_tot[0] | s_tot[1]) {
+            atomicAdd(&b.counters[0], s_tot[0]);
+            atomicAdd(&b.counters[1], s_tot[1]);
+        }
+        if (s_tot[2]) atomicAdd(b.bin_ctr, s_tot[2]);
+    }
 }
 
 // The batch projection over each slot's screen-cull candidates: block x takes candidates

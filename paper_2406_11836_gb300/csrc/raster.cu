@@ -237,12 +237,16 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
     __shared__ int8_t srank[64];
     stage_tree(tp, vp.rank_of, stp, srank);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    // groups of 32 splats are claimed from a device counter: the near (large) splats come
-    // first in depth order, so the heavy groups start first and spread over all warps
+    // groups of 32 splats are claimed, two at a time (half the atomics on the one queue
+    // counter), from a device counter: the near (large) splats come first in depth order, so
+    // the heavy groups start first and spread over all warps
     for (;;) {
         unsigned long long gq = 0;
         if (lane == 0) gq = atomicAdd(queue, 1ull);
-        const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 32;
+        const int64_t pc = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 64;
+        if (pc >= n_vis) break;
+      for (int half = 0; half < 2; ++half) {
+        const int64_t p0 = pc + 32 * half;
         if (p0 >= n_vis) break;
         const int64_t p = p0 + lane;
         uint32_t id = 0, base = 0;
@@ -290,6 +294,7 @@ emit_kernel(ViewParams vp, TreeParams tp, const uint32_t* __restrict__ sorted_id
             emit_one<kMulti>(vp, stp, srank, sid_, sbase, 0u, rect, mask, rec, cull, chunk, ikey, ival, lane,
                              s_start[wib], s_key0[wib], foot_side);
         }
+      }
     }
 }
 
