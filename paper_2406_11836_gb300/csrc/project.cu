@@ -468,19 +468,24 @@ __device__ __forceinline__ void project_fwd_body(const rgs_gaussians& g, int64_t
         c64 += __shfl_xor_sync(0xffffffffu, c64, o);
         vis_n += __shfl_xor_sync(0xffffffffu, vis_n, o);
     }
-    // blk_tot (shared, nullable): the block's totals, added to the counters once per block
-    // by the caller
+    // blk_tot (shared, nullable): the block's totals (instances, visible splats, first-group
+    // instances), added to the counters once per block by the caller
     if (b.cnt_bin) {
         unsigned long long cb = count_bin;
         for (int o = 16; o > 0; o >>= 1) cb += __shfl_xor_sync(0xffffffffu, cb, o);
         if (lane == 0 && cb) atomicAdd(blk_tot ? &blk_tot[2] : b.bin_ctr, cb);   // the first group's instances
     }
     if (lane == 0 && (c64 | vis_n)) {
-        atomicAdd(blk_tot ? &blk_tot[0] : &counters[0], c64);
-        atomicAdd(blk_tot ? &blk_tot[1] : &counters[1], (unsigned long long)vis_n);
-        if (slot_counters) {
-            atomicAdd(&slot_counters[0], c64);
-            atomicAdd(&slot_counters[1], (unsigned long long)vis_n);
+        if (blk_tot) {   // the caller adds them to counters (and the slot's) once per block
+            atomicAdd(&blk_tot[0], c64);
+            atomicAdd(&blk_tot[1], (unsigned long long)vis_n);
+        } else {
+            atomicAdd(&counters[0], c64);
+            atomicAdd(&counters[1], (unsigned long long)vis_n);
+            if (slot_counters) {
+                atomicAdd(&slot_counters[0], c64);
+                atomicAdd(&slot_counters[1], (unsigned long long)vis_n);
+            }
         }
     }
 }
@@ -518,19 +523,6 @@ __device__ __forceinline__ bool screen_keep(const rgs_gaussians& g, const ViewPa
         if (cxp + bx < 0.f || cxp - bx > (float)vp.W || cyp + by < 0.f || cyp - by > (float)vp.H) keep = false;
     }
     return keep;
-}
-
-// Appends the lanes that keep their splat to list[*count ...] (one atomic per warp).
-__device__ __forceinline__ void append_kept(bool keep, uint32_t value, uint32_t* __restrict__ list,
-                                            unsigned long long* __restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (bal) {
-        unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(count, (unsigned long long)__popc(bal));
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (keep) list[first + __popc(bal & ((1u << lane) - 1u))] = value;
-    }
 }
 
 // Four splats per thread (a block covers kCullPerBlock consecutive splats) and one append
@@ -575,9 +567,10 @@ screen_cull_kernel(rgs_gaussians g, ViewParams vp, uint32_t* __restrict__ cnt, u
     }
 }
 
-// The screen cull of a batch: block x tests splats [256 (x / kMaxSlots), +256) against the
-// view of slot x % kMaxSlots and appends the candidates to the slot's list (vis_pos from
-// slot * N on, counted in counters[kBatchCandCounters + slot]).
+// The screen cull of a batch: block x tests splats [kCullPerBlock (x / kMaxSlots),
+// +kCullPerBlock) against the view of slot x % kMaxSlots and appends the candidates to the
+// slot's list (vis_pos from slot * N on, counted in counters[kBatchCandCounters + slot]),
+// once per block.
 __global__ void __launch_bounds__(256)
 screen_cull_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, const BatchHeader* __restrict__ hdr,
                          uint32_t* __restrict__ cnt, uint32_t* __restrict__ cand,
@@ -591,10 +584,40 @@ screen_cull_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, c
         for (int w = threadIdx.x; w < (int)(sizeof(ViewParams) / 4); w += blockDim.x) dst[w] = src[w];
     }
     __syncthreads();
-    const int64_t i = (int64_t)(blockIdx.x / kMaxSlots) * blockDim.x + threadIdx.x;
-    const bool keep = i < g.n && screen_keep(g, svp, i);
-    if (i < g.n && !keep) cnt[(int64_t)slot * g.n + i] = 0u;
-    append_kept(keep, (uint32_t)i, cand + (int64_t)slot * g.n, &counters[kBatchCandCounters + slot]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ uint32_t s_off[8];
+    __shared__ unsigned long long s_base;
+    const int64_t i0 = (int64_t)(blockIdx.x / kMaxSlots) * kCullPerBlock + threadIdx.x;
+    unsigned bal[kCullPerThread];
+    uint32_t wn = 0;
+#pragma unroll
+    for (int k = 0; k < kCullPerThread; ++k) {
+        const int64_t i = i0 + 256 * k;
+        const bool keep = i < g.n && screen_keep(g, svp, i);
+        if (i < g.n && !keep) cnt[(int64_t)slot * g.n + i] = 0u;
+        bal[k] = __ballot_sync(0xffffffffu, keep);
+        wn += __popc(bal[k]);
+    }
+    if (lane == 0) s_off[warp] = wn;
+    __syncthreads();
+    if (threadIdx.x == 0) {   // one append per block
+        uint32_t run = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_off[w];
+            s_off[w] = run;
+            run += c;
+        }
+        s_base = run ? atomicAdd(&counters[kBatchCandCounters + slot], (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    uint32_t* list = cand + (int64_t)slot * g.n;
+    unsigned long long pos = s_base + s_off[warp];
+    const unsigned lower = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kCullPerThread; ++k) {
+        if ((bal[k] >> lane) & 1u) list[pos + __popc(bal[k] & lower)] = (uint32_t)(i0 + 256 * k);
+        pos += __popc(bal[k]);
+    }
 }
 
 // The projection over the candidates of screen_cull_kernel, one per thread; the grid
@@ -647,8 +670,22 @@ project_cand_batch_kernel(rgs_gaussians g, const BatchSlot* __restrict__ slots, 
     const unsigned long long c = c0 + threadIdx.x;
     const bool valid = c < nc;
     const int64_t i = valid ? (int64_t)b.vis_pos[(int64_t)slot * g.n + (int64_t)c] : 0;
-    project_fwd_body<DEG, kVecSH>(g, i, valid, svp, stp, srank, b, (int64_t)slot * g.n + i, counters,
-                                  counters + kBatchSlotCounters + 2 * slot);
+    __shared__ unsigned long long s_tot[3];
+    if (threadIdx.x < 3) s_tot[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long* slot_counters = counters + kBatchSlotCounters + 2 * slot;
+    project_fwd_body<DEG, kVecSH>(g, i, valid, svp, stp, srank, b, (int64_t)slot * g.n + i, counters, slot_counters,
+                                  s_tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // the block's totals, once (every splat of the block is in this slot)
+        if (s_tot[0] | s_tot[1]) {
+            atomicAdd(&counters[0], s_tot[0]);
+            atomicAdd(&counters[1], s_tot[1]);
+            atomicAdd(&slot_counters[0], s_tot[0]);
+            atomicAdd(&slot_counters[1], s_tot[1]);
+        }
+        if (s_tot[2]) atomicAdd(b.bin_ctr, s_tot[2]);
+    }
 }
 
 // ------------------------------------------------------------------ backward kernel
@@ -906,7 +943,8 @@ int launch_project_batch(const rgs_gaussians& g, const BatchSlot* slots, const B
     const unsigned grid = (unsigned)((g.n + 255) / 256) * (unsigned)kMaxSlots;
     // screen cull first: each slot's candidates to its part of vis_pos (the compaction
     // after the projection overwrites it); the projection then runs on full warps
-    screen_cull_batch_kernel<<<grid, 256, 0, s>>>(g, slots, hdr, b.cnt, b.vis_pos, counters);
+    const unsigned cgrid = (unsigned)((g.n + kCullPerBlock - 1) / kCullPerBlock) * (unsigned)kMaxSlots;
+    screen_cull_batch_kernel<<<cgrid, 256, 0, s>>>(g, slots, hdr, b.cnt, b.vis_pos, counters);
     RGS_CUDA_LAUNCH_CHECK();
     RGS_DISPATCH_SH(g.sh_degree, vec_sh(g),
                     (project_cand_batch_kernel<D, V><<<grid, 256, 0, s>>>(g, slots, hdr, tp, b, counters)));

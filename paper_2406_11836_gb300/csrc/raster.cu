@@ -597,9 +597,13 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned long long* queue = &counters[5 + kMulti];   // zeroed with the batch's counters
     for (;;) {
+        // two groups of 32 per claim: half the atomics on the one queue counter
         unsigned long long gq = 0;
         if (lane == 0) gq = atomicAdd(queue, 1ull);
-        const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 32;
+        const int64_t pc = (int64_t)__shfl_sync(0xffffffffu, gq, 0) * 64;
+        if (pc >= n) break;
+      for (int half = 0; half < 2; ++half) {
+        const int64_t p0 = pc + 32 * half;
         if (p0 >= n) break;
         const int64_t p = p0 + lane;
         uint32_t id = 0, base = 0;
@@ -632,6 +636,7 @@ emit_batch_kernel(const BatchSlot* __restrict__ slots, const BatchHeader* __rest
             emit_one<kMulti>(svp[ss], stp, svp[ss].rank_of, sid_, sb, sbase[ss], rect, mask, rec, nullptr, nullptr,
                              ikey, ival, lane, s_start[wib], s_key0[wib], nullptr);
         }
+      }
     }
 }
 
