@@ -80,6 +80,16 @@ def test_invalid_arguments_are_rejected(R):
                                    ctypes.c_void_p(fake), None, ctypes.c_void_p(fake), 1 << 20, ctypes.byref(over),
                                    None) == R.RGS_EINVAL
     assert b"kd" in lib.rgs_last_error()
+    # foot-reading backward: no image, then a NULL kd handle
+    gg = R.GaussianGrads(fake, fake, fake, fake, fake)
+    assert lib.rgs_render_bwd_foot(None, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), None,
+                                   ctypes.c_void_p(fake), ctypes.byref(gg), None, 0, ctypes.byref(over),
+                                   None) == R.RGS_EINVAL
+    assert b"render_bwd_foot" in lib.rgs_last_error()
+    assert lib.rgs_render_bwd_foot(None, ctypes.byref(g), ctypes.byref(cam), ctypes.byref(opts), ctypes.c_void_p(fake),
+                                   ctypes.c_void_p(fake), ctypes.byref(gg), ctypes.c_void_p(fake), 1 << 20,
+                                   ctypes.byref(over), None) == R.RGS_EINVAL
+    assert b"kd" in lib.rgs_last_error()
     # view order needs a handle; merge needs buffers
     assert lib.rgs_merge_partials(None, None, None, 0, 1, 1, None, None, None, None) == R.RGS_EINVAL
     assert lib.rgs_adam_step(None, None, None, None, 0, None, None, 0, ctypes.c_float(0.9), ctypes.c_float(0.999),
